@@ -1,0 +1,333 @@
+"""Pins of the oracle's bilinear forms (CPU).
+
+Independent routes used here (none re-calls the oracle's basis code):
+  * the shape functions are rebuilt with numpy.polynomial from the Gauss-Lobatto nodes;
+  * no interface (all cells inside): A is the Kronecker sum of 1D SIPG and mass matrices
+    integrated exactly with numpy polynomial antiderivatives;
+  * global polynomials u: the jump terms vanish and integration by parts (exact up to the
+    quadrature error) turns a(v, u) into -int v Lap u - int_Gamma d_n v u + tau/h int_Gamma v u;
+  * piecewise constants: only the SIPG and Nitsche penalties survive (face areas and Gamma area);
+  * u = (x_a - x_F)^j / j! on one side of a face and 0 on the other: the ghost penalty energy is
+    gamma_j |F|.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import forms, mesh
+
+
+def _oracle(cfg, kappa=None):
+    return forms.Oracle(mesh.problem_from_dict(cfg, kappa))
+
+
+def _lagrange_polys(n):
+    P = np.polynomial.legendre.Legendre.basis(n - 1).deriv()
+    inner = np.sort(P.roots().real) if n > 2 else np.array([])
+    nodes = np.concatenate([[0.0], 0.5 * (inner + 1.0), [1.0]])
+    polys = []
+    for i in range(n):
+        others = np.delete(nodes, i)
+        p = np.polynomial.Polynomial.fromroots(others)
+        polys.append(p / p(nodes[i]))
+    return nodes, polys
+
+
+class _DGFunction:
+    """A DG function given by DoF values, evaluated with numpy.polynomial shape functions."""
+
+    def __init__(self, o, values):
+        self.o = o
+        self.nodes, self.polys = _lagrange_polys(o.n)
+        self.v = np.asarray(values).reshape(o.mesh.n_active, -1)
+
+    def eval(self, e, X, deriv=None, order=1, fixed=None):
+        prob = self.o.prob
+        lo, _ = mesh.cell_box(prob, self.o.mesh.index_of(e))
+        out = np.zeros(len(X))
+        for l in range(self.o.ndof):
+            term = np.full(len(X), self.v[e, l])
+            for a in range(prob.dim):
+                ia = (l // self.o.n ** a) % self.o.n
+                xi = (X[:, a] - lo[a]) / prob.h
+                if fixed is not None and fixed[0] == a:
+                    xi = np.full(len(X), fixed[1])
+                pol = self.polys[ia]
+                if deriv == a:
+                    term = term * pol.deriv(order)(xi) / prob.h ** order
+                else:
+                    term = term * pol(xi)
+            out += term
+        return out
+
+
+def _interp(o, f):
+    """DoF vector of the function f (a polynomial of degree <= p: interpolation is exact)."""
+    nodes, _ = _lagrange_polys(o.n)
+    vals = np.zeros((o.mesh.n_active, o.ndof))
+    for e in range(o.mesh.n_active):
+        lo, _ = mesh.cell_box(o.prob, o.mesh.index_of(e))
+        X = np.array([[lo[a] + o.prob.h * nodes[(l // o.n ** a) % o.n] for a in range(o.prob.dim)]
+                      for l in range(o.ndof)])
+        vals[e] = f(X)
+    return vals.reshape(-1)
+
+
+def _poly3d(X):
+    x, y, z = X[:, 0], X[:, 1], X[:, 2]
+    return 0.3 + x - 2 * y + 0.5 * z + x * y - 0.7 * z * z + 0.2 * x * y * z + 0.4 * x ** 3
+
+
+def _poly3d_grad(X):
+    x, y, z = X[:, 0], X[:, 1], X[:, 2]
+    return np.stack([1 + y + 0.2 * y * z + 1.2 * x * x, -2 + x + 0.2 * x * z,
+                     0.5 - 1.4 * z + 0.2 * x * y], axis=1)
+
+
+def _poly3d_lap(X):
+    return -1.4 + 2.4 * X[:, 0]
+
+
+def _poly2d(X):
+    x, y = X[:, 0], X[:, 1]
+    return 0.3 + x - 2 * y + 0.5 * x * y
+
+
+def _poly2d_grad(X):
+    x, y = X[:, 0], X[:, 1]
+    return np.stack([1 + 0.5 * y, -2 + 0.5 * x], axis=1)
+
+
+def _poly2d_lap(X):
+    return np.zeros(len(X))
+
+
+CASES = {
+    "2d_q1": (workloads.small(p=1, N=10, dim=2), _poly2d, _poly2d_grad, _poly2d_lap),
+    "3d_q3": (workloads.small(p=3, N=5), _poly3d, _poly3d_grad, _poly3d_lap),
+}
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def case(request):
+    cfg, f, g, lap = CASES[request.param]
+    o = _oracle(cfg)
+    return o, o.assemble(), f, g, lap
+
+
+def test_symmetric_positive_definite(case):
+    o, A, *_ = case
+    assert abs(A - A.T).max() <= 1e-14 * abs(A).max()
+    ev = np.linalg.eigvalsh(A.toarray())
+    assert ev.min() > 0
+    assert np.all(A.diagonal() > 0)
+
+
+def test_constant_function(case):
+    """1^T A 1 = tau/h |Gamma|_h: every other term acts on gradients or jumps of the constant."""
+    o, A, *_ = case
+    one = np.ones(A.shape[0])
+    S = sum(o.cell_quadrature(e)[3].sum() for e in range(o.mesh.n_active))
+    assert abs(one @ A @ one - o.prob.nitsche_gamma / o.prob.h * S) < 1e-12 * abs(one @ A @ one)
+
+
+def _form_with_smooth_u(o, vfun, f, g, lap, ibp):
+    """a(v, u) for a global polynomial u, written with u evaluated analytically.
+
+    ibp=False: the form itself (volume grad.grad, -[v] d_n u on faces, Nitsche).
+    ibp=True : after integration by parts (exact up to the quadrature error on cut cells)."""
+    prob = o.prob
+    tau = prob.nitsche_gamma / prob.h
+    total = 0.0
+    for e in range(o.mesh.n_active):
+        vx, vw, sx, sw, sn = o.cell_quadrature(e)
+        if ibp:
+            total -= vw @ (vfun.eval(e, vx) * lap(vx))
+        else:
+            G = g(vx)
+            total += sum(vw @ (vfun.eval(e, vx, deriv=a) * G[:, a]) for a in range(prob.dim))
+        if len(sw):
+            v = vfun.eval(e, sx)
+            dnv = sum(sn[:, a] * vfun.eval(e, sx, deriv=a) for a in range(prob.dim))
+            dnu = np.sum(sn * g(sx), axis=1)
+            u = f(sx)
+            if ibp:
+                total += sw @ (-dnv * u + tau * v * u)
+            else:
+                total += sw @ (-dnv * u - v * dnu + tau * v * u)
+        if not ibp:
+            for axis in range(prob.dim):
+                ep = o.mesh.neighbor(e, axis, 1)
+                if ep < 0:
+                    continue
+                fx, fw = o.face_quadrature(e, axis)
+                if not len(fw):
+                    continue
+                jump_v = vfun.eval(e, fx, fixed=(axis, 1.0)) - vfun.eval(ep, fx, fixed=(axis, 0.0))
+                total -= fw @ (jump_v * g(fx)[:, axis])
+    return total
+
+
+def test_consistency_with_global_polynomial(case):
+    o, A, f, g, lap = case
+    u = _interp(o, f)
+    rng = np.random.default_rng(11)
+    v = rng.uniform(-1, 1, A.shape[0])
+    vfun = _DGFunction(o, v)
+    lhs = v @ (A @ u)
+    direct = _form_with_smooth_u(o, vfun, f, g, lap, ibp=False)
+    assert abs(lhs - direct) < 1e-11 * max(1.0, abs(lhs))
+    ibp = _form_with_smooth_u(o, vfun, f, g, lap, ibp=True)
+    # Integration by parts holds up to the quadrature error of the cut cells, which is large on
+    # these coarse grids (h = 0.24 in 2D with q = 2, h = 0.48 in 3D); a dropped or mis-signed
+    # term changes the result by O(1) relative.
+    tol = 5e-3 if o.prob.dim == 3 else 1e-4
+    assert abs(lhs - ibp) < tol * max(1.0, abs(lhs))
+
+
+def test_piecewise_constants(case):
+    """Only the SIPG penalty on F cap Omega and the Nitsche penalty see piecewise constants."""
+    o, A, *_ = case
+    prob = o.prob
+    rng = np.random.default_rng(5)
+    c = rng.uniform(-1, 1, o.mesh.n_active)
+    u = np.repeat(c, o.ndof)
+    want = 0.0
+    for e in range(o.mesh.n_active):
+        sw = o.cell_quadrature(e)[3]
+        want += prob.nitsche_gamma / prob.h * sw.sum() * c[e] ** 2
+        for axis in range(prob.dim):
+            ep = o.mesh.neighbor(e, axis, 1)
+            if ep >= 0:
+                fw = o.face_quadrature(e, axis)[1]
+                want += prob.sipg_gamma / prob.h * fw.sum() * (c[e] - c[ep]) ** 2
+    assert abs(u @ A @ u - want) < 1e-11 * want
+
+
+def test_ghost_penalty_single_order_jump():
+    cfg = workloads.small(p=3, N=5)
+    o = _oracle(cfg)
+    prob = o.prob
+    # a ghost-penalty face
+    for e in range(o.mesh.n_active):
+        ep = o.mesh.neighbor(e, 0, 1)
+        if ep >= 0 and o.mesh.active_type[e] == mesh.CUT:
+            break
+    G = o.gp_blocks(e, 0)
+    xF = mesh.cell_box(prob, o.mesh.index_of(e))[1][0]
+    nodes, _ = _lagrange_polys(o.n)
+    lo_p, _ = mesh.cell_box(prob, o.mesh.index_of(ep))
+    for j in range(1, prob.gp_max_order + 1):
+        # u = 0 on the '-' cell, (x - x_F)^j / j! on the '+' cell
+        up = np.array([(lo_p[0] + prob.h * nodes[l % o.n] - xF) ** j / math.factorial(j)
+                       for l in range(o.ndof)])
+        um = np.zeros(o.ndof)
+        energy = (um @ G[(0, 0)] @ um + um @ G[(0, 1)] @ up + up @ G[(1, 0)] @ um
+                  + up @ G[(1, 1)] @ up)
+        gam = prob.gp_gamma * prob.h ** (2 * j - 1) / math.factorial(j) ** 2
+        assert abs(energy - gam * prob.h ** 2) < 1e-12 * gam * prob.h ** 2
+
+
+def _sipg_1d(n, N, h, sigma):
+    """1D SIPG matrix (cell stiffness + interior point fluxes) and block-diagonal mass matrix."""
+    nodes, polys = _lagrange_polys(n)
+    K = np.zeros((n, n))
+    M = np.zeros((n, n))
+    for i in range(n):
+        for j in range(n):
+            ki = (polys[i].deriv() * polys[j].deriv()).integ()
+            mi = (polys[i] * polys[j]).integ()
+            K[i, j] = (ki(1.0) - ki(0.0)) / h
+            M[i, j] = (mi(1.0) - mi(0.0)) * h
+    v1 = np.array([p(1.0) for p in polys])
+    v0 = np.array([p(0.0) for p in polys])
+    d1 = np.array([p.deriv()(1.0) for p in polys]) / h
+    d0 = np.array([p.deriv()(0.0) for p in polys]) / h
+    S = np.kron(np.eye(N), K)
+    Mg = np.kron(np.eye(N), M)
+    V = (v1, v0)
+    D = (d1, d0)
+    sg = (1.0, -1.0)
+    for I in range(N - 1):
+        cells = (I, I + 1)
+        for s in range(2):
+            for t in range(2):
+                blk = (-0.5 * sg[t] * np.outer(D[s], V[t]) - 0.5 * sg[s] * np.outer(V[s], D[t])
+                       + sigma / h * sg[s] * sg[t] * np.outer(V[s], V[t]))
+                S[cells[s] * n:(cells[s] + 1) * n, cells[t] * n:(cells[t] + 1) * n] += blk
+    return S, Mg
+
+
+@pytest.mark.parametrize("dim,p,N", [(2, 3, (4, 3)), (3, 2, (3, 2, 3))])
+def test_uncut_operator_is_kronecker_sum(dim, p, N):
+    cfg = workloads.small(p=p, N=4, dim=dim)
+    cfg.update(n_cells=tuple(N) + (1,) * (3 - dim), radius=100.0)
+    L = 0.4
+    cfg.update(lo=(-L * N[0], -L * N[1], -L * (N[2] if dim == 3 else 0)),
+               hi=(L * N[0], L * N[1], L * (N[2] if dim == 3 else 0)))
+    o = _oracle(cfg)
+    assert o.mesh.n_active == int(np.prod(N))
+    A = o.assemble().toarray()
+    n = p + 1
+    h = o.prob.h
+    S = []
+    M = []
+    for a in range(dim):
+        s, m = _sipg_1d(n, N[a], h, o.prob.sipg_gamma)
+        S.append(s)
+        M.append(m)
+    want = np.zeros_like(A)
+    for a in range(dim):
+        mats = [S[b] if b == a else M[b] for b in range(dim)]
+        K = mats[0]
+        for b in range(1, dim):
+            K = np.kron(mats[b], K)  # tensor index with direction 0 fastest
+        want += K
+    # natural tensor index (g_0 + G_0 g_1 + ...), g_a = I_a n + i_a  ->  DG index e n^d + l
+    G = [N[a] * n for a in range(dim)]
+    perm = np.zeros(A.shape[0], dtype=int)
+    for nat in range(A.shape[0]):
+        rem = nat
+        e = 0
+        l = 0
+        stride_e = 1
+        stride_l = 1
+        for a in range(dim):
+            ga = rem % G[a]
+            rem //= G[a]
+            e += (ga // n) * stride_e
+            l += (ga % n) * stride_l
+            stride_e *= N[a]
+            stride_l *= n
+        perm[nat] = e * n ** dim + l
+    B = np.zeros_like(A)
+    B[np.ix_(perm, perm)] = want
+    assert np.max(np.abs(A - B)) < 1e-12 * np.max(np.abs(B))
+
+
+def test_rows_match_assembled(case):
+    o, A, *_ = case
+    x = np.random.default_rng(2).uniform(-1, 1, A.shape[0])
+    y = A @ x
+    cells = list(range(0, o.mesh.n_active, max(1, o.mesh.n_active // 13)))
+    rows = o.apply_rows(x, cells)
+    for r, e in enumerate(cells):
+        np.testing.assert_allclose(rows[r], y[e * o.ndof:(e + 1) * o.ndof], rtol=0,
+                                   atol=1e-13 * np.abs(y).max())
+
+
+def test_kappa_linearity():
+    """A(kappa) is linear in kappa: A(k1 + k2) = A(k1) + A(k2)."""
+    cfg = workloads.small(p=2, N=4)
+    o0 = _oracle(cfg)
+    n = o0.mesh.n_active
+    rng = np.random.default_rng(9)
+    k1 = rng.uniform(0.5, 2.0, n)
+    k2 = rng.uniform(0.5, 2.0, n)
+    A1 = _oracle(cfg, k1).assemble()
+    A2 = _oracle(cfg, k2).assemble()
+    A12 = _oracle(cfg, k1 + k2).assemble()
+    assert abs(A12 - A1 - A2).max() < 1e-13 * abs(A12).max()
+    assert abs(A1 - A1.T).max() < 1e-14 * abs(A1).max()

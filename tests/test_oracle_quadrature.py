@@ -1,0 +1,172 @@
+"""Pins of the oracle's dimension-reduction quadrature against closed forms (CPU).
+
+The rule itself has no printed reference; its integrals do: ball volume and sphere area, monomial
+moments of ball and sphere (closed form through Gamma functions), plane sections of the ball, and
+the divergence theorem on every cut cell (volume rule, surface rule and face rules together).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mesh, saye
+
+
+def _ball_moment(alpha, R, surface=False):
+    """int over the ball (or sphere) of radius R centred at 0 of prod_i y_i^alpha_i."""
+    if any(a % 2 for a in alpha):
+        return 0.0
+    d = len(alpha)
+    s = sum(alpha)
+    g = 2.0 * np.prod([math.gamma((a + 1) / 2.0) for a in alpha]) / math.gamma((s + d) / 2.0)
+    return g * R ** (s + d - 1) if surface else g * R ** (s + d) / (s + d)
+
+
+def _all_rules(prob):
+    m = mesh.Mesh(prob)
+    vol = []
+    surf = []
+    for e in range(m.n_active):
+        lo, hi = mesh.cell_box(prob, m.index_of(e))
+        if m.active_type[e] == mesh.INSIDE:
+            vol += saye.tensor_gauss(lo, hi, prob.quad_order)
+        else:
+            v, s = saye.cell_rules(prob, lo, hi)
+            vol += v
+            surf += s
+    vx = np.array([p for p, _ in vol])
+    vw = np.array([w for _, w in vol])
+    sx = np.array([p for p, _, _ in surf])
+    sw = np.array([w for _, w, _ in surf])
+    sn = np.array([nn for _, _, nn in surf])
+    return vx, vw, sx, sw, sn
+
+
+def _prob(dim, N, q, center, R=1.0):
+    return mesh.Problem(dim, 3, (N,) * dim, (-1.21,) * dim, (1.21,) * dim, center, R, q, 1, 1, 1, 0.5)
+
+
+@pytest.mark.parametrize("dim,center", [(2, (0.03, 0.02)), (3, (0.01, 0.02, 0.03))])
+def test_volume_and_area_converge(dim, center):
+    errs = []
+    for N in (6, 12, 24):
+        vx, vw, sx, sw, sn = _all_rules(_prob(dim, N, 4, center))
+        V = math.pi if dim == 2 else 4.0 / 3.0 * math.pi
+        S = 2.0 * math.pi if dim == 2 else 4.0 * math.pi
+        errs.append((abs(vw.sum() - V), abs(sw.sum() - S)))
+        # the surface normals integrate to zero (closed surface)
+        assert np.max(np.abs(sw @ sn)) < 10 * errs[-1][1] + 1e-13
+    # high order: two halvings of h gain at least 2^10 (order >= 5; q = 4 Gauss points)
+    assert errs[2][0] < errs[0][0] / 1024 and errs[2][1] < errs[0][1] / 1024
+    assert errs[-1][0] < 1e-10 and errs[-1][1] < 1e-9
+
+
+def test_monomial_moments_3d():
+    c = np.array([0.01, 0.02, 0.03])
+    vx, vw, sx, sw, sn = _all_rules(_prob(3, 16, 4, tuple(c)))
+    yv = vx - c
+    ys = sx - c
+    for alpha in [(0, 0, 0), (2, 0, 0), (0, 2, 2), (1, 0, 0), (2, 2, 0), (4, 0, 0), (1, 1, 2), (2, 1, 0)]:
+        fv = np.prod([yv[:, i] ** alpha[i] for i in range(3)], axis=0)
+        fs = np.prod([ys[:, i] ** alpha[i] for i in range(3)], axis=0)
+        assert abs(vw @ fv - _ball_moment(alpha, 1.0)) < 2e-9
+        assert abs(sw @ fs - _ball_moment(alpha, 1.0, surface=True)) < 2e-8
+
+
+def test_plane_sections_3d():
+    """The face rules of all faces in one grid plane integrate the disc section of the ball."""
+    prob = _prob(3, 20, 4, (0.01, 0.02, 0.03))
+    m = mesh.Mesh(prob)
+    for axis in range(3):
+        for plane in (6, 10, 13):
+            xa = prob.lo[axis] + plane * prob.h
+            total = 0.0
+            for e in range(m.n_active):
+                if m.index_of(e)[axis] != plane - 1:
+                    continue
+                ep = m.neighbor(e, axis, 1)
+                if ep < 0:
+                    continue
+                lo, hi = m.face_box(e, axis)
+                ft = m.face_type(e, axis)
+                if ft == mesh.FACE_FULL:
+                    total += prob.h ** 2
+                elif ft == mesh.FACE_CUT:
+                    total += sum(w for _, w in saye.face_rule(prob, lo, hi, axis))
+            dist = xa - prob.center[axis]
+            assert abs(total - math.pi * (1.0 - dist * dist)) < 1e-9
+
+
+def test_divergence_theorem_per_cut_cell():
+    """int_{K cap Omega} div F = int_{Gamma cap K} F.n + sum_faces int_{F cap Omega} F.n_K."""
+    prob = _prob(3, 8, 5, (0.01, 0.02, 0.03))
+    m = mesh.Mesh(prob)
+
+    def F(x):
+        return np.array([x[0] ** 2 * x[1], x[1] * x[2] ** 3 + x[0], x[0] * x[1] * x[2]])
+
+    def divF(x):
+        return 2 * x[0] * x[1] + x[2] ** 3 + x[0] * x[1]
+
+    worst = 0.0
+    for e in range(m.n_active):
+        if m.active_type[e] != mesh.CUT:
+            continue
+        lo, hi = mesh.cell_box(prob, m.index_of(e))
+        vol, surf = saye.cell_rules(prob, lo, hi)
+        lhs = sum(w * divF(x) for x, w in vol)
+        rhs = sum(w * F(x) @ np.array(nn) for x, w, nn in surf)
+        for axis in range(3):
+            for side, sign in ((0, -1.0), (1, 1.0)):
+                flo = list(lo)
+                fhi = list(hi)
+                if side == 0:
+                    fhi[axis] = lo[axis]
+                else:
+                    flo[axis] = hi[axis]
+                for x, w in saye.face_rule(prob, tuple(flo), tuple(fhi), axis):
+                    rhs += sign * w * F(x)[axis]
+        worst = max(worst, abs(lhs - rhs))
+    # quadrature error at h = 0.3 (q = 5) is ~1e-8; a dropped or mis-signed term gives O(h^2)
+    assert worst < 5e-8
+
+
+def test_brute_force_single_cell():
+    """One cut cell: Saye volume vs a 2^7-per-direction midpoint sampling of the indicator."""
+    lo, hi = (0.55, 0.52, 0.4), (0.85, 0.82, 0.7)
+    c, R = (0.0, 0.0, 0.0), 1.0
+    vol, surf = saye.sphere_rules(lo, hi, c, R * R, 4)
+    V = sum(w for _, w in vol)
+    k = 128
+    t = (np.arange(k) + 0.5) / k
+    X, Y, Z = np.meshgrid(*[lo[a] + (hi[a] - lo[a]) * t for a in range(3)], indexing="ij")
+    inside = (X ** 2 + Y ** 2 + Z ** 2) < 1.0
+    Vb = inside.mean() * np.prod(np.subtract(hi, lo))
+    assert 0 < V < np.prod(np.subtract(hi, lo))
+    assert abs(V - Vb) < 2e-3 * np.prod(np.subtract(hi, lo))
+
+
+def test_inside_box_is_tensor_gauss_and_exact():
+    lo, hi = (-0.2, -0.1, 0.0), (0.1, 0.2, 0.3)
+    vol, surf = saye.sphere_rules(lo, hi, (0.0, 0.0, 0.0), 1.0, 3)
+    assert not surf and len(vol) == 27
+    # exact for x^5 y^4 z^3
+    got = sum(w * x[0] ** 5 * x[1] ** 4 * x[2] ** 3 for x, w in vol)
+    want = ((hi[0] ** 6 - lo[0] ** 6) / 6) * ((hi[1] ** 5 - lo[1] ** 5) / 5) * ((hi[2] ** 4 - lo[2] ** 4) / 4)
+    assert abs(got - want) < 1e-17
+
+
+def test_subdivision_path():
+    """A box containing the centre of a small sphere needs bisection.  The children have height
+    functions that are steep near the bisection planes, so the integrals converge algebraically in
+    q there; check that they converge."""
+    lo, hi = (-0.3, -0.2, -0.25), (0.3, 0.4, 0.35)
+    c = (0.02, 0.01, -0.01)
+    R = 0.15
+    errs = []
+    for q in (4, 8, 12):
+        vol, surf = saye.sphere_rules(lo, hi, c, R * R, q)
+        errs.append((abs(sum(w for _, w in vol) / (4.0 / 3.0 * math.pi * R ** 3) - 1.0),
+                     abs(sum(w for _, w, _ in surf) / (4.0 * math.pi * R ** 2) - 1.0)))
+    assert errs[0][0] < 1e-5 and errs[0][1] < 5e-3
+    assert errs[2][0] < errs[0][0] / 10 and errs[2][1] < errs[0][1] / 100

@@ -1,0 +1,90 @@
+"""Seeded synthetic workloads: problem presets and input vectors.
+
+This module holds no arithmetic of the method.  It is the one place both sides of a parity test
+draw from: the CPU oracle (``oracle/``) and the CUDA library (``paper_2404_07911_gb300``) receive
+the same problem description and the same seeded vectors from here.
+
+Problem presets follow the workloads of arXiv 2404.07911 (unit-radius ball embedded in a
+Cartesian background grid, Sec. 4 and Sec. 5.1) with the sizes, penalties and seeds of the
+benchmark configurations:
+
+  * ``cfg_2d_q1``      2D, DG Q1, 16^2 background cells on [-1.21, 1.21]^2, disc |x-(0.03,0.02)| < 1,
+                       quadrature order q = 2, SIPG 8/h, Nitsche 20/h, ghost penalty order 1,
+                       gamma_1 = 0.5 h; x ~ U[-1, 1] seed 0.
+  * ``cfg_3d_q3``      3D, DG Q3 (64 DoF/cell), 64^3 cells on [-1.21, 1.21]^3, ball
+                       |x-(0.01,0.02,0.03)| < 1, q = 4, SIPG 2.5 (p+1)^2 / h, Nitsche 10 (p+1)^2 / h,
+                       ghost penalty orders 1..3 with gamma_j = 0.5 h^(2j-1) / (j!)^2; x ~ U[-1, 1]
+                       seed 1.
+  * ``cfg_sweep(p)``   3D, DG Q_p, p = 1..8, same ball and penalties, background cells per direction
+                       chosen so that the DoF count is about 2e7; q = p + 1; seed 2.
+  * ``cfg_kappa``      3D, DG Q3 on a 48^3 background, same ball and penalties; per-cell
+                       kappa ~ LogNormal(0, 0.5) seed 4; x then b ~ U[-1, 1] seed 5.
+  * ``small(...)``     reduced grids of the same geometry for tests the oracle finishes in seconds.
+
+Vectors are drawn with ``numpy.random.default_rng(seed)`` in DoF order (active cells
+lexicographic with x fastest, local index i + n j + n^2 k).
+"""
+import numpy as np
+
+SWEEP_N = {1: 202, 2: 134, 3: 100, 4: 80, 5: 66, 6: 56, 7: 49, 8: 43}
+
+
+def _penalties(p):
+    n = p + 1
+    return dict(sipg_gamma=2.5 * n * n, nitsche_gamma=10.0 * n * n, gp_max_order=p, gp_gamma=0.5)
+
+
+def cfg_2d_q1():
+    return dict(name="2d_dg_q1_16x16_disc", dim=2, degree=1, n_cells=(16, 16, 1),
+                lo=(-1.21, -1.21, 0.0), hi=(1.21, 1.21, 0.0), center=(0.03, 0.02, 0.0), radius=1.0,
+                quad_order=2, sipg_gamma=8.0, nitsche_gamma=20.0, gp_max_order=1, gp_gamma=0.5,
+                seed=0)
+
+
+def cfg_3d(p=3, N=64, center=(0.01, 0.02, 0.03), name=None, seed=1, quad_order=None):
+    return dict(name=name or f"3d_dg_q{p}_{N}^3_ball", dim=3, degree=p, n_cells=(N, N, N),
+                lo=(-1.21, -1.21, -1.21), hi=(1.21, 1.21, 1.21), center=center, radius=1.0,
+                quad_order=quad_order if quad_order is not None else 4 if p == 3 else p + 1,
+                seed=seed, **_penalties(p))
+
+
+def cfg_3d_q3():
+    return cfg_3d(3, 64, name="3d_dg_q3_64^3_ball", seed=1)
+
+
+def cfg_sweep(p):
+    return cfg_3d(p, SWEEP_N[p], name=f"3d_dg_q{p}_{SWEEP_N[p]}^3_ball_sweep", seed=2,
+                  quad_order=p + 1)
+
+
+def cfg_kappa(N=48):
+    return cfg_3d(3, N, name=f"3d_dg_q3_{N}^3_ball_kappa", seed=5)
+
+
+def small(p=3, N=8, dim=3, center=None, seed=7):
+    """A reduced grid of the same geometry (tests)."""
+    if dim == 2:
+        c = cfg_2d_q1()
+        c.update(name=f"2d_dg_q{p}_{N}^2", degree=p, n_cells=(N, N, 1), seed=seed)
+        if p != 1:
+            c.update(quad_order=p + 1, **_penalties(p))
+        if center is not None:
+            c["center"] = tuple(center) + (0.0,)
+        return c
+    return cfg_3d(p, N, center=center or (0.01, 0.02, 0.03), name=f"3d_dg_q{p}_{N}^3", seed=seed)
+
+
+def uniform_vector(n, seed):
+    """x ~ U[-1, 1], float64, length n."""
+    return np.random.default_rng(seed).uniform(-1.0, 1.0, n)
+
+
+def kappa_vector(n_active, seed=4):
+    """kappa ~ LogNormal(0, 0.5) per active cell."""
+    return np.random.default_rng(seed).lognormal(0.0, 0.5, n_active)
+
+
+def x_and_b(n, seed=5):
+    """x then b ~ U[-1, 1] from one generator."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-1.0, 1.0, n), rng.uniform(-1.0, 1.0, n)
