@@ -1,0 +1,407 @@
+#!/usr/bin/env python
+"""Throughput of the matrix-free unfitted DG operator on the 3D Q3 ball workload.
+
+Workload: 3D DG Q3 (64 DoF/cell), 64^3 background cells on [-1.21, 1.21]^3, ball
+|x - (0.01, 0.02, 0.03)| < 1 (84,218 active cells, 13,180 cut, 5,389,952 DoFs), dimension-
+reduction quadrature of order 4 on cut cells and cut faces, SIPG 2.5 (p+1)^2 / h, Nitsche
+10 (p+1)^2 / h, face ghost penalty orders 1..3; x ~ U[-1, 1] seed 1 (synthetic, as in the paper's
+sphere benchmarks).
+
+One step = the whole operator path on that input: y = A x in FP64, y = A x in FP32 and
+y = A^T x in FP64.  value = DoFs of the three applications / device time of the step (GDoF/s),
+summed over ranks (each rank runs an independent replica: weak scaling, no collective).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (plain FP64, naive full-basis quadrature) on the host cores
+on a bounded sample of cells of the same workload, with the same step composition.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+METRIC = "GDoF/s of unfitted DG A·x (3D, k=3) FP64/FP32 + adjoint, % of HBM roofline"
+UNIT = "GDoF/s"
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC = os.path.join(ROOT, "profiles", "dram_traffic.json")
+KERNEL_SOURCE = os.path.join(ROOT, "paper_2404_07911_gb300", "csrc", "uf_kernels.cuh")
+# Device arithmetic peaks from unit counts and the maximum SM clock (2070 MHz), 152 SMs:
+# FP64 2 FMA / clk / SM (GB300 ships a reduced FP64 pipe), FP32 128 FMA / clk / SM.
+SM_COUNT, SM_MAX_GHZ = 152, 2.070
+FP64_PEAK_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_GHZ / 1e3
+FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_GHZ / 1e3
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--cpu-sample-cells", type=int, default=120,
+                    help="cells of the oracle's bounded sample (cpu_baseline / reference arm)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------------------ oracle sample
+def oracle_sample(cfg, n_cells, seed=3):
+    """Active cells with the workload's inside / cut mix (fixed seed)."""
+    from oracle import mesh
+
+    m = mesh.Mesh(mesh.problem_from_dict(cfg))
+    rng = np.random.default_rng(seed)
+    cut = np.nonzero(m.active_type == mesh.CUT)[0]
+    inside = np.nonzero(m.active_type == mesh.INSIDE)[0]
+    n_cut = max(1, int(round(n_cells * len(cut) / m.n_active)))
+    cells = np.concatenate([rng.choice(cut, n_cut, replace=False),
+                            rng.choice(inside, n_cells - n_cut, replace=False)])
+    return sorted(int(c) for c in cells), m.n_dofs
+
+
+def oracle_step(cfg, x64, x32r, cells):
+    """One step of the oracle on the sample: A x (FP64), A x (FP32-rounded x), A^T x (FP64),
+    from a fresh oracle (quadrature and local forms recomputed as the oracle stands)."""
+    from oracle import forms, mesh
+
+    o = forms.Oracle(mesh.problem_from_dict(cfg))
+    o.apply_rows(x64, cells)
+    o.apply_rows(x32r, cells)
+    o.apply_rows(x64, cells, transpose=True)
+
+
+def _blas_single_thread():
+    try:
+        import threadpoolctl
+
+        threadpoolctl.threadpool_limits(1)
+        return 1
+    except Exception:
+        return None
+
+
+def cpu_baseline(cfg, n_cells, budget_s=20.0):
+    cores = _blas_single_thread() or 1
+    cells, n_dofs = oracle_sample(cfg, n_cells)
+    x64 = workloads.uniform_vector(n_dofs, cfg["seed"])
+    x32r = x64.astype(np.float32).astype(np.float64)
+    nd = (cfg["degree"] + 1) ** cfg["dim"]
+    times = []
+    t_start = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        oracle_step(cfg, x64, x32r, cells)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_start > budget_s or len(times) >= 5:
+            break
+    t = statistics.median(times)
+    return {"value": 3 * len(cells) * nd / t / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{len(cells)} active cells of the workload (inside/cut mix of the full grid, "
+                      f"seed 3), rows of A x FP64 + A x FP32-rounded + A^T x per step, "
+                      f"median of {len(times)} steps of {t:.2f} s each, BLAS 1 thread"}
+
+
+# ------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={CLOCK_FIELDS}", "--format=csv",
+                 "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path).read().splitlines()[1:]:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm = float(parts[1].split()[0])
+                smax = float(parts[2].split()[0])
+                pw = float(parts[3].split()[0]) if parts[3].split()[0] not in ("[N/A]", "N/A") else 0.0
+            except ValueError:
+                continue
+            rows.append((sm, smax, pw, parts[5:9]))
+        os.unlink(self.path)
+        if not rows:
+            return None
+        load = [r for r in rows if r[2] > 250.0] or rows
+        reasons = set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in load:
+            for name, flag in zip(names, r[3]):
+                if flag.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r[0] for r in load), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows), "samples_under_load": len(load)}
+
+
+# ------------------------------------------------------------------------------ our arm
+def measured_peaks():
+    try:
+        return json.load(open(MEASURED_PEAKS))
+    except Exception:
+        return {}
+
+
+def kernel_traffic(name):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on these sources."""
+    try:
+        rec = json.load(open(TRAFFIC))
+        digest = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()[:16]
+        if rec.get("source_sha256_16") != digest:
+            return None
+        return rec["kernels"].get(name)
+    except Exception:
+        return None
+
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    from paper_2404_07911_gb300 import UF_FP32, UF_FP64, UnfittedOperator
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    cfg = workloads.cfg_3d_q3()
+    op = UnfittedOperator(cfg, precisions=UF_FP64 | UF_FP32, device=local)
+    info = op.info
+    n = info["n_dofs"]
+    x_host = workloads.uniform_vector(n, cfg["seed"])
+    x64 = torch.from_numpy(x_host).cuda()
+    x32 = x64.float()
+    y64 = torch.empty_like(x64)
+    y32 = torch.empty_like(x32)
+    ya = torch.empty_like(x64)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def step():
+        op.vmult(x64, y64, stream)
+        op.vmult(x32, y32, stream)
+        op.vmult_adjoint(x64, ya, stream)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    K = args.steps
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    op.profile_begin(3 * K)
+    barrier()
+    for k in range(K):
+        flush.zero_()
+        ev_s[k].record(stream)
+        step()
+        ev_e[k].record(stream)
+    barrier()
+    step_ms = [ev_s[k].elapsed_time(ev_e[k]) for k in range(K)]
+    ktimes = op.profile_end()
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * K * 3 * n / (total_ms / 1e3) / 1e9
+
+    # ---- end to end through the C ABI with pinned host buffers (copies inside the region)
+    xh64 = torch.from_numpy(x_host).pin_memory()
+    xh32 = xh64.float().pin_memory()
+    yh64 = torch.empty_like(xh64).pin_memory()
+    yh32 = torch.empty_like(xh32).pin_memory()
+    yha = torch.empty_like(xh64).pin_memory()
+    sp = stream.cuda_stream
+
+    def e2e_step():
+        op.vmult_host_ptr(UF_FP64, yh64.data_ptr(), xh64.data_ptr(), sp)
+        op.vmult_host_ptr(UF_FP32, yh32.data_ptr(), xh32.data_ptr(), sp)
+        op.vmult_host_ptr(UF_FP64, yha.data_ptr(), xh64.data_ptr(), sp, adjoint=True)
+
+    for _ in range(max(args.warmup, 3)):
+        e2e_step()
+    K_e2e = max(3, min(K, 50))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(K_e2e):
+        e2e_step()
+    barrier()
+    t_e2e = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    clk = clocks.stop()
+    e2e = {"value": world * K_e2e * 3 * n / t_e2e / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": 20 * n, "d2h_bytes_per_step": 20 * n}
+
+    # ---- per-kernel figures from the events of the timed region
+    peaks = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    parts = {}
+    kernels = []
+    for (prec, kern, dirn), (ms, cnt) in ktimes.items():
+        ki = 0 if kern == "struct" else 1
+        byts = info["kernel_bytes_fp64" if prec == "fp64" else "kernel_bytes_fp32"][ki]
+        flops = info["kernel_flops"][ki]
+        avg_s = ms / cnt / 1e3
+        alu_peak = FP64_PEAK_TFLOPS if prec == "fp64" else FP32_PEAK_TFLOPS
+        gbs = byts / avg_s / 1e9
+        tfl = flops / avg_s / 1e12
+        name = f"{kern}_kernel_{prec}{'_adjoint' if dirn == 'adjoint' else ''}"
+        kernels.append((ms, name, prec, gbs, tfl, alu_peak, byts, flops, avg_s))
+        key = f"{prec}_{dirn}"
+        parts.setdefault(key, {"ms": 0.0})
+        parts[key]["ms"] += ms / cnt
+    for key in parts:
+        parts[key]["gdofs"] = n / (parts[key]["ms"] / 1e3) / 1e9
+        parts[key]["ms"] = round(parts[key]["ms"], 4)
+        parts[key]["gdofs"] = round(parts[key]["gdofs"], 3)
+    kernels.sort(reverse=True)
+    ms, name, prec, gbs, tfl, alu_peak, byts, flops, avg_s = kernels[0]
+    hbm_frac = gbs / hbm
+    alu_frac = tfl / alu_peak
+    traffic = kernel_traffic(name)
+    if alu_frac >= hbm_frac:
+        roof = {"bound": "alu", "achieved": round(tfl, 4), "peak": round(alu_peak, 4),
+                "unit": "TFLOP/s", "frac": round(alu_frac, 4), "traffic": traffic,
+                "kernel": name, "peak_source": f"derived: {SM_COUNT} SMs x "
+                f"{'2 FP64' if prec == 'fp64' else '128 FP32'} FMA/clk x 2 x {SM_MAX_GHZ} GHz",
+                "hbm_frac_of_measured": round(hbm_frac, 4)}
+    else:
+        roof = {"bound": "hbm", "achieved": round(gbs, 2), "peak": hbm, "unit": "GB/s",
+                "frac": round(hbm_frac, 4), "traffic": traffic, "kernel": name,
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
+                "alu_frac": round(alu_frac, 4)}
+    roof["algorithmic_bytes_per_launch"] = byts
+    roof["algorithmic_flops_per_launch"] = flops
+    roof["avg_launch_ms"] = round(avg_s * 1e3, 5)
+    kernel_table = {k[1]: {"avg_ms": round(k[8] * 1e3, 5), "gb_s": round(k[3], 1),
+                           "hbm_frac": round(k[3] / hbm, 4), "tflops": round(k[4], 3),
+                           "alu_frac": round(k[4] / k[5], 4)} for k in kernels}
+    launches = sum(cnt for (_, cnt) in ktimes.values())
+
+    result = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / K, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": cfg["name"], "n_dofs": n, "n_active": info["n_active"],
+                   "n_cut": info["n_cut"], "degree": cfg["degree"],
+                   "step": "A x FP64 + A x FP32 + A^T x FP64",
+                   "l2": "flushed before every step (256 MiB write, outside the step events)",
+                   "parallelism": f"replicas x{world}"},
+        "parts": parts,
+        "kernels": kernel_table,
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(cfg, args.cpu_sample_cells)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    op.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------ reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    cores = _blas_single_thread() or 1
+    cfg = workloads.cfg_3d_q3()
+    cells, n_dofs = oracle_sample(cfg, args.cpu_sample_cells)
+    x64 = workloads.uniform_vector(n_dofs, cfg["seed"])
+    x32r = x64.astype(np.float32).astype(np.float64)
+    nd = (cfg["degree"] + 1) ** cfg["dim"]
+    for _ in range(args.warmup):
+        oracle_step(cfg, x64, x32r, cells)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_step(cfg, x64, x32r, cells)
+    t = time.perf_counter() - t0
+    value = args.steps * 3 * len(cells) * nd / t / 1e9
+    sample = (f"{len(cells)} active cells of the workload (inside/cut mix of the full grid, seed 3), "
+              f"rows of A x FP64 + A x FP32-rounded + A^T x per step, fresh oracle per step")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": cfg["name"], "n_dofs": n_dofs, "degree": cfg["degree"],
+                   "step": "A x FP64 + A x FP32 + A^T x FP64 (rows of the sampled cells)",
+                   "parallelism": "rank 0 only"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse_args()
+    rank, world, local = dist_info()
+    if args.impl == "reference":
+        # keep the reference arm short: its steps are bounded samples
+        if args.steps > 20:
+            args.steps = 5
+        if args.warmup > 3:
+            args.warmup = 1
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,167 @@
+/*
+ * unfitted.h - C ABI of the GB300 matrix-free unfitted DG Poisson operator.
+ *
+ * The operator is the one of arXiv 2404.07911, Sec. 2.1 (Eq. bilinear_cg, Eq. bilinear_dg):
+ * a discontinuous Galerkin SIPG discretisation of -Lap u = f on Omega = {phi < 0} embedded in a
+ * Cartesian background grid, with the Dirichlet condition on Gamma imposed by Nitsche's method,
+ * stabilised by the face-based ghost penalty (Sec. 2.2) on jumps of normal derivatives of
+ * orders 1..J across every face of a cut cell, and an optional per-cell diffusion coefficient
+ * kappa that multiplies every term linearly (arithmetic face average {kappa} on face terms).
+ * Shape functions are tensor-product Lagrange polynomials of degree p in the Gauss-Lobatto
+ * points (Sec. 3.2); inside cells and full faces are integrated with structured (tensor Gauss)
+ * quadrature, cut cells, Gamma and cut faces with unstructured dimension-reduction quadrature
+ * generated once at creation (Sec. 2.3).
+ *
+ * DoF layout of every vector (x, y, g): active cells (inside + cut) numbered lexicographically
+ * over the background grid with the x index fastest; active cell e owns the contiguous block
+ * [e * n^d, (e + 1) * n^d), local index l = i + n j + n^2 k (n = p + 1), Sec. 3.2.
+ *
+ * Conventions for every call:
+ *   - Return value: UF_OK or an error code; errors never abort the process.  uf_last_error()
+ *     returns a thread-local message describing the last failure of the calling thread.
+ *   - Device pointers refer to memory of the operator's CUDA device; the caller owns them.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Stream-
+ *     ordered calls return once the work is enqueued; they never allocate and never synchronise.
+ */
+#ifndef UNFITTED_H
+#define UNFITTED_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct uf_operator uf_operator; /* opaque, owned by the library */
+
+typedef enum {
+  UF_OK = 0,
+  UF_EINVAL = 1,        /* invalid argument (NULL pointer, bad size, aliasing, bad parameter) */
+  UF_ENOMEM = 2,        /* host or device allocation failed during creation */
+  UF_ECUDA = 3,         /* a CUDA runtime call failed (message in uf_last_error) */
+  UF_EUNSUPPORTED = 4,  /* valid but not supported (e.g. anisotropic grid, degree > 8) */
+  UF_EGEOMETRY = 5,     /* quadrature generation failed (subdivision depth exceeded) */
+  UF_ENODEVICE = 6      /* the operator was created host-only (device = -1) */
+} uf_status;
+
+enum { UF_FP64 = 1, UF_FP32 = 2 };     /* precision flags (bit mask in uf_params.precisions) */
+enum { UF_LS_SPHERE = 0 };             /* level set kinds */
+
+/* Parameters of uf_create_unfitted_operator.  Penalties follow the paper's forms:
+ * SIPG penalty sigma/h (Eq. bilinear_dg), Nitsche penalty tau/h (Eq. bilinear_cg), ghost
+ * penalty gamma_j = gp_gamma * h^(2j-1) / (j!)^2 on [d^j u / dn^j], j = 1..gp_max_order. */
+typedef struct {
+  int dim;                /* 2 or 3 */
+  int degree;             /* polynomial degree p, 1..8 */
+  int n_cells[3];         /* background cells per direction (entries >= dim ignored) */
+  double lo[3], hi[3];    /* background box; cells must be cubes (isotropic h) */
+  int ls_kind;            /* UF_LS_SPHERE: phi(x) = |x - ls_center| - ls_radius */
+  double ls_center[3];
+  double ls_radius;
+  int quad_order;         /* q: Gauss points per interval of the cut-cell / cut-face rules */
+  double sipg_gamma;      /* sigma */
+  double nitsche_gamma;   /* tau */
+  int gp_max_order;       /* J (0 disables the ghost penalty), <= degree */
+  double gp_gamma;
+  int precisions;         /* UF_FP64 | UF_FP32: which device data to build */
+  int device;             /* CUDA device ordinal, or -1 for a host-only operator (no GPU use) */
+  const double *kappa;    /* host array [n_active] copied at creation, or NULL for kappa = 1 */
+} uf_params;
+
+/* Sizes and algorithmic traffic of an operator (uf_get_info). */
+typedef struct {
+  int64_t n_active, n_inside, n_cut, n_dofs;
+  int64_t n_faces, n_faces_full, n_faces_cut, n_faces_empty, n_faces_gp;
+  int64_t n_vol_points, n_surf_points, n_face_points; /* unstructured points (face points per side) */
+  int32_t dim, degree, dofs_per_cell, quad_order;
+  double h;
+  /* Algorithmic bytes of one vmult: read x once, write y once, read the unstructured point
+   * data and the per-cell metadata once, for FP64 and FP32 data respectively. */
+  double bytes_fp64, bytes_fp32;
+  /* Algorithmic floating-point operations of one vmult (FMA = 2) of the kernels as built. */
+  double flops;
+  /* Per kernel (index 0 = structured terms of all cells, 1 = unstructured terms of cut cells):
+   * algorithmic bytes for FP64 / FP32 data and floating-point operations of one launch. */
+  double kernel_bytes_fp64[2], kernel_bytes_fp32[2], kernel_flops[2];
+} uf_info;
+
+/* Per-kernel device times collected between uf_profile_begin and uf_profile_end, indexed
+ * [precision: 0 = FP64, 1 = FP32][kernel: 0 = structured, 1 = cut cells][0 = vmult, 1 = adjoint]. */
+typedef struct {
+  double ms_total[2][2][2];
+  int64_t launches[2][2][2];
+} uf_kernel_times;
+
+/* Build the operator: classify the background cells against the level set, number the active
+ * cells, type the interior faces, generate the dimension-reduction quadrature of every cut cell
+ * and cut face, and (device >= 0) upload everything to the device in the precisions requested.
+ * Untimed setup (the paper excludes it, Sec. 5.2).  On success *out owns all library memory.
+ * Errors: UF_EINVAL (NULL, dim/degree/q/sizes out of range), UF_EUNSUPPORTED (anisotropic cells,
+ * unknown level set), UF_EGEOMETRY, UF_ENOMEM, UF_ECUDA. */
+uf_status uf_create_unfitted_operator(const uf_params *params, uf_operator **out);
+
+/* Fill *info.  Errors: UF_EINVAL on NULL. */
+uf_status uf_get_info(const uf_operator *op, uf_info *info);
+
+/* y = A x (paper Eq. operatorevaluation / Eq. matrixfreeopcompact, Sec. 3.1), matrix-free.
+ * precision: UF_FP64 (x, y are double[n_dofs]) or UF_FP32 (float[n_dofs]); the operator must
+ * have been created with that precision.  x and y are device pointers that must not overlap.
+ * Stream-ordered; no allocation, no synchronisation.  Errors: UF_EINVAL, UF_ENODEVICE,
+ * UF_ECUDA (launch failure). */
+uf_status uf_vmult(uf_operator *op, int precision, void *y, const void *x, void *stream);
+
+/* y = A^T g.  Every term of the form is symmetric, so A^T = A; the adjoint is computed by the
+ * transposed cell-centric evaluation (each cell gathers the transposed couplings of its
+ * neighbours) and agrees with uf_vmult up to rounding.  Same arguments and errors as uf_vmult. */
+uf_status uf_vmult_adjoint(uf_operator *op, int precision, void *y, const void *g, void *stream);
+
+/* End-to-end y = A x with HOST buffers: copies x (host, pinned or pageable) to a library-owned
+ * device buffer allocated at creation, applies A, copies y back, and synchronises `stream`
+ * before returning.  Errors as uf_vmult. */
+uf_status uf_vmult_host(uf_operator *op, int precision, void *y_host, const void *x_host,
+                        void *stream);
+
+/* Same as uf_vmult_host for y = A^T g. */
+uf_status uf_vmult_adjoint_host(uf_operator *op, int precision, void *y_host, const void *g_host,
+                                void *stream);
+
+/* Kernel timing: uf_profile_begin creates `capacity` pairs of CUDA events (not stream-ordered;
+ * call it outside any timed region); every kernel that vmult / vmult_adjoint launches afterwards
+ * is bracketed by an event pair recorded on its stream, until the pairs run out.
+ * uf_profile_end waits for the recorded events, sums the elapsed times per kernel into *out and
+ * releases the events.  Errors: UF_EINVAL (capacity < 1, NULL out, no profiling active),
+ * UF_ENODEVICE, UF_ECUDA. */
+uf_status uf_profile_begin(uf_operator *op, int capacity);
+uf_status uf_profile_end(uf_operator *op, uf_kernel_times *out);
+
+/* Replace kappa: host array [n_active] of positive values.  Synchronous.  Errors: UF_EINVAL. */
+uf_status uf_set_kappa(uf_operator *op, const double *kappa_host);
+
+/* Export (host copies) of the setup product, for checks against an independent implementation.
+ * uf_export_cells: type[n_active] (0 inside, 1 cut) and index[n_active * 3] (background
+ *   multi-index i, j, k); either pointer may be NULL.
+ * uf_export_cut_cell_rule: for the c-th cut cell in active order, kind 0 = volume rule
+ *   (xi[count * dim] reference coordinates in [0,1]^d, w[count] physical weights), kind 1 =
+ *   surface rule (also normal[count * dim]).  Call with xi == NULL to get *count first.
+ * uf_export_cut_face_rule: rule on F cap Omega of the face of active cell e on (axis, side)
+ *   (side 0 = lower), in-face reference coordinates eta[count * (dim - 1)] (the other axes in
+ *   increasing order) and physical weights; *count = 0 unless the face is a cut face.
+ * Errors: UF_EINVAL (index out of range, NULL count). */
+uf_status uf_export_cells(const uf_operator *op, int32_t *type, int32_t *index);
+uf_status uf_export_cut_cell_rule(const uf_operator *op, int64_t c, int kind, double *xi,
+                                  double *w, double *normal, int64_t *count);
+uf_status uf_export_cut_face_rule(const uf_operator *op, int64_t e, int axis, int side,
+                                  double *eta, double *w, int64_t *count);
+
+/* Release every host and device resource of op.  NULL is accepted (no-op).  The caller must
+ * make sure no stream still runs work of op. */
+uf_status uf_destroy(uf_operator *op);
+
+/* Thread-local message of the last failing call of this thread ("" if none). */
+const char *uf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* UNFITTED_H */

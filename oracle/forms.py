@@ -218,19 +218,22 @@ class Oracle:
         A.sum_duplicates()
         return A
 
-    def apply_rows(self, x, cells):
-        """Rows of y = A x that belong to the listed active cells, computed one cell at a time.
-
-        Returns an array of shape (len(cells), n^d)."""
+    def apply_rows(self, x, cells, transpose=False):
+        """Rows of y = A x (or y = A^T x) that belong to the listed active cells, computed one
+        cell at a time.  Returns an array of shape (len(cells), n^d)."""
         nd = self.ndof
         X = np.asarray(x, dtype=np.float64).reshape(-1, nd)
         out = np.zeros((len(cells), nd))
         for r, e in enumerate(cells):
-            y = self.cell_matrix(e) @ X[e]
+            Ae = self.cell_matrix(e)
+            y = (Ae.T if transpose else Ae) @ X[e]
             for axis, side, nb in self.faces_of(e):
                 e_minus = e if side == 1 else nb
                 s = 0 if side == 1 else 1
                 blocks = self.face_blocks(e_minus, axis)
-                y += blocks[(s, s)] @ X[e] + blocks[(s, 1 - s)] @ X[nb]
+                if transpose:
+                    y += blocks[(s, s)].T @ X[e] + blocks[(1 - s, s)].T @ X[nb]
+                else:
+                    y += blocks[(s, s)] @ X[e] + blocks[(s, 1 - s)] @ X[nb]
             out[r] = y
         return out

@@ -1,0 +1,282 @@
+"""ctypes binding of libunfitted (argument marshalling only; every step of the operator runs in
+the library).  Names follow the C ABI of include/unfitted.h.
+
+PyTorch supplies device memory and streams: vmult takes torch CUDA tensors and passes their data
+pointers and the current (or given) stream to the library.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+UF_OK, UF_EINVAL, UF_ENOMEM, UF_ECUDA, UF_EUNSUPPORTED, UF_EGEOMETRY, UF_ENODEVICE = range(7)
+UF_FP64, UF_FP32 = 1, 2
+UF_LS_SPHERE = 0
+
+_STATUS = {0: "UF_OK", 1: "UF_EINVAL", 2: "UF_ENOMEM", 3: "UF_ECUDA", 4: "UF_EUNSUPPORTED",
+           5: "UF_EGEOMETRY", 6: "UF_ENODEVICE"}
+
+
+class UnfittedError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class uf_params(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int),
+        ("degree", ctypes.c_int),
+        ("n_cells", ctypes.c_int * 3),
+        ("lo", ctypes.c_double * 3),
+        ("hi", ctypes.c_double * 3),
+        ("ls_kind", ctypes.c_int),
+        ("ls_center", ctypes.c_double * 3),
+        ("ls_radius", ctypes.c_double),
+        ("quad_order", ctypes.c_int),
+        ("sipg_gamma", ctypes.c_double),
+        ("nitsche_gamma", ctypes.c_double),
+        ("gp_max_order", ctypes.c_int),
+        ("gp_gamma", ctypes.c_double),
+        ("precisions", ctypes.c_int),
+        ("device", ctypes.c_int),
+        ("kappa", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+class uf_info(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in (
+        "n_active", "n_inside", "n_cut", "n_dofs", "n_faces", "n_faces_full", "n_faces_cut",
+        "n_faces_empty", "n_faces_gp", "n_vol_points", "n_surf_points", "n_face_points")] + [
+        ("dim", ctypes.c_int32), ("degree", ctypes.c_int32), ("dofs_per_cell", ctypes.c_int32),
+        ("quad_order", ctypes.c_int32), ("h", ctypes.c_double), ("bytes_fp64", ctypes.c_double),
+        ("bytes_fp32", ctypes.c_double), ("flops", ctypes.c_double),
+        ("kernel_bytes_fp64", ctypes.c_double * 2), ("kernel_bytes_fp32", ctypes.c_double * 2),
+        ("kernel_flops", ctypes.c_double * 2)]
+
+
+class uf_kernel_times(ctypes.Structure):
+    _fields_ = [("ms_total", ctypes.c_double * 8), ("launches", ctypes.c_int64 * 8)]
+
+
+EXPORTED = ["uf_create_unfitted_operator", "uf_get_info", "uf_vmult", "uf_vmult_adjoint",
+            "uf_vmult_host", "uf_vmult_adjoint_host", "uf_profile_begin", "uf_profile_end",
+            "uf_set_kappa", "uf_export_cells", "uf_export_cut_cell_rule",
+            "uf_export_cut_face_rule", "uf_destroy", "uf_last_error"]
+
+_lib = None
+
+
+def load_library(path=None):
+    """Load libunfitted.so (building it first if it is missing or stale).  Raises if the
+    library cannot be built or loaded: there is no fallback implementation."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if path is None:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libunfitted not found at {path}")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    lib.uf_create_unfitted_operator.argtypes = [ctypes.POINTER(uf_params), ctypes.POINTER(P)]
+    lib.uf_get_info.argtypes = [P, ctypes.POINTER(uf_info)]
+    lib.uf_vmult.argtypes = [P, ctypes.c_int, P, P, P]
+    lib.uf_vmult_adjoint.argtypes = [P, ctypes.c_int, P, P, P]
+    lib.uf_vmult_host.argtypes = [P, ctypes.c_int, P, P, P]
+    lib.uf_vmult_adjoint_host.argtypes = [P, ctypes.c_int, P, P, P]
+    lib.uf_profile_begin.argtypes = [P, ctypes.c_int]
+    lib.uf_profile_end.argtypes = [P, ctypes.POINTER(uf_kernel_times)]
+    lib.uf_set_kappa.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
+    lib.uf_export_cells.argtypes = [P, P, P]
+    lib.uf_export_cut_cell_rule.argtypes = [P, ctypes.c_int64, ctypes.c_int, P, P, P,
+                                            ctypes.POINTER(ctypes.c_int64)]
+    lib.uf_export_cut_face_rule.argtypes = [P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, P, P,
+                                            ctypes.POINTER(ctypes.c_int64)]
+    lib.uf_destroy.argtypes = [P]
+    lib.uf_last_error.restype = ctypes.c_char_p
+    for name in EXPORTED:
+        if name != "uf_last_error":
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(st):
+    if st != UF_OK:
+        raise UnfittedError(st, _lib.uf_last_error().decode())
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def make_params(cfg, precisions=UF_FP64 | UF_FP32, device=0, kappa=None):
+    p = uf_params()
+    p.dim = int(cfg["dim"])
+    p.degree = int(cfg["degree"])
+    for a in range(3):
+        p.n_cells[a] = int(cfg["n_cells"][a]) if a < len(cfg["n_cells"]) else 1
+        p.lo[a] = float(cfg["lo"][a]) if a < len(cfg["lo"]) else 0.0
+        p.hi[a] = float(cfg["hi"][a]) if a < len(cfg["hi"]) else 0.0
+        p.ls_center[a] = float(cfg["center"][a]) if a < len(cfg["center"]) else 0.0
+    p.ls_kind = UF_LS_SPHERE
+    p.ls_radius = float(cfg["radius"])
+    p.quad_order = int(cfg["quad_order"])
+    p.sipg_gamma = float(cfg["sipg_gamma"])
+    p.nitsche_gamma = float(cfg["nitsche_gamma"])
+    p.gp_max_order = int(cfg["gp_max_order"])
+    p.gp_gamma = float(cfg["gp_gamma"])
+    p.precisions = int(precisions)
+    p.device = int(device)
+    p.kappa = None
+    return p
+
+
+class UnfittedOperator:
+    """Owner of one uf_operator.  device = -1 builds the host setup only (no GPU)."""
+
+    def __init__(self, cfg, precisions=UF_FP64 | UF_FP32, device=0, kappa=None):
+        lib = load_library()
+        self._keep = None
+        params = make_params(cfg, precisions, device)
+        if kappa is not None:
+            self._keep = np.ascontiguousarray(kappa, dtype=np.float64)
+            params.kappa = self._keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        handle = ctypes.c_void_p()
+        _check(lib.uf_create_unfitted_operator(ctypes.byref(params), ctypes.byref(handle)))
+        self._h = handle
+        self.device = device
+        self.precisions = precisions
+        self.info = self.get_info()
+        if kappa is not None and len(self._keep) != self.info["n_active"]:
+            self.close()
+            raise ValueError("kappa must have one entry per active cell")
+
+    # ---- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.uf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- queries
+    def get_info(self):
+        inf = uf_info()
+        _check(_lib.uf_get_info(self._h, ctypes.byref(inf)))
+        out = {}
+        for name, _ in uf_info._fields_:
+            v = getattr(inf, name)
+            out[name] = list(v) if isinstance(v, ctypes.Array) else v
+        return out
+
+    @property
+    def n_dofs(self):
+        return self.info["n_dofs"]
+
+    # ---- operator application (device tensors)
+    @staticmethod
+    def _stream_ptr(stream):
+        import torch
+
+        s = stream if stream is not None else torch.cuda.current_stream()
+        return ctypes.c_void_p(s.cuda_stream)
+
+    def _apply(self, fn, x, y, stream):
+        import torch
+
+        if not (x.is_cuda and x.is_contiguous() and x.numel() == self.n_dofs):
+            raise ValueError("x must be a contiguous CUDA tensor with n_dofs entries")
+        prec = {torch.float64: UF_FP64, torch.float32: UF_FP32}.get(x.dtype)
+        if prec is None:
+            raise ValueError("x must be float64 or float32")
+        if y is None:
+            y = torch.empty_like(x)
+        elif not (y.is_cuda and y.is_contiguous() and y.dtype == x.dtype and y.numel() == self.n_dofs):
+            raise ValueError("y must match x")
+        _check(fn(self._h, prec, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                  self._stream_ptr(stream)))
+        return y
+
+    def vmult(self, x, y=None, stream=None):
+        """y = A x on the device (stream-ordered)."""
+        return self._apply(_lib.uf_vmult, x, y, stream)
+
+    def vmult_adjoint(self, g, y=None, stream=None):
+        """y = A^T g on the device (stream-ordered)."""
+        return self._apply(_lib.uf_vmult_adjoint, g, y, stream)
+
+    def vmult_host(self, x, y=None, stream=None):
+        """y = A x with host numpy buffers (copies inside; synchronous)."""
+        x = np.ascontiguousarray(x)
+        prec = {np.dtype(np.float64): UF_FP64, np.dtype(np.float32): UF_FP32}[x.dtype]
+        if y is None:
+            y = np.empty_like(x)
+        st = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+        _check(_lib.uf_vmult_host(self._h, prec, _ptr(y), _ptr(x), st))
+        return y
+
+    def vmult_host_ptr(self, precision, y_ptr, x_ptr, stream_ptr, adjoint=False):
+        """uf_vmult_host / uf_vmult_adjoint_host on raw host pointers (pinned torch tensors)."""
+        fn = _lib.uf_vmult_adjoint_host if adjoint else _lib.uf_vmult_host
+        _check(fn(self._h, precision, ctypes.c_void_p(y_ptr), ctypes.c_void_p(x_ptr),
+                  ctypes.c_void_p(stream_ptr)))
+
+    def profile_begin(self, capacity):
+        """Bracket the next `capacity` operator applications' kernels with CUDA events."""
+        _check(_lib.uf_profile_begin(self._h, int(capacity)))
+
+    def profile_end(self):
+        """{(precision, kernel, direction): (total ms, launches)} of the profiled kernels."""
+        t = uf_kernel_times()
+        _check(_lib.uf_profile_end(self._h, ctypes.byref(t)))
+        out = {}
+        for pi, prec in enumerate(("fp64", "fp32")):
+            for ki, kern in enumerate(("struct", "cut")):
+                for di, dirn in enumerate(("vmult", "adjoint")):
+                    k = pi * 4 + ki * 2 + di
+                    if t.launches[k]:
+                        out[(prec, kern, dirn)] = (t.ms_total[k], t.launches[k])
+        return out
+
+    def set_kappa(self, kappa):
+        k = np.ascontiguousarray(kappa, dtype=np.float64)
+        if k.shape != (self.info["n_active"],):
+            raise ValueError("kappa must have one entry per active cell")
+        _check(_lib.uf_set_kappa(self._h, k.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+    # ---- exports of the setup product
+    def export_cells(self):
+        na = self.info["n_active"]
+        t = np.zeros(na, dtype=np.int32)
+        idx = np.zeros(na * 3, dtype=np.int32)
+        _check(_lib.uf_export_cells(self._h, _ptr(t), _ptr(idx)))
+        return t, idx.reshape(na, 3)
+
+    def export_cut_cell_rule(self, c, kind):
+        cnt = ctypes.c_int64()
+        _check(_lib.uf_export_cut_cell_rule(self._h, c, kind, None, None, None, ctypes.byref(cnt)))
+        d = self.info["dim"]
+        xi = np.zeros((cnt.value, d))
+        w = np.zeros(cnt.value)
+        nrm = np.zeros((cnt.value, d))
+        _check(_lib.uf_export_cut_cell_rule(self._h, c, kind, _ptr(xi), _ptr(w), _ptr(nrm),
+                                            ctypes.byref(cnt)))
+        return (xi, w, nrm) if kind == 1 else (xi, w)
+
+    def export_cut_face_rule(self, e, axis, side):
+        cnt = ctypes.c_int64()
+        _check(_lib.uf_export_cut_face_rule(self._h, e, axis, side, None, None, ctypes.byref(cnt)))
+        d = self.info["dim"]
+        eta = np.zeros((cnt.value, d - 1))
+        w = np.zeros(cnt.value)
+        _check(_lib.uf_export_cut_face_rule(self._h, e, axis, side, _ptr(eta), _ptr(w),
+                                            ctypes.byref(cnt)))
+        return eta, w

@@ -1,0 +1,620 @@
+// C ABI of libunfitted: creation (host setup + device upload), vmult / adjoint dispatch,
+// host-buffer vmult, exports.  Declarations and contracts: include/unfitted.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/unfitted.h"
+#include "uf_device.h"
+#include "uf_host.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+uf_status fail(uf_status st, const std::string &msg) {
+  g_last_error = msg;
+  return st;
+}
+
+template <typename T>
+struct PrecisionData {
+  bool present = false;
+  void *base = nullptr;        // one device allocation for all arrays of this precision
+  void *xbuf = nullptr;        // device staging buffers of uf_vmult_host
+  void *ybuf = nullptr;
+  T *kappa_dev = nullptr;
+  uf::DevArrays<T> arrays{};
+  std::vector<unsigned char> struct_tables;  // uf::StructTables<T, n>
+  std::vector<unsigned char> point_tables;   // uf::PointTables<T, n>
+  uf::Scalars<T> scalars{};
+};
+
+// Bump allocator over a byte count (256-byte aligned sub-arrays).
+struct Layout {
+  size_t bytes = 0;
+  size_t take(size_t n) {
+    size_t off = bytes;
+    bytes += (n + 255) / 256 * 256;
+    return off;
+  }
+};
+
+}  // namespace
+
+struct ProfSlot {
+  cudaEvent_t ev[4];
+  int prec;     // 0 FP64, 1 FP32
+  int adjoint;  // 0 vmult, 1 adjoint
+  bool used;
+};
+
+struct uf_operator {
+  uf::HostOperator host;
+  int device = -1;
+  int num_sms = 0;
+  PrecisionData<double> f64;
+  PrecisionData<float> f32;
+  std::vector<ProfSlot> prof;  // non-empty while profiling
+  size_t prof_next = 0;
+};
+
+namespace {
+
+// ------------------------------------------------------------------------------------------
+// Constant 1D matrices of the structured terms (see uf_device.h for their meaning).
+// ------------------------------------------------------------------------------------------
+void structured_matrices(const uf::HostOperator &op, std::vector<double> &out) {
+  const int n = op.n, nn = n * n, d = op.dim;
+  const uf::Tables1D &t = op.t;
+  const double h = op.h;
+  const double hf = std::pow(h, d - 1);
+  const double sig = op.params.sipg_gamma / h;
+  out.assign(16 * nn, 0.0);
+  double *kv = &out[0], *mass = &out[nn];
+  const double hv = std::pow(h, d - 2);
+  for (int i = 0; i < nn; ++i) {
+    kv[i] = hv * t.stiff[i];
+    mass[i] = t.mass[i];
+  }
+  double gam[uf::kMaxN] = {0};
+  for (int j = 1; j <= op.params.gp_max_order; ++j) {
+    double fact = 1.0;
+    for (int k = 2; k <= j; ++k) fact *= k;
+    gam[j] = op.params.gp_gamma * std::pow(h, 2 * j - 1) / (fact * fact);
+  }
+  for (int s = 0; s < 2; ++s) {
+    const double sgn = s ? 1.0 : -1.0;  // outward normal of the own face along the axis
+    double e_own[uf::kMaxN], d_own[uf::kMaxN], e_nb[uf::kMaxN], d_nb[uf::kMaxN];
+    double t_own[uf::kMaxN][uf::kMaxN], t_nb[uf::kMaxN][uf::kMaxN];  // [j][i]
+    for (int i = 0; i < n; ++i) {
+      e_own[i] = t.deriv_end[s][0][i];
+      e_nb[i] = t.deriv_end[1 - s][0][i];
+      d_own[i] = sgn * t.deriv_end[s][1][i] / h;
+      d_nb[i] = sgn * t.deriv_end[1 - s][1][i] / h;
+      double sj = 1.0, hj = 1.0;
+      for (int j = 1; j <= op.p; ++j) {
+        sj *= sgn;
+        hj *= h;
+        t_own[j][i] = sj * t.deriv_end[s][j][i] / hj;
+        t_nb[j][i] = sj * t.deriv_end[1 - s][j][i] / hj;
+      }
+    }
+    double *A = &out[(2 + s) * nn], *P = &out[(4 + s) * nn], *G = &out[(6 + s) * nn];
+    double *B = &out[(8 + s) * nn], *C = &out[(10 + s) * nn], *Q = &out[(12 + s) * nn];
+    double *H = &out[(14 + s) * nn];
+    for (int r = 0; r < n; ++r)
+      for (int m = 0; m < n; ++m) {
+        const int k = r * n + m;
+        A[k] = hf * -0.5 * (d_own[r] * e_own[m] + e_own[r] * d_own[m]);
+        P[k] = hf * sig * e_own[r] * e_own[m];
+        B[k] = hf * 0.5 * d_own[r] * e_nb[m];
+        C[k] = hf * -0.5 * e_own[r] * d_nb[m];
+        Q[k] = hf * -sig * e_own[r] * e_nb[m];
+        double g = 0.0, hh = 0.0;
+        for (int j = 1; j <= op.params.gp_max_order; ++j) {
+          g += gam[j] * t_own[j][r] * t_own[j][m];
+          hh += gam[j] * t_own[j][r] * t_nb[j][m];
+        }
+        G[k] = hf * g;
+        H[k] = -hf * hh;
+      }
+  }
+}
+
+template <typename T>
+uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
+  const uf::HostOperator &H = op->host;
+  const int d = H.dim, nf = 2 * d, n = H.n;
+  const int64_t na = H.n_active, nc = H.n_cut;
+  const int64_t nv = (int64_t)H.vol_w.size(), ns = (int64_t)H.surf_w.size();
+  const int64_t nfp = (int64_t)H.cface_w.size();
+  if (nv > INT32_MAX || ns > INT32_MAX || nfp > INT32_MAX)
+    return fail(UF_EUNSUPPORTED, "too many quadrature points for 32-bit offsets");
+
+  // cut cells ordered by decreasing work (points of volume, surface and cut faces)
+  std::vector<int32_t> order(nc);
+  std::iota(order.begin(), order.end(), 0);
+  std::vector<int64_t> cost(nc);
+  for (int64_t c = 0; c < nc; ++c)
+    cost[c] = (H.vol_off[c + 1] - H.vol_off[c]) + (H.surf_off[c + 1] - H.surf_off[c]) +
+              (H.cface_off[(c + 1) * nf] - H.cface_off[c * nf]);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
+  std::vector<int32_t> cut_list(nc), cut_idx(nc);
+  for (int64_t i = 0; i < nc; ++i) {
+    cut_idx[i] = order[i];
+    cut_list[i] = H.cut_cells[order[i]];
+  }
+
+  Layout L;
+  const size_t o_nbr = L.take(sizeof(int32_t) * na * nf);
+  const size_t o_flags = L.take(sizeof(uint32_t) * na);
+  const size_t o_kappa = L.take(sizeof(T) * na);
+  const size_t o_clist = L.take(sizeof(int32_t) * std::max<int64_t>(nc, 1));
+  const size_t o_cidx = L.take(sizeof(int32_t) * std::max<int64_t>(nc, 1));
+  const size_t o_voff = L.take(sizeof(int32_t) * (nc + 1));
+  const size_t o_soff = L.take(sizeof(int32_t) * (nc + 1));
+  const size_t o_foff = L.take(sizeof(int32_t) * (nc * nf + 1));
+  size_t o_vxi[3], o_sxi[3], o_sn[3], o_feta[2];
+  for (int a = 0; a < d; ++a) o_vxi[a] = L.take(sizeof(T) * std::max<int64_t>(nv, 1));
+  const size_t o_vw = L.take(sizeof(T) * std::max<int64_t>(nv, 1));
+  for (int a = 0; a < d; ++a) o_sxi[a] = L.take(sizeof(T) * std::max<int64_t>(ns, 1));
+  const size_t o_sw = L.take(sizeof(T) * std::max<int64_t>(ns, 1));
+  for (int a = 0; a < d; ++a) o_sn[a] = L.take(sizeof(T) * std::max<int64_t>(ns, 1));
+  for (int a = 0; a < d - 1; ++a) o_feta[a] = L.take(sizeof(T) * std::max<int64_t>(nfp, 1));
+  const size_t o_fw = L.take(sizeof(T) * std::max<int64_t>(nfp, 1));
+
+  std::vector<unsigned char> img(L.bytes, 0);
+  auto put = [&](size_t off, const void *src, size_t bytes) {
+    if (bytes) std::memcpy(img.data() + off, src, bytes);
+  };
+  auto put_t = [&](size_t off, const std::vector<double> &v) {
+    T *dst = reinterpret_cast<T *>(img.data() + off);
+    for (size_t i = 0; i < v.size(); ++i) dst[i] = (T)v[i];
+  };
+  auto put_off = [&](size_t off, const std::vector<int64_t> &v) {
+    int32_t *dst = reinterpret_cast<int32_t *>(img.data() + off);
+    for (size_t i = 0; i < v.size(); ++i) dst[i] = (int32_t)v[i];
+  };
+  put(o_nbr, H.nbr.data(), sizeof(int32_t) * na * nf);
+  put(o_flags, H.flags.data(), sizeof(uint32_t) * na);
+  put_t(o_kappa, H.kappa);
+  put(o_clist, cut_list.data(), sizeof(int32_t) * nc);
+  put(o_cidx, cut_idx.data(), sizeof(int32_t) * nc);
+  put_off(o_voff, H.vol_off);
+  put_off(o_soff, H.surf_off);
+  put_off(o_foff, H.cface_off);
+  for (int a = 0; a < d; ++a) {
+    put_t(o_vxi[a], H.vol_xi[a]);
+    put_t(o_sxi[a], H.surf_xi[a]);
+    put_t(o_sn[a], H.surf_n[a]);
+  }
+  put_t(o_vw, H.vol_w);
+  put_t(o_sw, H.surf_w);
+  for (int a = 0; a < d - 1; ++a) put_t(o_feta[a], H.cface_eta[a]);
+  put_t(o_fw, H.cface_w);
+
+  cudaError_t err = cudaMalloc(&pd.base, L.bytes);
+  if (err != cudaSuccess) return fail(UF_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(err));
+  const size_t vec_bytes = sizeof(T) * (size_t)H.n_active * H.ndof;
+  err = cudaMalloc(&pd.xbuf, vec_bytes);
+  if (err == cudaSuccess) err = cudaMalloc(&pd.ybuf, vec_bytes);
+  if (err != cudaSuccess) return fail(UF_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(err));
+  err = cudaMemcpy(pd.base, img.data(), L.bytes, cudaMemcpyHostToDevice);
+  if (err != cudaSuccess) return fail(UF_ECUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(err));
+
+  unsigned char *b = static_cast<unsigned char *>(pd.base);
+  uf::DevArrays<T> &A = pd.arrays;
+  A.nbr = reinterpret_cast<const int32_t *>(b + o_nbr);
+  A.flags = reinterpret_cast<const uint32_t *>(b + o_flags);
+  pd.kappa_dev = reinterpret_cast<T *>(b + o_kappa);
+  A.kappa = pd.kappa_dev;
+  A.cut_list = reinterpret_cast<const int32_t *>(b + o_clist);
+  A.cut_idx = reinterpret_cast<const int32_t *>(b + o_cidx);
+  A.vol_off = reinterpret_cast<const int32_t *>(b + o_voff);
+  A.surf_off = reinterpret_cast<const int32_t *>(b + o_soff);
+  A.cface_off = reinterpret_cast<const int32_t *>(b + o_foff);
+  for (int a = 0; a < 3; ++a) {
+    A.vol_xi[a] = (a < d) ? reinterpret_cast<const T *>(b + o_vxi[a]) : nullptr;
+    A.surf_xi[a] = (a < d) ? reinterpret_cast<const T *>(b + o_sxi[a]) : nullptr;
+    A.surf_n[a] = (a < d) ? reinterpret_cast<const T *>(b + o_sn[a]) : nullptr;
+  }
+  A.vol_w = reinterpret_cast<const T *>(b + o_vw);
+  A.surf_w = reinterpret_cast<const T *>(b + o_sw);
+  for (int a = 0; a < 2; ++a)
+    A.cface_eta[a] = (a < d - 1) ? reinterpret_cast<const T *>(b + o_feta[a]) : nullptr;
+  A.cface_w = reinterpret_cast<const T *>(b + o_fw);
+  A.n_active = (int32_t)na;
+  A.n_cut = (int32_t)nc;
+
+  // constant tables
+  std::vector<double> mats;
+  structured_matrices(H, mats);
+  pd.struct_tables.assign(sizeof(T) * mats.size(), 0);
+  T *st = reinterpret_cast<T *>(pd.struct_tables.data());
+  for (size_t i = 0; i < mats.size(); ++i) st[i] = (T)mats[i];
+  pd.point_tables.assign(sizeof(T) * 6 * n, 0);
+  T *ptab = reinterpret_cast<T *>(pd.point_tables.data());
+  for (int i = 0; i < n; ++i) {
+    ptab[i] = (T)H.t.z[i];
+    ptab[n + i] = (T)H.t.den_inv[i];
+    ptab[2 * n + i] = (T)H.t.deriv_end[0][0][i];
+    ptab[3 * n + i] = (T)H.t.deriv_end[1][0][i];
+    ptab[4 * n + i] = (T)H.t.deriv_end[0][1][i];
+    ptab[5 * n + i] = (T)H.t.deriv_end[1][1][i];
+  }
+  pd.scalars.h = (T)H.h;
+  pd.scalars.inv_h = (T)(1.0 / H.h);
+  pd.scalars.inv_h2 = (T)(1.0 / (H.h * H.h));
+  pd.scalars.sipg_over_h = (T)(H.params.sipg_gamma / H.h);
+  pd.scalars.nitsche_over_h = (T)(H.params.nitsche_gamma / H.h);
+  pd.present = true;
+  return UF_OK;
+}
+
+template <typename T>
+void release(PrecisionData<T> &pd) {
+  if (pd.base) cudaFree(pd.base);
+  if (pd.xbuf) cudaFree(pd.xbuf);
+  if (pd.ybuf) cudaFree(pd.ybuf);
+  pd.base = pd.xbuf = pd.ybuf = nullptr;
+  pd.present = false;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+      changed = (cudaSetDevice(dev) == cudaSuccess);
+    }
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+};
+
+template <typename T>
+uf_status vmult_t(uf_operator *op, PrecisionData<T> &pd, void *y, const void *x, void *stream,
+                  bool adjoint) {
+  if (!pd.present) return fail(UF_EINVAL, "operator was not created with this precision");
+  const size_t bytes = sizeof(T) * (size_t)op->host.n_active * op->host.ndof;
+  const char *xb = static_cast<const char *>(x);
+  const char *yb = static_cast<const char *>(y);
+  if (xb < yb + bytes && yb < xb + bytes) return fail(UF_EINVAL, "x and y overlap");
+  DeviceGuard guard(op->device);
+  void *const *ev = nullptr;
+  if (op->prof_next < op->prof.size()) {
+    ProfSlot &slot = op->prof[op->prof_next++];
+    slot.prec = sizeof(T) == 8 ? 0 : 1;
+    slot.adjoint = adjoint ? 1 : 0;
+    slot.used = true;
+    ev = reinterpret_cast<void *const *>(slot.ev);
+  }
+  int err = uf::launch_vmult<T>(op->host.dim, op->host.n, pd.arrays, pd.struct_tables.data(),
+                                pd.point_tables.data(), pd.scalars, static_cast<T *>(y),
+                                static_cast<const T *>(x), adjoint, stream, ev);
+  if (err != 0)
+    return fail(UF_ECUDA, std::string("kernel launch: ") + cudaGetErrorString((cudaError_t)err));
+  return UF_OK;
+}
+
+uf_status check_vmult_args(uf_operator *op, int precision, void *y, const void *x) {
+  if (!op || !y || !x) return fail(UF_EINVAL, "NULL argument");
+  if (op->device < 0) return fail(UF_ENODEVICE, "operator was created host-only");
+  if (precision != UF_FP64 && precision != UF_FP32) return fail(UF_EINVAL, "bad precision");
+  return UF_OK;
+}
+
+uf_status vmult_dispatch(uf_operator *op, int precision, void *y, const void *x, void *stream,
+                         bool adjoint) {
+  uf_status st = check_vmult_args(op, precision, y, x);
+  if (st != UF_OK) return st;
+  if (precision == UF_FP64) return vmult_t<double>(op, op->f64, y, x, stream, adjoint);
+  return vmult_t<float>(op, op->f32, y, x, stream, adjoint);
+}
+
+}  // namespace
+
+extern "C" {
+
+uf_status uf_create_unfitted_operator(const uf_params *params, uf_operator **out) {
+  if (!params || !out) return fail(UF_EINVAL, "NULL argument");
+  *out = nullptr;
+  if ((params->precisions & ~(UF_FP64 | UF_FP32)) != 0)
+    return fail(UF_EINVAL, "precisions must be a mask of UF_FP64 | UF_FP32");
+  uf_operator *op = new (std::nothrow) uf_operator();
+  if (!op) return fail(UF_ENOMEM, "host allocation failed");
+  std::string msg;
+  uf_status st;
+  try {
+    st = uf::build_host_operator(*params, op->host, msg);
+  } catch (const std::bad_alloc &) {
+    st = UF_ENOMEM;
+    msg = "host allocation failed during setup";
+  }
+  if (st != UF_OK) {
+    delete op;
+    return fail(st, msg);
+  }
+  if (params->kappa) {
+    for (int64_t e = 0; e < op->host.n_active; ++e) {
+      if (!(params->kappa[e] > 0.0) || !std::isfinite(params->kappa[e])) {
+        delete op;
+        return fail(UF_EINVAL, "kappa must be positive and finite");
+      }
+      op->host.kappa[e] = params->kappa[e];
+    }
+  }
+  op->device = params->device;
+  if (op->device >= 0) {
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || op->device >= ndev) {
+      delete op;
+      return fail(UF_EINVAL, "CUDA device not available");
+    }
+    DeviceGuard guard(op->device);
+    cudaDeviceGetAttribute(&op->num_sms, cudaDevAttrMultiProcessorCount, op->device);
+    try {
+      if (params->precisions & UF_FP64) st = upload<double>(op, op->f64);
+      if (st == UF_OK && (params->precisions & UF_FP32)) st = upload<float>(op, op->f32);
+    } catch (const std::bad_alloc &) {
+      st = fail(UF_ENOMEM, "host allocation failed during upload");
+    }
+    if (st != UF_OK) {
+      release(op->f64);
+      release(op->f32);
+      delete op;
+      return st;
+    }
+  }
+  *out = op;
+  return UF_OK;
+}
+
+uf_status uf_get_info(const uf_operator *op, uf_info *info) {
+  if (!op || !info) return fail(UF_EINVAL, "NULL argument");
+  const uf::HostOperator &H = op->host;
+  std::memset(info, 0, sizeof(*info));
+  info->n_active = H.n_active;
+  info->n_inside = H.n_inside;
+  info->n_cut = H.n_cut;
+  info->n_dofs = H.n_active * H.ndof;
+  info->n_faces = H.n_faces;
+  info->n_faces_full = H.n_faces_full;
+  info->n_faces_cut = H.n_faces_cut;
+  info->n_faces_empty = H.n_faces_empty;
+  info->n_faces_gp = H.n_faces_gp;
+  info->n_vol_points = (int64_t)H.vol_w.size();
+  info->n_surf_points = (int64_t)H.surf_w.size();
+  info->n_face_points = H.n_face_points_unique;
+  info->dim = H.dim;
+  info->degree = H.p;
+  info->dofs_per_cell = H.ndof;
+  info->quad_order = H.q;
+  info->h = H.h;
+  const int d = H.dim, nf = 2 * d;
+  for (int s = 0; s < 2; ++s) {
+    const double S = s == 0 ? 8.0 : 4.0;
+    double b = 2.0 * S * (double)info->n_dofs;                 // read x, write y
+    b += (double)H.n_active * (4.0 * nf + 4.0 + S);             // neighbours, flags, kappa
+    b += (double)H.n_cut * (4.0 * 3 + 4.0 * nf + 8.0);          // offsets, cut list
+    b += S * ((d + 1.0) * info->n_vol_points + (2.0 * d + 1.0) * info->n_surf_points +
+              (double)d * info->n_face_points);                 // point data
+    (s == 0 ? info->bytes_fp64 : info->bytes_fp32) = b;
+  }
+  // Per-kernel algorithmic bytes: the structured kernel reads x of every cell once (neighbour
+  // lines are L2 hits) and writes y once, plus neighbours / flags / kappa; the cut-cell kernel
+  // reads x of the cut cells and of their cut-face neighbours, reads and writes their y rows,
+  // and reads the point data and offsets once.
+  for (int s = 0; s < 2; ++s) {
+    const double S = s == 0 ? 8.0 : 4.0;
+    double *kb = s == 0 ? info->kernel_bytes_fp64 : info->kernel_bytes_fp32;
+    kb[0] = 2.0 * S * (double)info->n_dofs + (double)H.n_active * (4.0 * nf + 4.0 + S);
+    kb[1] = 3.0 * S * (double)H.n_cut * H.ndof + (double)H.n_cut * (4.0 * 3 + 4.0 * nf + 8.0 + S) +
+            S * ((d + 1.0) * info->n_vol_points + (2.0 * d + 1.0) * info->n_surf_points +
+                 (double)d * info->n_face_points);
+  }
+  // FMA counts of the kernels as built (x2 for flops).
+  const double n = H.n, nd = H.ndof, nline = nd / n;
+  double fma = 0.0;
+  int64_t nb_faces = 0;
+  for (int64_t e = 0; e < H.n_active; ++e)
+    for (int f = 0; f < nf; ++f) {
+      const uint32_t fl = H.flags[e];
+      if (fl & (uf::face_bit_sipg_full(f) | uf::face_bit_gp(f))) ++nb_faces;
+    }
+  fma += (double)H.n_active * d * (nline * n * n) * d;  // L along the axis + (d - 1) mass sweeps
+  fma += (double)nb_faces * nline * n * n;              // neighbour couplings
+  const double fma_struct = fma;
+  const double pt_eval = (d == 3) ? 2 * n * n * n + 3 * n * n + 4 * n : 2 * n * n + 3 * n;
+  const double pt_basis = d * 6.0 * n;
+  const double pt_integrate = nd * (d == 3 ? 6.0 : 4.0);
+  fma += (double)(info->n_vol_points + info->n_surf_points) * (pt_eval + pt_basis + pt_integrate);
+  const double fp = 2.0 * (double)info->n_face_points;  // both sides
+  fma += fp * (4.0 * (nline + (d == 3 ? n : 0)) + 2.0 * nline + (d - 1) * 6.0 * n);
+  fma += 2.0 * (double)H.n_faces_cut * (4.0 * nd + 2.0 * nd);  // traces and expansion
+  info->flops = 2.0 * fma;
+  info->kernel_flops[0] = 2.0 * fma_struct;
+  info->kernel_flops[1] = 2.0 * (fma - fma_struct);
+  return UF_OK;
+}
+
+uf_status uf_vmult(uf_operator *op, int precision, void *y, const void *x, void *stream) {
+  return vmult_dispatch(op, precision, y, x, stream, false);
+}
+
+uf_status uf_vmult_adjoint(uf_operator *op, int precision, void *y, const void *g, void *stream) {
+  return vmult_dispatch(op, precision, y, g, stream, true);
+}
+
+static uf_status vmult_host_impl(uf_operator *op, int precision, void *y_host,
+                                 const void *x_host, void *stream, bool adjoint) {
+  uf_status st = check_vmult_args(op, precision, y_host, x_host);
+  if (st != UF_OK) return st;
+  DeviceGuard guard(op->device);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const size_t elem = precision == UF_FP64 ? sizeof(double) : sizeof(float);
+  const size_t bytes = elem * (size_t)op->host.n_active * op->host.ndof;
+  void *xb = precision == UF_FP64 ? op->f64.xbuf : op->f32.xbuf;
+  void *yb = precision == UF_FP64 ? op->f64.ybuf : op->f32.ybuf;
+  if (!xb || !yb) return fail(UF_EINVAL, "operator was not created with this precision");
+  cudaError_t err = cudaMemcpyAsync(xb, x_host, bytes, cudaMemcpyHostToDevice, s);
+  if (err != cudaSuccess) return fail(UF_ECUDA, std::string("H2D copy: ") + cudaGetErrorString(err));
+  st = vmult_dispatch(op, precision, yb, xb, stream, adjoint);
+  if (st != UF_OK) return st;
+  err = cudaMemcpyAsync(y_host, yb, bytes, cudaMemcpyDeviceToHost, s);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  if (err != cudaSuccess) return fail(UF_ECUDA, std::string("D2H copy: ") + cudaGetErrorString(err));
+  return UF_OK;
+}
+
+uf_status uf_vmult_host(uf_operator *op, int precision, void *y_host, const void *x_host,
+                        void *stream) {
+  return vmult_host_impl(op, precision, y_host, x_host, stream, false);
+}
+
+uf_status uf_vmult_adjoint_host(uf_operator *op, int precision, void *y_host, const void *g_host,
+                                void *stream) {
+  return vmult_host_impl(op, precision, y_host, g_host, stream, true);
+}
+
+uf_status uf_profile_begin(uf_operator *op, int capacity) {
+  if (!op || capacity < 1) return fail(UF_EINVAL, "NULL operator or capacity < 1");
+  if (op->device < 0) return fail(UF_ENODEVICE, "operator was created host-only");
+  if (!op->prof.empty()) return fail(UF_EINVAL, "profiling already active");
+  DeviceGuard guard(op->device);
+  op->prof.resize(capacity);
+  for (ProfSlot &slot : op->prof) {
+    slot.used = false;
+    for (int k = 0; k < 4; ++k) {
+      cudaError_t err = cudaEventCreate(&slot.ev[k]);
+      if (err != cudaSuccess) {
+        op->prof.clear();
+        return fail(UF_ECUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(err));
+      }
+    }
+  }
+  op->prof_next = 0;
+  return UF_OK;
+}
+
+uf_status uf_profile_end(uf_operator *op, uf_kernel_times *out) {
+  if (!op || !out) return fail(UF_EINVAL, "NULL argument");
+  if (op->prof.empty()) return fail(UF_EINVAL, "profiling not active");
+  DeviceGuard guard(op->device);
+  std::memset(out, 0, sizeof(*out));
+  cudaError_t first_err = cudaSuccess;
+  for (ProfSlot &slot : op->prof) {
+    if (slot.used) {
+      for (int kern = 0; kern < 2; ++kern) {
+        float ms = 0.f;
+        cudaError_t err = cudaEventSynchronize(slot.ev[2 * kern + 1]);
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, slot.ev[2 * kern], slot.ev[2 * kern + 1]);
+        if (err != cudaSuccess && first_err == cudaSuccess) first_err = err;
+        out->ms_total[slot.prec][kern][slot.adjoint] += ms;
+        out->launches[slot.prec][kern][slot.adjoint] += 1;
+      }
+    }
+    for (int k = 0; k < 4; ++k) cudaEventDestroy(slot.ev[k]);
+  }
+  op->prof.clear();
+  op->prof_next = 0;
+  if (first_err != cudaSuccess) return fail(UF_ECUDA, cudaGetErrorString(first_err));
+  return UF_OK;
+}
+
+uf_status uf_set_kappa(uf_operator *op, const double *kappa_host) {
+  if (!op || !kappa_host) return fail(UF_EINVAL, "NULL argument");
+  for (int64_t e = 0; e < op->host.n_active; ++e)
+    if (!(kappa_host[e] > 0.0) || !std::isfinite(kappa_host[e]))
+      return fail(UF_EINVAL, "kappa must be positive and finite");
+  std::copy(kappa_host, kappa_host + op->host.n_active, op->host.kappa.begin());
+  if (op->device < 0) return UF_OK;
+  DeviceGuard guard(op->device);
+  const int64_t na = op->host.n_active;
+  if (op->f64.present) {
+    cudaError_t err = cudaMemcpy(op->f64.kappa_dev, kappa_host, sizeof(double) * na, cudaMemcpyHostToDevice);
+    if (err != cudaSuccess) return fail(UF_ECUDA, cudaGetErrorString(err));
+  }
+  if (op->f32.present) {
+    std::vector<float> k32(kappa_host, kappa_host + na);
+    cudaError_t err = cudaMemcpy(op->f32.kappa_dev, k32.data(), sizeof(float) * na, cudaMemcpyHostToDevice);
+    if (err != cudaSuccess) return fail(UF_ECUDA, cudaGetErrorString(err));
+  }
+  return UF_OK;
+}
+
+uf_status uf_export_cells(const uf_operator *op, int32_t *type, int32_t *index) {
+  if (!op) return fail(UF_EINVAL, "NULL argument");
+  const uf::HostOperator &H = op->host;
+  for (int64_t e = 0; e < H.n_active; ++e) {
+    if (type) type[e] = H.act_type[e];
+    if (index)
+      for (int a = 0; a < 3; ++a) index[e * 3 + a] = H.act_index[e * 3 + a];
+  }
+  return UF_OK;
+}
+
+uf_status uf_export_cut_cell_rule(const uf_operator *op, int64_t c, int kind, double *xi,
+                                  double *w, double *normal, int64_t *count) {
+  if (!op || !count) return fail(UF_EINVAL, "NULL argument");
+  const uf::HostOperator &H = op->host;
+  if (c < 0 || c >= H.n_cut || (kind != 0 && kind != 1)) return fail(UF_EINVAL, "index out of range");
+  const std::vector<int64_t> &off = kind == 0 ? H.vol_off : H.surf_off;
+  const int64_t b = off[c], e = off[c + 1];
+  *count = e - b;
+  if (!xi) return UF_OK;
+  const int d = H.dim;
+  for (int64_t i = b; i < e; ++i) {
+    for (int a = 0; a < d; ++a) {
+      xi[(i - b) * d + a] = kind == 0 ? H.vol_xi[a][i] : H.surf_xi[a][i];
+      if (kind == 1 && normal) normal[(i - b) * d + a] = H.surf_n[a][i];
+    }
+    if (w) w[i - b] = kind == 0 ? H.vol_w[i] : H.surf_w[i];
+  }
+  return UF_OK;
+}
+
+uf_status uf_export_cut_face_rule(const uf_operator *op, int64_t e, int axis, int side,
+                                  double *eta, double *w, int64_t *count) {
+  if (!op || !count) return fail(UF_EINVAL, "NULL argument");
+  const uf::HostOperator &H = op->host;
+  if (e < 0 || e >= H.n_active || axis < 0 || axis >= H.dim || (side != 0 && side != 1))
+    return fail(UF_EINVAL, "index out of range");
+  *count = 0;
+  const int c = H.cut_of[e];
+  const int f = 2 * axis + side, nf = 2 * H.dim;
+  if (c < 0) return UF_OK;
+  const int64_t b = H.cface_off[c * nf + f], en = H.cface_off[c * nf + f + 1];
+  *count = en - b;
+  if (!eta) return UF_OK;
+  for (int64_t i = b; i < en; ++i) {
+    for (int a = 0; a < H.dim - 1; ++a) eta[(i - b) * (H.dim - 1) + a] = H.cface_eta[a][i];
+    if (w) w[i - b] = H.cface_w[i];
+  }
+  return UF_OK;
+}
+
+uf_status uf_destroy(uf_operator *op) {
+  if (!op) return UF_OK;
+  if (op->device >= 0) {
+    DeviceGuard guard(op->device);
+    for (ProfSlot &slot : op->prof)
+      for (int k = 0; k < 4; ++k) cudaEventDestroy(slot.ev[k]);
+    release(op->f64);
+    release(op->f32);
+  }
+  delete op;
+  return UF_OK;
+}
+
+const char *uf_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

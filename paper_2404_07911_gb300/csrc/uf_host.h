@@ -1,0 +1,95 @@
+// Host-side setup product of the unfitted DG operator (internal to libunfitted).
+//
+// The setup follows arXiv 2404.07911, Sec. 2.3 (quadrature classification): background cells
+// are classified as inside / cut / outside against the level set, interior faces as full / cut /
+// empty, and the cut cells and cut faces receive dimension-reduction quadrature (Saye's method,
+// cited in Sec. 1) generated once; Sec. 5.2 excludes this setup from the timed operator.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/unfitted.h"
+
+namespace uf {
+
+constexpr int kMaxDim = 3;
+constexpr int kMaxN = 9;  // degree <= 8
+
+// Per-cell flag bits.  Bit 0: the cell is cut.  For face f = 2 * axis + side (side 0 = lower):
+enum : uint32_t {
+  kCellCut = 1u,
+};
+inline uint32_t face_bit_sipg_full(int f) { return 1u << (1 + 3 * f); }
+inline uint32_t face_bit_sipg_cut(int f) { return 1u << (2 + 3 * f); }
+inline uint32_t face_bit_gp(int f) { return 1u << (3 + 3 * f); }
+
+// 1D tables (all FP64), n = p + 1 Gauss-Lobatto Lagrange polynomials on [0, 1].
+struct Tables1D {
+  int n = 0, p = 0;
+  double z[kMaxN];              // Gauss-Lobatto nodes
+  double den_inv[kMaxN];        // 1 / prod_{m != i} (z_i - z_m)
+  double gauss_x[kMaxN], gauss_w[kMaxN];
+  double mass[kMaxN * kMaxN];   // int_0^1 phi_i phi_j
+  double stiff[kMaxN * kMaxN];  // int_0^1 phi_i' phi_j'
+  // deriv_end[s][j][i] = phi_i^(j)(s), s = 0, 1, j = 0..p
+  double deriv_end[2][kMaxN][kMaxN];
+};
+
+struct Fn {  // psi(x) = |x - c|^2 - rho on an m-dimensional box
+  double c[kMaxDim];
+  double rho;
+};
+
+struct QPoint {
+  double x[kMaxDim];
+  double w;
+  double nrm[kMaxDim];
+};
+
+struct HostOperator {
+  uf_params params{};
+  int dim = 0, p = 0, n = 0, ndof = 0, q = 0;
+  int64_t N[kMaxDim] = {1, 1, 1};
+  double lo[kMaxDim] = {0, 0, 0};
+  double h = 0;
+  double center[kMaxDim] = {0, 0, 0};
+  double radius = 0;
+
+  Tables1D t;
+
+  // classification / numbering
+  int64_t n_background = 0;
+  std::vector<int32_t> id_map;    // background flat index (x fastest) -> active id, -1 outside
+  std::vector<int32_t> act_index; // [n_active * 3] multi-index of each active cell
+  std::vector<int8_t> act_type;   // 0 inside, 1 cut
+  int64_t n_active = 0, n_inside = 0, n_cut = 0;
+
+  // per active cell
+  std::vector<int32_t> nbr;       // [n_active * 2 * dim], -1 = none
+  std::vector<uint32_t> flags;    // kCellCut | face bits
+  std::vector<double> kappa;      // [n_active]
+
+  // cut cells (active order)
+  std::vector<int32_t> cut_cells; // active id of each cut cell
+  std::vector<int32_t> cut_of;    // [n_active] -> cut index or -1
+  std::vector<int64_t> vol_off, surf_off;   // [n_cut + 1]
+  std::vector<double> vol_xi[kMaxDim], vol_w;                 // reference coordinates, weights
+  std::vector<double> surf_xi[kMaxDim], surf_w, surf_n[kMaxDim];
+  // cut-face rules, stored per (cut cell, face) side: [n_cut * 2 * dim + 1]
+  std::vector<int64_t> cface_off;
+  std::vector<double> cface_eta[kMaxDim - 1], cface_w;
+
+  // counts
+  int64_t n_faces = 0, n_faces_full = 0, n_faces_cut = 0, n_faces_empty = 0, n_faces_gp = 0;
+  int64_t n_face_points_unique = 0;
+};
+
+// Builds everything above from params (no device work).  Returns UF_OK or an error with msg.
+uf_status build_host_operator(const uf_params &params, HostOperator &op, std::string &msg);
+
+// 1D tables (exposed for the device upload).
+void build_tables_1d(int p, Tables1D &t);
+
+}  // namespace uf

@@ -1,0 +1,682 @@
+// Host setup of the unfitted DG operator: 1D tables, classification, numbering, face typing and
+// dimension-reduction quadrature (arXiv 2404.07911, Sec. 2.3; Saye's method as cited in Sec. 1).
+//
+// Compiled with -ffp-contract=off so that every floating-point decision of the quadrature
+// generator (classification, one-signedness, root brackets, sign of a piece) is taken with the
+// same correctly rounded operations on every host architecture.
+//
+// Reading of the quadrature method (the paper gives no details; restated for level sets
+// psi(x) = |x - c|^2 - rho, whose roots along coordinate lines have closed forms):
+//  * volume / surface rule on a box U: inside -> tensor Gauss q^m, outside -> nothing; else the
+//    height direction k maximises |mid_k - c_k| (first index on ties); if lo_k < c_k < hi_k the
+//    box is bisected in all directions (children ordered with direction 0 fastest, depth <= 8);
+//    otherwise the outer rule is the full-box rule on U without direction k for the restrictions
+//    of psi to x_k = lo_k and x_k = hi_k, and each outer line is split at its root: pieces with
+//    psi(mid) < 0 get q Gauss points, the root is a surface point of weight w' R / |t - c_k|.
+//  * full-box rule: drop one-signed functions; none left -> tensor Gauss; m = 1 -> split at
+//    every root; else recurse on the lower-dimensional box with the restrictions of the kept
+//    functions to both k-faces and split each line at the roots of the kept functions.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "uf_host.h"
+
+namespace uf {
+namespace {
+
+constexpr int kMaxDepth = 8;
+
+// ------------------------------------------------------------------------------------------
+// 1D polynomials
+// ------------------------------------------------------------------------------------------
+
+// Legendre P_m and its first two derivatives at t in (-1, 1), by the three-term recurrence.
+void legendre(int m, double t, double &P, double &dP, double &d2P) {
+  double pm1 = 1.0, pcur = t;
+  if (m == 0) {
+    P = 1.0;
+    dP = 0.0;
+    d2P = 0.0;
+    return;
+  }
+  for (int k = 2; k <= m; ++k) {
+    double pn = ((2.0 * k - 1.0) * t * pcur - (k - 1.0) * pm1) / k;
+    pm1 = pcur;
+    pcur = pn;
+  }
+  P = pcur;
+  dP = m * (pm1 - t * pcur) / (1.0 - t * t);
+  d2P = (2.0 * t * dP - m * (m + 1.0) * pcur) / (1.0 - t * t);
+}
+
+void gauss_rule(int n, double *x, double *w) {
+  for (int i = 0; i < n; ++i) {
+    // i-th root counted from the right end of [-1, 1]
+    double t = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double P, dP, d2P;
+      legendre(n, t, P, dP, d2P);
+      double dt = P / dP;
+      t -= dt;
+      if (std::fabs(dt) < 1e-16) break;
+    }
+    double P, dP, d2P;
+    legendre(n, t, P, dP, d2P);
+    x[n - 1 - i] = 0.5 * (1.0 + t);
+    w[n - 1 - i] = 1.0 / ((1.0 - t * t) * dP * dP);  // half of 2 / ((1 - t^2) P'^2)
+  }
+}
+
+void lobatto_nodes(int n, double *z) {
+  z[0] = 0.0;
+  z[n - 1] = 1.0;
+  const int m = n - 1;
+  for (int i = 1; i < m; ++i) {
+    double t = -std::cos(M_PI * i / m);
+    for (int it = 0; it < 100; ++it) {
+      double P, dP, d2P;
+      legendre(m, t, P, dP, d2P);
+      double dt = dP / d2P;
+      t -= dt;
+      if (std::fabs(dt) < 1e-16) break;
+    }
+    z[i] = 0.5 * (1.0 + t);
+  }
+  std::sort(z + 1, z + n - 1);
+}
+
+// Derivatives 0..J of the i-th Lagrange polynomial at x: the product of linear factors is
+// accumulated factor by factor with D^j[P (x - z)] = (x - z) D^j P + j D^{j-1} P.
+void lagrange_derivs(const Tables1D &t, int i, double x, int J, double *out) {
+  double d[kMaxN + 1];
+  for (int j = 0; j <= J; ++j) d[j] = (j == 0) ? 1.0 : 0.0;
+  for (int m = 0; m < t.n; ++m) {
+    if (m == i) continue;
+    const double f = x - t.z[m];
+    for (int j = J; j >= 1; --j) d[j] = f * d[j] + j * d[j - 1];
+    d[0] = f * d[0];
+  }
+  for (int j = 0; j <= J; ++j) out[j] = d[j] * t.den_inv[i];
+}
+
+// ------------------------------------------------------------------------------------------
+// Dimension-reduction quadrature for psi = |x - c|^2 - rho
+// ------------------------------------------------------------------------------------------
+
+struct Box {
+  int m;
+  double lo[kMaxDim], hi[kMaxDim];
+};
+
+struct Gauss1 {
+  int q;
+  double x[32], w[32];
+};
+
+void box_dist2(const double *c, const Box &b, double &dmin2, double &dmax2) {
+  dmin2 = 0.0;
+  dmax2 = 0.0;
+  for (int a = 0; a < b.m; ++a) {
+    const double dl = b.lo[a] - c[a];
+    const double dh = b.hi[a] - c[a];
+    const double e = std::fmax(std::fmax(dl, 0.0), -dh);
+    dmin2 += e * e;
+    dmax2 += std::fmax(dl * dl, dh * dh);
+  }
+}
+
+double dist2(const double *x, const double *c, int m) {
+  double r = 0.0;
+  for (int i = 0; i < m; ++i) {
+    const double d = x[i] - c[i];
+    r += d * d;
+  }
+  return r;
+}
+
+void tensor_rule(const Box &b, const Gauss1 &g, std::vector<QPoint> &out) {
+  int total = 1;
+  for (int a = 0; a < b.m; ++a) total *= g.q;
+  for (int flat = 0; flat < total; ++flat) {
+    QPoint p{};
+    double wt = 1.0;
+    int rem = flat;
+    for (int a = 0; a < b.m; ++a) {
+      const int i = rem % g.q;
+      rem /= g.q;
+      p.x[a] = b.lo[a] + (b.hi[a] - b.lo[a]) * g.x[i];
+      wt *= (b.hi[a] - b.lo[a]) * g.w[i];
+    }
+    p.w = wt;
+    out.push_back(p);
+  }
+}
+
+int height_dir(const double *c, const Box &b) {
+  int k = 0;
+  double best = -1.0;
+  for (int i = 0; i < b.m; ++i) {
+    const double v = std::fabs(0.5 * (b.lo[i] + b.hi[i]) - c[i]);
+    if (v > best) {
+      best = v;
+      k = i;
+    }
+  }
+  return k;
+}
+
+Box child(const Box &b, int bits) {
+  Box c = b;
+  for (int a = 0; a < b.m; ++a) {
+    const double mid = 0.5 * (b.lo[a] + b.hi[a]);
+    if ((bits >> a) & 1)
+      c.lo[a] = mid;
+    else
+      c.hi[a] = mid;
+  }
+  return c;
+}
+
+Box drop_dim(const Box &b, int k) {
+  Box r;
+  r.m = b.m - 1;
+  for (int a = 0, j = 0; a < b.m; ++a)
+    if (a != k) {
+      r.lo[j] = b.lo[a];
+      r.hi[j] = b.hi[a];
+      ++j;
+    }
+  return r;
+}
+
+void drop_vec(const double *v, int m, int k, double *out) {
+  for (int a = 0, j = 0; a < m; ++a)
+    if (a != k) out[j++] = v[a];
+}
+
+// x (m - 1 coordinates) with value t inserted at position k
+void insert_coord(const double *x, int m, int k, double t, double *out) {
+  for (int a = 0, j = 0; a < m; ++a) out[a] = (a == k) ? t : x[j++];
+}
+
+// Break points of [a, b] at the sorted roots, zero-length pieces dropped.
+int make_pieces(double a, double b, double *roots, int nr, double *pa, double *pb) {
+  std::sort(roots, roots + nr);
+  double brk[16];
+  int nb = 0;
+  brk[nb++] = a;
+  for (int i = 0; i < nr; ++i) brk[nb++] = roots[i];
+  brk[nb++] = b;
+  int np = 0;
+  for (int i = 0; i + 1 < nb; ++i)
+    if (brk[i + 1] > brk[i]) {
+      pa[np] = brk[i];
+      pb[np] = brk[i + 1];
+      ++np;
+    }
+  return np;
+}
+
+struct QuadError {};
+
+void full_box_rule(const Box &b, const std::vector<Fn> &fns, const Gauss1 &g, int depth,
+                   std::vector<QPoint> &out) {
+  std::vector<Fn> keep;
+  for (const Fn &f : fns) {
+    double dmin2, dmax2;
+    box_dist2(f.c, b, dmin2, dmax2);
+    if (!(dmin2 >= f.rho || dmax2 <= f.rho)) keep.push_back(f);
+  }
+  if (keep.empty()) {
+    tensor_rule(b, g, out);
+    return;
+  }
+  const double *c = keep[0].c;
+  if (b.m == 1) {
+    double roots[16];
+    int nr = 0;
+    for (const Fn &f : keep) {
+      const double s = std::sqrt(f.rho);
+      const double cand[2] = {f.c[0] - s, f.c[0] + s};
+      for (double t : cand)
+        if (b.lo[0] < t && t < b.hi[0]) roots[nr++] = t;
+    }
+    double pa[16], pb[16];
+    const int np = make_pieces(b.lo[0], b.hi[0], roots, nr, pa, pb);
+    for (int ip = 0; ip < np; ++ip)
+      for (int i = 0; i < g.q; ++i) {
+        QPoint p{};
+        p.x[0] = pa[ip] + (pb[ip] - pa[ip]) * g.x[i];
+        p.w = (pb[ip] - pa[ip]) * g.w[i];
+        out.push_back(p);
+      }
+    return;
+  }
+  const int k = height_dir(c, b);
+  if (b.lo[k] < c[k] && c[k] < b.hi[k]) {
+    if (depth >= kMaxDepth) throw QuadError{};
+    for (int bits = 0; bits < (1 << b.m); ++bits) full_box_rule(child(b, bits), keep, g, depth + 1, out);
+    return;
+  }
+  double csub[kMaxDim];
+  drop_vec(c, b.m, k, csub);
+  const double dl = b.lo[k] - c[k];
+  const double dh = b.hi[k] - c[k];
+  std::vector<Fn> fns2;
+  for (const Fn &f : keep) {
+    Fn a{}, bb{};
+    std::memcpy(a.c, csub, sizeof(csub));
+    std::memcpy(bb.c, csub, sizeof(csub));
+    a.rho = f.rho - dl * dl;
+    bb.rho = f.rho - dh * dh;
+    fns2.push_back(a);
+    fns2.push_back(bb);
+  }
+  std::vector<QPoint> outer;
+  full_box_rule(drop_dim(b, k), fns2, g, depth, outer);
+  const bool up = c[k] <= b.lo[k];
+  for (const QPoint &op : outer) {
+    const double r = dist2(op.x, csub, b.m - 1);
+    double roots[16];
+    int nr = 0;
+    for (const Fn &f : keep) {
+      const double r2 = f.rho - r;
+      if (r2 > 0.0) {
+        const double s = std::sqrt(r2);
+        const double t = up ? c[k] + s : c[k] - s;
+        if (b.lo[k] < t && t < b.hi[k]) roots[nr++] = t;
+      }
+    }
+    double pa[16], pb[16];
+    const int np = make_pieces(b.lo[k], b.hi[k], roots, nr, pa, pb);
+    for (int ip = 0; ip < np; ++ip)
+      for (int i = 0; i < g.q; ++i) {
+        QPoint p{};
+        insert_coord(op.x, b.m, k, pa[ip] + (pb[ip] - pa[ip]) * g.x[i], p.x);
+        p.w = op.w * ((pb[ip] - pa[ip]) * g.w[i]);
+        out.push_back(p);
+      }
+  }
+}
+
+void sphere_box_rules(const Box &b, const double *c, double rho, const Gauss1 &g, int depth,
+                      bool surface, std::vector<QPoint> &vol, std::vector<QPoint> &surf) {
+  double dmin2, dmax2;
+  box_dist2(c, b, dmin2, dmax2);
+  if (dmax2 <= rho) {
+    tensor_rule(b, g, vol);
+    return;
+  }
+  if (dmin2 >= rho) return;
+  if (b.m == 1) {
+    const double s = std::sqrt(rho);
+    double roots[2];
+    int nr = 0;
+    const double cand[2] = {c[0] - s, c[0] + s};
+    for (double t : cand)
+      if (b.lo[0] < t && t < b.hi[0]) roots[nr++] = t;
+    double surf_t[2] = {roots[0], roots[1]};
+    const int ns = nr;
+    double pa[16], pb[16];
+    const int np = make_pieces(b.lo[0], b.hi[0], roots, nr, pa, pb);
+    for (int ip = 0; ip < np; ++ip) {
+      const double mid = 0.5 * (pa[ip] + pb[ip]);
+      if ((mid - c[0]) * (mid - c[0]) - rho < 0.0)
+        for (int i = 0; i < g.q; ++i) {
+          QPoint p{};
+          p.x[0] = pa[ip] + (pb[ip] - pa[ip]) * g.x[i];
+          p.w = (pb[ip] - pa[ip]) * g.w[i];
+          vol.push_back(p);
+        }
+    }
+    if (surface)
+      for (int i = 0; i < ns; ++i) {
+        QPoint p{};
+        p.x[0] = surf_t[i];
+        p.w = 1.0;
+        p.nrm[0] = surf_t[i] > c[0] ? 1.0 : -1.0;
+        surf.push_back(p);
+      }
+    return;
+  }
+  const int k = height_dir(c, b);
+  if (b.lo[k] < c[k] && c[k] < b.hi[k]) {
+    if (depth >= kMaxDepth) throw QuadError{};
+    for (int bits = 0; bits < (1 << b.m); ++bits)
+      sphere_box_rules(child(b, bits), c, rho, g, depth + 1, surface, vol, surf);
+    return;
+  }
+  double csub[kMaxDim];
+  drop_vec(c, b.m, k, csub);
+  const double dl = b.lo[k] - c[k];
+  const double dh = b.hi[k] - c[k];
+  std::vector<Fn> fns(2);
+  std::memcpy(fns[0].c, csub, sizeof(csub));
+  std::memcpy(fns[1].c, csub, sizeof(csub));
+  fns[0].rho = rho - dl * dl;
+  fns[1].rho = rho - dh * dh;
+  std::vector<QPoint> outer;
+  full_box_rule(drop_dim(b, k), fns, g, 0, outer);
+  const bool up = c[k] <= b.lo[k];
+  const double R = std::sqrt(rho);
+  for (const QPoint &op : outer) {
+    const double r = dist2(op.x, csub, b.m - 1);
+    const double r2 = rho - r;
+    bool has_root = false;
+    double t = 0.0;
+    if (r2 > 0.0) {
+      const double s = std::sqrt(r2);
+      const double tt = up ? c[k] + s : c[k] - s;
+      if (b.lo[k] < tt && tt < b.hi[k]) {
+        has_root = true;
+        t = tt;
+      }
+    }
+    double roots[1] = {t};
+    double pa[4], pb[4];
+    const int np = make_pieces(b.lo[k], b.hi[k], roots, has_root ? 1 : 0, pa, pb);
+    for (int ip = 0; ip < np; ++ip) {
+      const double mid = 0.5 * (pa[ip] + pb[ip]);
+      const double dm = mid - c[k];
+      if ((r + dm * dm) - rho < 0.0)
+        for (int i = 0; i < g.q; ++i) {
+          QPoint p{};
+          insert_coord(op.x, b.m, k, pa[ip] + (pb[ip] - pa[ip]) * g.x[i], p.x);
+          p.w = op.w * ((pb[ip] - pa[ip]) * g.w[i]);
+          vol.push_back(p);
+        }
+    }
+    if (surface && has_root) {
+      QPoint p{};
+      insert_coord(op.x, b.m, k, t, p.x);
+      const double nrm = std::sqrt(dist2(p.x, c, b.m));
+      for (int a = 0; a < b.m; ++a) p.nrm[a] = (p.x[a] - c[a]) / nrm;
+      p.w = op.w * (R / std::fabs(t - c[k]));
+      surf.push_back(p);
+    }
+  }
+}
+
+}  // namespace
+
+void build_tables_1d(int p, Tables1D &t) {
+  std::memset(&t, 0, sizeof(t));
+  t.p = p;
+  t.n = p + 1;
+  const int n = t.n;
+  lobatto_nodes(n, t.z);
+  for (int i = 0; i < n; ++i) {
+    double den = 1.0;
+    for (int m = 0; m < n; ++m)
+      if (m != i) den *= t.z[i] - t.z[m];
+    t.den_inv[i] = 1.0 / den;
+  }
+  gauss_rule(n, t.gauss_x, t.gauss_w);
+  double val[kMaxN][kMaxN], der[kMaxN][kMaxN];  // [q][i]
+  for (int qp = 0; qp < n; ++qp)
+    for (int i = 0; i < n; ++i) {
+      double d[kMaxN + 1];
+      lagrange_derivs(t, i, t.gauss_x[qp], 1, d);
+      val[qp][i] = d[0];
+      der[qp][i] = d[1];
+    }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double m = 0.0, k = 0.0;
+      for (int qp = 0; qp < n; ++qp) {
+        m += t.gauss_w[qp] * val[qp][i] * val[qp][j];
+        k += t.gauss_w[qp] * der[qp][i] * der[qp][j];
+      }
+      t.mass[i * n + j] = m;
+      t.stiff[i * n + j] = k;
+    }
+  for (int s = 0; s < 2; ++s)
+    for (int i = 0; i < n; ++i) {
+      double d[kMaxN + 1];
+      lagrange_derivs(t, i, (double)s, p, d);
+      for (int j = 0; j <= p; ++j) t.deriv_end[s][j][i] = d[j];
+    }
+}
+
+uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::string &msg) {
+  op.params = prm;
+  op.params.kappa = nullptr;
+  const int d = prm.dim;
+  if (d != 2 && d != 3) {
+    msg = "dim must be 2 or 3";
+    return UF_EINVAL;
+  }
+  if (prm.degree < 1 || prm.degree > 8) {
+    msg = "degree must be in 1..8";
+    return prm.degree < 1 ? UF_EINVAL : UF_EUNSUPPORTED;
+  }
+  if (prm.quad_order < 1 || prm.quad_order > 32) {
+    msg = "quad_order must be in 1..32";
+    return UF_EINVAL;
+  }
+  if (prm.gp_max_order < 0 || prm.gp_max_order > prm.degree) {
+    msg = "gp_max_order must be in 0..degree";
+    return UF_EINVAL;
+  }
+  if (prm.ls_kind != UF_LS_SPHERE) {
+    msg = "only the sphere level set is supported";
+    return UF_EUNSUPPORTED;
+  }
+  if (!(prm.ls_radius > 0.0)) {
+    msg = "ls_radius must be positive";
+    return UF_EINVAL;
+  }
+  op.dim = d;
+  op.p = prm.degree;
+  op.n = prm.degree + 1;
+  op.q = prm.quad_order;
+  op.ndof = 1;
+  for (int a = 0; a < d; ++a) op.ndof *= op.n;
+  double hv[kMaxDim];
+  int64_t total = 1;
+  for (int a = 0; a < d; ++a) {
+    if (prm.n_cells[a] < 1 || !(prm.hi[a] > prm.lo[a])) {
+      msg = "n_cells must be >= 1 and hi > lo";
+      return UF_EINVAL;
+    }
+    op.N[a] = prm.n_cells[a];
+    op.lo[a] = prm.lo[a];
+    op.center[a] = prm.ls_center[a];
+    hv[a] = (prm.hi[a] - prm.lo[a]) / (double)prm.n_cells[a];
+    total *= op.N[a];
+  }
+  if (total > (int64_t)1 << 30) {
+    msg = "background grid too large";
+    return UF_EUNSUPPORTED;
+  }
+  double hmin = hv[0], hmax = hv[0];
+  for (int a = 1; a < d; ++a) {
+    hmin = std::min(hmin, hv[a]);
+    hmax = std::max(hmax, hv[a]);
+  }
+  if (hmax - hmin > 1e-14 * hmax) {
+    msg = "cells must be cubes (isotropic h)";
+    return UF_EUNSUPPORTED;
+  }
+  op.h = hv[0];
+  op.radius = prm.ls_radius;
+  build_tables_1d(op.p, op.t);
+
+  // ---- classification and numbering (x index fastest)
+  const double r2 = op.radius * op.radius;
+  op.n_background = total;
+  op.id_map.assign(total, -1);
+  std::vector<int8_t> bg_type(total);
+  for (int64_t flat = 0; flat < total; ++flat) {
+    Box b;
+    b.m = d;
+    int64_t rem = flat;
+    for (int a = 0; a < d; ++a) {
+      const int64_t I = rem % op.N[a];
+      rem /= op.N[a];
+      b.lo[a] = op.lo[a] + (double)I * hv[a];
+      b.hi[a] = op.lo[a] + (double)(I + 1) * hv[a];
+    }
+    double dmin2, dmax2;
+    box_dist2(op.center, b, dmin2, dmax2);
+    bg_type[flat] = dmax2 <= r2 ? 0 : (dmin2 >= r2 ? 2 : 1);
+  }
+  for (int64_t flat = 0; flat < total; ++flat) {
+    if (bg_type[flat] == 2) continue;
+    op.id_map[flat] = (int32_t)op.n_active;
+    int64_t rem = flat;
+    for (int a = 0; a < kMaxDim; ++a) {
+      int64_t I = 0;
+      if (a < d) {
+        I = rem % op.N[a];
+        rem /= op.N[a];
+      }
+      op.act_index.push_back((int32_t)I);
+    }
+    op.act_type.push_back(bg_type[flat]);
+    ++op.n_active;
+  }
+  if (op.n_active == 0) {
+    msg = "no active cell: the level set does not meet the background grid";
+    return UF_EGEOMETRY;
+  }
+  if (op.n_active * (int64_t)op.ndof > ((int64_t)1 << 31) - 1) {
+    msg = "too many DoFs for 32-bit cell offsets";
+    return UF_EUNSUPPORTED;
+  }
+  op.kappa.assign(op.n_active, 1.0);
+
+  // ---- neighbours, face typing
+  const int nf = 2 * d;
+  op.nbr.assign(op.n_active * nf, -1);
+  op.flags.assign(op.n_active, 0u);
+  op.cut_of.assign(op.n_active, -1);
+  for (int64_t e = 0; e < op.n_active; ++e) {
+    if (op.act_type[e] == 1) {
+      op.flags[e] |= kCellCut;
+      op.cut_of[e] = (int32_t)op.n_cut++;
+      op.cut_cells.push_back((int32_t)e);
+    } else {
+      ++op.n_inside;
+    }
+  }
+  const bool use_gp = prm.gp_max_order > 0;
+  auto face_box = [&](int64_t e_minus, int axis) {
+    Box b;
+    b.m = d;
+    for (int a = 0; a < d; ++a) {
+      const int64_t I = op.act_index[e_minus * 3 + a];
+      b.lo[a] = op.lo[a] + (double)I * hv[a];
+      b.hi[a] = op.lo[a] + (double)(I + 1) * hv[a];
+    }
+    b.lo[axis] = b.hi[axis];
+    return b;
+  };
+  for (int64_t e = 0; e < op.n_active; ++e) {
+    for (int axis = 0; axis < d; ++axis)
+      for (int side = 0; side < 2; ++side) {
+        int64_t I[kMaxDim];
+        for (int a = 0; a < d; ++a) I[a] = op.act_index[e * 3 + a];
+        I[axis] += side ? 1 : -1;
+        if (I[axis] < 0 || I[axis] >= op.N[axis]) continue;
+        int64_t flat = 0, stride = 1;
+        for (int a = 0; a < d; ++a) {
+          flat += I[a] * stride;
+          stride *= op.N[a];
+        }
+        const int32_t nb = op.id_map[flat];
+        if (nb < 0) continue;
+        const int f = 2 * axis + side;
+        op.nbr[e * nf + f] = nb;
+        const int64_t e_minus = side ? e : nb;
+        Box fb = face_box(e_minus, axis);
+        double dmin2, dmax2;
+        box_dist2(op.center, fb, dmin2, dmax2);
+        const int ftype = dmax2 <= r2 ? 0 : (dmin2 >= r2 ? 2 : 1);  // full, cut, empty
+        const bool gp = use_gp && (op.act_type[e] == 1 || op.act_type[nb] == 1);
+        if (ftype == 0) op.flags[e] |= face_bit_sipg_full(f);
+        if (ftype == 1) op.flags[e] |= face_bit_sipg_cut(f);
+        if (gp) op.flags[e] |= face_bit_gp(f);
+        if (ftype == 1 && op.act_type[e] == 0) {
+          msg = "internal: an inside cell has a cut face";
+          return UF_EGEOMETRY;
+        }
+        if (side == 1) {
+          ++op.n_faces;
+          if (ftype == 0) ++op.n_faces_full;
+          if (ftype == 1) ++op.n_faces_cut;
+          if (ftype == 2) ++op.n_faces_empty;
+          if (gp) ++op.n_faces_gp;
+        }
+      }
+  }
+
+  // ---- quadrature of cut cells and their cut faces
+  Gauss1 g;
+  g.q = op.q;
+  gauss_rule(op.q, g.x, g.w);
+  op.vol_off.assign(1, 0);
+  op.surf_off.assign(1, 0);
+  op.cface_off.assign(1, 0);
+  std::vector<QPoint> vol, surf, fq;
+  try {
+    for (int64_t c = 0; c < op.n_cut; ++c) {
+      const int64_t e = op.cut_cells[c];
+      Box b;
+      b.m = d;
+      for (int a = 0; a < d; ++a) {
+        const int64_t I = op.act_index[e * 3 + a];
+        b.lo[a] = op.lo[a] + (double)I * hv[a];
+        b.hi[a] = op.lo[a] + (double)(I + 1) * hv[a];
+      }
+      vol.clear();
+      surf.clear();
+      sphere_box_rules(b, op.center, op.radius * op.radius, g, 0, true, vol, surf);
+      for (const QPoint &p : vol) {
+        for (int a = 0; a < d; ++a) op.vol_xi[a].push_back((p.x[a] - b.lo[a]) / op.h);
+        op.vol_w.push_back(p.w);
+      }
+      for (const QPoint &p : surf) {
+        for (int a = 0; a < d; ++a) {
+          op.surf_xi[a].push_back((p.x[a] - b.lo[a]) / op.h);
+          op.surf_n[a].push_back(p.nrm[a]);
+        }
+        op.surf_w.push_back(p.w);
+      }
+      op.vol_off.push_back((int64_t)op.vol_w.size());
+      op.surf_off.push_back((int64_t)op.surf_w.size());
+      for (int f = 0; f < nf; ++f) {
+        if (op.flags[e] & face_bit_sipg_cut(f)) {
+          const int axis = f / 2, side = f % 2;
+          const int64_t e_minus = side ? e : op.nbr[e * nf + f];
+          Box fb = face_box(e_minus, axis);
+          const double xa = fb.lo[axis];
+          const double da = xa - op.center[axis];
+          const double rho = op.radius * op.radius - da * da;
+          Box sub = drop_dim(fb, axis);
+          double csub[kMaxDim];
+          drop_vec(op.center, d, axis, csub);
+          fq.clear();
+          std::vector<QPoint> dummy;
+          sphere_box_rules(sub, csub, rho, g, 0, false, fq, dummy);
+          Box sb = drop_dim(b, axis);
+          for (const QPoint &p : fq) {
+            for (int a = 0; a < d - 1; ++a) op.cface_eta[a].push_back((p.x[a] - sb.lo[a]) / op.h);
+            op.cface_w.push_back(p.w);
+          }
+          if (side == 1) op.n_face_points_unique += (int64_t)fq.size();
+        }
+        op.cface_off.push_back((int64_t)op.cface_w.size());
+      }
+    }
+  } catch (const QuadError &) {
+    msg = "quadrature subdivision depth exceeded";
+    return UF_EGEOMETRY;
+  }
+  return UF_OK;
+}
+
+}  // namespace uf

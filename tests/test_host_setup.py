@@ -1,0 +1,68 @@
+"""The library's host setup (C++) against the oracle (Python): classification, numbering and the
+dimension-reduction rules of every cut cell and cut face.  The two are independent
+implementations of the same reading of the method, so they must agree to rounding; in practice
+they agree bit for bit."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import forms, mesh
+from paper_2404_07911_gb300.binding import UnfittedOperator
+
+CASES = {
+    "2d_q1": workloads.cfg_2d_q1(),
+    "2d_q4": workloads.small(p=4, N=12, dim=2),
+    "3d_q3_8": workloads.small(p=3, N=8),
+    "3d_q2_center_on_grid": workloads.small(p=2, N=10, center=(0.0, 0.0, 0.0)),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_setup_matches_oracle(name):
+    cfg = CASES[name]
+    op = UnfittedOperator(cfg, device=-1)
+    o = forms.Oracle(mesh.problem_from_dict(cfg))
+    counts = o.mesh.counts()
+    for k in ("n_active", "n_inside", "n_cut", "n_faces", "n_faces_full", "n_faces_cut",
+              "n_faces_empty", "n_faces_gp"):
+        assert op.info[k] == counts[k], k
+    typ, idx = op.export_cells()
+    assert np.array_equal(typ, o.mesh.active_type)
+    assert np.array_equal(idx[:, :cfg["dim"]], o.mesh.active_idx)
+    cut = np.nonzero(typ == 1)[0]
+    for c, e in enumerate(cut):
+        xi, w = op.export_cut_cell_rule(c, 0)
+        vx, vw, sx, sw, sn = o.cell_quadrature(e)
+        lo, _ = mesh.cell_box(o.prob, o.mesh.index_of(e))
+        assert xi.shape == vx.shape
+        np.testing.assert_allclose(xi, (vx - np.array(lo)) / o.prob.h, rtol=0, atol=1e-14)
+        np.testing.assert_allclose(w, vw, rtol=1e-14, atol=0)
+        sxi, swl, snl = op.export_cut_cell_rule(c, 1)
+        assert sxi.shape == sx.shape
+        np.testing.assert_allclose(sxi, (sx - np.array(lo)) / o.prob.h, rtol=0, atol=1e-14)
+        np.testing.assert_allclose(swl, sw, rtol=1e-14, atol=0)
+        np.testing.assert_allclose(snl, sn, rtol=0, atol=1e-14)
+        for axis in range(cfg["dim"]):
+            for side in range(2):
+                eta, fw = op.export_cut_face_rule(e, axis, side)
+                nb = o.mesh.neighbor(e, axis, side)
+                em = e if side == 1 else nb
+                if nb < 0 or o.mesh.face_type(em, axis) != mesh.FACE_CUT:
+                    assert len(fw) == 0
+                    continue
+                fx, fwo = o.face_quadrature(em, axis)
+                assert len(fw) == len(fwo)
+                np.testing.assert_allclose(fw, fwo, rtol=1e-14, atol=0)
+                other = [a for a in range(cfg["dim"]) if a != axis]
+                np.testing.assert_allclose(eta, (fx[:, other] - np.array(lo)[other]) / o.prob.h,
+                                           rtol=0, atol=1e-14)
+
+
+def test_benchmark_workload_setup():
+    """Counts of the 3D Q3 64^3 ball workload and its point totals (setup under a second)."""
+    op = UnfittedOperator(workloads.cfg_3d_q3(), device=-1)
+    i = op.info
+    assert (i["n_active"], i["n_cut"], i["n_dofs"]) == (84218, 13180, 5389952)
+    assert (i["n_faces"], i["n_faces_full"], i["n_faces_cut"], i["n_faces_gp"]) == (
+        245746, 219390, 26356, 38904)
+    assert i["n_vol_points"] > 64 * i["n_cut"] and i["n_surf_points"] > 10 * i["n_cut"]
