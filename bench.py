@@ -36,7 +36,7 @@ import workloads  # noqa: E402
 METRIC = "GDoF/s of unfitted DG A·x (3D, k=3) FP64/FP32 + adjoint, % of HBM roofline"
 UNIT = "GDoF/s"
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-TRAFFIC = os.path.join(ROOT, "profiles", "dram_traffic.json")
+TRAFFIC = os.path.join(ROOT, "profiles", "dram_traffic.txt")
 KERNEL_SOURCE = os.path.join(ROOT, "paper_2404_07911_gb300", "csrc", "uf_kernels.cuh")
 # Device arithmetic peaks from unit counts and the maximum SM clock (2070 MHz), 152 SMs:
 # FP64 2 FMA / clk / SM (GB300 ships a reduced FP64 pipe), FP32 128 FMA / clk / SM.
@@ -186,11 +186,15 @@ def measured_peaks():
 def kernel_traffic(name):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on these sources."""
     try:
-        rec = json.load(open(TRAFFIC))
+        rec = {}
+        for line in open(TRAFFIC):
+            parts = line.split()
+            if len(parts) == 2 and not line.startswith("#"):
+                rec[parts[0]] = parts[1]
         digest = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()[:16]
-        if rec.get("source_sha256_16") != digest:
+        if rec.get("source_sha256_16") != digest or name not in rec:
             return None
-        return rec["kernels"].get(name)
+        return float(rec[name])
     except Exception:
         return None
 

@@ -79,11 +79,16 @@ typedef struct {
   /* Algorithmic bytes of one vmult: read x once, write y once, read the unstructured point
    * data and the per-cell metadata once, for FP64 and FP32 data respectively. */
   double bytes_fp64, bytes_fp32;
-  /* Algorithmic floating-point operations of one vmult (FMA = 2) of the kernels as built. */
+  /* Algorithmic floating-point operations of one vmult (FMA = 2) from the paper's arithmetic
+   * complexity model (Sec. 4.1: structured cell 6 k^4, structured face 7 k^3, unstructured cell
+   * point 2 k^3 + 3 k^2 + 4 k, unstructured face point 3 k^2 + 4 k plus k^3 per face side, each
+   * for evaluation and again for integration, k = p + 1) applied to this operator's inside cells,
+   * structured faces, ghost-penalty orders, and unstructured points. */
   double flops;
   /* Per kernel (index 0 = structured terms of all cells, 1 = unstructured terms of cut cells):
-   * algorithmic bytes for FP64 / FP32 data and floating-point operations of one launch. */
-  double kernel_bytes_fp64[2], kernel_bytes_fp32[2], kernel_flops[2];
+   * algorithmic bytes for FP64 / FP32 data and algorithmic floating-point operations (model
+   * above) of one launch, and the floating-point operations the kernels execute as built. */
+  double kernel_bytes_fp64[2], kernel_bytes_fp32[2], kernel_flops[2], kernel_flops_built[2];
 } uf_info;
 
 /* Per-kernel device times collected between uf_profile_begin and uf_profile_end, indexed
