@@ -73,11 +73,13 @@ typedef struct {
 typedef struct {
   int64_t n_active, n_inside, n_cut, n_dofs;
   int64_t n_faces, n_faces_full, n_faces_cut, n_faces_empty, n_faces_gp;
-  int64_t n_vol_points, n_surf_points, n_face_points; /* unstructured points (face points per side) */
+  int64_t n_vol_points, n_surf_points, n_face_points; /* unstructured points (face: unique) */
+  int64_t n_vol_lines, n_face_lines;  /* lines of the dimension-reduction rules (face: per side) */
   int32_t dim, degree, dofs_per_cell, quad_order;
   double h;
-  /* Algorithmic bytes of one vmult: read x once, write y once, read the unstructured point
-   * data and the per-cell metadata once, for FP64 and FP32 data respectively. */
+  /* Algorithmic bytes of one vmult: read x once, write y once, read the per-cell metadata and
+   * the unstructured point data once (per point: coordinate along its line and weight, plus the
+   * surface normal; per line: two outer coordinates and offsets), FP64 and FP32 data. */
   double bytes_fp64, bytes_fp32;
   /* Algorithmic floating-point operations of one vmult (FMA = 2) from the paper's arithmetic
    * complexity model (Sec. 4.1: structured cell 6 k^4, structured face 7 k^3, unstructured cell

@@ -49,7 +49,8 @@ class uf_params(ctypes.Structure):
 class uf_info(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
         "n_active", "n_inside", "n_cut", "n_dofs", "n_faces", "n_faces_full", "n_faces_cut",
-        "n_faces_empty", "n_faces_gp", "n_vol_points", "n_surf_points", "n_face_points")] + [
+        "n_faces_empty", "n_faces_gp", "n_vol_points", "n_surf_points", "n_face_points",
+        "n_vol_lines", "n_face_lines")] + [
         ("dim", ctypes.c_int32), ("degree", ctypes.c_int32), ("dofs_per_cell", ctypes.c_int32),
         ("quad_order", ctypes.c_int32), ("h", ctypes.c_double), ("bytes_fp64", ctypes.c_double),
         ("bytes_fp32", ctypes.c_double), ("flops", ctypes.c_double),

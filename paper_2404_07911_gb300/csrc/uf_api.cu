@@ -34,6 +34,8 @@ struct PrecisionData {
   std::vector<unsigned char> struct_tables;  // uf::StructTables<T, n>
   std::vector<unsigned char> point_tables;   // uf::PointTables<T, n>
   uf::Scalars<T> scalars{};
+  size_t device_bytes = 0;
+  int64_t n_vlines = 0, n_flines = 0;
 };
 
 // Bump allocator over a byte count (256-byte aligned sub-arrays).
@@ -71,13 +73,21 @@ namespace {
 // Constant 1D matrices of the structured terms (see uf_device.h for their meaning).
 // ------------------------------------------------------------------------------------------
 void structured_matrices(const uf::HostOperator &op, std::vector<double> &out) {
+  // layout of uf::StructTables: 16 matrices (n x n), then dow[2][n], dnb[2][n]
   const int n = op.n, nn = n * n, d = op.dim;
   const uf::Tables1D &t = op.t;
   const double h = op.h;
   const double hf = std::pow(h, d - 1);
   const double sig = op.params.sipg_gamma / h;
-  out.assign(16 * nn, 0.0);
+  out.assign(16 * nn + 4 * n, 0.0);
   double *kv = &out[0], *mass = &out[nn];
+  for (int s = 0; s < 2; ++s) {
+    const double sgn = s ? 1.0 : -1.0;
+    for (int i = 0; i < n; ++i) {
+      out[16 * nn + s * n + i] = sgn * t.deriv_end[s][1][i] / h;          // dow[s]
+      out[16 * nn + 2 * n + s * n + i] = sgn * t.deriv_end[1 - s][1][i] / h;  // dnb[s]
+    }
+  }
   const double hv = std::pow(h, d - 2);
   for (int i = 0; i < nn; ++i) {
     kv[i] = hv * t.stiff[i];
@@ -128,6 +138,38 @@ void structured_matrices(const uf::HostOperator &op, std::vector<double> &out) {
   }
 }
 
+// kappa = 1 variants of the per-axis self matrix (32, indexed by inside | full_lo << 1 |
+// gp_lo << 2 | full_hi << 3 | gp_hi << 4) and of a ghost-penalty neighbour coupling
+// (4, indexed by 2 * side + full), from the constant matrices of structured_matrices.
+void variant_tables(const uf::HostOperator &op, const std::vector<double> &m,
+                    std::vector<double> &lself, std::vector<double> &lnbgp) {
+  const int nn = op.n * op.n;
+  auto M = [&](int which, int s) { return &m[(which + s) * nn]; };  // which: 2 a, 4 pen, ...
+  lself.assign(32 * nn, 0.0);
+  for (int v = 0; v < 32; ++v)
+    for (int i = 0; i < nn; ++i) {
+      double acc = (v & 1) ? m[i] : 0.0;  // kv
+      for (int s = 0; s < 2; ++s) {
+        const bool full = (v >> (1 + 2 * s)) & 1, gp = (v >> (2 + 2 * s)) & 1;
+        if (full) acc += M(2, s)[i] + M(4, s)[i];
+        if (gp) acc += M(6, s)[i];
+      }
+      lself[v * nn + i] = acc;
+    }
+  lnbgp.assign(4 * nn, 0.0);
+  for (int s = 0; s < 2; ++s)
+    for (int full = 0; full < 2; ++full)
+      for (int i = 0; i < nn; ++i)
+        lnbgp[(2 * s + full) * nn + i] =
+            (full ? M(8, s)[i] + M(10, s)[i] + M(12, s)[i] : 0.0) + M(14, s)[i];
+}
+
+bool kappa_is_uniform(const std::vector<double> &k) {
+  for (double v : k)
+    if (v != k[0]) return false;
+  return true;
+}
+
 template <typename T>
 uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   const uf::HostOperator &H = op->host;
@@ -152,23 +194,93 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
     cut_list[i] = H.cut_cells[order[i]];
   }
 
+  // ---- line-structured point data (lines of a cell sorted by axis)
+  std::vector<int32_t> vline_koff(nc * 4), vpt_off, lsurf, fline_koff(nc * nf * 3), fpt_off;
+  std::vector<double> vline_o0, vline_o1, vpt_t, vpt_w, spt_t, spt_w, spt_n[3];
+  std::vector<double> fline_o, fpt_t, fpt_w;
+  vpt_off.push_back(0);
+  fpt_off.push_back(0);
+  for (int64_t c = 0; c < nc; ++c) {
+    std::vector<uf::QLine> ls(H.vol_lines.begin() + H.vline_off[c],
+                              H.vol_lines.begin() + H.vline_off[c + 1]);
+    std::stable_sort(ls.begin(), ls.end(), [](const uf::QLine &a, const uf::QLine &b) { return a.k < b.k; });
+    for (int k = 0; k < 4; ++k) {
+      vline_koff[c * 4 + k] = (int32_t)lsurf.size();
+      if (k < d)
+        for (const uf::QLine &ln : ls) {
+          if (ln.k != k) continue;
+          int ob = (k == 0) ? 1 : 0, oc = (k == 2) ? 1 : 2;
+          if (d == 2) ob = 1 - k;
+          const bool from_vol = ln.vcnt > 0;
+          const int64_t p0 = from_vol ? ln.vbeg : ln.sidx;
+          const std::vector<double> *xi = from_vol ? H.vol_xi : H.surf_xi;
+          vline_o0.push_back(xi[ob][p0]);
+          vline_o1.push_back(d == 3 ? xi[oc][p0] : 0.0);
+          for (int64_t p = ln.vbeg; p < ln.vbeg + ln.vcnt; ++p) {
+            vpt_t.push_back(H.vol_xi[k][p]);
+            vpt_w.push_back(H.vol_w[p]);
+          }
+          vpt_off.push_back((int32_t)vpt_t.size());
+          if (ln.sidx >= 0) {
+            lsurf.push_back((int32_t)spt_t.size());
+            spt_t.push_back(H.surf_xi[k][ln.sidx]);
+            spt_w.push_back(H.surf_w[ln.sidx]);
+            for (int a = 0; a < 3; ++a) spt_n[a].push_back(a < d ? H.surf_n[a][ln.sidx] : 0.0);
+          } else {
+            lsurf.push_back(-1);
+          }
+        }
+    }
+    for (int f = 0; f < nf; ++f) {
+      std::vector<uf::QLine> fls(H.face_lines.begin() + H.fline_off[c * nf + f],
+                                 H.face_lines.begin() + H.fline_off[c * nf + f + 1]);
+      std::stable_sort(fls.begin(), fls.end(), [](const uf::QLine &a, const uf::QLine &b) { return a.k < b.k; });
+      for (int kk = 0; kk < 3; ++kk) {
+        fline_koff[(c * nf + f) * 3 + kk] = (int32_t)fline_o.size();
+        if (kk < d - 1)
+          for (const uf::QLine &ln : fls) {
+            if (ln.k != kk) continue;
+            fline_o.push_back(d == 3 ? H.cface_eta[1 - kk][ln.vbeg] : 0.0);
+            for (int64_t p = ln.vbeg; p < ln.vbeg + ln.vcnt; ++p) {
+              fpt_t.push_back(H.cface_eta[kk][p]);
+              fpt_w.push_back(H.cface_w[p]);
+            }
+            fpt_off.push_back((int32_t)fpt_t.size());
+          }
+      }
+    }
+  }
+  const int64_t nvl = (int64_t)lsurf.size(), nfl = (int64_t)fline_o.size();
+  if ((int64_t)vpt_t.size() != nv || (int64_t)spt_t.size() != ns || (int64_t)fpt_t.size() != nfp)
+    return fail(UF_EGEOMETRY, "internal: line structure does not cover every quadrature point");
+
   Layout L;
   const size_t o_nbr = L.take(sizeof(int32_t) * na * nf);
   const size_t o_flags = L.take(sizeof(uint32_t) * na);
   const size_t o_kappa = L.take(sizeof(T) * na);
   const size_t o_clist = L.take(sizeof(int32_t) * std::max<int64_t>(nc, 1));
   const size_t o_cidx = L.take(sizeof(int32_t) * std::max<int64_t>(nc, 1));
-  const size_t o_voff = L.take(sizeof(int32_t) * (nc + 1));
-  const size_t o_soff = L.take(sizeof(int32_t) * (nc + 1));
-  const size_t o_foff = L.take(sizeof(int32_t) * (nc * nf + 1));
-  size_t o_vxi[3], o_sxi[3], o_sn[3], o_feta[2];
-  for (int a = 0; a < d; ++a) o_vxi[a] = L.take(sizeof(T) * std::max<int64_t>(nv, 1));
-  const size_t o_vw = L.take(sizeof(T) * std::max<int64_t>(nv, 1));
-  for (int a = 0; a < d; ++a) o_sxi[a] = L.take(sizeof(T) * std::max<int64_t>(ns, 1));
-  const size_t o_sw = L.take(sizeof(T) * std::max<int64_t>(ns, 1));
-  for (int a = 0; a < d; ++a) o_sn[a] = L.take(sizeof(T) * std::max<int64_t>(ns, 1));
-  for (int a = 0; a < d - 1; ++a) o_feta[a] = L.take(sizeof(T) * std::max<int64_t>(nfp, 1));
-  const size_t o_fw = L.take(sizeof(T) * std::max<int64_t>(nfp, 1));
+  const size_t o_vlk = L.take(sizeof(int32_t) * std::max<int64_t>(nc * 4, 1));
+  const size_t o_vo0 = L.take(sizeof(T) * std::max<int64_t>(nvl, 1));
+  const size_t o_vo1 = L.take(sizeof(T) * std::max<int64_t>(nvl, 1));
+  const size_t o_vpo = L.take(sizeof(int32_t) * (nvl + 1));
+  const size_t o_lsf = L.take(sizeof(int32_t) * std::max<int64_t>(nvl, 1));
+  const size_t o_vpt = L.take(sizeof(T) * std::max<int64_t>(nv, 1));
+  const size_t o_vpw = L.take(sizeof(T) * std::max<int64_t>(nv, 1));
+  const size_t o_spt = L.take(sizeof(T) * std::max<int64_t>(ns, 1));
+  const size_t o_spw = L.take(sizeof(T) * std::max<int64_t>(ns, 1));
+  size_t o_spn[3];
+  for (int a = 0; a < 3; ++a) o_spn[a] = L.take(sizeof(T) * std::max<int64_t>(ns, 1));
+  const size_t o_flk = L.take(sizeof(int32_t) * std::max<int64_t>(nc * nf * 3, 1));
+  const size_t o_flo = L.take(sizeof(T) * std::max<int64_t>(nfl, 1));
+  const size_t o_fpo = L.take(sizeof(int32_t) * (nfl + 1));
+  const size_t o_fpt = L.take(sizeof(T) * std::max<int64_t>(nfp, 1));
+  const size_t o_fpw = L.take(sizeof(T) * std::max<int64_t>(nfp, 1));
+  std::vector<double> mats, lself, lnbgp;
+  structured_matrices(H, mats);
+  variant_tables(H, mats, lself, lnbgp);
+  const size_t o_lself = L.take(sizeof(T) * lself.size());
+  const size_t o_lnbgp = L.take(sizeof(T) * lnbgp.size());
 
   std::vector<unsigned char> img(L.bytes, 0);
   auto put = [&](size_t off, const void *src, size_t bytes) {
@@ -178,27 +290,31 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
     T *dst = reinterpret_cast<T *>(img.data() + off);
     for (size_t i = 0; i < v.size(); ++i) dst[i] = (T)v[i];
   };
-  auto put_off = [&](size_t off, const std::vector<int64_t> &v) {
-    int32_t *dst = reinterpret_cast<int32_t *>(img.data() + off);
-    for (size_t i = 0; i < v.size(); ++i) dst[i] = (int32_t)v[i];
+  auto put_i = [&](size_t off, const std::vector<int32_t> &v) {
+    put(off, v.data(), sizeof(int32_t) * v.size());
   };
   put(o_nbr, H.nbr.data(), sizeof(int32_t) * na * nf);
   put(o_flags, H.flags.data(), sizeof(uint32_t) * na);
   put_t(o_kappa, H.kappa);
   put(o_clist, cut_list.data(), sizeof(int32_t) * nc);
   put(o_cidx, cut_idx.data(), sizeof(int32_t) * nc);
-  put_off(o_voff, H.vol_off);
-  put_off(o_soff, H.surf_off);
-  put_off(o_foff, H.cface_off);
-  for (int a = 0; a < d; ++a) {
-    put_t(o_vxi[a], H.vol_xi[a]);
-    put_t(o_sxi[a], H.surf_xi[a]);
-    put_t(o_sn[a], H.surf_n[a]);
-  }
-  put_t(o_vw, H.vol_w);
-  put_t(o_sw, H.surf_w);
-  for (int a = 0; a < d - 1; ++a) put_t(o_feta[a], H.cface_eta[a]);
-  put_t(o_fw, H.cface_w);
+  put_i(o_vlk, vline_koff);
+  put_t(o_vo0, vline_o0);
+  put_t(o_vo1, vline_o1);
+  put_i(o_vpo, vpt_off);
+  put_i(o_lsf, lsurf);
+  put_t(o_vpt, vpt_t);
+  put_t(o_vpw, vpt_w);
+  put_t(o_spt, spt_t);
+  put_t(o_spw, spt_w);
+  for (int a = 0; a < 3; ++a) put_t(o_spn[a], spt_n[a]);
+  put_i(o_flk, fline_koff);
+  put_t(o_flo, fline_o);
+  put_i(o_fpo, fpt_off);
+  put_t(o_fpt, fpt_t);
+  put_t(o_fpw, fpt_w);
+  put_t(o_lself, lself);
+  put_t(o_lnbgp, lnbgp);
 
   cudaError_t err = cudaMalloc(&pd.base, L.bytes);
   if (err != cudaSuccess) return fail(UF_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(err));
@@ -208,34 +324,42 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   if (err != cudaSuccess) return fail(UF_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(err));
   err = cudaMemcpy(pd.base, img.data(), L.bytes, cudaMemcpyHostToDevice);
   if (err != cudaSuccess) return fail(UF_ECUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(err));
+  pd.device_bytes = L.bytes;
 
   unsigned char *b = static_cast<unsigned char *>(pd.base);
+  auto I32 = [&](size_t off) { return reinterpret_cast<const int32_t *>(b + off); };
+  auto TP = [&](size_t off) { return reinterpret_cast<const T *>(b + off); };
   uf::DevArrays<T> &A = pd.arrays;
-  A.nbr = reinterpret_cast<const int32_t *>(b + o_nbr);
+  A.nbr = I32(o_nbr);
   A.flags = reinterpret_cast<const uint32_t *>(b + o_flags);
   pd.kappa_dev = reinterpret_cast<T *>(b + o_kappa);
   A.kappa = pd.kappa_dev;
-  A.cut_list = reinterpret_cast<const int32_t *>(b + o_clist);
-  A.cut_idx = reinterpret_cast<const int32_t *>(b + o_cidx);
-  A.vol_off = reinterpret_cast<const int32_t *>(b + o_voff);
-  A.surf_off = reinterpret_cast<const int32_t *>(b + o_soff);
-  A.cface_off = reinterpret_cast<const int32_t *>(b + o_foff);
-  for (int a = 0; a < 3; ++a) {
-    A.vol_xi[a] = (a < d) ? reinterpret_cast<const T *>(b + o_vxi[a]) : nullptr;
-    A.surf_xi[a] = (a < d) ? reinterpret_cast<const T *>(b + o_sxi[a]) : nullptr;
-    A.surf_n[a] = (a < d) ? reinterpret_cast<const T *>(b + o_sn[a]) : nullptr;
-  }
-  A.vol_w = reinterpret_cast<const T *>(b + o_vw);
-  A.surf_w = reinterpret_cast<const T *>(b + o_sw);
-  for (int a = 0; a < 2; ++a)
-    A.cface_eta[a] = (a < d - 1) ? reinterpret_cast<const T *>(b + o_feta[a]) : nullptr;
-  A.cface_w = reinterpret_cast<const T *>(b + o_fw);
+  A.cut_list = I32(o_clist);
+  A.cut_idx = I32(o_cidx);
+  A.vline_koff = I32(o_vlk);
+  A.vline_o0 = TP(o_vo0);
+  A.vline_o1 = TP(o_vo1);
+  A.vpt_off = I32(o_vpo);
+  A.lsurf = I32(o_lsf);
+  A.vpt_t = TP(o_vpt);
+  A.vpt_w = TP(o_vpw);
+  A.spt_t = TP(o_spt);
+  A.spt_w = TP(o_spw);
+  for (int a = 0; a < 3; ++a) A.spt_n[a] = TP(o_spn[a]);
+  A.fline_koff = I32(o_flk);
+  A.fline_o = TP(o_flo);
+  A.fpt_off = I32(o_fpo);
+  A.fpt_t = TP(o_fpt);
+  A.fpt_w = TP(o_fpw);
+  A.lself = TP(o_lself);
+  A.lnbgp = TP(o_lnbgp);
+  A.kappa_uniform = kappa_is_uniform(H.kappa) ? 1 : 0;
   A.n_active = (int32_t)na;
   A.n_cut = (int32_t)nc;
+  pd.n_vlines = nvl;
+  pd.n_flines = nfl;
 
   // constant tables
-  std::vector<double> mats;
-  structured_matrices(H, mats);
   pd.struct_tables.assign(sizeof(T) * mats.size(), 0);
   T *st = reinterpret_cast<T *>(pd.struct_tables.data());
   for (size_t i = 0; i < mats.size(); ++i) st[i] = (T)mats[i];
@@ -254,6 +378,7 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   pd.scalars.inv_h2 = (T)(1.0 / (H.h * H.h));
   pd.scalars.sipg_over_h = (T)(H.params.sipg_gamma / H.h);
   pd.scalars.nitsche_over_h = (T)(H.params.nitsche_gamma / H.h);
+  pd.scalars.hf = (T)std::pow(H.h, d - 1);
   pd.present = true;
   return UF_OK;
 }
@@ -394,36 +519,32 @@ uf_status uf_get_info(const uf_operator *op, uf_info *info) {
   info->n_vol_points = (int64_t)H.vol_w.size();
   info->n_surf_points = (int64_t)H.surf_w.size();
   info->n_face_points = H.n_face_points_unique;
+  info->n_vol_lines = (int64_t)H.vol_lines.size();
+  info->n_face_lines = (int64_t)H.face_lines.size();
   info->dim = H.dim;
   info->degree = H.p;
   info->dofs_per_cell = H.ndof;
   info->quad_order = H.q;
   info->h = H.h;
   const int d = H.dim, nf = 2 * d;
-  for (int s = 0; s < 2; ++s) {
-    const double S = s == 0 ? 8.0 : 4.0;
-    double b = 2.0 * S * (double)info->n_dofs;                 // read x, write y
-    b += (double)H.n_active * (4.0 * nf + 4.0 + S);             // neighbours, flags, kappa
-    b += (double)H.n_cut * (4.0 * 3 + 4.0 * nf + 8.0);          // offsets, cut list
-    b += S * ((d + 1.0) * info->n_vol_points + (2.0 * d + 1.0) * info->n_surf_points +
-              (double)d * info->n_face_points);                 // point data
-    (s == 0 ? info->bytes_fp64 : info->bytes_fp32) = b;
-  }
   // Per-kernel algorithmic bytes: the structured kernel reads x of every cell once (neighbour
   // lines are L2 hits) and writes y once, plus neighbours / flags / kappa; the cut-cell kernel
-  // reads x of the cut cells and of their cut-face neighbours, reads and writes their y rows,
-  // and reads the point data and offsets once.
+  // reads x of the cut cells (own and cut-face neighbours are L2 hits), reads and writes their y
+  // rows, and reads the line-structured point data and offsets once.
+  const double vl = (double)info->n_vol_lines, flh = 0.5 * (double)info->n_face_lines;
   for (int s = 0; s < 2; ++s) {
     const double S = s == 0 ? 8.0 : 4.0;
     double *kb = s == 0 ? info->kernel_bytes_fp64 : info->kernel_bytes_fp32;
     kb[0] = 2.0 * S * (double)info->n_dofs + (double)H.n_active * (4.0 * nf + 4.0 + S);
-    kb[1] = 3.0 * S * (double)H.n_cut * H.ndof + (double)H.n_cut * (4.0 * 3 + 4.0 * nf + 8.0 + S) +
-            S * ((d + 1.0) * info->n_vol_points + (2.0 * d + 1.0) * info->n_surf_points +
-                 (double)d * info->n_face_points);
+    kb[1] = 3.0 * S * (double)H.n_cut * H.ndof +
+            (double)H.n_cut * (4.0 * 2 + 4.0 * 4 + 4.0 * 3 * nf + S) +
+            S * (2.0 * info->n_vol_points + (2.0 + d) * info->n_surf_points +
+                 2.0 * info->n_face_points) +
+            vl * (2.0 * S + 8.0) + flh * (S + 4.0);
+    (s == 0 ? info->bytes_fp64 : info->bytes_fp32) = kb[0] + kb[1];
   }
-  // FMA counts of the kernels as built (x2 for flops).
+  // Floating-point operations of the kernels as built (FMA = 2, every FP op counted once).
   const double n = H.n, nd = H.ndof, nline = nd / n;
-  double fma = 0.0;
   int64_t nb_faces = 0, struct_faces = 0;
   for (int64_t e = 0; e < H.n_active; ++e)
     for (int f = 0; f < nf; ++f) {
@@ -433,18 +554,44 @@ uf_status uf_get_info(const uf_operator *op, uf_info *info) {
         if (f % 2 == 1) ++struct_faces;  // count each interior face once (from its lower cell)
       }
     }
-  fma += (double)H.n_active * d * (nline * n * n) * d;  // L along the axis + (d - 1) mass sweeps
-  fma += (double)nb_faces * nline * n * n;              // neighbour couplings
-  const double fma_struct = fma;
-  const double pt_eval = (d == 3) ? 2 * n * n * n + 3 * n * n + 4 * n : 2 * n * n + 3 * n;
-  const double pt_basis = d * 6.0 * n;
-  const double pt_integrate = nd * (d == 3 ? 6.0 : 4.0);
-  fma += (double)(info->n_vol_points + info->n_surf_points) * (pt_eval + pt_basis + pt_integrate);
-  const double fp = 2.0 * (double)info->n_face_points;  // both sides
-  fma += fp * (4.0 * (nline + (d == 3 ? n : 0)) + 2.0 * nline + (d - 1) * 6.0 * n);
-  fma += 2.0 * (double)H.n_faces_cut * (4.0 * nd + 2.0 * nd);  // traces and expansion
-  info->kernel_flops_built[0] = 2.0 * fma_struct;
-  info->kernel_flops_built[1] = 2.0 * (fma - fma_struct);
+  // structured kernel: per cell and axis one L line sweep (n^{d+1} FMA + n^d scalings),
+  // ghost-penalty neighbour couplings as full line sweeps (n^{d+1} FMA), SIPG-only neighbour
+  // couplings in rank-2 form (4n + 8 flops per line), and the shared in-face mass sweeps
+  // (5 in 3D, 2 in 2D, n^{d+1} FMA each); plus the per-cell matrix build if kappa varies.
+  int64_t gp_faces_cell = 0, r2_faces_cell = 0;
+  for (int64_t e = 0; e < H.n_active; ++e)
+    for (int f = 0; f < nf; ++f) {
+      const uint32_t fl = H.flags[e];
+      if (fl & uf::face_bit_gp(f))
+        ++gp_faces_cell;
+      else if (fl & uf::face_bit_sipg_full(f))
+        ++r2_faces_cell;
+    }
+  const double sweep = nline * n * n;  // FMA per line sweep of a cell
+  const bool uni = kappa_is_uniform(H.kappa);
+  double fl_struct = 2.0 * ((double)H.n_active * (d * sweep + (d == 3 ? 5 : 2) * sweep) +
+                            (double)gp_faces_cell * sweep) +
+                     (double)H.n_active * d * nd + (double)r2_faces_cell * nline * (4 * n + 8);
+  if (!uni) fl_struct += (double)H.n_active * d * n * n * 2.0 * 13.0;
+  // cut-cell kernel: 1D basis (values and derivatives) 14n - 8, values only 6n - 4 flops
+  const double fb = 14 * n - 8, fbv = 6 * n - 4;
+  const double vlines = (double)H.vol_lines.size(), flines = (double)H.face_lines.size();
+  double fl_cut = 0.0;
+  if (d == 3) {
+    fl_cut += vlines * (2 * fb + 2 * (2 * n * n * n + 3 * n * n) + 4 * n * n + 4 * n * n * n);
+    fl_cut += (double)info->n_vol_points * (fb + 2 * 3 * n + 4 + 2 * 3 * n);
+    fl_cut += (double)info->n_surf_points * (fb + 2 * 4 * n + 16 + 2 * 3 * n + 6);
+    fl_cut += flines * (fbv + 2 * 4 * n * n + 2 * 2 * n * n);
+  } else {
+    fl_cut += vlines * (fb + 2 * 2 * n * n + 2 * 2 * n * n);
+    fl_cut += (double)info->n_vol_points * (fb + 2 * 2 * n + 3 + 2 * 2 * n);
+    fl_cut += (double)info->n_surf_points * (fb + 2 * 3 * n + 12 + 2 * 2 * n + 4);
+    fl_cut += flines * (2 * 2 * n);
+  }
+  fl_cut += 2.0 * (double)info->n_face_points * (fbv + 2 * 4 * n + 10 + 2 * 2 * n);
+  fl_cut += 2.0 * (double)H.n_faces_cut * (2 * 4 * nd + 4 * nd);  // traces and expansion
+  info->kernel_flops_built[0] = fl_struct;
+  info->kernel_flops_built[1] = fl_cut;
 
   // Algorithmic FMAs from the paper's complexity model (evaluation + integration = x2).
   const double k = n;
@@ -567,6 +714,9 @@ uf_status uf_set_kappa(uf_operator *op, const double *kappa_host) {
     if (!(kappa_host[e] > 0.0) || !std::isfinite(kappa_host[e]))
       return fail(UF_EINVAL, "kappa must be positive and finite");
   std::copy(kappa_host, kappa_host + op->host.n_active, op->host.kappa.begin());
+  const int32_t uni = kappa_is_uniform(op->host.kappa) ? 1 : 0;
+  op->f64.arrays.kappa_uniform = uni;
+  op->f32.arrays.kappa_uniform = uni;
   if (op->device < 0) return UF_OK;
   DeviceGuard guard(op->device);
   const int64_t na = op->host.n_active;

@@ -21,12 +21,19 @@ constexpr int kMaxNdev = 9;
 //   qn[s]   SIPG penalty, own-neighbour                (x {kappa})
 //   hn[s]   ghost penalty, own-neighbour               (x {kappa})
 // Face matrices carry the face measure h^{d-1} and the normal-derivative scalings 1/h^j.
+//   dow[s]  sgn_s phi'(s) / h          (own outward normal derivative at the face)
+//   dnb[s]  sgn_s phi'(1 - s) / h      (neighbour's derivative along the own outward normal)
+// A full face without ghost penalty couples to the neighbour through rank 2 only:
+//   (kappa_K b + kappa_nb c + {kappa} qn) u_nb
+//     = h^{d-1} [ kappa_K/2 dow (u_nb at its face node) - e_own (kappa_nb/2 dnb.u_nb
+//                 + sigma/h {kappa} u_nb at its face node) ]   (delta property of the basis).
 template <typename T, int N>
 struct StructTables {
   T kv[N * N];
   T mass[N * N];
   T a[2][N * N], pen[2][N * N], gp[2][N * N];
   T b[2][N * N], c[2][N * N], qn[2][N * N], hn[2][N * N];
+  T dow[2][N], dnb[2][N];
 };
 
 // 1D data for point evaluation of the Lagrange basis at arbitrary reference coordinates.
@@ -44,9 +51,18 @@ struct Scalars {
   T h, inv_h, inv_h2;
   T sipg_over_h;     // sigma / h
   T nitsche_over_h;  // tau / h
+  T hf;              // face measure scaling h^{d-1}
 };
 
 // Pointers into device memory (one allocation per precision).
+//
+// Unstructured points are stored line by line: a line of the dimension-reduction rule holds the
+// points that share every reference coordinate except the one along its axis k.  Lines of a cut
+// cell are sorted by k; vline_koff[ci * 4 + k] .. vline_koff[ci * 4 + k + 1] are the lines of
+// cut cell ci along axis k (entries beyond the dimension repeat the end).  Line l owns volume
+// points vpt_off[l] .. vpt_off[l + 1] (coordinate along k and weight) and surface point
+// lsurf[l] (-1 if none).  Cut faces: fline_koff[(ci * 2d + f) * 3 + k'] for the two in-face
+// axes k' (0 = lower one), same scheme with face points.
 template <typename T>
 struct DevArrays {
   const int32_t *nbr;       // [n_active * 2d]
@@ -54,10 +70,24 @@ struct DevArrays {
   const T *kappa;           // [n_active]
   const int32_t *cut_list;  // [n_cut] active ids, most expensive first
   const int32_t *cut_idx;   // [n_cut] cut index of cut_list[i] (row of the offset arrays)
-  const int32_t *vol_off, *surf_off, *cface_off;  // [n_cut + 1], [n_cut + 1], [n_cut * 2d + 1]
-  const T *vol_xi[3], *vol_w;
-  const T *surf_xi[3], *surf_w, *surf_n[3];
-  const T *cface_eta[2], *cface_w;
+  // volume / surface lines
+  const int32_t *vline_koff;  // [n_cut * 4]
+  const T *vline_o0, *vline_o1;  // outer reference coordinates (lower, upper other axis)
+  const int32_t *vpt_off;     // [n_vlines + 1]
+  const int32_t *lsurf;       // [n_vlines]
+  const T *vpt_t, *vpt_w;     // [n_vol_points] coordinate along the line, weight
+  const T *spt_t, *spt_w, *spt_n[3];  // [n_surf_points]
+  // cut-face lines
+  const int32_t *fline_koff;  // [n_cut * 2d * 3]
+  const T *fline_o;           // outer in-face reference coordinate (3D)
+  const int32_t *fpt_off;     // [n_flines + 1]
+  const T *fpt_t, *fpt_w;     // [n_face_points]
+  // Structured 1D matrices for kappa = 1, indexed by the face flags of one axis:
+  // lself[v], v = inside | full_lo << 1 | gp_lo << 2 | full_hi << 3 | gp_hi << 4, and
+  // lnbgp[2 * s + full] for a ghost-penalty face on side s.  When kappa is uniform
+  // (kappa_uniform != 0) every structured term scales with that value.
+  const T *lself, *lnbgp;
+  int32_t kappa_uniform;
   int32_t n_active, n_cut;
 };
 

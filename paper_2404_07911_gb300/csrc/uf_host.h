@@ -48,6 +48,14 @@ struct QPoint {
   double nrm[kMaxDim];
 };
 
+// A line of the dimension-reduction rule: points that share every coordinate except the one
+// along axis k (the height direction of the box, or axis 0 of a tensor box).  vbeg / vcnt index
+// volume points, sidx the surface point of the line (-1 if none).
+struct QLine {
+  int k;
+  int64_t vbeg, vcnt, sidx;
+};
+
 struct HostOperator {
   uf_params params{};
   int dim = 0, p = 0, n = 0, ndof = 0, q = 0;
@@ -80,6 +88,11 @@ struct HostOperator {
   // cut-face rules, stored per (cut cell, face) side: [n_cut * 2 * dim + 1]
   std::vector<int64_t> cface_off;
   std::vector<double> cface_eta[kMaxDim - 1], cface_w;
+  // line structure of the rules (indices into the arrays above): volume/surface lines of cut
+  // cell c are vol_lines[vline_off[c] .. vline_off[c + 1]); face lines of (c, face f) are
+  // face_lines[fline_off[c * 2d + f] .. ], with k an in-face axis (0 = lower of the two).
+  std::vector<QLine> vol_lines, face_lines;
+  std::vector<int64_t> vline_off, fline_off;
 
   // counts
   int64_t n_faces = 0, n_faces_full = 0, n_faces_cut = 0, n_faces_empty = 0, n_faces_gp = 0;

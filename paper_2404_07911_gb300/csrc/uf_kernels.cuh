@@ -59,58 +59,82 @@ __device__ __forceinline__ uint32_t bit_full(int f) { return 1u << (1 + 3 * f); 
 __device__ __forceinline__ uint32_t bit_cut(int f) { return 1u << (2 + 3 * f); }
 __device__ __forceinline__ uint32_t bit_gp(int f) { return 1u << (3 + 3 * f); }
 
-template <int N>
-__host__ __device__ constexpr int struct_cells_per_block(int NL) {
-  return (NL >= 128) ? 1 : (128 / NL);
+// Cells per CTA of the structured kernel: one thread per line (n^{d-1} per cell), at most 128
+// threads, and the shared memory of the cells (u, W per axis, per-cell matrices) under 40 KB.
+template <typename T, int DIM, int N>
+__host__ __device__ constexpr int struct_cells_per_block() {
+  constexpr int ND = (DIM == 2) ? N * N : N * N * N;
+  constexpr int NL = (DIM == 2) ? N : N * N;
+  constexpr int by_threads = (NL >= 128) ? 1 : (128 / NL);
+  constexpr int cell_bytes = (int)sizeof(T) * (ND * (1 + DIM) + DIM * 3 * N * N);
+  constexpr int by_smem = 40960 / cell_bytes;
+  constexpr int cpb = by_threads < by_smem ? by_threads : by_smem;
+  return cpb < 1 ? 1 : cpb;
 }
 
 // ------------------------------------------------------------------------------------------
 // Structured terms
 // ------------------------------------------------------------------------------------------
+//
+// y_K = sum_a (M .. L_a .. M) u_K + sum_faces (M .. L_f .. M) u_nb with W_a = L_a u_K +
+// sum_{faces along a} L_f u_nb computed line by line (phase 1), then the in-face mass sweeps
+// shared between axes (phase 2):
+//   3D: y = M_z (M_y W_x + M_x W_y) + M_y M_x W_z     (5 sweeps instead of 6)
+//   2D: y = M_y W_x + M_x W_y
+template <typename T, int N>
+__device__ __forceinline__ void apply_line(const T *__restrict__ Lm, T scale, const T *u, T *w,
+                                           bool transpose, bool accumulate) {
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+    T acc = T(0);
+#pragma unroll
+    for (int m = 0; m < N; ++m) acc = fma(Lm[transpose ? (m * N + r) : (r * N + m)], u[m], acc);
+    w[r] = accumulate ? fma(scale, acc, w[r]) : scale * acc;
+  }
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void mass_line(const T *__restrict__ M, T *v, int base, int st) {
+  T a[N], b[N];
+#pragma unroll
+  for (int m = 0; m < N; ++m) a[m] = v[base + m * st];
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+    T acc = T(0);
+#pragma unroll
+    for (int m = 0; m < N; ++m) acc = fma(M[r * N + m], a[m], acc);
+    b[r] = acc;
+  }
+#pragma unroll
+  for (int r = 0; r < N; ++r) v[base + r * st] = b[r];
+}
+
 template <typename T, int DIM, int N, bool ADJ>
 __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ StructTables<T, N> tab,
-                                                     const DevArrays<T> d, T *__restrict__ y,
-                                                     const T *__restrict__ x) {
+                                                     const DevArrays<T> d, const Scalars<T> sc,
+                                                     T *__restrict__ y, const T *__restrict__ x) {
   using G = Geo<DIM, N>;
   constexpr int ND = G::ND, NL = G::NL, NF = G::NF, NN = N * N;
-  constexpr int CPB = struct_cells_per_block<N>(NL);
+  constexpr int CPB = struct_cells_per_block<T, DIM, N>();
   constexpr int TPC = NL;
 
-  __shared__ T s_tab[16 * NN];
   __shared__ T s_u[CPB][ND];
-  __shared__ T s_w[CPB][ND];
-  __shared__ T s_y[CPB][ND];
-  __shared__ T s_l[CPB][3][NN];
+  __shared__ T s_w[DIM][CPB][ND];
+  __shared__ T s_l[CPB][DIM][3][NN];  // per-cell matrices when kappa is not uniform
 
   const int tid = threadIdx.x;
-  // Copy the constant 1D matrices to shared memory (the L-build reads them per entry).
-  {
-    const T *src = reinterpret_cast<const T *>(&tab);
-    for (int i = tid; i < 16 * NN; i += blockDim.x) s_tab[i] = src[i];
-  }
-  const T *kv = s_tab;
-  const T *mass = s_tab + NN;
-  auto A = [&](int s) { return s_tab + (2 + s) * NN; };
-  auto P = [&](int s) { return s_tab + (4 + s) * NN; };
-  auto GP = [&](int s) { return s_tab + (6 + s) * NN; };
-  auto B = [&](int s) { return s_tab + (8 + s) * NN; };
-  auto C = [&](int s) { return s_tab + (10 + s) * NN; };
-  auto Q = [&](int s) { return s_tab + (12 + s) * NN; };
-  auto H = [&](int s) { return s_tab + (14 + s) * NN; };
-
   const int first = blockIdx.x * CPB;
   const int c = tid / TPC;
   const int t = tid % TPC;
   const bool active_thread = (c < CPB);
   const int e = first + c;
   const bool has_cell = active_thread && (e < d.n_active);
+  const bool uniform = d.kappa_uniform != 0;
 
-  // Cooperative, coalesced load of the block's contiguous cells.
   {
     const int ncell = min(CPB, d.n_active - first);
     const T *src = x + (size_t)first * ND;
     for (int i = tid; i < ncell * ND; i += blockDim.x) (&s_u[0][0])[i] = src[i];
-    for (int i = tid; i < CPB * ND; i += blockDim.x) (&s_y[0][0])[i] = T(0);
   }
 
   uint32_t fl = 0;
@@ -134,107 +158,149 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
     }
   }
   const bool inside = has_cell && !(fl & 1u);
-  __syncthreads();
 
-#pragma unroll 1
-  for (int axis = 0; axis < DIM; ++axis) {
-    // ---- per-cell 1D matrices for this axis: s_l[c][0] self, [1] lower neighbour, [2] upper
-    if (active_thread) {
+  if (!uniform && has_cell) {
+    // per-cell 1D matrices from the constant ones and kappa
+    for (int a = 0; a < DIM; ++a)
       for (int idx = t; idx < NN; idx += TPC) {
         const int r = idx / N, m = idx % N;
-        const int tr = ADJ ? (m * N + r) : idx;  // transposed entry for the adjoint
-        T self = inside ? kap * kv[tr] : T(0);
+        const int tr = ADJ ? (m * N + r) : idx;
+        T self = inside ? kap * tab.kv[tr] : T(0);
         T ln[2] = {T(0), T(0)};
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
-          const int f = 2 * axis + s;
+          const int f = 2 * a + s;
           if (nb[f] < 0) continue;
           const bool full = bit(fl, bit_full(f));
           const bool gp = bit(fl, bit_gp(f));
-          if (full) self += kap * A(s)[tr] + kavg[f] * P(s)[tr];
-          if (gp) self += kavg[f] * GP(s)[tr];
-          if (!ADJ) {
-            if (full) ln[s] += kap * B(s)[idx] + knb[f] * C(s)[idx] + kavg[f] * Q(s)[idx];
-            if (gp) ln[s] += kavg[f] * H(s)[idx];
-          } else {
-            // transpose of the neighbour's coupling toward this cell (its face 1 - s)
-            const int so = 1 - s;
-            if (full) ln[s] += knb[f] * B(so)[tr] + kap * C(so)[tr] + kavg[f] * Q(so)[tr];
-            if (gp) ln[s] += kavg[f] * H(so)[tr];
+          if (full) self += kap * tab.a[s][tr] + kavg[f] * tab.pen[s][tr];
+          if (gp) self += kavg[f] * tab.gp[s][tr];
+          if (gp) {
+            if (!ADJ) {
+              if (full) ln[s] += kap * tab.b[s][idx] + knb[f] * tab.c[s][idx] + kavg[f] * tab.qn[s][idx];
+              ln[s] += kavg[f] * tab.hn[s][idx];
+            } else {
+              // transpose of the neighbour's coupling toward this cell (its face 1 - s)
+              const int so = 1 - s;
+              if (full) ln[s] += knb[f] * tab.b[so][tr] + kap * tab.c[so][tr] + kavg[f] * tab.qn[so][tr];
+              ln[s] += kavg[f] * tab.hn[so][tr];
+            }
           }
         }
-        s_l[c][0][idx] = self;
-        s_l[c][1][idx] = ln[0];
-        s_l[c][2][idx] = ln[1];
+        s_l[c][a][0][idx] = self;
+        s_l[c][a][1][idx] = ln[0];
+        s_l[c][a][2][idx] = ln[1];
       }
-    }
-    __syncthreads();
+  }
+  __syncthreads();
 
-    // ---- L along `axis` (own line from shared memory, neighbour lines from global memory)
-    if (has_cell) {
-      const int base = line_base<DIM, N>(axis, t);
-      const int st = stride_of<N>(axis);
+  // ---- phase 1: W_a = L_a u + neighbour couplings, one line per thread and axis
+  if (has_cell) {
+#pragma unroll 1
+    for (int a = 0; a < DIM; ++a) {
+      const int base = line_base<DIM, N>(a, t);
+      const int st = stride_of<N>(a);
       T u[N], w[N];
 #pragma unroll
       for (int m = 0; m < N; ++m) u[m] = s_u[c][base + m * st];
-#pragma unroll
-      for (int r = 0; r < N; ++r) {
-        T acc = T(0);
-#pragma unroll
-        for (int m = 0; m < N; ++m) acc = fma(s_l[c][0][r * N + m], u[m], acc);
-        w[r] = acc;
+      if (uniform) {
+        int v = inside ? 1 : 0;
+        v |= bit(fl, bit_full(2 * a)) ? 2 : 0;
+        v |= bit(fl, bit_gp(2 * a)) ? 4 : 0;
+        v |= bit(fl, bit_full(2 * a + 1)) ? 8 : 0;
+        v |= bit(fl, bit_gp(2 * a + 1)) ? 16 : 0;
+        apply_line<T, N>(d.lself + v * NN, kap, u, w, ADJ, false);
+      } else {
+        apply_line<T, N>(s_l[c][a][0], T(1), u, w, false, false);
       }
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
-        const int f = 2 * axis + s;
-        if (nb[f] >= 0 && (bit(fl, bit_full(f)) || bit(fl, bit_gp(f)))) {
-          const T *xn = x + (size_t)nb[f] * ND + base;
+        const int f = 2 * a + s;
+        if (nb[f] < 0) continue;
+        const bool full = bit(fl, bit_full(f));
+        const bool gp = bit(fl, bit_gp(f));
+        if (!full && !gp) continue;
+        T un[N];
+        const T *xn = x + (size_t)nb[f] * ND + base;
 #pragma unroll
-          for (int m = 0; m < N; ++m) u[m] = __ldg(xn + m * st);
-#pragma unroll
-          for (int r = 0; r < N; ++r) {
-            T acc = w[r];
-#pragma unroll
-            for (int m = 0; m < N; ++m) acc = fma(s_l[c][1 + s][r * N + m], u[m], acc);
-            w[r] = acc;
+        for (int m = 0; m < N; ++m) un[m] = __ldg(xn + m * st);
+        if (gp) {
+          if (uniform) {
+            // transpose of the neighbour's table entry (its face 1 - s) for the adjoint
+            const T *Lg = d.lnbgp + (2 * (ADJ ? 1 - s : s) + (full ? 1 : 0)) * NN;
+            apply_line<T, N>(Lg, kap, un, w, ADJ, true);
+          } else {
+            apply_line<T, N>(s_l[c][a][1 + s], T(1), un, w, false, true);
           }
+        } else {
+          // rank-2 SIPG coupling (the transposed coupling of a symmetric flux is the same form)
+          const T alpha = un[s ? 0 : N - 1];
+          T beta = T(0);
+#pragma unroll
+          for (int m = 0; m < N; ++m) beta = fma(tab.dnb[s][m], un[m], beta);
+          const T ca = T(0.5) * sc.hf * kap * alpha;
+#pragma unroll
+          for (int r = 0; r < N; ++r) w[r] = fma(ca, tab.dow[s][r], w[r]);
+          w[s ? N - 1 : 0] -= sc.hf * (T(0.5) * knb[f] * beta + sc.sipg_over_h * kavg[f] * alpha);
         }
       }
 #pragma unroll
-      for (int r = 0; r < N; ++r) s_w[c][base + r * st] = w[r];
-    }
-    __syncthreads();
-
-    // ---- 1D mass along the other axes, accumulate into s_y
-#pragma unroll 1
-    for (int ob = 0; ob < DIM; ++ob) {
-      if (ob == axis) continue;
-      const bool last = (ob == DIM - 1) || (axis == DIM - 1 && ob == DIM - 2);
-      if (has_cell) {
-        const int base = line_base<DIM, N>(ob, t);
-        const int st = stride_of<N>(ob);
-        T v[N];
-#pragma unroll
-        for (int m = 0; m < N; ++m) v[m] = s_w[c][base + m * st];
-#pragma unroll
-        for (int r = 0; r < N; ++r) {
-          T acc = T(0);
-#pragma unroll
-          for (int m = 0; m < N; ++m) acc = fma(mass[r * N + m], v[m], acc);
-          if (last)
-            s_y[c][base + r * st] += acc;
-          else
-            s_w[c][base + r * st] = acc;
-        }
-      }
-      __syncthreads();
+      for (int r = 0; r < N; ++r) s_w[a][c][base + r * st] = w[r];
     }
   }
+  __syncthreads();
 
-  {
-    const int ncell = min(CPB, d.n_active - first);
-    T *dst = y + (size_t)first * ND;
-    for (int i = tid; i < ncell * ND; i += blockDim.x) dst[i] = (&s_y[0][0])[i];
+  // ---- phase 2: in-face mass sweeps (M symmetric: the adjoint uses the same sweeps)
+  const T *M = tab.mass;
+  if constexpr (DIM == 2) {
+    if (has_cell) {
+      mass_line<T, N>(M, s_w[0][c], line_base<DIM, N>(1, t), N);  // M_y W_x
+      mass_line<T, N>(M, s_w[1][c], line_base<DIM, N>(0, t), 1);  // M_x W_y
+    }
+    __syncthreads();
+    if (has_cell) {
+      // y = W_x + W_y; thread t writes the x-line t
+      const int base = line_base<DIM, N>(0, t);
+#pragma unroll
+      for (int r = 0; r < N; ++r)
+        y[(size_t)e * ND + base + r] = s_w[0][c][base + r] + s_w[1][c][base + r];
+    }
+  } else {
+    if (has_cell) {
+      mass_line<T, N>(M, s_w[0][c], line_base<DIM, N>(1, t), N);  // W_x <- M_y W_x
+      mass_line<T, N>(M, s_w[2][c], line_base<DIM, N>(0, t), 1);  // W_z <- M_x W_z
+    }
+    __syncthreads();
+    if (has_cell) {
+      // W_x += M_x W_y (x-lines)
+      const int bx = line_base<DIM, N>(0, t);
+      T a[N];
+#pragma unroll
+      for (int m = 0; m < N; ++m) a[m] = s_w[1][c][bx + m];
+#pragma unroll
+      for (int r = 0; r < N; ++r) {
+        T acc = s_w[0][c][bx + r];
+#pragma unroll
+        for (int m = 0; m < N; ++m) acc = fma(M[r * N + m], a[m], acc);
+        s_w[0][c][bx + r] = acc;
+      }
+      mass_line<T, N>(M, s_w[2][c], line_base<DIM, N>(1, t), N);  // W_z <- M_y W_z
+    }
+    __syncthreads();
+    if (has_cell) {
+      // y = M_z W_x + W_z along z-lines
+      const int bz = line_base<DIM, N>(2, t);
+      T a[N];
+#pragma unroll
+      for (int m = 0; m < N; ++m) a[m] = s_w[0][c][bz + m * N * N];
+#pragma unroll
+      for (int r = 0; r < N; ++r) {
+        T acc = s_w[2][c][bz + r * N * N];
+#pragma unroll
+        for (int m = 0; m < N; ++m) acc = fma(M[r * N + m], a[m], acc);
+        y[(size_t)e * ND + bz + r * N * N] = acc;
+      }
+    }
   }
 }
 
@@ -269,10 +335,49 @@ __device__ __forceinline__ void basis_1d(const PointTables<T, N> &pt, T xi, T *v
   }
 }
 
+// phi_i(xi) only.
+template <typename T, int N>
+__device__ __forceinline__ void basis_1d_val(const PointTables<T, N> &pt, T xi, T *val) {
+  T pre[N], suf[N];
+  pre[0] = T(1);
+#pragma unroll
+  for (int i = 1; i < N; ++i) pre[i] = pre[i - 1] * (xi - pt.z[i - 1]);
+  suf[N - 1] = T(1);
+#pragma unroll
+  for (int i = N - 2; i >= 0; --i) suf[i] = suf[i + 1] * (xi - pt.z[i + 1]);
+#pragma unroll
+  for (int i = 0; i < N; ++i) val[i] = pre[i] * suf[i] * pt.den_inv[i];
+}
+
+// Lines per chunk (= threads per CTA) of the cut-cell kernel; bounded by the per-line shared
+// memory (2 n^{d-1} + 2 n values per line).
 template <int N>
 __host__ __device__ constexpr int cut_chunk() {
-  return (N <= 5) ? 128 : (N <= 8 ? 64 : 32);
+  return (N <= 6) ? 32 : 16;
 }
+
+// Other axes of a line along axis k (lower first) in 3D.
+__device__ __forceinline__ void other_axes(int k, int &b, int &c) {
+  b = (k == 0) ? 1 : 0;
+  c = (k == 2) ? 1 : 2;
+}
+
+// Dynamic shared memory of the cut-cell kernel (offsets in elements of T, then CH ints).
+template <typename T, int DIM, int N>
+struct CutSmem {
+  static constexpr int ND = Geo<DIM, N>::ND, NL = Geo<DIM, N>::NL, NF = Geo<DIM, N>::NF;
+  static constexpr int CH = cut_chunk<N>();
+  static constexpr int u = 0;                    // [ND] the cell's DoFs
+  static constexpr int acc = u + ND;             // [ND] accumulated output rows
+  static constexpr int lt0 = acc + ND;           // [CH][NL] per line partial integrals
+  static constexpr int lt1 = lt0 + CH * NL;
+  static constexpr int lvb = lt1 + CH * NL;      // [CH][N] per line outer basis (values)
+  static constexpr int ldb = lvb + CH * N;       // [CH][N] (derivatives)
+  static constexpr int tr = ldb + CH * N;        // [NF][4][NL] traces of every cut face
+  static constexpr int ft = tr + NF * 4 * NL;    // [NF][2][NL] face accumulators
+  static constexpr int total = ft + NF * 2 * NL;
+  static constexpr size_t bytes = (size_t)total * sizeof(T) + CH * sizeof(int);
+};
 
 template <typename T, int DIM, int N>
 __global__ void __launch_bounds__(cut_chunk<N>()) cut_kernel(const __grid_constant__ PointTables<T, N> pt,
@@ -280,16 +385,21 @@ __global__ void __launch_bounds__(cut_chunk<N>()) cut_kernel(const __grid_consta
                                                             T *__restrict__ y,
                                                             const T *__restrict__ x) {
   using G = Geo<DIM, N>;
+  using SM = CutSmem<T, DIM, N>;
   constexpr int ND = G::ND, NL = G::NL, NF = G::NF;
-  constexpr int CH = cut_chunk<N>();
-  constexpr int PSTRIDE = 2 * DIM * N + DIM + 1;  // per point: values, derivatives, coefficients
+  constexpr int CH = SM::CH;
 
-  __shared__ T s_u[ND];
-  __shared__ T s_un[ND];
-  __shared__ T s_acc[ND];
-  __shared__ T s_pts[CH * PSTRIDE];
-  __shared__ T s_tr[4][NL];   // traces: own value, own d/dn, neighbour value, neighbour d/dn
-  __shared__ T s_ft[2][NL];   // face accumulators: value, d/dn
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *sm = reinterpret_cast<T *>(smem_raw);
+  T *s_u = sm + SM::u;
+  T *s_acc = sm + SM::acc;
+  T (*s_lt0)[NL] = reinterpret_cast<T (*)[NL]>(sm + SM::lt0);
+  T (*s_lt1)[NL] = reinterpret_cast<T (*)[NL]>(sm + SM::lt1);
+  T (*s_lvb)[N] = reinterpret_cast<T (*)[N]>(sm + SM::lvb);
+  T (*s_ldb)[N] = reinterpret_cast<T (*)[N]>(sm + SM::ldb);
+  T (*s_tr)[4][NL] = reinterpret_cast<T (*)[4][NL]>(sm + SM::tr);
+  T (*s_ft)[2][NL] = reinterpret_cast<T (*)[2][NL]>(sm + SM::ft);
+  int *s_tag = reinterpret_cast<int *>(sm + SM::total);
 
   const int tid = threadIdx.x;
   const int slot = blockIdx.x;
@@ -305,243 +415,307 @@ __global__ void __launch_bounds__(cut_chunk<N>()) cut_kernel(const __grid_consta
   }
   __syncthreads();
 
-  // ---- volume (Poisson) and surface (Nitsche) points
+  // ---- volume (Poisson) and surface (Nitsche) points, line by line (Eq. unstructured_cell:
+  // the contractions along the two outer axes are shared by every point of a line)
 #pragma unroll 1
-  for (int pass = 0; pass < 2; ++pass) {
-    const int beg = __ldg((pass == 0 ? d.vol_off : d.surf_off) + ci);
-    const int end = __ldg((pass == 0 ? d.vol_off : d.surf_off) + ci + 1);
+  for (int k = 0; k < DIM; ++k) {
+    const int lbeg = __ldg(d.vline_koff + ci * 4 + k);
+    const int lend = __ldg(d.vline_koff + ci * 4 + k + 1);
+    int ob = 0, oc = 0;
+    if constexpr (DIM == 3) {
+      other_axes(k, ob, oc);
+    } else {
+      ob = 1 - k;
+    }
+    const int sk = stride_of<N>(k), sb = stride_of<N>(ob), scc = stride_of<N>(oc);
 #pragma unroll 1
-    for (int p0 = beg; p0 < end; p0 += CH) {
-      const int q = p0 + tid;
-      T *mine = s_pts + tid * PSTRIDE;
-      if (q < end) {
-        T val[DIM][N], der[DIM][N];
+    for (int l0 = lbeg; l0 < lend; l0 += CH) {
+      const int line = l0 + tid;
+      if (line < lend) {
+        T vb[N], db[N], vc[N], dc[N];
+        basis_1d<T, N>(pt, __ldg(d.vline_o0 + line), vb, db);
+        if constexpr (DIM == 3) basis_1d<T, N>(pt, __ldg(d.vline_o1 + line), vc, dc);
+        // w0 = (phi_b phi_c) u, w1 = (phi_b' phi_c) u, w2 = (phi_b phi_c') u along the line
+        T w0[N], w1[N], w2[N];
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) {
-          const T xi = __ldg((pass == 0 ? d.vol_xi[a] : d.surf_xi[a]) + q);
-          basis_1d<T, N>(pt, xi, val[a], der[a]);
+        for (int m = 0; m < N; ++m) {
+          w0[m] = T(0);
+          w1[m] = T(0);
+          w2[m] = T(0);
         }
-        // value and reference gradient at the point, one direction at a time
-        T u = T(0), g[DIM];
+        constexpr int NC = (DIM == 3) ? N : 1;
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) g[a] = T(0);
-        if constexpr (DIM == 3) {
+        for (int m = 0; m < N; ++m) {
 #pragma unroll
-          for (int k = 0; k < N; ++k) {
-            T t0 = T(0), t1 = T(0), t2 = T(0);
-#pragma unroll
-            for (int j = 0; j < N; ++j) {
-              T s0 = T(0), s1 = T(0);
-#pragma unroll
-              for (int i = 0; i < N; ++i) {
-                const T v = s_u[i + N * j + N * N * k];
-                s0 = fma(val[0][i], v, s0);
-                s1 = fma(der[0][i], v, s1);
-              }
-              t0 = fma(val[1][j], s0, t0);
-              t1 = fma(der[1][j], s0, t1);
-              t2 = fma(val[1][j], s1, t2);
-            }
-            u = fma(val[2][k], t0, u);
-            g[2] = fma(der[2][k], t0, g[2]);
-            g[1] = fma(val[2][k], t1, g[1]);
-            g[0] = fma(val[2][k], t2, g[0]);
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < N; ++j) {
+          for (int ic = 0; ic < NC; ++ic) {
             T s0 = T(0), s1 = T(0);
 #pragma unroll
-            for (int i = 0; i < N; ++i) {
-              const T v = s_u[i + N * j];
-              s0 = fma(val[0][i], v, s0);
-              s1 = fma(der[0][i], v, s1);
+            for (int ib = 0; ib < N; ++ib) {
+              const T v = s_u[ib * sb + ic * scc + m * sk];
+              s0 = fma(vb[ib], v, s0);
+              s1 = fma(db[ib], v, s1);
             }
-            u = fma(val[1][j], s0, u);
-            g[1] = fma(der[1][j], s0, g[1]);
-            g[0] = fma(val[1][j], s1, g[0]);
+            if constexpr (DIM == 3) {
+              w0[m] = fma(vc[ic], s0, w0[m]);
+              w1[m] = fma(vc[ic], s1, w1[m]);
+              w2[m] = fma(dc[ic], s0, w2[m]);
+            } else {
+              w0[m] = s0;
+              w1[m] = s1;
+            }
           }
         }
-        T cv, cg[DIM];
-        if (pass == 0) {
+        T z0[N], z1[N], z2[N];
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+          z0[m] = T(0);
+          z1[m] = T(0);
+          z2[m] = T(0);
+        }
+        const int pb = __ldg(d.vpt_off + line), pe = __ldg(d.vpt_off + line + 1);
+        const T cfv = kap * sc.inv_h2;
+#pragma unroll 1
+        for (int p = pb; p < pe; ++p) {
+          T cv[N], cd[N];
+          basis_1d<T, N>(pt, __ldg(d.vpt_t + p), cv, cd);
+          T gk = T(0), gb = T(0), gc = T(0);
+#pragma unroll
+          for (int m = 0; m < N; ++m) {
+            gk = fma(cd[m], w0[m], gk);
+            gb = fma(cv[m], w1[m], gb);
+            if constexpr (DIM == 3) gc = fma(cv[m], w2[m], gc);
+          }
           // kappa int grad v . grad u: reference gradients carry 1/h each
-          const T wk = kap * __ldg(d.vol_w + q) * sc.inv_h2;
-          cv = T(0);
+          const T cf = cfv * __ldg(d.vpt_w + p);
+          gk *= cf;
+          gb *= cf;
+          gc *= cf;
 #pragma unroll
-          for (int a = 0; a < DIM; ++a) cg[a] = wk * g[a];
-        } else {
-          // kappa int_Gamma [ -d_n v u - v d_n u + tau/h v u ]
-          const T wk = kap * __ldg(d.surf_w + q);
-          T nr[DIM];
-          T dn = T(0);
-#pragma unroll
-          for (int a = 0; a < DIM; ++a) {
-            nr[a] = __ldg(d.surf_n[a] + q);
-            dn = fma(nr[a], g[a], dn);
+          for (int m = 0; m < N; ++m) {
+            z0[m] = fma(gk, cd[m], z0[m]);
+            z1[m] = fma(gb, cv[m], z1[m]);
+            if constexpr (DIM == 3) z2[m] = fma(gc, cv[m], z2[m]);
           }
-          dn *= sc.inv_h;
-          cv = wk * (sc.nitsche_over_h * u - dn);
-#pragma unroll
-          for (int a = 0; a < DIM; ++a) cg[a] = -wk * u * nr[a] * sc.inv_h;
         }
+        const int sp = __ldg(d.lsurf + line);
+        if (sp >= 0) {
+          // kappa int_Gamma [ -d_n v u - v d_n u + tau/h v u ]
+          T cv[N], cd[N];
+          basis_1d<T, N>(pt, __ldg(d.spt_t + sp), cv, cd);
+          T u = T(0), gk = T(0), gb = T(0), gc = T(0);
 #pragma unroll
-        for (int a = 0; a < DIM; ++a)
-#pragma unroll
-          for (int i = 0; i < N; ++i) {
-            mine[a * N + i] = val[a][i];
-            mine[DIM * N + a * N + i] = der[a][i];
+          for (int m = 0; m < N; ++m) {
+            u = fma(cv[m], w0[m], u);
+            gk = fma(cd[m], w0[m], gk);
+            gb = fma(cv[m], w1[m], gb);
+            if constexpr (DIM == 3) gc = fma(cv[m], w2[m], gc);
           }
-        mine[2 * DIM * N] = cv;
+          const T nk = __ldg(d.spt_n[k] + sp), nb = __ldg(d.spt_n[ob] + sp);
+          const T nc = (DIM == 3) ? __ldg(d.spt_n[oc] + sp) : T(0);
+          const T wk = kap * __ldg(d.spt_w + sp);
+          const T dn = (nk * gk + nb * gb + nc * gc) * sc.inv_h;
+          const T cval = wk * (sc.nitsche_over_h * u - dn);
+          const T cu = -wk * u * sc.inv_h;
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) mine[2 * DIM * N + 1 + a] = cg[a];
-      } else {
-        for (int i = 0; i < PSTRIDE; ++i) mine[i] = T(0);
+          for (int m = 0; m < N; ++m) {
+            z0[m] = fma(cval, cv[m], fma(cu * nk, cd[m], z0[m]));
+            z1[m] = fma(cu * nb, cv[m], z1[m]);
+            if constexpr (DIM == 3) z2[m] = fma(cu * nc, cv[m], z2[m]);
+          }
+        }
+        // partial integration along the upper other axis; the lower one is done by the DoFs
+#pragma unroll
+        for (int ic = 0; ic < NC; ++ic)
+#pragma unroll
+          for (int m = 0; m < N; ++m) {
+            if constexpr (DIM == 3) {
+              s_lt0[tid][ic * N + m] = fma(vc[ic], z0[m], dc[ic] * z2[m]);
+              s_lt1[tid][ic * N + m] = vc[ic] * z1[m];
+            } else {
+              s_lt0[tid][m] = z0[m];
+              s_lt1[tid][m] = z1[m];
+            }
+          }
+#pragma unroll
+        for (int ib = 0; ib < N; ++ib) {
+          s_lvb[tid][ib] = vb[ib];
+          s_ldb[tid][ib] = db[ib];
+        }
       }
       __syncthreads();
-      const int npt = min(CH, end - p0);
-      // integrate: every DoF gathers the chunk's points (transposed contraction)
+      const int nlines = min(CH, lend - l0);
       for (int l = tid; l < ND; l += CH) {
-        const int i0 = l % N;
-        const int i1 = (l / N) % N;
+        const int ib = (l / sb) % N, m = (l / sk) % N;
+        const int col = (DIM == 3) ? (((l / scc) % N) * N + m) : m;
         T acc = T(0);
-        if constexpr (DIM == 3) {
-          const int i2 = l / (N * N);
-#pragma unroll 4
-          for (int pidx = 0; pidx < npt; ++pidx) {
-            const T *pp = s_pts + pidx * PSTRIDE;
-            const T v0 = pp[i0], v1 = pp[N + i1], v2 = pp[2 * N + i2];
-            const T d0 = pp[3 * N + i0], d1 = pp[4 * N + i1], d2 = pp[5 * N + i2];
-            const T cv = pp[6 * N], c0 = pp[6 * N + 1], c1 = pp[6 * N + 2], c2 = pp[6 * N + 3];
-            const T v12 = v1 * v2;
-            acc = fma(fma(cv, v0, c0 * d0), v12, acc);
-            acc = fma(v0, fma(c1 * d1, v2, c2 * v1 * d2), acc);
-          }
-        } else {
-#pragma unroll 4
-          for (int pidx = 0; pidx < npt; ++pidx) {
-            const T *pp = s_pts + pidx * PSTRIDE;
-            const T v0 = pp[i0], v1 = pp[N + i1];
-            const T d0 = pp[2 * N + i0], d1 = pp[3 * N + i1];
-            const T cv = pp[4 * N], c0 = pp[4 * N + 1], c1 = pp[4 * N + 2];
-            acc = fma(fma(cv, v0, c0 * d0), v1, acc);
-            acc = fma(v0 * c1, d1, acc);
-          }
-        }
+        for (int q = 0; q < nlines; ++q)
+          acc = fma(s_lvb[q][ib], s_lt0[q][col], fma(s_ldb[q][ib], s_lt1[q][col], acc));
         s_acc[l] += acc;
       }
       __syncthreads();
     }
   }
 
-  // ---- SIPG on cut faces: F cap Omega with unstructured in-face points (Eq. unstructured_face)
-#pragma unroll 1
-  for (int f = 0; f < NF; ++f) {
-    if (!bit(fl, bit_cut(f))) continue;
-    const int beg = __ldg(d.cface_off + (size_t)ci * NF + f);
-    const int end = __ldg(d.cface_off + (size_t)ci * NF + f + 1);
-    if (end <= beg) continue;
-    const int axis = f / 2, side = f % 2;
-    const int nbe = __ldg(d.nbr + (size_t)e * NF + f);
-    const T knb = __ldg(d.kappa + nbe);
-    const T kavg = T(0.5) * (kap + knb);
-    const T sgn = side ? T(1) : T(-1);
-    const int st = stride_of<N>(axis);
-    for (int i = tid; i < ND; i += CH) s_un[i] = __ldg(x + (size_t)nbe * ND + i);
-    __syncthreads();
-    // traces on the face: values (delta property of the Lobatto basis) and n_K-derivatives
-    for (int tl = tid; tl < NL; tl += CH) {
+  // ---- SIPG on cut faces: F cap Omega, in-face lines (Eq. unstructured_face).  All cut faces
+  // of the cell are processed together so that the warp's lanes stay busy.
+  int cfl[NF];
+  int ncf = 0;
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+    if (bit(fl, bit_cut(f))) cfl[ncf++] = f;
+  if (ncf > 0) {
+    // traces on each cut face: values (delta property of the Lobatto basis) and
+    // n_K-derivatives, indexed by the in-face DoF tl = i_b' + n i_c' (b' < c' in-face axes);
+    // the neighbour's lines are read from global memory (L2)
+    for (int item = tid; item < ncf * NL; item += CH) {
+      const int fi = item / NL, tl = item % NL;
+      const int f = cfl[fi], axis = f / 2, side = f % 2;
+      const int nbe = __ldg(d.nbr + (size_t)e * NF + f);
       const int base = line_base<DIM, N>(axis, tl);
+      const int st = stride_of<N>(axis);
+      const T *xn = x + (size_t)nbe * ND + base;
       T ov = T(0), od = T(0), nv = T(0), nd = T(0);
 #pragma unroll
       for (int m = 0; m < N; ++m) {
         const T uo = s_u[base + m * st];
-        const T un = s_un[base + m * st];
+        const T un = __ldg(xn + m * st);
         ov = fma(pt.end_val[side][m], uo, ov);
         od = fma(pt.end_der[side][m], uo, od);
         nv = fma(pt.end_val[1 - side][m], un, nv);
         nd = fma(pt.end_der[1 - side][m], un, nd);
       }
-      s_tr[0][tl] = ov;
-      s_tr[1][tl] = sgn * sc.inv_h * od;
-      s_tr[2][tl] = nv;
-      s_tr[3][tl] = sgn * sc.inv_h * nd;
-      s_ft[0][tl] = T(0);
-      s_ft[1][tl] = T(0);
+      const T sgn = side ? T(1) : T(-1);
+      s_tr[fi][0][tl] = ov;
+      s_tr[fi][1][tl] = sgn * sc.inv_h * od;
+      s_tr[fi][2][tl] = nv;
+      s_tr[fi][3][tl] = sgn * sc.inv_h * nd;
+      s_ft[fi][0][tl] = T(0);
+      s_ft[fi][1][tl] = T(0);
     }
     __syncthreads();
-    constexpr int FSTRIDE = 2 * N + 2;
+    const int *koff_cell = d.fline_koff + (size_t)ci * NF * 3;
+    const int fl_beg = __ldg(koff_cell);
+    const int fl_end = __ldg(koff_cell + (NF - 1) * 3 + 2);
 #pragma unroll 1
-    for (int p0 = beg; p0 < end; p0 += CH) {
-      const int q = p0 + tid;
-      T *mine = s_pts + tid * FSTRIDE;
-      if (q < end) {
-        T vb[N], vc[N], dummy[N];
-        basis_1d<T, N>(pt, __ldg(d.cface_eta[0] + q), vb, dummy);
-        if constexpr (DIM == 3) {
-          basis_1d<T, N>(pt, __ldg(d.cface_eta[1] + q), vc, dummy);
-        } else {
-#pragma unroll
-          for (int i = 0; i < N; ++i) vc[i] = (i == 0) ? T(1) : T(0);
-        }
-        T ev[4] = {T(0), T(0), T(0), T(0)};
-        constexpr int NC = (DIM == 3) ? N : 1;
-#pragma unroll
-        for (int tc = 0; tc < NC; ++tc) {
-          T part[4] = {T(0), T(0), T(0), T(0)};
-#pragma unroll
-          for (int tb = 0; tb < N; ++tb) {
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) part[kk] = fma(vb[tb], s_tr[kk][tb + N * tc], part[kk]);
+    for (int l0 = fl_beg; l0 < fl_end; l0 += CH) {
+      const int line = l0 + tid;
+      int tag = -1;
+      if (line < fl_end) {
+        int fi = 0, kk = 0;
+        for (int j = 0; j < ncf; ++j) {
+          const int *ko = koff_cell + cfl[j] * 3;
+          if (line >= __ldg(ko) && line < __ldg(ko + 2)) {
+            fi = j;
+            kk = (line < __ldg(ko + 1)) ? 0 : 1;
           }
-#pragma unroll
-          for (int kk = 0; kk < 4; ++kk) ev[kk] = fma(vc[tc], part[kk], ev[kk]);
         }
-        const T w = __ldg(d.cface_w + q);
-        const T jump = ev[0] - ev[2];
-        const T avg = T(0.5) * (kap * ev[1] + knb * ev[3]);
-        // coefficients of the own trace value and own normal derivative of the test function
-        const T cvv = w * (sc.sipg_over_h * kavg * jump - avg);
-        const T cdd = w * (T(-0.5) * kap * jump);
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-          mine[i] = vb[i];
-          mine[N + i] = vc[i];
+        tag = 2 * fi + kk;
+        const int f = cfl[fi];
+        const int nbe = __ldg(d.nbr + (size_t)e * NF + f);
+        const T knb = __ldg(d.kappa + nbe);
+        const T kavg = T(0.5) * (kap + knb);
+        // in-face strides of the line axis and of the outer axis in tl = i_b' + n i_c'
+        const int s_line = (kk == 0) ? 1 : N, s_out = (kk == 0) ? N : 1;
+        T vo[N];
+        if constexpr (DIM == 3) {
+          basis_1d_val<T, N>(pt, __ldg(d.fline_o + line), vo);
         }
-        mine[2 * N] = cvv;
-        mine[2 * N + 1] = cdd;
-      } else {
-        for (int i = 0; i < FSTRIDE; ++i) mine[i] = T(0);
+        // traces contracted along the outer in-face axis
+        T r[4][N];
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if constexpr (DIM == 3) {
+              T acc = T(0);
+#pragma unroll
+              for (int io = 0; io < N; ++io) acc = fma(vo[io], s_tr[fi][q][io * s_out + m * s_line], acc);
+              r[q][m] = acc;
+            } else {
+              r[q][m] = s_tr[fi][q][m];
+            }
+          }
+        }
+        T zv[N], zd[N];
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+          zv[m] = T(0);
+          zd[m] = T(0);
+        }
+        const int pb = __ldg(d.fpt_off + line), pe = __ldg(d.fpt_off + line + 1);
+#pragma unroll 1
+        for (int p = pb; p < pe; ++p) {
+          T cv[N];
+          basis_1d_val<T, N>(pt, __ldg(d.fpt_t + p), cv);
+          T ev[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+          for (int m = 0; m < N; ++m)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) ev[q] = fma(cv[m], r[q][m], ev[q]);
+          const T w = __ldg(d.fpt_w + p);
+          const T jump = ev[0] - ev[2];
+          const T avg = T(0.5) * (kap * ev[1] + knb * ev[3]);
+          // coefficients of the own trace value and own normal derivative of the test function
+          const T cvv = w * (sc.sipg_over_h * kavg * jump - avg);
+          const T cdd = w * (T(-0.5) * kap * jump);
+#pragma unroll
+          for (int m = 0; m < N; ++m) {
+            zv[m] = fma(cvv, cv[m], zv[m]);
+            zd[m] = fma(cdd, cv[m], zd[m]);
+          }
+        }
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+          s_lt0[tid][m] = zv[m];
+          s_lt1[tid][m] = zd[m];
+          s_lvb[tid][m] = (DIM == 3) ? vo[m] : T(1);
+        }
       }
+      s_tag[tid] = tag;
       __syncthreads();
-      const int npt = min(CH, end - p0);
-      for (int tl = tid; tl < NL; tl += CH) {
-        const int tb = tl % N, tc = tl / N;
+      const int nlines = min(CH, fl_end - l0);
+      for (int item = tid; item < ncf * NL; item += CH) {
+        const int fi = item / NL, tl = item % NL;
         T av = T(0), ad = T(0);
-        for (int pidx = 0; pidx < npt; ++pidx) {
-          const T *pp = s_pts + pidx * FSTRIDE;
-          const T phi = pp[tb] * pp[N + tc];
-          av = fma(pp[2 * N], phi, av);
-          ad = fma(pp[2 * N + 1], phi, ad);
+        for (int q = 0; q < nlines; ++q) {
+          const int tg = s_tag[q];
+          if ((tg >> 1) != fi) continue;
+          const int kk = tg & 1;
+          int m, io;
+          if constexpr (DIM == 3) {
+            m = (kk == 0) ? (tl % N) : (tl / N);
+            io = (kk == 0) ? (tl / N) : (tl % N);
+          } else {
+            m = tl;
+            io = 0;
+          }
+          av = fma(s_lvb[q][io], s_lt0[q][m], av);
+          ad = fma(s_lvb[q][io], s_lt1[q][m], ad);
         }
-        s_ft[0][tl] += av;
-        s_ft[1][tl] += ad;
+        s_ft[fi][0][tl] += av;
+        s_ft[fi][1][tl] += ad;
       }
       __syncthreads();
     }
     // expand the face accumulators into the cell: phi_l = phi_{i_a}(side) x in-face product
     for (int l = tid; l < ND; l += CH) {
-      const int ia = (l / stride_of<N>(axis)) % N;
-      int tl;
-      if constexpr (DIM == 2) {
-        tl = (axis == 0) ? l / N : l % N;
-      } else {
-        const int i0 = l % N, i1 = (l / N) % N, i2 = l / (N * N);
-        tl = (axis == 0) ? (i1 + N * i2) : (axis == 1) ? (i0 + N * i2) : (i0 + N * i1);
+      T add = T(0);
+      for (int fi = 0; fi < ncf; ++fi) {
+        const int f = cfl[fi], axis = f / 2, side = f % 2;
+        const T sgn = side ? T(1) : T(-1);
+        const int ia = (l / stride_of<N>(axis)) % N;
+        int tl;
+        if constexpr (DIM == 2) {
+          tl = (axis == 0) ? l / N : l % N;
+        } else {
+          const int i0 = l % N, i1 = (l / N) % N, i2 = l / (N * N);
+          tl = (axis == 0) ? (i1 + N * i2) : (axis == 1) ? (i0 + N * i2) : (i0 + N * i1);
+        }
+        add += pt.end_val[side][ia] * s_ft[fi][0][tl] +
+               sgn * sc.inv_h * pt.end_der[side][ia] * s_ft[fi][1][tl];
       }
-      s_acc[l] += pt.end_val[side][ia] * s_ft[0][tl] +
-                  sgn * sc.inv_h * pt.end_der[side][ia] * s_ft[1][tl];
+      s_acc[l] += add;
     }
-    __syncthreads();
   }
 
   for (int i = tid; i < ND; i += CH) y[(size_t)e * ND + i] += s_acc[i];
@@ -555,16 +729,16 @@ int launch_vmult_t(const DevArrays<T> &d, const void *tables_struct, const void 
                    const Scalars<T> &s, T *y, const T *x, bool adjoint, cudaStream_t stream,
                    void *const *ev) {
   using G = Geo<DIM, N>;
-  constexpr int CPB = struct_cells_per_block<N>(G::NL);
+  constexpr int CPB = struct_cells_per_block<T, DIM, N>();
   const int threads = ((CPB * G::NL + 31) / 32) * 32;
   const int blocks = (d.n_active + CPB - 1) / CPB;
   const auto &tab = *reinterpret_cast<const StructTables<T, N> *>(tables_struct);
   if (ev) cudaEventRecord(static_cast<cudaEvent_t>(ev[0]), stream);
   if (blocks > 0) {
     if (adjoint)
-      struct_kernel<T, DIM, N, true><<<blocks, threads, 0, stream>>>(tab, d, y, x);
+      struct_kernel<T, DIM, N, true><<<blocks, threads, 0, stream>>>(tab, d, s, y, x);
     else
-      struct_kernel<T, DIM, N, false><<<blocks, threads, 0, stream>>>(tab, d, y, x);
+      struct_kernel<T, DIM, N, false><<<blocks, threads, 0, stream>>>(tab, d, s, y, x);
   }
   if (ev) cudaEventRecord(static_cast<cudaEvent_t>(ev[1]), stream);
   cudaError_t err = cudaGetLastError();
@@ -572,7 +746,13 @@ int launch_vmult_t(const DevArrays<T> &d, const void *tables_struct, const void 
   if (ev) cudaEventRecord(static_cast<cudaEvent_t>(ev[2]), stream);
   if (d.n_cut > 0) {
     const auto &ptab = *reinterpret_cast<const PointTables<T, N> *>(tables_point);
-    cut_kernel<T, DIM, N><<<d.n_cut, cut_chunk<N>(), 0, stream>>>(ptab, d, s, y, x);
+    constexpr size_t smem = CutSmem<T, DIM, N>::bytes;
+    if (smem > 48 * 1024) {
+      err = cudaFuncSetAttribute(cut_kernel<T, DIM, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+      if (err != cudaSuccess) return (int)err;
+    }
+    cut_kernel<T, DIM, N><<<d.n_cut, cut_chunk<N>(), smem, stream>>>(ptab, d, s, y, x);
   }
   if (ev) cudaEventRecord(static_cast<cudaEvent_t>(ev[3]), stream);
   return (int)cudaGetLastError();

@@ -137,7 +137,15 @@ double dist2(const double *x, const double *c, int m) {
   return r;
 }
 
-void tensor_rule(const Box &b, const Gauss1 &g, std::vector<QPoint> &out) {
+void tensor_rule(const Box &b, const Gauss1 &g, std::vector<QPoint> &out,
+                 std::vector<QLine> *lines = nullptr) {
+  if (lines) {
+    // lines along axis 0: consecutive runs of q points in the direction-0-fastest order
+    int64_t nl = 1;
+    for (int a = 1; a < b.m; ++a) nl *= g.q;
+    for (int64_t l = 0; l < nl; ++l)
+      lines->push_back(QLine{0, (int64_t)out.size() + l * g.q, g.q, -1});
+  }
   int total = 1;
   for (int a = 0; a < b.m; ++a) total *= g.q;
   for (int flat = 0; flat < total; ++flat) {
@@ -303,11 +311,12 @@ void full_box_rule(const Box &b, const std::vector<Fn> &fns, const Gauss1 &g, in
 }
 
 void sphere_box_rules(const Box &b, const double *c, double rho, const Gauss1 &g, int depth,
-                      bool surface, std::vector<QPoint> &vol, std::vector<QPoint> &surf) {
+                      bool surface, std::vector<QPoint> &vol, std::vector<QPoint> &surf,
+                      std::vector<QLine> *lines = nullptr) {
   double dmin2, dmax2;
   box_dist2(c, b, dmin2, dmax2);
   if (dmax2 <= rho) {
-    tensor_rule(b, g, vol);
+    tensor_rule(b, g, vol, lines);
     return;
   }
   if (dmin2 >= rho) return;
@@ -322,6 +331,7 @@ void sphere_box_rules(const Box &b, const double *c, double rho, const Gauss1 &g
     const int ns = nr;
     double pa[16], pb[16];
     const int np = make_pieces(b.lo[0], b.hi[0], roots, nr, pa, pb);
+    const int64_t vbeg = (int64_t)vol.size();
     for (int ip = 0; ip < np; ++ip) {
       const double mid = 0.5 * (pa[ip] + pb[ip]);
       if ((mid - c[0]) * (mid - c[0]) - rho < 0.0)
@@ -332,6 +342,8 @@ void sphere_box_rules(const Box &b, const double *c, double rho, const Gauss1 &g
           vol.push_back(p);
         }
     }
+    if (lines && (int64_t)vol.size() > vbeg)
+      lines->push_back(QLine{0, vbeg, (int64_t)vol.size() - vbeg, -1});
     if (surface)
       for (int i = 0; i < ns; ++i) {
         QPoint p{};
@@ -346,7 +358,7 @@ void sphere_box_rules(const Box &b, const double *c, double rho, const Gauss1 &g
   if (b.lo[k] < c[k] && c[k] < b.hi[k]) {
     if (depth >= kMaxDepth) throw QuadError{};
     for (int bits = 0; bits < (1 << b.m); ++bits)
-      sphere_box_rules(child(b, bits), c, rho, g, depth + 1, surface, vol, surf);
+      sphere_box_rules(child(b, bits), c, rho, g, depth + 1, surface, vol, surf, lines);
     return;
   }
   double csub[kMaxDim];
@@ -378,6 +390,8 @@ void sphere_box_rules(const Box &b, const double *c, double rho, const Gauss1 &g
     double roots[1] = {t};
     double pa[4], pb[4];
     const int np = make_pieces(b.lo[k], b.hi[k], roots, has_root ? 1 : 0, pa, pb);
+    const int64_t vbeg = (int64_t)vol.size();
+    const int64_t sidx = (surface && has_root) ? (int64_t)surf.size() : -1;
     for (int ip = 0; ip < np; ++ip) {
       const double mid = 0.5 * (pa[ip] + pb[ip]);
       const double dm = mid - c[k];
@@ -397,6 +411,8 @@ void sphere_box_rules(const Box &b, const double *c, double rho, const Gauss1 &g
       p.w = op.w * (R / std::fabs(t - c[k]));
       surf.push_back(p);
     }
+    if (lines && ((int64_t)vol.size() > vbeg || sidx >= 0))
+      lines->push_back(QLine{k, vbeg, (int64_t)vol.size() - vbeg, sidx});
   }
 }
 
@@ -621,7 +637,10 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
   op.vol_off.assign(1, 0);
   op.surf_off.assign(1, 0);
   op.cface_off.assign(1, 0);
+  op.vline_off.assign(1, 0);
+  op.fline_off.assign(1, 0);
   std::vector<QPoint> vol, surf, fq;
+  std::vector<QLine> lines;
   try {
     for (int64_t c = 0; c < op.n_cut; ++c) {
       const int64_t e = op.cut_cells[c];
@@ -634,7 +653,12 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
       }
       vol.clear();
       surf.clear();
-      sphere_box_rules(b, op.center, op.radius * op.radius, g, 0, true, vol, surf);
+      lines.clear();
+      sphere_box_rules(b, op.center, op.radius * op.radius, g, 0, true, vol, surf, &lines);
+      const int64_t vbase = (int64_t)op.vol_w.size(), sbase = (int64_t)op.surf_w.size();
+      for (const QLine &ln : lines)
+        op.vol_lines.push_back(QLine{ln.k, vbase + ln.vbeg, ln.vcnt, ln.sidx >= 0 ? sbase + ln.sidx : -1});
+      op.vline_off.push_back((int64_t)op.vol_lines.size());
       for (const QPoint &p : vol) {
         for (int a = 0; a < d; ++a) op.vol_xi[a].push_back((p.x[a] - b.lo[a]) / op.h);
         op.vol_w.push_back(p.w);
@@ -660,8 +684,11 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
           double csub[kMaxDim];
           drop_vec(op.center, d, axis, csub);
           fq.clear();
+          lines.clear();
           std::vector<QPoint> dummy;
-          sphere_box_rules(sub, csub, rho, g, 0, false, fq, dummy);
+          sphere_box_rules(sub, csub, rho, g, 0, false, fq, dummy, &lines);
+          const int64_t fbase = (int64_t)op.cface_w.size();
+          for (const QLine &ln : lines) op.face_lines.push_back(QLine{ln.k, fbase + ln.vbeg, ln.vcnt, -1});
           Box sb = drop_dim(b, axis);
           for (const QPoint &p : fq) {
             for (int a = 0; a < d - 1; ++a) op.cface_eta[a].push_back((p.x[a] - sb.lo[a]) / op.h);
@@ -670,6 +697,7 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
           if (side == 1) op.n_face_points_unique += (int64_t)fq.size();
         }
         op.cface_off.push_back((int64_t)op.cface_w.size());
+        op.fline_off.push_back((int64_t)op.face_lines.size());
       }
     }
   } catch (const QuadError &) {

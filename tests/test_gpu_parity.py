@@ -94,6 +94,17 @@ def test_parity_kappa_lognormal():
     assert _rel(_apply(op, x), A2 @ x) <= TOL64
 
 
+def test_uniform_kappa_scales_the_operator():
+    """kappa = 2.5 everywhere: A(kappa) = 2.5 A(1) (the uniform-coefficient path)."""
+    cfg = workloads.small(p=3, N=6)
+    o = forms.Oracle(mesh.problem_from_dict(cfg))
+    A = o.assemble()
+    op = _gpu_op(cfg, kappa=np.full(o.mesh.n_active, 2.5))
+    x = workloads.uniform_vector(op.n_dofs, 12)
+    assert _rel(_apply(op, x), 2.5 * (A @ x)) <= TOL64
+    assert _rel(_apply(op, x, adjoint=True), 2.5 * (A.T @ x)) <= TOL64
+
+
 def test_all_cells_inside_no_cut_cells():
     cfg = workloads.small(p=3, N=5)
     cfg.update(radius=50.0)
