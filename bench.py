@@ -57,6 +57,8 @@ def parse_args():
     ap.add_argument("--cpu-sample-cells", type=int, default=120,
                     help="cells of the oracle's bounded sample (cpu_baseline / reference arm)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-csr", action="store_true",
+                    help="skip the assembled-matrix (CSR SpMV) comparison")
     return ap.parse_args()
 
 
@@ -358,6 +360,8 @@ def run_ours(args, rank, world, local):
         "gpu_launches": int(launches),
         "clocks": clk,
     }
+    if not args.no_csr:
+        result["csr_spmv"] = csr_comparison(op, x64, flush, stream, hbm, K)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(cfg, args.cpu_sample_cells)
     if rank == 0:
@@ -365,6 +369,37 @@ def run_ours(args, rank, world, local):
     op.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def csr_comparison(op, x64, flush, stream, hbm, K):
+    """The paper's matrix-based comparison: the same operator assembled into CSR (int32
+    columns, FP64 values) on the device, and a hand-written SpMV; timed like the step."""
+    import torch
+
+    from paper_2404_07911_gb300 import UF_FP64
+
+    t0 = time.perf_counter()
+    op.assemble_csr(UF_FP64)
+    t_asm = time.perf_counter() - t0
+    nnz, byts = op.csr_info(UF_FP64)
+    y = torch.empty_like(x64)
+    for _ in range(3):
+        op.csr_spmv(x64, y, stream)
+    K = max(5, min(K, 50))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for k in range(K):
+        flush.zero_()
+        ev[k][0].record(stream)
+        op.csr_spmv(x64, y, stream)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    n = op.n_dofs
+    op.release_csr()
+    return {"ms": round(ms, 4), "gdofs": round(n / (ms / 1e3) / 1e9, 4), "nnz": nnz,
+            "algorithmic_bytes": byts, "gb_s": round(byts / (ms / 1e3) / 1e9, 1),
+            "hbm_frac": round(byts / (ms / 1e3) / 1e9 / hbm, 4), "assembly_s": round(t_asm, 2),
+            "dtype": "f64 values, int32 columns, int64 row offsets"}
 
 
 # ------------------------------------------------------------------------------ reference arm

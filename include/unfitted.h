@@ -142,6 +142,24 @@ uf_status uf_vmult_adjoint_host(uf_operator *op, int precision, void *y_host, co
 uf_status uf_profile_begin(uf_operator *op, int capacity);
 uf_status uf_profile_end(uf_operator *op, uf_kernel_times *out);
 
+/* Assembled-matrix baseline (paper Sec. 3.1 / Sec. 4.1, matrix-based evaluation).
+ * uf_assemble_csr builds the operator's matrix on the device in CSR form (int64 row offsets
+ * [n_dofs + 1], int32 column indices, values in `precision`; columns ascending per row) by
+ * applying the FP64 matrix-free operator to distance-2-coloured unit vectors (n^d applications
+ * per colour; 7 colours in 3D, 5 in 2D).  Synchronous; allocates the matrix (library-owned) and a
+ * temporary n^d x n_dofs FP64 staging block.  Needs the FP64 operator.  Errors: UF_EINVAL,
+ * UF_ENODEVICE, UF_ENOMEM (checked against free device memory first), UF_ECUDA.
+ * uf_csr_info: nonzeros and algorithmic bytes of one SpMV (values + column indices + row
+ * offsets + x + y).  uf_csr_spmv: y = A x with the assembled matrix (device pointers, stream-
+ * ordered, one warp per row).  uf_export_csr: host copies (any pointer may be NULL; values as
+ * double).  uf_release_csr: frees both precisions' matrices (NULL-safe). */
+uf_status uf_assemble_csr(uf_operator *op, int precision);
+uf_status uf_csr_info(const uf_operator *op, int precision, int64_t *nnz, double *bytes);
+uf_status uf_csr_spmv(uf_operator *op, int precision, void *y, const void *x, void *stream);
+uf_status uf_export_csr(const uf_operator *op, int precision, int64_t *row_ptr, int32_t *col,
+                        double *val);
+uf_status uf_release_csr(uf_operator *op);
+
 /* Replace kappa: host array [n_active] of positive values.  Synchronous.  Errors: UF_EINVAL. */
 uf_status uf_set_kappa(uf_operator *op, const double *kappa_host);
 

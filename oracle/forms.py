@@ -237,3 +237,23 @@ class Oracle:
                     y += blocks[(s, s)] @ X[e] + blocks[(s, 1 - s)] @ X[nb]
             out[r] = y
         return out
+
+    def kappa_gradient(self, x, r, cells=None):
+        """dk_K = r^T A_K x with A_K = dA/dkappa_K (A is linear in kappa: A = sum_K kappa_K A_K),
+        by the definition: kappa set to the indicator of K, rows of K and of its neighbours."""
+        if cells is None:
+            cells = range(self.mesh.n_active)
+        nd = self.ndof
+        R = np.asarray(r, dtype=np.float64).reshape(-1, nd)
+        saved = self.mesh.kappa.copy()
+        out = []
+        try:
+            for K in cells:
+                self.mesh.kappa[:] = 0.0
+                self.mesh.kappa[K] = 1.0
+                rows = [K] + [nb for _, _, nb in self.faces_of(K)]
+                Y = self.apply_rows(x, rows)
+                out.append(float(sum(R[c] @ Y[i] for i, c in enumerate(rows))))
+        finally:
+            self.mesh.kappa[:] = saved
+        return np.array(out)

@@ -65,7 +65,8 @@ class uf_kernel_times(ctypes.Structure):
 EXPORTED = ["uf_create_unfitted_operator", "uf_get_info", "uf_vmult", "uf_vmult_adjoint",
             "uf_vmult_host", "uf_vmult_adjoint_host", "uf_profile_begin", "uf_profile_end",
             "uf_set_kappa", "uf_export_cells", "uf_export_cut_cell_rule",
-            "uf_export_cut_face_rule", "uf_destroy", "uf_last_error"]
+            "uf_export_cut_face_rule", "uf_assemble_csr", "uf_csr_info", "uf_csr_spmv",
+            "uf_export_csr", "uf_release_csr", "uf_destroy", "uf_last_error"]
 
 _lib = None
 
@@ -96,6 +97,12 @@ def load_library(path=None):
                                             ctypes.POINTER(ctypes.c_int64)]
     lib.uf_export_cut_face_rule.argtypes = [P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, P, P,
                                             ctypes.POINTER(ctypes.c_int64)]
+    lib.uf_assemble_csr.argtypes = [P, ctypes.c_int]
+    lib.uf_csr_info.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                ctypes.POINTER(ctypes.c_double)]
+    lib.uf_csr_spmv.argtypes = [P, ctypes.c_int, P, P, P]
+    lib.uf_export_csr.argtypes = [P, ctypes.c_int, P, P, P]
+    lib.uf_release_csr.argtypes = [P]
     lib.uf_destroy.argtypes = [P]
     lib.uf_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -252,6 +259,33 @@ class UnfittedOperator:
         if k.shape != (self.info["n_active"],):
             raise ValueError("kappa must have one entry per active cell")
         _check(_lib.uf_set_kappa(self._h, k.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+    # ---- assembled-matrix baseline
+    def assemble_csr(self, precision=UF_FP64):
+        """Assemble the operator's CSR matrix on the device (synchronous)."""
+        _check(_lib.uf_assemble_csr(self._h, precision))
+
+    def csr_info(self, precision=UF_FP64):
+        nnz = ctypes.c_int64()
+        byts = ctypes.c_double()
+        _check(_lib.uf_csr_info(self._h, precision, ctypes.byref(nnz), ctypes.byref(byts)))
+        return nnz.value, byts.value
+
+    def csr_spmv(self, x, y=None, stream=None):
+        """y = A x with the assembled CSR matrix (device tensors)."""
+        return self._apply(_lib.uf_csr_spmv, x, y, stream)
+
+    def export_csr(self, precision=UF_FP64):
+        """(row_ptr, col, val) host copies of the assembled matrix."""
+        nnz, _ = self.csr_info(precision)
+        rp = np.zeros(self.n_dofs + 1, dtype=np.int64)
+        col = np.zeros(nnz, dtype=np.int32)
+        val = np.zeros(nnz)
+        _check(_lib.uf_export_csr(self._h, precision, _ptr(rp), _ptr(col), _ptr(val)))
+        return rp, col, val
+
+    def release_csr(self):
+        _check(_lib.uf_release_csr(self._h))
 
     # ---- exports of the setup product
     def export_cells(self):

@@ -13,30 +13,10 @@
 #include "../../include/unfitted.h"
 #include "uf_device.h"
 #include "uf_host.h"
+#include "uf_operator.h"
 
 namespace {
-
 thread_local std::string g_last_error;
-
-uf_status fail(uf_status st, const std::string &msg) {
-  g_last_error = msg;
-  return st;
-}
-
-template <typename T>
-struct PrecisionData {
-  bool present = false;
-  void *base = nullptr;        // one device allocation for all arrays of this precision
-  void *xbuf = nullptr;        // device staging buffers of uf_vmult_host
-  void *ybuf = nullptr;
-  T *kappa_dev = nullptr;
-  uf::DevArrays<T> arrays{};
-  std::vector<unsigned char> struct_tables;  // uf::StructTables<T, n>
-  std::vector<unsigned char> point_tables;   // uf::PointTables<T, n>
-  uf::Scalars<T> scalars{};
-  size_t device_bytes = 0;
-  int64_t n_vlines = 0, n_flines = 0;
-};
 
 // Bump allocator over a byte count (256-byte aligned sub-arrays).
 struct Layout {
@@ -47,25 +27,19 @@ struct Layout {
     return off;
   }
 };
-
 }  // namespace
 
-struct ProfSlot {
-  cudaEvent_t ev[4];
-  int prec;     // 0 FP64, 1 FP32
-  int adjoint;  // 0 vmult, 1 adjoint
-  bool used;
-};
+namespace uf {
+uf_status fail(uf_status st, const std::string &msg) {
+  g_last_error = msg;
+  return st;
+}
+}  // namespace uf
 
-struct uf_operator {
-  uf::HostOperator host;
-  int device = -1;
-  int num_sms = 0;
-  PrecisionData<double> f64;
-  PrecisionData<float> f32;
-  std::vector<ProfSlot> prof;  // non-empty while profiling
-  size_t prof_next = 0;
-};
+using uf::fail;
+using uf::PrecisionData;
+using uf::ProfSlot;
+using uf::DeviceGuard;
 
 namespace {
 
@@ -392,18 +366,6 @@ void release(PrecisionData<T> &pd) {
   pd.present = false;
 }
 
-struct DeviceGuard {
-  int prev = -1;
-  bool changed = false;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
-      changed = (cudaSetDevice(dev) == cudaSuccess);
-    }
-  }
-  ~DeviceGuard() {
-    if (changed) cudaSetDevice(prev);
-  }
-};
 
 template <typename T>
 uf_status vmult_t(uf_operator *op, PrecisionData<T> &pd, void *y, const void *x, void *stream,
@@ -436,6 +398,16 @@ uf_status check_vmult_args(uf_operator *op, int precision, void *y, const void *
   if (precision != UF_FP64 && precision != UF_FP32) return fail(UF_EINVAL, "bad precision");
   return UF_OK;
 }
+
+}  // namespace
+
+uf_status uf::vmult_launch(uf_operator *op, int precision, void *y, const void *x, void *stream,
+                           bool adjoint) {
+  if (precision == UF_FP64) return vmult_t<double>(op, op->f64, y, x, stream, adjoint);
+  return vmult_t<float>(op, op->f32, y, x, stream, adjoint);
+}
+
+namespace {
 
 uf_status vmult_dispatch(uf_operator *op, int precision, void *y, const void *x, void *stream,
                          bool adjoint) {
@@ -787,6 +759,8 @@ uf_status uf_destroy(uf_operator *op) {
   if (!op) return UF_OK;
   if (op->device >= 0) {
     DeviceGuard guard(op->device);
+    uf::release_csr(op->csr64);
+    uf::release_csr(op->csr32);
     for (ProfSlot &slot : op->prof)
       for (int k = 0; k < 4; ++k) cudaEventDestroy(slot.ev[k]);
     release(op->f64);

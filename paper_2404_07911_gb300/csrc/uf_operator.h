@@ -1,0 +1,79 @@
+// Internal definition of uf_operator (shared by uf_api.cu and uf_csr.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/unfitted.h"
+#include "uf_device.h"
+#include "uf_host.h"
+
+namespace uf {
+
+// Sets the thread-local message returned by uf_last_error and returns st.
+uf_status fail(uf_status st, const std::string &msg);
+
+template <typename T>
+struct PrecisionData {
+  bool present = false;
+  void *base = nullptr;        // one device allocation for all arrays of this precision
+  void *xbuf = nullptr;        // device staging buffers of uf_vmult_host
+  void *ybuf = nullptr;
+  T *kappa_dev = nullptr;
+  DevArrays<T> arrays{};
+  std::vector<unsigned char> struct_tables;  // StructTables<T, n>
+  std::vector<unsigned char> point_tables;   // PointTables<T, n>
+  Scalars<T> scalars{};
+  size_t device_bytes = 0;
+  int64_t n_vlines = 0, n_flines = 0;
+};
+
+struct ProfSlot {
+  cudaEvent_t ev[4];
+  int prec;     // 0 FP64, 1 FP32
+  int adjoint;  // 0 vmult, 1 adjoint
+  bool used;
+};
+
+// Assembled CSR matrix of the operator (device memory, one precision).
+struct CsrData {
+  bool present = false;
+  int64_t nnz = 0;
+  int64_t *row_ptr = nullptr;  // [n_dofs + 1]
+  int32_t *col = nullptr;      // [nnz]
+  void *val = nullptr;         // [nnz] double or float
+};
+
+// Restores the calling thread's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) changed = (cudaSetDevice(dev) == cudaSuccess);
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace uf
+
+struct uf_operator {
+  uf::HostOperator host;
+  int device = -1;
+  int num_sms = 0;
+  uf::PrecisionData<double> f64;
+  uf::PrecisionData<float> f32;
+  std::vector<uf::ProfSlot> prof;  // non-empty while profiling
+  size_t prof_next = 0;
+  uf::CsrData csr64, csr32;
+};
+
+namespace uf {
+// Launch y = A x (or A^T x) of the operator's kernels on `stream` (no argument checks).
+uf_status vmult_launch(uf_operator *op, int precision, void *y, const void *x, void *stream,
+                       bool adjoint);
+void release_csr(CsrData &c);
+}  // namespace uf
