@@ -160,6 +160,23 @@ uf_status uf_export_csr(const uf_operator *op, int precision, int64_t *row_ptr, 
                         double *val);
 uf_status uf_release_csr(uf_operator *op);
 
+/* Gradient of r^T A(kappa) x with respect to the per-cell coefficient (FP64):
+ * dk[e] = r^T (dA / dkappa_e) x for every active cell e.  A is linear in kappa, so for the loss
+ * J = 1/2 ||A(kappa) x - b||^2 the kappa gradient is this with r = A x - b (and A^T r is the
+ * x gradient, uf_vmult_adjoint).  Quadrature-point values of r and x are recomputed, nothing is
+ * stored by uf_vmult.  dk [n_active], r and x [n_dofs] are FP64 device pointers; stream-
+ * ordered; no allocation (a per-cell partial buffer owned by the operator is overwritten, so
+ * calls on one operator must not overlap on different streams).  Needs the FP64 operator.
+ * Errors: UF_EINVAL, UF_ENODEVICE, UF_ECUDA.  (Not in the paper: the differentiable operator.) */
+uf_status uf_kappa_gradient(uf_operator *op, double *dk, const double *r, const double *x,
+                            void *stream);
+
+/* Replace kappa from a DEVICE array [n_active] (FP64), stream-ordered (the FP32 copy is
+ * converted on the device); the operator then always takes the general per-cell coefficient
+ * path.  The host copy used by uf_get_info is not updated.  Errors: UF_EINVAL, UF_ENODEVICE,
+ * UF_ECUDA.  Positivity is the caller's responsibility. */
+uf_status uf_set_kappa_device(uf_operator *op, const double *kappa_dev, void *stream);
+
 /* Replace kappa: host array [n_active] of positive values.  Synchronous.  Errors: UF_EINVAL. */
 uf_status uf_set_kappa(uf_operator *op, const double *kappa_host);
 

@@ -66,7 +66,8 @@ EXPORTED = ["uf_create_unfitted_operator", "uf_get_info", "uf_vmult", "uf_vmult_
             "uf_vmult_host", "uf_vmult_adjoint_host", "uf_profile_begin", "uf_profile_end",
             "uf_set_kappa", "uf_export_cells", "uf_export_cut_cell_rule",
             "uf_export_cut_face_rule", "uf_assemble_csr", "uf_csr_info", "uf_csr_spmv",
-            "uf_export_csr", "uf_release_csr", "uf_destroy", "uf_last_error"]
+            "uf_export_csr", "uf_release_csr", "uf_kappa_gradient", "uf_set_kappa_device",
+            "uf_destroy", "uf_last_error"]
 
 _lib = None
 
@@ -103,6 +104,8 @@ def load_library(path=None):
     lib.uf_csr_spmv.argtypes = [P, ctypes.c_int, P, P, P]
     lib.uf_export_csr.argtypes = [P, ctypes.c_int, P, P, P]
     lib.uf_release_csr.argtypes = [P]
+    lib.uf_kappa_gradient.argtypes = [P, P, P, P, P]
+    lib.uf_set_kappa_device.argtypes = [P, P, P]
     lib.uf_destroy.argtypes = [P]
     lib.uf_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -259,6 +262,30 @@ class UnfittedOperator:
         if k.shape != (self.info["n_active"],):
             raise ValueError("kappa must have one entry per active cell")
         _check(_lib.uf_set_kappa(self._h, k.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+    # ---- differentiation with respect to the per-cell coefficient
+    def kappa_gradient(self, r, x, dk=None, stream=None):
+        """dk[e] = r^T (dA/dkappa_e) x (FP64 device tensors)."""
+        import torch
+
+        for t in (r, x):
+            if not (t.is_cuda and t.is_contiguous() and t.dtype == torch.float64 and t.numel() == self.n_dofs):
+                raise ValueError("r and x must be contiguous float64 CUDA tensors with n_dofs entries")
+        if dk is None:
+            dk = torch.empty(self.info["n_active"], dtype=torch.float64, device=r.device)
+        _check(_lib.uf_kappa_gradient(self._h, ctypes.c_void_p(dk.data_ptr()), ctypes.c_void_p(r.data_ptr()),
+                                      ctypes.c_void_p(x.data_ptr()), self._stream_ptr(stream)))
+        return dk
+
+    def set_kappa_device(self, kappa, stream=None):
+        """Replace kappa from a float64 CUDA tensor [n_active] (stream-ordered)."""
+        import torch
+
+        if not (kappa.is_cuda and kappa.dtype == torch.float64 and kappa.numel() == self.info["n_active"]):
+            raise ValueError("kappa must be a float64 CUDA tensor with n_active entries")
+        kappa = kappa.contiguous()
+        _check(_lib.uf_set_kappa_device(self._h, ctypes.c_void_p(kappa.data_ptr()), self._stream_ptr(stream)))
+        self._kappa_ref = kappa  # keep alive until the copy has run
 
     # ---- assembled-matrix baseline
     def assemble_csr(self, precision=UF_FP64):

@@ -327,6 +327,16 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   A.fpt_w = TP(o_fpw);
   A.lself = TP(o_lself);
   A.lnbgp = TP(o_lnbgp);
+  if (sizeof(T) == sizeof(double)) {
+    // kappa gradient (FP64): derivative tables and the per-cell partial buffer
+    std::vector<double> kg;
+    uf::kgrad_tables(H.n, mats, kg);
+    err = cudaMalloc(&op->kg_tables, kg.size() * sizeof(double));
+    if (err == cudaSuccess) err = cudaMalloc(&op->kg_scratch, (size_t)na * (1 + nf) * sizeof(double));
+    if (err != cudaSuccess) return fail(UF_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(err));
+    err = cudaMemcpy(op->kg_tables, kg.data(), kg.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (err != cudaSuccess) return fail(UF_ECUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(err));
+  }
   A.kappa_uniform = kappa_is_uniform(H.kappa) ? 1 : 0;
   A.n_active = (int32_t)na;
   A.n_cut = (int32_t)nc;
@@ -467,6 +477,8 @@ uf_status uf_create_unfitted_operator(const uf_params *params, uf_operator **out
     if (st != UF_OK) {
       release(op->f64);
       release(op->f32);
+      if (op->kg_tables) cudaFree(op->kg_tables);
+      if (op->kg_scratch) cudaFree(op->kg_scratch);
       delete op;
       return st;
     }
@@ -761,6 +773,8 @@ uf_status uf_destroy(uf_operator *op) {
     DeviceGuard guard(op->device);
     uf::release_csr(op->csr64);
     uf::release_csr(op->csr32);
+    if (op->kg_tables) cudaFree(op->kg_tables);
+    if (op->kg_scratch) cudaFree(op->kg_scratch);
     for (ProfSlot &slot : op->prof)
       for (int k = 0; k < 4; ++k) cudaEventDestroy(slot.ev[k]);
     release(op->f64);

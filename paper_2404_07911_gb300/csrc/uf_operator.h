@@ -69,6 +69,8 @@ struct uf_operator {
   std::vector<uf::ProfSlot> prof;  // non-empty while profiling
   size_t prof_next = 0;
   uf::CsrData csr64, csr32;
+  double *kg_tables = nullptr;   // kappa-derivative 1D matrices (FP64)
+  double *kg_scratch = nullptr;  // [n_active][1 + 2d] per-cell partials of the kappa gradient
 };
 
 namespace uf {
@@ -76,4 +78,6 @@ namespace uf {
 uf_status vmult_launch(uf_operator *op, int precision, void *y, const void *x, void *stream,
                        bool adjoint);
 void release_csr(CsrData &c);
+// kappa-derivative 1D matrices from the constant matrices of the structured terms.
+void kgrad_tables(int n, const std::vector<double> &m, std::vector<double> &out);
 }  // namespace uf
