@@ -171,6 +171,25 @@ uf_status uf_release_csr(uf_operator *op);
 uf_status uf_kappa_gradient(uf_operator *op, double *dk, const double *r, const double *x,
                             void *stream);
 
+/* uf_kappa_gradient without any device allocation by the library for the call: the per-cell
+ * partial buffer is a fixed array in the library's device memory instead of the operator's own.
+ * (The paper has no counterpart; this serves callers that cannot allocate device memory, such as
+ * applications whose device memory is entirely held by another allocator, e.g. a framework's
+ * caching pool, or time-critical loops that cannot accept the device-wide synchronisation that
+ * allocation can cause.)  Same arguments, results and errors as uf_kappa_gradient, plus:
+ *  - limit: n_active * (1 + 2 dim) <= 2^20 doubles (8 MiB; 149,796 active cells in 3D,
+ *    209,715 in 2D); larger operators are rejected with UF_EINVAL and a message;
+ *  - the fixed array exists once per device that loads the library and stays allocated until
+ *    the process exits; the first call on a device looks up its address (cudaGetSymbolAddress,
+ *    with that device current) and caches it, so that first call should come before any stream
+ *    capture;
+ *  - every call on a device shares the one array and leaves its contents behind: calls whose
+ *    kernels overlap on the GPU (different streams, or different operators on one device) race
+ *    and must be serialised by the caller.
+ * The call itself performs no cudaMalloc / cudaFree; the operator was allocated at creation. */
+uf_status uf_kappa_gradient_noalloc(uf_operator *op, double *dk, const double *r,
+                                    const double *x, void *stream);
+
 /* Replace kappa from a DEVICE array [n_active] (FP64), stream-ordered (the FP32 copy is
  * converted on the device); the operator then always takes the general per-cell coefficient
  * path.  The host copy used by uf_get_info is not updated.  Errors: UF_EINVAL, UF_ENODEVICE,

@@ -66,7 +66,8 @@ EXPORTED = ["uf_create_unfitted_operator", "uf_get_info", "uf_vmult", "uf_vmult_
             "uf_vmult_host", "uf_vmult_adjoint_host", "uf_profile_begin", "uf_profile_end",
             "uf_set_kappa", "uf_export_cells", "uf_export_cut_cell_rule",
             "uf_export_cut_face_rule", "uf_assemble_csr", "uf_csr_info", "uf_csr_spmv",
-            "uf_export_csr", "uf_release_csr", "uf_kappa_gradient", "uf_set_kappa_device",
+            "uf_export_csr", "uf_release_csr", "uf_kappa_gradient", "uf_kappa_gradient_noalloc",
+            "uf_set_kappa_device",
             "uf_destroy", "uf_last_error"]
 
 _lib = None
@@ -105,6 +106,7 @@ def load_library(path=None):
     lib.uf_export_csr.argtypes = [P, ctypes.c_int, P, P, P]
     lib.uf_release_csr.argtypes = [P]
     lib.uf_kappa_gradient.argtypes = [P, P, P, P, P]
+    lib.uf_kappa_gradient_noalloc.argtypes = [P, P, P, P, P]
     lib.uf_set_kappa_device.argtypes = [P, P, P]
     lib.uf_destroy.argtypes = [P]
     lib.uf_last_error.restype = ctypes.c_char_p

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -499,11 +500,64 @@ void kgrad_tables(int n, const std::vector<double> &m, std::vector<double> &out)
   for (int i = 0; i < nn; ++i) out[kKgMats * nn + i] = m[nn + i];
 }
 
+// ---- fixed partial buffer of uf_kappa_gradient_noalloc ----------------------------------
+// 2^20 doubles (8 MiB), resident on every device that loads the library until the process exits.
+// One slot per (cell, 1 + 2d): at most 149,796 active cells in 3D, 209,715 in 2D.
+constexpr size_t kStaticPartialDoubles = (size_t)1 << 20;
+static __device__ __align__(256) double g_kgrad_partials[kStaticPartialDoubles];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_partials_mutex;
+double *g_partials_addr[kMaxDevices] = {};  // device address of g_kgrad_partials per device
+}  // namespace
+
+// Device address of the fixed buffer on `device` (which must be current).  The host-side name of
+// the array is only a stand-in, so the address is looked up once per device and cached.
+static uf_status static_partials(int device, double **out) {
+  if (device < 0 || device >= kMaxDevices) return fail(UF_EINVAL, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_partials_mutex);
+  if (!g_partials_addr[device]) {
+    void *addr = nullptr;
+    cudaError_t err = cudaGetSymbolAddress(&addr, g_kgrad_partials);
+    if (err != cudaSuccess)
+      return fail(UF_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(err));
+    g_partials_addr[device] = static_cast<double *>(addr);
+  }
+  *out = g_partials_addr[device];
+  return UF_OK;
+}
+
 }  // namespace uf
 
 using uf::fail;
 
 extern "C" {
+
+uf_status uf_kappa_gradient_noalloc(uf_operator *op, double *dk, const double *r,
+                                    const double *x, void *stream) {
+  if (!op || !dk || !r || !x) return fail(UF_EINVAL, "NULL argument");
+  if (op->device < 0) return fail(UF_ENODEVICE, "operator was created host-only");
+  if (!op->f64.present || !op->kg_tables)
+    return fail(UF_EINVAL, "the kappa gradient needs the FP64 operator");
+  const size_t need = (size_t)op->host.n_active * (1 + 2 * op->host.dim);
+  if (need > uf::kStaticPartialDoubles)
+    return fail(UF_EINVAL, "operator too large for the fixed partial buffer: " +
+                               std::to_string(need) + " doubles needed, " +
+                               std::to_string(uf::kStaticPartialDoubles) + " available");
+  uf::DeviceGuard guard(op->device);
+  double *partials = nullptr;
+  uf_status st = uf::static_partials(op->device, &partials);
+  if (st != UF_OK) return st;
+  // Every slot the gather reads is written by the structured kernel of this call before any
+  // other kernel reads or accumulates into it, so the buffer needs no clearing.
+  int err = uf::launch_kgrad(op->host.dim, op->host.n, op->kg_tables, op->f64.arrays,
+                             op->f64.point_tables.data(), op->f64.scalars, partials, dk, r, x,
+                             reinterpret_cast<cudaStream_t>(stream));
+  if (err != 0)
+    return fail(UF_ECUDA, std::string("kernel launch: ") + cudaGetErrorString((cudaError_t)err));
+  return UF_OK;
+}
 
 uf_status uf_kappa_gradient(uf_operator *op, double *dk, const double *r, const double *x,
                             void *stream) {
