@@ -32,7 +32,14 @@ from . import basis, mesh, saye
 
 
 class Oracle:
-    def __init__(self, prob):
+    """discretization = "dg": the SIPG operator of Eq. bilinear_dg; "cg": the continuous
+    operator of Eq. bilinear_cg (Poisson + Nitsche) with the face ghost penalty, on the
+    continuous Q_p space whose nodes are the Gauss-Lobatto lattice points of the active cells."""
+
+    def __init__(self, prob, discretization="dg"):
+        if discretization not in ("dg", "cg"):
+            raise ValueError("discretization must be 'dg' or 'cg'")
+        self.discretization = discretization
         self.prob = prob
         self.mesh = mesh.Mesh(prob)
         self.n = prob.n
@@ -174,9 +181,11 @@ class Oracle:
         return blocks
 
     def face_blocks(self, e_minus, axis):
-        """SIPG + ghost-penalty blocks of one interior face."""
-        a = self.sipg_blocks(e_minus, axis)
+        """SIPG (DG only) + ghost-penalty blocks of one interior face."""
         b = self.gp_blocks(e_minus, axis)
+        if self.discretization == "cg":
+            return b
+        a = self.sipg_blocks(e_minus, axis)
         return {key: a[key] + b[key] for key in a}
 
     # ----------------------------------------------------------------- global operator
@@ -257,3 +266,41 @@ class Oracle:
         finally:
             self.mesh.kappa[:] = saved
         return np.array(out)
+
+    # ----------------------------------------------------------------- continuous Q_p
+    def cg_numbering(self):
+        """Global node of every (active cell, local DoF): lattice point p I_a + i_a, nodes of the
+        active cells numbered lexicographically (x fastest).  Returns (n_cg, loc2glob[n_active, nd])."""
+        p = self.prob.degree
+        d = self.prob.dim
+        dims = [p * N + 1 for N in self.prob.n_cells]
+        lat = np.zeros((self.mesh.n_active, self.ndof), dtype=np.int64)
+        stride = 1
+        for a in range(d):
+            lat += (self.mesh.active_idx[:, a:a + 1] * p + self.lidx[None, :, a]) * stride
+            stride *= dims[a]
+        used, loc2glob = np.unique(lat, return_inverse=True)
+        return len(used), loc2glob.reshape(lat.shape)
+
+    def cg_prolongation(self):
+        n_cg, l2g = self.cg_numbering()
+        n_loc = l2g.size
+        return sp.csr_matrix((np.ones(n_loc), (np.arange(n_loc), l2g.reshape(-1))), shape=(n_loc, n_cg))
+
+    def cg_matrix(self):
+        """A_cg = P^T A_loc P with A_loc the cell-local operator (no SIPG) and P the map from
+        global nodes to cell-local DoFs."""
+        P = self.cg_prolongation()
+        return (P.T @ self.assemble() @ P).tocsr()
+
+    def load_vector(self, f=1.0):
+        """b_l = int_{K cap Omega} f phi_l for every cell-local DoF (constant f)."""
+        out = np.zeros((self.mesh.n_active, self.ndof))
+        for e in range(self.mesh.n_active):
+            vx, vw, _, _, _ = self.cell_quadrature(e)
+            if len(vw):
+                out[e] = f * (vw @ self.basis_at(e, vx))
+        return out.reshape(-1)
+
+    def cg_load_vector(self, f=1.0):
+        return self.cg_prolongation().T @ self.load_vector(f)
