@@ -47,6 +47,7 @@ typedef enum {
 
 enum { UF_FP64 = 1, UF_FP32 = 2 };     /* precision flags (bit mask in uf_params.precisions) */
 enum { UF_LS_SPHERE = 0 };             /* level set kinds */
+enum { UF_DG = 0, UF_CG = 1 };         /* discretizations (uf_params.discretization) */
 
 /* Parameters of uf_create_unfitted_operator.  Penalties follow the paper's forms:
  * SIPG penalty sigma/h (Eq. bilinear_dg), Nitsche penalty tau/h (Eq. bilinear_cg), ghost
@@ -67,6 +68,9 @@ typedef struct {
   int precisions;         /* UF_FP64 | UF_FP32: which device data to build */
   int device;             /* CUDA device ordinal, or -1 for a host-only operator (no GPU use) */
   const double *kappa;    /* host array [n_active] copied at creation, or NULL for kappa = 1 */
+  int discretization;     /* UF_DG: SIPG (Eq. bilinear_dg), DoFs per cell; UF_CG: continuous Q_p
+                             (Eq. bilinear_cg, no SIPG), DoFs on the Gauss-Lobatto lattice points of
+                             the active cells numbered lexicographically (x fastest) */
 } uf_params;
 
 /* Sizes and algorithmic traffic of an operator (uf_get_info). */
@@ -147,8 +151,9 @@ uf_status uf_profile_end(uf_operator *op, uf_kernel_times *out);
  * [n_dofs + 1], int32 column indices, values in `precision`; columns ascending per row) by
  * applying the FP64 matrix-free operator to distance-2-coloured unit vectors (n^d applications
  * per colour; 7 colours in 3D, 5 in 2D).  Synchronous; allocates the matrix (library-owned) and a
- * temporary n^d x n_dofs FP64 staging block.  Needs the FP64 operator.  Errors: UF_EINVAL,
- * UF_ENODEVICE, UF_ENOMEM (checked against free device memory first), UF_ECUDA.
+ * temporary n^d x n_dofs FP64 staging block.  Needs the FP64 DG operator.  Errors: UF_EINVAL,
+ * UF_ENODEVICE, UF_EUNSUPPORTED (UF_CG operator), UF_ENOMEM (checked against free device memory
+ * first), UF_ECUDA.
  * uf_csr_info: nonzeros and algorithmic bytes of one SpMV (values + column indices + row
  * offsets + x + y).  uf_csr_spmv: y = A x with the assembled matrix (device pointers, stream-
  * ordered, one warp per row).  uf_export_csr: host copies (any pointer may be NULL; values as
@@ -167,7 +172,9 @@ uf_status uf_release_csr(uf_operator *op);
  * stored by uf_vmult.  dk [n_active], r and x [n_dofs] are FP64 device pointers; stream-
  * ordered; no allocation (a per-cell partial buffer owned by the operator is overwritten, so
  * calls on one operator must not overlap on different streams).  Needs the FP64 operator.
- * Errors: UF_EINVAL, UF_ENODEVICE, UF_ECUDA.  (Not in the paper: the differentiable operator.) */
+ * For a UF_CG operator r and x are global vectors and dk_e = (P r)^T A_loc,e (P x) with their
+ * cell-local gathers.  Errors: UF_EINVAL, UF_ENODEVICE, UF_ECUDA.  (Not in the paper: the
+ * differentiable operator.) */
 uf_status uf_kappa_gradient(uf_operator *op, double *dk, const double *r, const double *x,
                             void *stream);
 
@@ -214,6 +221,41 @@ uf_status uf_export_cut_cell_rule(const uf_operator *op, int64_t c, int kind, do
                                   double *w, double *normal, int64_t *count);
 uf_status uf_export_cut_face_rule(const uf_operator *op, int64_t e, int axis, int side,
                                   double *eta, double *w, int64_t *count);
+
+/* Continuous (UF_CG) operators: host copies of the global node of every cell-local DoF
+ * (l2g[n_active * n^d]), of the load vector for f = 1 (rhs[n_dofs], b_i = int_Omega phi_i; the
+ * Dirichlet data is zero) and of the diagonal of A (diag[n_dofs]), all computed at creation in
+ * FP64.  Any pointer may be NULL.  Errors: UF_EINVAL (NULL op, not a UF_CG operator). */
+uf_status uf_export_cg(const uf_operator *op, int32_t *l2g, double *rhs, double *diag);
+
+/* Solve A x = b for a continuous (UF_CG) operator with Jacobi-preconditioned CG (the solver of
+ * the paper's Sec. 3.5 is a PCG; its multigrid preconditioner is out of scope):
+ *   UF_SOLVE_FP64  PCG in FP64 on the correction of the initial guess until
+ *                  ||b - A x|| <= tol ||b||;
+ *   UF_SOLVE_IR    iterative refinement: FP64 residual r = b - A x, FP32 PCG on A d = r / ||r||
+ *                  to a relative reduction inner_tol, FP64 update x += ||r|| d, repeated until
+ *                  the FP64 relative residual is <= tol (FP64 only for the outer residual and the
+ *                  update; the FP32 operator carries the Nitsche and ghost-penalty terms).
+ * x (in: initial guess, out: solution) and b are FP64 device vectors [n_dofs].  Synchronous: the
+ * dot products (deterministic two-pass reductions) are read back every iteration.  max_iter caps
+ * the CG iterations (all inner iterations in IR mode), max_outer the refinement steps.
+ * Work vectors are allocated at creation; no allocation here.  Errors: UF_EINVAL (not a UF_CG
+ * operator, missing precision, bad parameters, breakdown), UF_ENODEVICE, UF_ECUDA. */
+enum { UF_SOLVE_FP64 = 0, UF_SOLVE_IR = 1 };
+typedef struct {
+  int mode;
+  double tol;
+  double inner_tol;
+  int max_iter;
+  int max_outer;
+} uf_solve_params;
+typedef struct {
+  int converged, outer, iterations;
+  double rel_residual;  /* final ||b - A x|| / ||b|| in FP64 */
+  double seconds;       /* device time of the solve (CUDA events on `stream`) */
+} uf_solve_stats;
+uf_status uf_solve(uf_operator *op, const uf_solve_params *params, double *x, const double *b,
+                   uf_solve_stats *stats, void *stream);
 
 /* Release every host and device resource of op.  NULL is accepted (no-op).  The caller must
  * make sure no stream still runs work of op. */

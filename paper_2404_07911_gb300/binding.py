@@ -14,6 +14,7 @@ from . import build as _build
 UF_OK, UF_EINVAL, UF_ENOMEM, UF_ECUDA, UF_EUNSUPPORTED, UF_EGEOMETRY, UF_ENODEVICE = range(7)
 UF_FP64, UF_FP32 = 1, 2
 UF_LS_SPHERE = 0
+UF_DG, UF_CG = 0, 1
 
 _STATUS = {0: "UF_OK", 1: "UF_EINVAL", 2: "UF_ENOMEM", 3: "UF_ECUDA", 4: "UF_EUNSUPPORTED",
            5: "UF_EGEOMETRY", 6: "UF_ENODEVICE"}
@@ -43,6 +44,7 @@ class uf_params(ctypes.Structure):
         ("precisions", ctypes.c_int),
         ("device", ctypes.c_int),
         ("kappa", ctypes.POINTER(ctypes.c_double)),
+        ("discretization", ctypes.c_int),
     ]
 
 
@@ -62,12 +64,24 @@ class uf_kernel_times(ctypes.Structure):
     _fields_ = [("ms_total", ctypes.c_double * 8), ("launches", ctypes.c_int64 * 8)]
 
 
+class uf_solve_params(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("max_outer", ctypes.c_int)]
+
+
+class uf_solve_stats(ctypes.Structure):
+    _fields_ = [("converged", ctypes.c_int), ("outer", ctypes.c_int), ("iterations", ctypes.c_int),
+                ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+
+UF_SOLVE_FP64, UF_SOLVE_IR = 0, 1
+
 EXPORTED = ["uf_create_unfitted_operator", "uf_get_info", "uf_vmult", "uf_vmult_adjoint",
             "uf_vmult_host", "uf_vmult_adjoint_host", "uf_profile_begin", "uf_profile_end",
             "uf_set_kappa", "uf_export_cells", "uf_export_cut_cell_rule",
             "uf_export_cut_face_rule", "uf_assemble_csr", "uf_csr_info", "uf_csr_spmv",
             "uf_export_csr", "uf_release_csr", "uf_kappa_gradient", "uf_kappa_gradient_noalloc",
-            "uf_set_kappa_device",
+            "uf_set_kappa_device", "uf_export_cg", "uf_solve",
             "uf_destroy", "uf_last_error"]
 
 _lib = None
@@ -108,6 +122,8 @@ def load_library(path=None):
     lib.uf_kappa_gradient.argtypes = [P, P, P, P, P]
     lib.uf_kappa_gradient_noalloc.argtypes = [P, P, P, P, P]
     lib.uf_set_kappa_device.argtypes = [P, P, P]
+    lib.uf_export_cg.argtypes = [P, P, P, P]
+    lib.uf_solve.argtypes = [P, ctypes.POINTER(uf_solve_params), P, P, ctypes.POINTER(uf_solve_stats), P]
     lib.uf_destroy.argtypes = [P]
     lib.uf_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -145,6 +161,7 @@ def make_params(cfg, precisions=UF_FP64 | UF_FP32, device=0, kappa=None):
     p.precisions = int(precisions)
     p.device = int(device)
     p.kappa = None
+    p.discretization = UF_CG if cfg.get("discretization", "dg") == "cg" else UF_DG
     return p
 
 
@@ -334,6 +351,30 @@ class UnfittedOperator:
         _check(_lib.uf_export_cut_cell_rule(self._h, c, kind, _ptr(xi), _ptr(w), _ptr(nrm),
                                             ctypes.byref(cnt)))
         return (xi, w, nrm) if kind == 1 else (xi, w)
+
+    def solve(self, b, x=None, mode="ir", tol=1e-10, inner_tol=1e-4, max_iter=100000,
+              max_outer=50, stream=None):
+        """Solve A x = b (continuous operators); b, x float64 CUDA tensors.  Returns (x, stats)."""
+        import torch
+
+        if x is None:
+            x = torch.zeros_like(b)
+        prm = uf_solve_params(UF_SOLVE_IR if mode == "ir" else UF_SOLVE_FP64, tol, inner_tol,
+                              max_iter, max_outer)
+        st = uf_solve_stats()
+        _check(_lib.uf_solve(self._h, ctypes.byref(prm), ctypes.c_void_p(x.data_ptr()),
+                             ctypes.c_void_p(b.contiguous().data_ptr()), ctypes.byref(st),
+                             self._stream_ptr(stream)))
+        return x, {name: getattr(st, name) for name, _ in uf_solve_stats._fields_}
+
+    def export_cg(self):
+        """(l2g[n_active, n^d], rhs[n_dofs], diag[n_dofs]) of a continuous operator."""
+        na, nd = self.info["n_active"], self.info["dofs_per_cell"]
+        l2g = np.zeros(na * nd, dtype=np.int32)
+        rhs = np.zeros(self.n_dofs)
+        diag = np.zeros(self.n_dofs)
+        _check(_lib.uf_export_cg(self._h, _ptr(l2g), _ptr(rhs), _ptr(diag)))
+        return l2g.reshape(na, nd), rhs, diag
 
     def export_cut_face_rule(self, e, axis, side):
         cnt = ctypes.c_int64()

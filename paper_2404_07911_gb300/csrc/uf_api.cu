@@ -41,12 +41,10 @@ using uf::PrecisionData;
 using uf::ProfSlot;
 using uf::DeviceGuard;
 
-namespace {
-
 // ------------------------------------------------------------------------------------------
 // Constant 1D matrices of the structured terms (see uf_device.h for their meaning).
 // ------------------------------------------------------------------------------------------
-void structured_matrices(const uf::HostOperator &op, std::vector<double> &out) {
+void uf::structured_matrices(const uf::HostOperator &op, std::vector<double> &out) {
   // layout of uf::StructTables: 16 matrices (n x n), then dow[2][n], dnb[2][n]
   const int n = op.n, nn = n * n, d = op.dim;
   const uf::Tables1D &t = op.t;
@@ -111,6 +109,9 @@ void structured_matrices(const uf::HostOperator &op, std::vector<double> &out) {
       }
   }
 }
+
+namespace {
+using uf::structured_matrices;
 
 // kappa = 1 variants of the per-axis self matrix (32, indexed by inside | full_lo << 1 |
 // gp_lo << 2 | full_hi << 3 | gp_hi << 4) and of a ghost-penalty neighbour coupling
@@ -299,6 +300,19 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   err = cudaMemcpy(pd.base, img.data(), L.bytes, cudaMemcpyHostToDevice);
   if (err != cudaSuccess) return fail(UF_ECUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(err));
   pd.device_bytes = L.bytes;
+  if (H.cg) {
+    const int64_t n_loc = H.n_active * H.ndof;
+    err = cudaMalloc(&pd.cg_l2g, n_loc * sizeof(int32_t));
+    if (err == cudaSuccess) err = cudaMalloc(&pd.cg_own_off, (H.n_cg + 1) * sizeof(int32_t));
+    if (err == cudaSuccess) err = cudaMalloc(&pd.cg_own_idx, n_loc * sizeof(int32_t));
+    if (err == cudaSuccess) err = cudaMalloc(&pd.x_loc, n_loc * sizeof(T));
+    if (err == cudaSuccess) err = cudaMalloc(&pd.y_loc, n_loc * sizeof(T));
+    if (err != cudaSuccess) return fail(UF_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(err));
+    cudaMemcpy(pd.cg_l2g, H.cg_l2g.data(), n_loc * sizeof(int32_t), cudaMemcpyHostToDevice);
+    cudaMemcpy(pd.cg_own_off, H.cg_own_off.data(), (H.n_cg + 1) * sizeof(int32_t), cudaMemcpyHostToDevice);
+    err = cudaMemcpy(pd.cg_own_idx, H.cg_own_idx.data(), n_loc * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (err != cudaSuccess) return fail(UF_ECUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(err));
+  }
 
   unsigned char *b = static_cast<unsigned char *>(pd.base);
   auto I32 = [&](size_t off) { return reinterpret_cast<const int32_t *>(b + off); };
@@ -369,6 +383,11 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
 
 template <typename T>
 void release(PrecisionData<T> &pd) {
+  void *cg[] = {pd.cg_l2g, pd.cg_own_off, pd.cg_own_idx, pd.x_loc, pd.y_loc};
+  for (void *p : cg)
+    if (p) cudaFree(p);
+  pd.cg_l2g = pd.cg_own_off = pd.cg_own_idx = nullptr;
+  pd.x_loc = pd.y_loc = nullptr;
   if (pd.base) cudaFree(pd.base);
   if (pd.xbuf) cudaFree(pd.xbuf);
   if (pd.ybuf) cudaFree(pd.ybuf);
@@ -381,7 +400,9 @@ template <typename T>
 uf_status vmult_t(uf_operator *op, PrecisionData<T> &pd, void *y, const void *x, void *stream,
                   bool adjoint) {
   if (!pd.present) return fail(UF_EINVAL, "operator was not created with this precision");
-  const size_t bytes = sizeof(T) * (size_t)op->host.n_active * op->host.ndof;
+  const bool cg = op->host.cg;
+  const int64_t nvec = cg ? op->host.n_cg : op->host.n_active * op->host.ndof;
+  const size_t bytes = sizeof(T) * (size_t)nvec;
   const char *xb = static_cast<const char *>(x);
   const char *yb = static_cast<const char *>(y);
   if (xb < yb + bytes && yb < xb + bytes) return fail(UF_EINVAL, "x and y overlap");
@@ -394,9 +415,16 @@ uf_status vmult_t(uf_operator *op, PrecisionData<T> &pd, void *y, const void *x,
     slot.used = true;
     ev = reinterpret_cast<void *const *>(slot.ev);
   }
-  int err = uf::launch_vmult<T>(op->host.dim, op->host.n, pd.arrays, pd.struct_tables.data(),
-                                pd.point_tables.data(), pd.scalars, static_cast<T *>(y),
-                                static_cast<const T *>(x), adjoint, stream, ev);
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t n_loc = op->host.n_active * op->host.ndof;
+  int err = 0;
+  if (cg) err = uf::cg_gather<T>(pd.x_loc, static_cast<const T *>(x), pd.cg_l2g, n_loc, cs);
+  if (err == 0)
+    err = uf::launch_vmult<T>(op->host.dim, op->host.n, pd.arrays, pd.struct_tables.data(),
+                              pd.point_tables.data(), pd.scalars, cg ? pd.y_loc : static_cast<T *>(y),
+                              cg ? pd.x_loc : static_cast<const T *>(x), adjoint, stream, ev);
+  if (err == 0 && cg)
+    err = uf::cg_node_sum<T>(static_cast<T *>(y), pd.y_loc, pd.cg_own_off, pd.cg_own_idx, op->host.n_cg, cs);
   if (err != 0)
     return fail(UF_ECUDA, std::string("kernel launch: ") + cudaGetErrorString((cudaError_t)err));
   return UF_OK;
@@ -459,6 +487,14 @@ uf_status uf_create_unfitted_operator(const uf_params *params, uf_operator **out
       op->host.kappa[e] = params->kappa[e];
     }
   }
+  if (op->host.cg) {
+    try {
+      uf::cg_host_vectors(op->host);
+    } catch (const std::bad_alloc &) {
+      delete op;
+      return fail(UF_ENOMEM, "host allocation failed during setup");
+    }
+  }
   op->device = params->device;
   if (op->device >= 0) {
     int ndev = 0;
@@ -471,12 +507,14 @@ uf_status uf_create_unfitted_operator(const uf_params *params, uf_operator **out
     try {
       if (params->precisions & UF_FP64) st = upload<double>(op, op->f64);
       if (st == UF_OK && (params->precisions & UF_FP32)) st = upload<float>(op, op->f32);
+      if (st == UF_OK && op->host.cg) st = uf::cg_alloc(op);
     } catch (const std::bad_alloc &) {
       st = fail(UF_ENOMEM, "host allocation failed during upload");
     }
     if (st != UF_OK) {
       release(op->f64);
       release(op->f32);
+      uf::cg_free(op);
       if (op->kg_tables) cudaFree(op->kg_tables);
       if (op->kg_scratch) cudaFree(op->kg_scratch);
       delete op;
@@ -494,7 +532,7 @@ uf_status uf_get_info(const uf_operator *op, uf_info *info) {
   info->n_active = H.n_active;
   info->n_inside = H.n_inside;
   info->n_cut = H.n_cut;
-  info->n_dofs = H.n_active * H.ndof;
+  info->n_dofs = H.cg ? H.n_cg : H.n_active * H.ndof;
   info->n_faces = H.n_faces;
   info->n_faces_full = H.n_faces_full;
   info->n_faces_cut = H.n_faces_cut;
@@ -623,7 +661,7 @@ static uf_status vmult_host_impl(uf_operator *op, int precision, void *y_host,
   DeviceGuard guard(op->device);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const size_t elem = precision == UF_FP64 ? sizeof(double) : sizeof(float);
-  const size_t bytes = elem * (size_t)op->host.n_active * op->host.ndof;
+  const size_t bytes = elem * (size_t)(op->host.cg ? op->host.n_cg : op->host.n_active * op->host.ndof);
   void *xb = precision == UF_FP64 ? op->f64.xbuf : op->f32.xbuf;
   void *yb = precision == UF_FP64 ? op->f64.ybuf : op->f32.ybuf;
   if (!xb || !yb) return fail(UF_EINVAL, "operator was not created with this precision");
@@ -698,6 +736,7 @@ uf_status uf_set_kappa(uf_operator *op, const double *kappa_host) {
     if (!(kappa_host[e] > 0.0) || !std::isfinite(kappa_host[e]))
       return fail(UF_EINVAL, "kappa must be positive and finite");
   std::copy(kappa_host, kappa_host + op->host.n_active, op->host.kappa.begin());
+  if (op->host.cg) uf::cg_host_vectors(op->host);
   const int32_t uni = kappa_is_uniform(op->host.kappa) ? 1 : 0;
   op->f64.arrays.kappa_uniform = uni;
   op->f32.arrays.kappa_uniform = uni;
@@ -713,6 +752,7 @@ uf_status uf_set_kappa(uf_operator *op, const double *kappa_host) {
     cudaError_t err = cudaMemcpy(op->f32.kappa_dev, k32.data(), sizeof(float) * na, cudaMemcpyHostToDevice);
     if (err != cudaSuccess) return fail(UF_ECUDA, cudaGetErrorString(err));
   }
+  if (op->host.cg && op->cgs.ready) return uf::cg_upload_diag(op);
   return UF_OK;
 }
 
@@ -767,12 +807,23 @@ uf_status uf_export_cut_face_rule(const uf_operator *op, int64_t e, int axis, in
   return UF_OK;
 }
 
+uf_status uf_export_cg(const uf_operator *op, int32_t *l2g, double *rhs, double *diag) {
+  if (!op) return fail(UF_EINVAL, "NULL argument");
+  const uf::HostOperator &H = op->host;
+  if (!H.cg) return fail(UF_EINVAL, "not a continuous (UF_CG) operator");
+  if (l2g) std::copy(H.cg_l2g.begin(), H.cg_l2g.end(), l2g);
+  if (rhs) std::copy(H.cg_rhs.begin(), H.cg_rhs.end(), rhs);
+  if (diag) std::copy(H.cg_diag.begin(), H.cg_diag.end(), diag);
+  return UF_OK;
+}
+
 uf_status uf_destroy(uf_operator *op) {
   if (!op) return UF_OK;
   if (op->device >= 0) {
     DeviceGuard guard(op->device);
     uf::release_csr(op->csr64);
     uf::release_csr(op->csr32);
+    uf::cg_free(op);
     if (op->kg_tables) cudaFree(op->kg_tables);
     if (op->kg_scratch) cudaFree(op->kg_scratch);
     for (ProfSlot &slot : op->prof)

@@ -1,0 +1,534 @@
+// Continuous Q_p operator (Eq. bilinear_cg with the face ghost penalty, no SIPG): load vector,
+// Jacobi diagonal, global <-> cell-local maps, and the preconditioned CG solvers in FP64 and as
+// FP32 inner iterations inside FP64 iterative refinement.
+//
+// The continuous operator is A = P^T A_loc P, with P the map from global lattice nodes to
+// cell-local DoFs and A_loc the cell-local operator that the DG kernels evaluate when the face
+// flags carry no SIPG term: y = A x is a gather (x_loc = P x), the cell-centric kernels
+// (y_loc = A_loc x_loc), and a node sum (y = P^T y_loc) over each node's owners in a fixed order,
+// so no floating-point atomics are needed and the result is deterministic.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "uf_operator.h"
+
+namespace uf {
+
+// ------------------------------------------------------------------------------------------
+// Host: load vector (f = 1) and diagonal of A, FP64
+// ------------------------------------------------------------------------------------------
+void cg_host_vectors(HostOperator &op) {
+  const int d = op.dim, n = op.n, nd = op.ndof, nf = 2 * d, nn = n * n;
+  const Tables1D &t = op.t;
+  const double h = op.h;
+  std::vector<double> m;
+  structured_matrices(op, m);
+  const double *Kv = &m[0], *M = &m[nn];
+  auto mat = [&](int which, int s) { return &m[(which + s) * nn]; };  // 2 a, 4 pen, 6 gp, 8 b, 10 c, 12 qn, 14 hn
+  // integrals of the 1D basis: w_i = int_0^1 phi_i
+  double wi[kMaxN] = {0};
+  for (int q = 0; q < n; ++q)
+    for (int i = 0; i < n; ++i) {
+      double v[kMaxN], dv[kMaxN];
+      lagrange_values(t, t.gauss_x[q], v, dv);
+      wi[i] += t.gauss_w[q] * v[i];
+    }
+  const double hd = std::pow(h, d);
+  std::vector<double> bloc((size_t)op.n_active * nd, 0.0), dloc((size_t)op.n_active * nd, 0.0);
+  auto idx3 = [&](int l, int *ia) {
+    for (int a = 0; a < 3; ++a) {
+      ia[a] = (a < d) ? l % n : 0;
+      l /= n;
+    }
+  };
+  for (int64_t e = 0; e < op.n_active; ++e) {
+    double *b = &bloc[e * nd], *dg = &dloc[e * nd];
+    const uint32_t fl = op.flags[e];
+    const bool inside = op.act_type[e] == 0;
+    const double kap = op.kappa[e];
+    // ---- structured terms: diag of sum_a (L_a along a) (x) M (x) M and ghost-penalty cross terms
+    double Lself[kMaxDim][kMaxN * kMaxN];
+    double cross[kMaxDim][2];  // L_nb[own][nb] at the face node of each side (0 if no coupling)
+    for (int a = 0; a < d; ++a) {
+      for (int i = 0; i < nn; ++i) Lself[a][i] = inside ? kap * Kv[i] : 0.0;
+      for (int s = 0; s < 2; ++s) {
+        cross[a][s] = 0.0;
+        const int f = 2 * a + s;
+        const int nb = op.nbr[e * nf + f];
+        if (nb < 0) continue;
+        const double kavg = 0.5 * (kap + op.kappa[nb]);
+        const bool full = fl & face_bit_sipg_full(f), gp = fl & face_bit_gp(f);
+        const int io = s ? n - 1 : 0, inb = s ? 0 : n - 1;
+        for (int i = 0; i < nn; ++i) {
+          if (full) Lself[a][i] += kap * mat(2, s)[i] + kavg * mat(4, s)[i];
+          if (gp) Lself[a][i] += kavg * mat(6, s)[i];
+        }
+        double c = 0.0;
+        if (full) c += kap * mat(8, s)[io * n + inb] + op.kappa[nb] * mat(10, s)[io * n + inb] +
+                       kavg * mat(12, s)[io * n + inb];
+        if (gp) c += kavg * mat(14, s)[io * n + inb];
+        cross[a][s] = c;
+      }
+    }
+    for (int l = 0; l < nd; ++l) {
+      int ia[3];
+      idx3(l, ia);
+      double acc = 0.0;
+      for (int a = 0; a < d; ++a) {
+        double mm = 1.0;
+        for (int bb = 0; bb < d; ++bb)
+          if (bb != a) mm *= M[ia[bb] * n + ia[bb]];
+        acc += Lself[a][ia[a] * n + ia[a]] * mm;
+        for (int s = 0; s < 2; ++s)
+          if (ia[a] == (s ? n - 1 : 0)) acc += cross[a][s] * mm;
+      }
+      dg[l] = acc;
+      if (inside) {
+        double v = hd;
+        for (int a = 0; a < d; ++a) v *= wi[ia[a]];
+        b[l] = v;
+      }
+    }
+    if (inside) continue;
+    // ---- unstructured terms of a cut cell, line by line
+    const int64_t c = op.cut_of[e];
+    for (int64_t li = op.vline_off[c]; li < op.vline_off[c + 1]; ++li) {
+      const QLine &ln = op.vol_lines[li];
+      const int k = ln.k;
+      int ob = (k == 0) ? 1 : 0, oc = (k == 2) ? 1 : 2;
+      if (d == 2) ob = 1 - k;
+      const bool has_vol = ln.vcnt > 0;
+      const int64_t p0 = has_vol ? ln.vbeg : ln.sidx;
+      const std::vector<double> *xi = has_vol ? op.vol_xi : op.surf_xi;
+      double A[kMaxN], Ad[kMaxN], B[kMaxN] = {1.0}, Bd[kMaxN] = {0.0};
+      lagrange_values(t, xi[ob][p0], A, Ad);
+      if (d == 3) lagrange_values(t, xi[oc][p0], B, Bd);
+      const int nbm = (d == 3) ? n : 1;
+      // volume: S0_k = sum w C_k, S1_k = sum w C_k^2, S2_k = sum w C_k'^2
+      double S0[kMaxN] = {0}, S1[kMaxN] = {0}, S2[kMaxN] = {0};
+      for (int64_t p = ln.vbeg; p < ln.vbeg + ln.vcnt; ++p) {
+        double C[kMaxN], Cd[kMaxN];
+        lagrange_values(t, op.vol_xi[k][p], C, Cd);
+        const double w = op.vol_w[p];
+        for (int q = 0; q < n; ++q) {
+          S0[q] += w * C[q];
+          S1[q] += w * C[q] * C[q];
+          S2[q] += w * Cd[q] * Cd[q];
+        }
+      }
+      const double sk = kap / (h * h);
+      for (int ib = 0; ib < n; ++ib)
+        for (int ic = 0; ic < nbm; ++ic)
+          for (int q = 0; q < n; ++q) {
+            int l = ib * (ob == 0 ? 1 : (ob == 1 ? n : n * n)) + q * (k == 0 ? 1 : (k == 1 ? n : n * n));
+            if (d == 3) l += ic * (oc == 0 ? 1 : (oc == 1 ? n : n * n));
+            const double a2 = A[ib] * A[ib], ad2 = Ad[ib] * Ad[ib];
+            const double b2 = B[ic] * B[ic], bd2 = Bd[ic] * Bd[ic];
+            dg[l] += sk * (ad2 * b2 * S1[q] + a2 * bd2 * S1[q] + a2 * b2 * S2[q]);
+            b[l] += A[ib] * B[ic] * S0[q];
+          }
+      // Nitsche at the surface point of the line
+      if (ln.sidx >= 0) {
+        const int64_t sp = ln.sidx;
+        double C[kMaxN], Cd[kMaxN];
+        lagrange_values(t, op.surf_xi[k][sp], C, Cd);
+        const double w = op.surf_w[sp] * kap, tau = op.params.nitsche_gamma / h;
+        const double nk = op.surf_n[k][sp], nbn = op.surf_n[ob][sp], nc = (d == 3) ? op.surf_n[oc][sp] : 0.0;
+        for (int ib = 0; ib < n; ++ib)
+          for (int ic = 0; ic < nbm; ++ic)
+            for (int q = 0; q < n; ++q) {
+              int l = ib * (ob == 0 ? 1 : (ob == 1 ? n : n * n)) + q * (k == 0 ? 1 : (k == 1 ? n : n * n));
+              if (d == 3) l += ic * (oc == 0 ? 1 : (oc == 1 ? n : n * n));
+              const double phi = A[ib] * B[ic] * C[q];
+              const double dn = (nbn * Ad[ib] * B[ic] * C[q] + nc * A[ib] * Bd[ic] * C[q] +
+                                 nk * A[ib] * B[ic] * Cd[q]) / h;
+              dg[l] += w * (-2.0 * phi * dn + tau * phi * phi);
+            }
+      }
+    }
+  }
+  op.cg_rhs.assign(op.n_cg, 0.0);
+  op.cg_diag.assign(op.n_cg, 0.0);
+  for (int64_t g = 0; g < op.n_cg; ++g)
+    for (int32_t o = op.cg_own_off[g]; o < op.cg_own_off[g + 1]; ++o) {
+      op.cg_rhs[g] += bloc[op.cg_own_idx[o]];
+      op.cg_diag[g] += dloc[op.cg_own_idx[o]];
+    }
+}
+
+}  // namespace uf
+
+// ------------------------------------------------------------------------------------------
+// Device: gather, node sum, vector kernels
+// ------------------------------------------------------------------------------------------
+namespace uf {
+namespace {
+
+constexpr int kDotBlocks = 608;  // 4 x 152 SMs; partial sums reduced in a fixed order
+constexpr int kDotThreads = 256;
+
+template <typename T>
+__global__ void k_gather(T *__restrict__ xl, const T *__restrict__ x, const int32_t *__restrict__ l2g,
+                         int64_t n_loc) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_loc) xl[i] = x[l2g[i]];
+}
+
+template <typename T>
+__global__ void k_node_sum(T *__restrict__ y, const T *__restrict__ yl, const int32_t *__restrict__ off,
+                           const int32_t *__restrict__ idx, int64_t n) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  T acc = T(0);
+  for (int32_t o = off[g]; o < off[g + 1]; ++o) acc += yl[idx[o]];
+  y[g] = acc;
+}
+
+// Block partial sums of sum_i a_i b_i (and of sum_i a_i a_i if two > 0) in FP64, fixed order.
+template <typename T>
+__global__ void __launch_bounds__(kDotThreads) k_dot_partial(const T *__restrict__ a, const T *__restrict__ b,
+                                                             int64_t n, double *__restrict__ part, int two) {
+  __shared__ double s0[kDotThreads], s1[kDotThreads];
+  double acc0 = 0.0, acc1 = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double av = (double)a[i];
+    acc0 = fma(av, (double)b[i], acc0);
+    if (two) acc1 = fma(av, av, acc1);
+  }
+  s0[threadIdx.x] = acc0;
+  s1[threadIdx.x] = acc1;
+  __syncthreads();
+  for (int w = kDotThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      s0[threadIdx.x] += s0[threadIdx.x + w];
+      s1[threadIdx.x] += s1[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = s0[0];
+    part[kDotBlocks + blockIdx.x] = s1[0];
+  }
+}
+
+__global__ void k_dot_final(const double *__restrict__ part, double *__restrict__ out) {
+  __shared__ double s0[kDotThreads], s1[kDotThreads];
+  double a0 = 0.0, a1 = 0.0;
+  for (int i = threadIdx.x; i < kDotBlocks; i += kDotThreads) {
+    a0 += part[i];
+    a1 += part[kDotBlocks + i];
+  }
+  s0[threadIdx.x] = a0;
+  s1[threadIdx.x] = a1;
+  __syncthreads();
+  for (int w = kDotThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      s0[threadIdx.x] += s0[threadIdx.x + w];
+      s1[threadIdx.x] += s1[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = s0[0];
+    out[1] = s1[0];
+  }
+}
+
+// z = invd * r
+template <typename T>
+__global__ void k_jacobi(T *__restrict__ z, const T *__restrict__ r, const T *__restrict__ invd, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) z[i] = invd[i] * r[i];
+}
+
+// x += alpha p, r -= alpha q
+template <typename T>
+__global__ void k_update_xr(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p,
+                            const T *__restrict__ q, T alpha, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    x[i] = fma(alpha, p[i], x[i]);
+    r[i] = fma(-alpha, q[i], r[i]);
+  }
+}
+
+// p = z + beta p
+template <typename T>
+__global__ void k_update_p(T *__restrict__ p, const T *__restrict__ z, T beta, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = fma(beta, p[i], z[i]);
+}
+
+// r = b - q
+__global__ void k_residual(double *__restrict__ r, const double *__restrict__ b, const double *__restrict__ q,
+                           int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) r[i] = b[i] - q[i];
+}
+
+// r32 = (float)(r * s)
+__global__ void k_scale_to_f32(float *__restrict__ r32, const double *__restrict__ r, double s, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) r32[i] = (float)(r[i] * s);
+}
+
+// x += s * d32
+__global__ void k_refine(double *__restrict__ x, const float *__restrict__ d32, double s, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = fma(s, (double)d32[i], x[i]);
+}
+
+// x += d
+__global__ void k_add(double *__restrict__ x, const double *__restrict__ d, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] += d[i];
+}
+
+template <typename T>
+__global__ void k_fill(T *__restrict__ x, T v, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = v;
+}
+
+inline unsigned nblk(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+}  // namespace
+
+template <typename T>
+int cg_gather(T *x_loc, const T *x, const int32_t *l2g, int64_t n_loc, cudaStream_t s) {
+  k_gather<T><<<nblk(n_loc), 256, 0, s>>>(x_loc, x, l2g, n_loc);
+  return (int)cudaGetLastError();
+}
+
+template <typename T>
+int cg_node_sum(T *y, const T *y_loc, const int32_t *off, const int32_t *idx, int64_t n, cudaStream_t s) {
+  k_node_sum<T><<<nblk(n), 256, 0, s>>>(y, y_loc, off, idx, n);
+  return (int)cudaGetLastError();
+}
+
+template int cg_gather<double>(double *, const double *, const int32_t *, int64_t, cudaStream_t);
+template int cg_gather<float>(float *, const float *, const int32_t *, int64_t, cudaStream_t);
+template int cg_node_sum<double>(double *, const double *, const int32_t *, const int32_t *, int64_t, cudaStream_t);
+template int cg_node_sum<float>(float *, const float *, const int32_t *, const int32_t *, int64_t, cudaStream_t);
+
+// ------------------------------------------------------------------------------------------
+// Solvers
+// ------------------------------------------------------------------------------------------
+namespace {
+
+struct SolveCtx {
+  uf_operator *op;
+  cudaStream_t s;
+  int64_t n;
+  double *dot_part;  // [2 * kDotBlocks]
+  double *dot_out;   // [2] device
+  double *dot_host;  // [2] pinned host
+};
+
+template <typename T>
+uf_status dots(SolveCtx &c, const T *a, const T *b, bool two, double &ab, double &aa) {
+  k_dot_partial<T><<<kDotBlocks, kDotThreads, 0, c.s>>>(a, b, c.n, c.dot_part, two ? 1 : 0);
+  k_dot_final<<<1, kDotThreads, 0, c.s>>>(c.dot_part, c.dot_out);
+  cudaError_t err = cudaMemcpyAsync(c.dot_host, c.dot_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.s);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(c.s);
+  if (err != cudaSuccess) return fail(UF_ECUDA, std::string("reduction: ") + cudaGetErrorString(err));
+  ab = c.dot_host[0];
+  aa = c.dot_host[1];
+  return UF_OK;
+}
+
+// Jacobi-preconditioned CG on A x = r (x starts at zero, r is overwritten by the residual) until
+// ||r|| <= rtol ||r_0|| or `maxit` iterations; returns the iterations done in *its.
+template <typename T>
+uf_status pcg(SolveCtx &c, int precision, const T *invd, T *x, T *r, T *z, T *p, T *q, double rtol,
+              int maxit, int *its, double *rel) {
+  const int64_t n = c.n;
+  k_fill<T><<<nblk(n), 256, 0, c.s>>>(x, T(0), n);
+  k_jacobi<T><<<nblk(n), 256, 0, c.s>>>(z, r, invd, n);
+  cudaMemcpyAsync(p, z, n * sizeof(T), cudaMemcpyDeviceToDevice, c.s);
+  double rz, rr;
+  uf_status st = dots<T>(c, r, z, true, rz, rr);
+  if (st != UF_OK) return st;
+  const double r0 = std::sqrt(rr);
+  *its = 0;
+  *rel = 1.0;
+  if (r0 == 0.0) return UF_OK;
+  for (int it = 1; it <= maxit; ++it) {
+    st = vmult_launch(c.op, precision, q, p, c.s, false);
+    if (st != UF_OK) return st;
+    double pq, dummy;
+    st = dots<T>(c, p, q, false, pq, dummy);
+    if (st != UF_OK) return st;
+    if (!(pq > 0.0)) return fail(UF_EINVAL, "CG breakdown: the operator is not positive definite");
+    const double alpha = rz / pq;
+    k_update_xr<T><<<nblk(n), 256, 0, c.s>>>(x, r, p, q, (T)alpha, n);
+    k_jacobi<T><<<nblk(n), 256, 0, c.s>>>(z, r, invd, n);
+    double rz_new;
+    st = dots<T>(c, r, z, true, rz_new, rr);
+    if (st != UF_OK) return st;
+    *its = it;
+    *rel = std::sqrt(rr) / r0;
+    if (*rel <= rtol) break;
+    const double beta = rz_new / rz;
+    rz = rz_new;
+    k_update_p<T><<<nblk(n), 256, 0, c.s>>>(p, z, (T)beta, n);
+  }
+  return UF_OK;
+}
+
+}  // namespace
+}  // namespace uf
+
+using uf::fail;
+
+extern "C" uf_status uf_solve(uf_operator *op, const uf_solve_params *prm, double *x, const double *b,
+                              uf_solve_stats *stats, void *stream) {
+  if (!op || !prm || !x || !b || !stats) return fail(UF_EINVAL, "NULL argument");
+  if (op->device < 0) return fail(UF_ENODEVICE, "operator was created host-only");
+  if (!op->host.cg || !op->cgs.ready) return fail(UF_EINVAL, "uf_solve needs a continuous (UF_CG) operator");
+  if (prm->mode != UF_SOLVE_FP64 && prm->mode != UF_SOLVE_IR) return fail(UF_EINVAL, "bad solve mode");
+  if (prm->mode == UF_SOLVE_IR && !op->f32.present) return fail(UF_EINVAL, "IR needs the FP32 operator");
+  if (!op->f64.present) return fail(UF_EINVAL, "uf_solve needs the FP64 operator");
+  if (!(prm->tol > 0.0) || prm->max_iter < 1) return fail(UF_EINVAL, "bad tolerance or iteration cap");
+  uf::DeviceGuard guard(op->device);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t n = op->host.n_cg;
+  uf::CgSolveData &w = op->cgs;
+  uf::SolveCtx c{op, s, n, w.dot_part, w.dot_out, w.dot_host};
+  std::memset(stats, 0, sizeof(*stats));
+  cudaEvent_t t0, t1;
+  cudaEventCreate(&t0);
+  cudaEventCreate(&t1);
+  cudaEventRecord(t0, s);
+  uf_status st = UF_OK;
+  double bb, dummy;
+  st = uf::dots<double>(c, b, b, false, bb, dummy);
+  const double bnorm = std::sqrt(bb);
+  auto residual64 = [&]() -> uf_status {  // r64 = b - A x (FP64)
+    uf_status s2 = uf::vmult_launch(op, UF_FP64, w.q64, x, s, false);
+    if (s2 != UF_OK) return s2;
+    uf::k_residual<<<uf::nblk(n), 256, 0, s>>>(w.r64, b, w.q64, n);
+    return UF_OK;
+  };
+  int total_it = 0, outer = 0;
+  double rel = 1.0;
+  if (st == UF_OK && bnorm == 0.0) {
+    uf::k_fill<double><<<uf::nblk(n), 256, 0, s>>>(x, 0.0, n);
+    rel = 0.0;
+  } else if (st == UF_OK && prm->mode == UF_SOLVE_FP64) {
+    // FP64 PCG for the correction of the initial guess: A d = b - A x, x += d
+    st = residual64();
+    int its = 0;
+    double rr, rn;
+    if (st == UF_OK) st = uf::dots<double>(c, w.r64, w.r64, false, rr, dummy);
+    rn = std::sqrt(rr);
+    if (st == UF_OK && rn > prm->tol * bnorm) {
+      st = uf::pcg<double>(c, UF_FP64, w.invd64, w.d64, w.r64, w.z64, w.p64, w.q64,
+                           prm->tol * bnorm / rn, prm->max_iter, &its, &rel);
+      if (st == UF_OK) uf::k_add<<<uf::nblk(n), 256, 0, s>>>(x, w.d64, n);
+    }
+    total_it = its;
+    outer = 1;
+    if (st == UF_OK) st = residual64();
+    if (st == UF_OK) st = uf::dots<double>(c, w.r64, w.r64, false, rr, dummy);
+    rel = std::sqrt(rr) / bnorm;
+  } else if (st == UF_OK) {
+    // FP32 inner PCG inside FP64 iterative refinement
+    st = residual64();
+    for (outer = 0; st == UF_OK && outer < std::max(prm->max_outer, 1); ++outer) {
+      double rr;
+      st = uf::dots<double>(c, w.r64, w.r64, false, rr, dummy);
+      if (st != UF_OK) break;
+      const double rn = std::sqrt(rr);
+      rel = rn / bnorm;
+      if (rel <= prm->tol || total_it >= prm->max_iter) break;
+      uf::k_scale_to_f32<<<uf::nblk(n), 256, 0, s>>>(w.r32, w.r64, 1.0 / rn, n);
+      int its = 0;
+      double rel_in;
+      st = uf::pcg<float>(c, UF_FP32, w.invd32, w.d32, w.r32, w.z32, w.p32, w.q32,
+                          prm->inner_tol > 0.0 ? prm->inner_tol : 1e-4, prm->max_iter - total_it,
+                          &its, &rel_in);
+      if (st != UF_OK) break;
+      total_it += its;
+      uf::k_refine<<<uf::nblk(n), 256, 0, s>>>(x, w.d32, rn, n);
+      st = residual64();
+    }
+  }
+  cudaEventRecord(t1, s);
+  cudaEventSynchronize(t1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, t0, t1);
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  stats->iterations = total_it;
+  stats->outer = outer;
+  stats->rel_residual = rel;
+  stats->converged = (st == UF_OK && rel <= prm->tol) ? 1 : 0;
+  stats->seconds = ms * 1e-3;
+  return st;
+}
+
+namespace uf {
+
+uf_status cg_alloc(uf_operator *op) {
+  CgSolveData &w = op->cgs;
+  const int64_t n = op->host.n_cg;
+  cudaError_t err = cudaSuccess;
+  auto A = [&](void **p, size_t bytes) {
+    if (err == cudaSuccess) err = cudaMalloc(p, bytes);
+  };
+  if (op->f64.present) {
+    A((void **)&w.r64, n * 8);
+    A((void **)&w.q64, n * 8);
+    A((void **)&w.d64, n * 8);
+    A((void **)&w.z64, n * 8);
+    A((void **)&w.p64, n * 8);
+    A((void **)&w.invd64, n * 8);
+  }
+  if (op->f32.present) {
+    A((void **)&w.r32, n * 4);
+    A((void **)&w.q32, n * 4);
+    A((void **)&w.d32, n * 4);
+    A((void **)&w.z32, n * 4);
+    A((void **)&w.p32, n * 4);
+    A((void **)&w.invd32, n * 4);
+  }
+  A((void **)&w.dot_part, 2 * kDotBlocks * sizeof(double));
+  A((void **)&w.dot_out, 2 * sizeof(double));
+  if (err == cudaSuccess) err = cudaMallocHost((void **)&w.dot_host, 2 * sizeof(double));
+  if (err != cudaSuccess) return fail(UF_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(err));
+  return cg_upload_diag(op);
+}
+
+uf_status cg_upload_diag(uf_operator *op) {
+  CgSolveData &w = op->cgs;
+  const int64_t n = op->host.n_cg;
+  std::vector<double> inv(n);
+  for (int64_t i = 0; i < n; ++i) inv[i] = 1.0 / op->host.cg_diag[i];
+  cudaError_t err = cudaSuccess;
+  if (w.invd64) err = cudaMemcpy(w.invd64, inv.data(), n * 8, cudaMemcpyHostToDevice);
+  if (err == cudaSuccess && w.invd32) {
+    std::vector<float> inv32(inv.begin(), inv.end());
+    err = cudaMemcpy(w.invd32, inv32.data(), n * 4, cudaMemcpyHostToDevice);
+  }
+  if (err != cudaSuccess) return fail(UF_ECUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(err));
+  w.ready = true;
+  return UF_OK;
+}
+
+void cg_free(uf_operator *op) {
+  CgSolveData &w = op->cgs;
+  void *ptrs[] = {w.r64, w.q64, w.d64, w.z64, w.p64, w.invd64, w.r32, w.q32, w.d32,
+                  w.z32, w.p32, w.invd32, w.dot_part, w.dot_out};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  if (w.dot_host) cudaFreeHost(w.dot_host);
+  w = CgSolveData{};
+}
+
+}  // namespace uf

@@ -106,6 +106,7 @@ uf_status uf_assemble_csr(uf_operator *op, int precision) {
   if (op->device < 0) return fail(UF_ENODEVICE, "operator was created host-only");
   if (precision != UF_FP64 && precision != UF_FP32) return fail(UF_EINVAL, "bad precision");
   if (!op->f64.present) return fail(UF_EINVAL, "CSR assembly needs the FP64 operator");
+  if (op->host.cg) return fail(UF_EUNSUPPORTED, "CSR assembly is built for the DG operator");
   uf::DeviceGuard guard(op->device);
   const uf::HostOperator &H = op->host;
   const int d = H.dim, nf = 2 * d, nd = H.ndof;

@@ -94,6 +94,15 @@ struct HostOperator {
   std::vector<QLine> vol_lines, face_lines;
   std::vector<int64_t> vline_off, fline_off;
 
+  // continuous Q_p (discretization == UF_CG): global node of every cell-local DoF and, per global
+  // node, its owners (cell * n^d + l, ascending); load vector (f = 1) and diagonal of A (FP64)
+  bool cg = false;
+  int64_t n_cg = 0;
+  std::vector<int32_t> cg_l2g;            // [n_active * n^d]
+  std::vector<int32_t> cg_own_off;        // [n_cg + 1]
+  std::vector<int32_t> cg_own_idx;        // [n_active * n^d]
+  std::vector<double> cg_rhs, cg_diag;    // [n_cg]
+
   // counts
   int64_t n_faces = 0, n_faces_full = 0, n_faces_cut = 0, n_faces_empty = 0, n_faces_gp = 0;
   int64_t n_face_points_unique = 0;
@@ -104,5 +113,8 @@ uf_status build_host_operator(const uf_params &params, HostOperator &op, std::st
 
 // 1D tables (exposed for the device upload).
 void build_tables_1d(int p, Tables1D &t);
+
+// phi_i(x) and phi_i'(x), i = 0..n-1, of the Lobatto Lagrange basis of t.
+void lagrange_values(const Tables1D &t, double x, double *val, double *der);
 
 }  // namespace uf

@@ -549,11 +549,19 @@ uf_status uf_kappa_gradient_noalloc(uf_operator *op, double *dk, const double *r
   double *partials = nullptr;
   uf_status st = uf::static_partials(op->device, &partials);
   if (st != UF_OK) return st;
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  const double *rl = r, *xl = x;
+  if (op->host.cg) {
+    const int64_t n_loc = op->host.n_active * op->host.ndof;
+    uf::cg_gather<double>(op->f64.x_loc, x, op->f64.cg_l2g, n_loc, cs);
+    uf::cg_gather<double>(op->f64.y_loc, r, op->f64.cg_l2g, n_loc, cs);
+    xl = op->f64.x_loc;
+    rl = op->f64.y_loc;
+  }
   // Every slot the gather reads is written by the structured kernel of this call before any
   // other kernel reads or accumulates into it, so the buffer needs no clearing.
   int err = uf::launch_kgrad(op->host.dim, op->host.n, op->kg_tables, op->f64.arrays,
-                             op->f64.point_tables.data(), op->f64.scalars, partials, dk, r, x,
-                             reinterpret_cast<cudaStream_t>(stream));
+                             op->f64.point_tables.data(), op->f64.scalars, partials, dk, rl, xl, cs);
   if (err != 0)
     return fail(UF_ECUDA, std::string("kernel launch: ") + cudaGetErrorString((cudaError_t)err));
   return UF_OK;
@@ -566,9 +574,19 @@ uf_status uf_kappa_gradient(uf_operator *op, double *dk, const double *r, const 
   if (!op->f64.present || !op->kg_tables || !op->kg_scratch)
     return fail(UF_EINVAL, "the kappa gradient needs the FP64 operator");
   uf::DeviceGuard guard(op->device);
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  const double *rl = r, *xl = x;
+  if (op->host.cg) {
+    // continuous space: dk_K = (P r)^T A_loc,K (P x) with the cell-local gathers of r and x
+    const int64_t n_loc = op->host.n_active * op->host.ndof;
+    uf::cg_gather<double>(op->f64.x_loc, x, op->f64.cg_l2g, n_loc, cs);
+    uf::cg_gather<double>(op->f64.y_loc, r, op->f64.cg_l2g, n_loc, cs);
+    xl = op->f64.x_loc;
+    rl = op->f64.y_loc;
+  }
   int err = uf::launch_kgrad(op->host.dim, op->host.n, op->kg_tables, op->f64.arrays,
-                             op->f64.point_tables.data(), op->f64.scalars, op->kg_scratch, dk, r,
-                             x, reinterpret_cast<cudaStream_t>(stream));
+                             op->f64.point_tables.data(), op->f64.scalars, op->kg_scratch, dk, rl,
+                             xl, cs);
   if (err != 0)
     return fail(UF_ECUDA, std::string("kernel launch: ") + cudaGetErrorString((cudaError_t)err));
   return UF_OK;

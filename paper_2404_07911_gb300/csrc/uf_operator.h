@@ -28,6 +28,20 @@ struct PrecisionData {
   Scalars<T> scalars{};
   size_t device_bytes = 0;
   int64_t n_vlines = 0, n_flines = 0;
+  // continuous operators: global node of every cell-local DoF, owners of every node, and the
+  // cell-local work vectors of the gather / kernels / node-sum sequence
+  int32_t *cg_l2g = nullptr, *cg_own_off = nullptr, *cg_own_idx = nullptr;
+  T *x_loc = nullptr, *y_loc = nullptr;
+};
+
+// Work vectors of the CG solvers (continuous operators).
+struct CgSolveData {
+  bool ready = false;
+  double *r64 = nullptr, *q64 = nullptr, *d64 = nullptr, *z64 = nullptr, *p64 = nullptr;
+  double *invd64 = nullptr;
+  float *r32 = nullptr, *q32 = nullptr, *d32 = nullptr, *z32 = nullptr, *p32 = nullptr;
+  float *invd32 = nullptr;
+  double *dot_part = nullptr, *dot_out = nullptr, *dot_host = nullptr;
 };
 
 struct ProfSlot {
@@ -69,6 +83,7 @@ struct uf_operator {
   std::vector<uf::ProfSlot> prof;  // non-empty while profiling
   size_t prof_next = 0;
   uf::CsrData csr64, csr32;
+  uf::CgSolveData cgs;           // continuous operators: solver work vectors
   double *kg_tables = nullptr;   // kappa-derivative 1D matrices (FP64)
   double *kg_scratch = nullptr;  // [n_active][1 + 2d] per-cell partials of the kappa gradient
 };
@@ -80,4 +95,15 @@ uf_status vmult_launch(uf_operator *op, int precision, void *y, const void *x, v
 void release_csr(CsrData &c);
 // kappa-derivative 1D matrices from the constant matrices of the structured terms.
 void kgrad_tables(int n, const std::vector<double> &m, std::vector<double> &out);
+// Constant 1D matrices of the structured terms (layout of StructTables, FP64).
+void structured_matrices(const HostOperator &op, std::vector<double> &out);
+// Continuous Q_p: load vector (f = 1) and diagonal of A on the host, FP64 (uf_cg.cu).
+void cg_host_vectors(HostOperator &op);
+uf_status cg_alloc(uf_operator *op);        // solver work vectors + Jacobi diagonal upload
+uf_status cg_upload_diag(uf_operator *op);  // (re)upload 1 / diag(A)
+void cg_free(uf_operator *op);
+template <typename T>
+int cg_gather(T *x_loc, const T *x, const int32_t *l2g, int64_t n_loc, cudaStream_t s);
+template <typename T>
+int cg_node_sum(T *y, const T *y_loc, const int32_t *off, const int32_t *idx, int64_t n, cudaStream_t s);
 }  // namespace uf

@@ -418,6 +418,15 @@ void sphere_box_rules(const Box &b, const double *c, double rho, const Gauss1 &g
 
 }  // namespace
 
+void lagrange_values(const Tables1D &t, double x, double *val, double *der) {
+  for (int i = 0; i < t.n; ++i) {
+    double dd[kMaxN + 1];
+    lagrange_derivs(t, i, x, 1, dd);
+    val[i] = dd[0];
+    der[i] = dd[1];
+  }
+}
+
 void build_tables_1d(int p, Tables1D &t) {
   std::memset(&t, 0, sizeof(t));
   t.p = p;
@@ -485,6 +494,11 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
     msg = "ls_radius must be positive";
     return UF_EINVAL;
   }
+  if (prm.discretization != UF_DG && prm.discretization != UF_CG) {
+    msg = "discretization must be UF_DG or UF_CG";
+    return UF_EINVAL;
+  }
+  op.cg = prm.discretization == UF_CG;
   op.dim = d;
   op.p = prm.degree;
   op.n = prm.degree + 1;
@@ -613,10 +627,11 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
         box_dist2(op.center, fb, dmin2, dmax2);
         const int ftype = dmax2 <= r2 ? 0 : (dmin2 >= r2 ? 2 : 1);  // full, cut, empty
         const bool gp = use_gp && (op.act_type[e] == 1 || op.act_type[nb] == 1);
-        if (ftype == 0) op.flags[e] |= face_bit_sipg_full(f);
-        if (ftype == 1) op.flags[e] |= face_bit_sipg_cut(f);
+        // the continuous space has no SIPG term
+        if (ftype == 0 && !op.cg) op.flags[e] |= face_bit_sipg_full(f);
+        if (ftype == 1 && !op.cg) op.flags[e] |= face_bit_sipg_cut(f);
         if (gp) op.flags[e] |= face_bit_gp(f);
-        if (ftype == 1 && op.act_type[e] == 0) {
+        if (ftype == 1 && op.act_type[e] == 0 && !op.cg) {
           msg = "internal: an inside cell has a cut face";
           return UF_EGEOMETRY;
         }
@@ -703,6 +718,43 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
   } catch (const QuadError &) {
     msg = "quadrature subdivision depth exceeded";
     return UF_EGEOMETRY;
+  }
+  if (op.cg) {
+    // lattice point p I_a + i_a of every cell-local DoF; used points numbered in lexicographic
+    // order (x fastest), which is the order of their linear lattice index
+    int64_t ldim[kMaxDim] = {1, 1, 1};
+    for (int a = 0; a < d; ++a) ldim[a] = op.p * op.N[a] + 1;
+    const int64_t n_loc = op.n_active * op.ndof;
+    std::vector<int64_t> lat(n_loc);
+    for (int64_t e = 0; e < op.n_active; ++e)
+      for (int l = 0; l < op.ndof; ++l) {
+        int64_t key = 0, stride = 1, rem = l;
+        for (int a = 0; a < d; ++a) {
+          const int64_t ia = rem % op.n;
+          rem /= op.n;
+          key += (op.act_index[e * 3 + a] * op.p + ia) * stride;
+          stride *= ldim[a];
+        }
+        lat[e * op.ndof + l] = key;
+      }
+    std::vector<int64_t> order(n_loc);
+    for (int64_t i = 0; i < n_loc; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return lat[a] < lat[b]; });
+    op.cg_l2g.assign(n_loc, -1);
+    op.cg_own_idx.assign(n_loc, 0);
+    op.cg_own_off.clear();
+    int64_t g = -1;
+    for (int64_t k = 0; k < n_loc; ++k) {
+      const int64_t i = order[k];
+      if (k == 0 || lat[i] != lat[order[k - 1]]) {
+        ++g;
+        op.cg_own_off.push_back((int32_t)k);
+      }
+      op.cg_l2g[i] = (int32_t)g;
+      op.cg_own_idx[k] = (int32_t)i;  // owners ascending (stable sort of ascending indices)
+    }
+    op.n_cg = g + 1;
+    op.cg_own_off.push_back((int32_t)n_loc);
   }
   return UF_OK;
 }
