@@ -59,6 +59,10 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-csr", action="store_true",
                     help="skip the assembled-matrix (CSR SpMV) comparison")
+    ap.add_argument("--config", choices=("q3", "solve", "sweep", "kappa"), default="q3",
+                    help="q3: the headline step (default); solve: CG Q4 time to solution, IR vs "
+                         "FP64; sweep: degree sweep p = 1..8 at ~2e7 DoFs; kappa: forward vs "
+                         "forward + backward of the differentiable operator")
     return ap.parse_args()
 
 
@@ -67,6 +71,21 @@ def dist_info():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def replica_throughput(local_seconds, units_per_rank, world, device=None):
+    """Whole-job throughput of independent replicas: every rank processed `units_per_rank`;
+    the job time is the maximum of the ranks' times (all_reduce MAX when world > 1).
+    Returns (units / s over all ranks, job seconds)."""
+    t = local_seconds
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        buf = torch.tensor([float(local_seconds)], dtype=torch.float64, device=device)
+        dist.all_reduce(buf, op=dist.ReduceOp.MAX)
+        t = float(buf.item())
+    return world * units_per_rank / t, t
 
 
 # ------------------------------------------------------------------------------ oracle sample
@@ -254,12 +273,9 @@ def run_ours(args, rank, world, local):
     barrier()
     step_ms = [ev_s[k].elapsed_time(ev_e[k]) for k in range(K)]
     ktimes = op.profile_end()
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * K * 3 * n / (total_ms / 1e3) / 1e9
+    value, total_s = replica_throughput(sum(step_ms) / 1e3, K * 3 * n, world, device="cuda")
+    value /= 1e9
+    total_ms = total_s * 1e3
 
     # ---- end to end through the C ABI with pinned host buffers (copies inside the region)
     xh64 = torch.from_numpy(x_host).pin_memory()
@@ -282,13 +298,9 @@ def run_ours(args, rank, world, local):
     for _ in range(K_e2e):
         e2e_step()
     barrier()
-    t_e2e = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_e2e = float(t.item())
+    e2e_value, t_e2e = replica_throughput(time.perf_counter() - t0, K_e2e * 3 * n, world, device="cuda")
     clk = clocks.stop()
-    e2e = {"value": world * K_e2e * 3 * n / t_e2e / 1e9, "unit": UNIT,
+    e2e = {"value": e2e_value / 1e9, "unit": UNIT,
            "h2d_bytes_per_step": 20 * n, "d2h_bytes_per_step": 20 * n}
 
     # ---- per-kernel figures from the events of the timed region
@@ -402,6 +414,144 @@ def csr_comparison(op, x64, flush, stream, hbm, K):
             "dtype": "f64 values, int32 columns, int64 row offsets"}
 
 
+# ------------------------------------------------------------------------------ extra workloads
+def _event_ms(fn, K, stream, flush=None):
+    import torch
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for k in range(K):
+        if flush is not None:
+            flush.zero_()
+        ev[k][0].record(stream)
+        fn()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return statistics.median(a.elapsed_time(b) for a, b in ev)
+
+
+def run_solve(args, local):
+    """CG Q4 ball solve: FP32 PCG inside FP64 refinement vs all-FP64 PCG, same final residual."""
+    import torch
+
+    from paper_2404_07911_gb300 import UF_FP32, UF_FP64, UnfittedOperator
+
+    torch.cuda.set_device(local)
+    cfg = workloads.cfg_cg_q4()
+    t0 = time.perf_counter()
+    op = UnfittedOperator(cfg, precisions=UF_FP64 | UF_FP32, device=local)
+    t_setup = time.perf_counter() - t0
+    _, rhs, _ = op.export_cg()
+    b = torch.from_numpy(rhs).cuda()
+    stream = torch.cuda.current_stream()
+    x64 = torch.zeros_like(b)
+    x32 = torch.zeros(op.n_dofs, dtype=torch.float32, device="cuda")
+    ms64 = _event_ms(lambda: op.vmult(b, x64, stream), 20, stream)
+    ms32 = _event_ms(lambda: op.vmult(b.float(), x32, stream), 20, stream)
+    xi, st_ir = op.solve(b, mode="ir", tol=1e-10, max_iter=200000)
+    xf, st_64 = op.solve(b, mode="fp64", tol=1e-10, max_iter=200000)
+    diff = ((xi - xf).abs().max() / xf.abs().max()).item()
+    print(json.dumps({
+        "metric": "time to solution of the continuous Q4 ball solve (relative residual 1e-10)",
+        "value": round(st_ir["seconds"], 4), "unit": "s", "higher_is_better": False,
+        "config": {"workload": cfg["name"], "n_dofs": op.n_dofs, "n_active": op.info["n_active"],
+                   "n_cut": op.info["n_cut"], "setup_s": round(t_setup, 2)},
+        "ir_fp32_in_fp64": st_ir, "fp64": st_64,
+        "speedup_ir_vs_fp64": round(st_64["seconds"] / st_ir["seconds"], 3),
+        "solution_rel_diff": diff,
+        "vmult_ms": {"fp64": round(ms64, 4), "fp32": round(ms32, 4)},
+        "data": "synthetic (f = 1)"}), flush=True)
+
+
+def run_sweep(args, local):
+    """Degree sweep p = 1..8 at about 2e7 DoFs: FP64 / FP32 GDoF/s and errors vs the oracle."""
+    import torch
+
+    from oracle import forms, mesh
+    from paper_2404_07911_gb300 import UF_FP32, UF_FP64, UnfittedOperator
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for p in range(1, 9):
+        cfg = workloads.cfg_sweep(p)
+        op = UnfittedOperator(cfg, precisions=UF_FP64 | UF_FP32, device=local)
+        n, nd = op.n_dofs, op.info["dofs_per_cell"]
+        xh = workloads.uniform_vector(n, cfg["seed"])
+        x64 = torch.from_numpy(xh).cuda()
+        x32 = x64.float()
+        y64 = torch.empty_like(x64)
+        y32 = torch.empty_like(x32)
+        for _ in range(3):
+            op.vmult(x64, y64, stream)
+            op.vmult(x32, y32, stream)
+        K = 20
+        ms64 = _event_ms(lambda: op.vmult(x64, y64, stream), K, stream, flush)
+        ms32 = _event_ms(lambda: op.vmult(x32, y32, stream), K, stream, flush)
+        o = forms.Oracle(mesh.problem_from_dict(cfg))
+        cut = np.nonzero(o.mesh.active_type == mesh.CUT)[0]
+        ins = np.nonzero(o.mesh.active_type == mesh.INSIDE)[0]
+        rng = np.random.default_rng(p)
+        cells = sorted(set(int(c) for c in list(rng.choice(cut, 4, replace=False)) +
+                           list(rng.choice(ins, 2, replace=False))))
+        ref = o.apply_rows(xh, cells)
+        ref32 = o.apply_rows(xh.astype(np.float32).astype(np.float64), cells)
+        g64 = y64.cpu().numpy().reshape(-1, nd)[cells]
+        g32 = y32.double().cpu().numpy().reshape(-1, nd)[cells]
+        sc = np.max(np.abs(ref))
+        print(json.dumps({
+            "metric": "degree sweep: GDoF/s of A x and relative error vs the oracle (sampled rows)",
+            "degree": p, "config": {"workload": cfg["name"], "n_dofs": n, "n_active": op.info["n_active"],
+                                    "n_cut": op.info["n_cut"]},
+            "fp64": {"ms": round(ms64, 4), "gdofs": round(n / ms64 / 1e6, 3),
+                     "rel_err": float(np.max(np.abs(g64 - ref)) / sc)},
+            "fp32": {"ms": round(ms32, 4), "gdofs": round(n / ms32 / 1e6, 3),
+                     "rel_err_vs_rounded_input": float(np.max(np.abs(g32 - ref32)) / sc),
+                     "rel_err_vs_fp64_oracle": float(np.max(np.abs(g32 - ref)) / sc)},
+            "l2": "flushed before every launch"}), flush=True)
+        op.close()
+        del x64, x32, y64, y32
+        torch.cuda.empty_cache()
+
+
+def run_kappa(args, local):
+    """Differentiable operator on the 48^3 kappa workload: forward vs forward + backward."""
+    import torch
+
+    from paper_2404_07911_gb300 import UF_FP64, UnfittedOperator
+    from paper_2404_07911_gb300.autograd import unfitted_poisson
+
+    torch.cuda.set_device(local)
+    cfg = workloads.cfg_kappa(48)
+    op = UnfittedOperator(cfg, precisions=UF_FP64, device=local)
+    kappa = torch.from_numpy(workloads.kappa_vector(op.info["n_active"], seed=4)).cuda()
+    xh, bh = workloads.x_and_b(op.n_dofs, seed=5)
+    x0 = torch.from_numpy(xh).cuda()
+    b = torch.from_numpy(bh).cuda()
+    stream = torch.cuda.current_stream()
+
+    def fwd():
+        with torch.no_grad():
+            y = unfitted_poisson(x0, kappa, op)
+            return 0.5 * torch.sum((y - b) ** 2)
+
+    def fwd_bwd():
+        x = x0.clone().requires_grad_(True)
+        k = kappa.clone().requires_grad_(True)
+        loss = 0.5 * torch.sum((unfitted_poisson(x, k, op) - b) ** 2)
+        loss.backward()
+
+    for _ in range(5):
+        fwd()
+        fwd_bwd()
+    ms_f = _event_ms(fwd, 20, stream)
+    ms_fb = _event_ms(fwd_bwd, 20, stream)
+    print(json.dumps({
+        "metric": "differentiable operator: forward vs forward + backward (loss 1/2 ||A(kappa) x - b||^2)",
+        "config": {"workload": cfg["name"], "n_dofs": op.n_dofs, "n_active": op.info["n_active"]},
+        "forward_ms": round(ms_f, 4), "forward_backward_ms": round(ms_fb, 4),
+        "ratio": round(ms_fb / ms_f, 3), "dtype": "f64"}), flush=True)
+
+
 # ------------------------------------------------------------------------------ reference arm
 def run_reference(args, rank, world):
     if rank != 0:
@@ -445,6 +595,12 @@ def main():
         if args.warmup > 3:
             args.warmup = 1
         run_reference(args, rank, world)
+    elif args.config == "solve":
+        run_solve(args, local)
+    elif args.config == "sweep":
+        run_sweep(args, local)
+    elif args.config == "kappa":
+        run_kappa(args, local)
     else:
         run_ours(args, rank, world, local)
 

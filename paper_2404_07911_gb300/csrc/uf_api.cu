@@ -256,6 +256,52 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   variant_tables(H, mats, lself, lnbgp);
   const size_t o_lself = L.take(sizeof(T) * lself.size());
   const size_t o_lnbgp = L.take(sizeof(T) * lnbgp.size());
+  // FP64: the 1D basis at every line and point (the FP64 pipe is the bottleneck there, HBM is not)
+  const bool pre = sizeof(T) == sizeof(double);
+  std::vector<double> vline_b, vpt_b, spt_b, fline_b, fpt_b;
+  if (pre) {
+    double v[uf::kMaxN], dv[uf::kMaxN];
+    vline_b.assign((size_t)std::max<int64_t>(nvl, 1) * 4 * n, 0.0);
+    for (int64_t l = 0; l < nvl; ++l) {
+      uf::lagrange_values(H.t, vline_o0[l], v, dv);
+      for (int i = 0; i < n; ++i) {
+        vline_b[l * 4 * n + i] = v[i];
+        vline_b[l * 4 * n + n + i] = dv[i];
+      }
+      if (d == 3) {
+        uf::lagrange_values(H.t, vline_o1[l], v, dv);
+        for (int i = 0; i < n; ++i) {
+          vline_b[l * 4 * n + 2 * n + i] = v[i];
+          vline_b[l * 4 * n + 3 * n + i] = dv[i];
+        }
+      }
+    }
+    auto pts = [&](const std::vector<double> &tt, std::vector<double> &out, bool deriv) {
+      const int w = deriv ? 2 * n : n;
+      out.assign((size_t)std::max<size_t>(tt.size(), 1) * w, 0.0);
+      for (size_t p = 0; p < tt.size(); ++p) {
+        uf::lagrange_values(H.t, tt[p], v, dv);
+        for (int i = 0; i < n; ++i) {
+          out[p * w + i] = v[i];
+          if (deriv) out[p * w + n + i] = dv[i];
+        }
+      }
+    };
+    pts(vpt_t, vpt_b, true);
+    pts(spt_t, spt_b, true);
+    pts(fpt_t, fpt_b, false);
+    fline_b.assign((size_t)std::max<int64_t>(nfl, 1) * n, 0.0);
+    if (d == 3)
+      for (int64_t l = 0; l < nfl; ++l) {
+        uf::lagrange_values(H.t, fline_o[l], v, dv);
+        for (int i = 0; i < n; ++i) fline_b[l * n + i] = v[i];
+      }
+  }
+  const size_t o_vlb = pre ? L.take(sizeof(T) * vline_b.size()) : 0;
+  const size_t o_vpb = pre ? L.take(sizeof(T) * vpt_b.size()) : 0;
+  const size_t o_spb = pre ? L.take(sizeof(T) * spt_b.size()) : 0;
+  const size_t o_flb = pre ? L.take(sizeof(T) * fline_b.size()) : 0;
+  const size_t o_fpb = pre ? L.take(sizeof(T) * fpt_b.size()) : 0;
 
   std::vector<unsigned char> img(L.bytes, 0);
   auto put = [&](size_t off, const void *src, size_t bytes) {
@@ -290,6 +336,13 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   put_t(o_fpw, fpt_w);
   put_t(o_lself, lself);
   put_t(o_lnbgp, lnbgp);
+  if (pre) {
+    put_t(o_vlb, vline_b);
+    put_t(o_vpb, vpt_b);
+    put_t(o_spb, spt_b);
+    put_t(o_flb, fline_b);
+    put_t(o_fpb, fpt_b);
+  }
 
   cudaError_t err = cudaMalloc(&pd.base, L.bytes);
   if (err != cudaSuccess) return fail(UF_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(err));
@@ -341,6 +394,11 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   A.fpt_w = TP(o_fpw);
   A.lself = TP(o_lself);
   A.lnbgp = TP(o_lnbgp);
+  A.vline_b = pre ? TP(o_vlb) : nullptr;
+  A.vpt_b = pre ? TP(o_vpb) : nullptr;
+  A.spt_b = pre ? TP(o_spb) : nullptr;
+  A.fline_b = pre ? TP(o_flb) : nullptr;
+  A.fpt_b = pre ? TP(o_fpb) : nullptr;
   if (sizeof(T) == sizeof(double)) {
     // kappa gradient (FP64): derivative tables and the per-cell partial buffer
     std::vector<double> kg;

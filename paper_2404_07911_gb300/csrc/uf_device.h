@@ -87,6 +87,10 @@ struct DevArrays {
   // lnbgp[2 * s + full] for a ghost-penalty face on side s.  When kappa is uniform
   // (kappa_uniform != 0) every structured term scales with that value.
   const T *lself, *lnbgp;
+  // FP64 only (null otherwise): the 1D basis at every line and point, precomputed at creation
+  // (values and derivatives; faces values only): vline_b [line][4n] = phi, phi' of the lower and
+  // upper outer coordinate; vpt_b / spt_b [point][2n]; fline_b [face line][n]; fpt_b [point][n].
+  const T *vline_b, *vpt_b, *spt_b, *fline_b, *fpt_b;
   int32_t kappa_uniform;
   int32_t n_active, n_cut;
 };

@@ -349,6 +349,27 @@ __device__ __forceinline__ void basis_1d_val(const PointTables<T, N> &pt, T xi, 
   for (int i = 0; i < N; ++i) val[i] = pre[i] * suf[i] * pt.den_inv[i];
 }
 
+// FP64 reads the 1D basis values at lines and points from tables built at creation (the FP64 pipe
+// runs at 1/64 of the FP32 rate on this part, so loading 2n values is cheaper than evaluating
+// them); FP32 evaluates them in registers.
+template <typename T>
+constexpr bool kPrecomputedBasis = sizeof(T) == sizeof(double);
+
+template <typename T, int N>
+__device__ __forceinline__ void point_basis(const PointTables<T, N> &pt, const T *tab, const T *tt,
+                                            int p, T *val, T *der) {
+  if constexpr (kPrecomputedBasis<T>) {
+    const T *bp = tab + (size_t)p * 2 * N;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      val[i] = __ldg(bp + i);
+      der[i] = __ldg(bp + N + i);
+    }
+  } else {
+    basis_1d<T, N>(pt, __ldg(tt + p), val, der);
+  }
+}
+
 // Lines per chunk (= threads per CTA) of the cut-cell kernel; bounded by the per-line shared
 // memory (2 n^{d-1} + 2 n values per line).
 template <int N>
@@ -433,8 +454,21 @@ __global__ void __launch_bounds__(cut_chunk<N>()) cut_kernel(const __grid_consta
       const int line = l0 + tid;
       if (line < lend) {
         T vb[N], db[N], vc[N], dc[N];
-        basis_1d<T, N>(pt, __ldg(d.vline_o0 + line), vb, db);
-        if constexpr (DIM == 3) basis_1d<T, N>(pt, __ldg(d.vline_o1 + line), vc, dc);
+        if constexpr (kPrecomputedBasis<T>) {
+          const T *bp = d.vline_b + (size_t)line * 4 * N;
+#pragma unroll
+          for (int i = 0; i < N; ++i) {
+            vb[i] = __ldg(bp + i);
+            db[i] = __ldg(bp + N + i);
+            if constexpr (DIM == 3) {
+              vc[i] = __ldg(bp + 2 * N + i);
+              dc[i] = __ldg(bp + 3 * N + i);
+            }
+          }
+        } else {
+          basis_1d<T, N>(pt, __ldg(d.vline_o0 + line), vb, db);
+          if constexpr (DIM == 3) basis_1d<T, N>(pt, __ldg(d.vline_o1 + line), vc, dc);
+        }
         // w0 = (phi_b phi_c) u, w1 = (phi_b' phi_c) u, w2 = (phi_b phi_c') u along the line
         T w0[N], w1[N], w2[N];
 #pragma unroll
@@ -477,7 +511,7 @@ __global__ void __launch_bounds__(cut_chunk<N>()) cut_kernel(const __grid_consta
 #pragma unroll 1
         for (int p = pb; p < pe; ++p) {
           T cv[N], cd[N];
-          basis_1d<T, N>(pt, __ldg(d.vpt_t + p), cv, cd);
+          point_basis<T, N>(pt, d.vpt_b, d.vpt_t, p, cv, cd);
           T gk = T(0), gb = T(0), gc = T(0);
 #pragma unroll
           for (int m = 0; m < N; ++m) {
@@ -501,7 +535,7 @@ __global__ void __launch_bounds__(cut_chunk<N>()) cut_kernel(const __grid_consta
         if (sp >= 0) {
           // kappa int_Gamma [ -d_n v u - v d_n u + tau/h v u ]
           T cv[N], cd[N];
-          basis_1d<T, N>(pt, __ldg(d.spt_t + sp), cv, cd);
+          point_basis<T, N>(pt, d.spt_b, d.spt_t, sp, cv, cd);
           T u = T(0), gk = T(0), gb = T(0), gc = T(0);
 #pragma unroll
           for (int m = 0; m < N; ++m) {
@@ -618,7 +652,12 @@ __global__ void __launch_bounds__(cut_chunk<N>()) cut_kernel(const __grid_consta
         const int s_line = (kk == 0) ? 1 : N, s_out = (kk == 0) ? N : 1;
         T vo[N];
         if constexpr (DIM == 3) {
-          basis_1d_val<T, N>(pt, __ldg(d.fline_o + line), vo);
+          if constexpr (kPrecomputedBasis<T>) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) vo[i] = __ldg(d.fline_b + (size_t)line * N + i);
+          } else {
+            basis_1d_val<T, N>(pt, __ldg(d.fline_o + line), vo);
+          }
         }
         // traces contracted along the outer in-face axis
         T r[4][N];
@@ -646,7 +685,12 @@ __global__ void __launch_bounds__(cut_chunk<N>()) cut_kernel(const __grid_consta
 #pragma unroll 1
         for (int p = pb; p < pe; ++p) {
           T cv[N];
-          basis_1d_val<T, N>(pt, __ldg(d.fpt_t + p), cv);
+          if constexpr (kPrecomputedBasis<T>) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) cv[i] = __ldg(d.fpt_b + (size_t)p * N + i);
+          } else {
+            basis_1d_val<T, N>(pt, __ldg(d.fpt_t + p), cv);
+          }
           T ev[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
           for (int m = 0; m < N; ++m)

@@ -226,8 +226,18 @@ __global__ void __launch_bounds__(32) kgrad_cut_kernel(const __grid_constant__ P
 #pragma unroll 1
     for (int line = lbeg + lane; line < lend; line += 32) {
       double vb[N], db[N], vc[N], dc[N];
-      basis_1d<double, N>(pt, __ldg(d.vline_o0 + line), vb, db);
-      if constexpr (DIM == 3) basis_1d<double, N>(pt, __ldg(d.vline_o1 + line), vc, dc);
+      {
+        const double *bp = d.vline_b + (size_t)line * 4 * N;  // precomputed at creation (FP64)
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          vb[i] = __ldg(bp + i);
+          db[i] = __ldg(bp + N + i);
+          if constexpr (DIM == 3) {
+            vc[i] = __ldg(bp + 2 * N + i);
+            dc[i] = __ldg(bp + 3 * N + i);
+          }
+        }
+      }
       double wx[3][N], wr[3][N];
 #pragma unroll
       for (int m = 0; m < N; ++m)
@@ -267,7 +277,7 @@ __global__ void __launch_bounds__(32) kgrad_cut_kernel(const __grid_constant__ P
 #pragma unroll 1
       for (int p = pb; p < pe; ++p) {
         double cv[N], cd[N];
-        basis_1d<double, N>(pt, __ldg(d.vpt_t + p), cv, cd);
+        point_basis<double, N>(pt, d.vpt_b, d.vpt_t, p, cv, cd);
         double gx[3] = {0, 0, 0}, gr[3] = {0, 0, 0};
 #pragma unroll
         for (int m = 0; m < N; ++m) {
@@ -285,7 +295,7 @@ __global__ void __launch_bounds__(32) kgrad_cut_kernel(const __grid_constant__ P
       const int sp = __ldg(d.lsurf + line);
       if (sp >= 0) {
         double cv[N], cd[N];
-        basis_1d<double, N>(pt, __ldg(d.spt_t + sp), cv, cd);
+        point_basis<double, N>(pt, d.spt_b, d.spt_t, sp, cv, cd);
         double ux = 0.0, ur = 0.0, gx[3] = {0, 0, 0}, gr[3] = {0, 0, 0};
 #pragma unroll
         for (int m = 0; m < N; ++m) {
@@ -357,7 +367,9 @@ __global__ void __launch_bounds__(32) kgrad_cut_kernel(const __grid_constant__ P
         }
       }
       double vo[N];
-      if constexpr (DIM == 3) basis_1d_val<double, N>(pt, __ldg(d.fline_o + line), vo);
+      if constexpr (DIM == 3)
+#pragma unroll
+        for (int i = 0; i < N; ++i) vo[i] = __ldg(d.fline_b + (size_t)line * N + i);
       double rr[6][N];
 #pragma unroll
       for (int m = 0; m < N; ++m)
@@ -380,7 +392,8 @@ __global__ void __launch_bounds__(32) kgrad_cut_kernel(const __grid_constant__ P
 #pragma unroll 1
       for (int p = pb; p < pe; ++p) {
         double cv[N];
-        basis_1d_val<double, N>(pt, __ldg(d.fpt_t + p), cv);
+#pragma unroll
+        for (int i = 0; i < N; ++i) cv[i] = __ldg(d.fpt_b + (size_t)p * N + i);
         double ev[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
         for (int m = 0; m < N; ++m)

@@ -19,6 +19,8 @@ benchmark configurations:
                        chosen so that the DoF count is about 2e7; q = p + 1; seed 2.
   * ``cfg_kappa``      3D, DG Q3 on a 48^3 background, same ball and penalties; per-cell
                        kappa ~ LogNormal(0, 0.5) seed 4; x then b ~ U[-1, 1] seed 5.
+  * ``cfg_cg_q4``      3D continuous Q4 on an 80^3 background, ball of radius 1 at the origin,
+                       Nitsche u = 0, ghost penalty orders 1..4, f = 1 (the solve workload).
   * ``small(...)``     reduced grids of the same geometry for tests the oracle finishes in seconds.
 
 Vectors are drawn with ``numpy.random.default_rng(seed)`` in DoF order (active cells
@@ -59,6 +61,15 @@ def cfg_sweep(p):
 
 def cfg_kappa(N=48):
     return cfg_3d(3, N, name=f"3d_dg_q3_{N}^3_ball_kappa", seed=5)
+
+
+def cfg_cg_q4(N=80):
+    """Continuous Q4 solve: ball of radius 1 at the origin, 80^3 background cells on
+    [-1.21, 1.21]^3, Nitsche u = 0 on the sphere (10 (p+1)^2 / h), face ghost penalty orders
+    1..4, f = 1, quadrature order p + 1."""
+    c = cfg_3d(4, N, center=(0.0, 0.0, 0.0), name=f"3d_cg_q4_{N}^3_ball_solve", seed=0, quad_order=5)
+    c["discretization"] = "cg"
+    return c
 
 
 def small(p=3, N=8, dim=3, center=None, seed=7):
