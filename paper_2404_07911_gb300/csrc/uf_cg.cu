@@ -246,20 +246,148 @@ __global__ void k_jacobi(T *__restrict__ z, const T *__restrict__ r, const T *__
   if (i < n) z[i] = invd[i] * r[i];
 }
 
-// x += alpha p, r -= alpha q
+// Block sums of (s0, s1) over kDotThreads threads, written to part[blockIdx.x] and
+// part[kDotBlocks + blockIdx.x] (fixed order).
+__device__ __forceinline__ void block_sums(double a0, double a1, double *__restrict__ part) {
+  __shared__ double s0[kDotThreads], s1[kDotThreads];
+  s0[threadIdx.x] = a0;
+  s1[threadIdx.x] = a1;
+  __syncthreads();
+  for (int w = kDotThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      s0[threadIdx.x] += s0[threadIdx.x + w];
+      s1[threadIdx.x] += s1[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = s0[0];
+    part[kDotBlocks + blockIdx.x] = s1[0];
+  }
+}
+
+// PCG start: pcg_init_final reads the block sums of r.z and r.r.
+__global__ void k_pcg_init_final(const double *__restrict__ part, PcgScalars *__restrict__ sc, double rtol) {
+  __shared__ double s0[kDotThreads], s1[kDotThreads];
+  double a0 = 0.0, a1 = 0.0;
+  for (int i = threadIdx.x; i < kDotBlocks; i += kDotThreads) {
+    a0 += part[i];
+    a1 += part[kDotBlocks + i];
+  }
+  s0[threadIdx.x] = a0;
+  s1[threadIdx.x] = a1;
+  __syncthreads();
+  for (int w = kDotThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      s0[threadIdx.x] += s0[threadIdx.x + w];
+      s1[threadIdx.x] += s1[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    sc->rz = s0[0];
+    sc->rr = s1[0];
+    sc->rr_stop = rtol * rtol * s1[0];
+    sc->pq = sc->alpha = sc->beta = 0.0;
+    sc->its = 0;
+    sc->status = (s1[0] == 0.0) ? 1 : 0;
+  }
+}
+
+// alpha = rz / pq from the block sums of p.q (breakdown if pq <= 0).
+__global__ void k_pcg_alpha(const double *__restrict__ part, PcgScalars *__restrict__ sc) {
+  if (sc->status != 0) return;
+  __shared__ double s0[kDotThreads];
+  double a0 = 0.0;
+  for (int i = threadIdx.x; i < kDotBlocks; i += kDotThreads) a0 += part[i];
+  s0[threadIdx.x] = a0;
+  __syncthreads();
+  for (int w = kDotThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) s0[threadIdx.x] += s0[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double pq = s0[0];
+    sc->pq = pq;
+    if (pq > 0.0) {
+      sc->alpha = sc->rz / pq;
+    } else {
+      sc->alpha = 0.0;
+      sc->status = 2;
+    }
+  }
+}
+
+// Block sums of p.q (grid of kDotBlocks), skipped once the run has stopped.
 template <typename T>
-__global__ void k_update_xr(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p,
-                            const T *__restrict__ q, T alpha, int64_t n) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) {
+__global__ void __launch_bounds__(kDotThreads) k_pcg_pq(const T *__restrict__ p, const T *__restrict__ q,
+                                                        int64_t n, double *__restrict__ part,
+                                                        const PcgScalars *__restrict__ sc) {
+  if (sc->status != 0) return;
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc = fma((double)p[i], (double)q[i], acc);
+  block_sums(acc, 0.0, part);
+}
+
+// x += alpha p, r -= alpha q, z = invd r, and the block sums of r.z and r.r (grid of kDotBlocks).
+template <typename T>
+__global__ void __launch_bounds__(kDotThreads)
+    k_pcg_update(T *__restrict__ x, T *__restrict__ r, T *__restrict__ z, const T *__restrict__ p,
+                 const T *__restrict__ q, const T *__restrict__ invd, int64_t n, double *__restrict__ part,
+                 const PcgScalars *__restrict__ sc) {
+  if (sc->status != 0) return;
+  const T alpha = (T)sc->alpha;
+  double a0 = 0.0, a1 = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     x[i] = fma(alpha, p[i], x[i]);
-    r[i] = fma(-alpha, q[i], r[i]);
+    const T ri = fma(-alpha, q[i], r[i]);
+    const T zi = invd[i] * ri;
+    r[i] = ri;
+    z[i] = zi;
+    a0 = fma((double)ri, (double)zi, a0);
+    a1 = fma((double)ri, (double)ri, a1);
+  }
+  block_sums(a0, a1, part);
+}
+
+// New r.z and r.r: stop test, then beta = rz_new / rz.
+__global__ void k_pcg_beta(const double *__restrict__ part, PcgScalars *__restrict__ sc) {
+  if (sc->status != 0) return;
+  __shared__ double s0[kDotThreads], s1[kDotThreads];
+  double a0 = 0.0, a1 = 0.0;
+  for (int i = threadIdx.x; i < kDotBlocks; i += kDotThreads) {
+    a0 += part[i];
+    a1 += part[kDotBlocks + i];
+  }
+  s0[threadIdx.x] = a0;
+  s1[threadIdx.x] = a1;
+  __syncthreads();
+  for (int w = kDotThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      s0[threadIdx.x] += s0[threadIdx.x + w];
+      s1[threadIdx.x] += s1[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    sc->its += 1;
+    sc->rr = s1[0];
+    if (s1[0] <= sc->rr_stop) {
+      sc->status = 1;
+    } else {
+      sc->beta = s0[0] / sc->rz;
+      sc->rz = s0[0];
+    }
   }
 }
 
 // p = z + beta p
 template <typename T>
-__global__ void k_update_p(T *__restrict__ p, const T *__restrict__ z, T beta, int64_t n) {
+__global__ void k_pcg_direction(T *__restrict__ p, const T *__restrict__ z, int64_t n,
+                                const PcgScalars *__restrict__ sc) {
+  if (sc->status != 0) return;
+  const T beta = (T)sc->beta;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) p[i] = fma(beta, p[i], z[i]);
 }
@@ -325,25 +453,33 @@ struct SolveCtx {
   uf_operator *op;
   cudaStream_t s;
   int64_t n;
-  double *dot_part;  // [2 * kDotBlocks]
-  double *dot_out;   // [2] device
-  double *dot_host;  // [2] pinned host
+  double *dot_part;        // [2 * kDotBlocks]
+  double *dot_out;         // [2] device
+  double *dot_host;        // [2] pinned host
+  PcgScalars *sc;          // device
+  PcgScalars *sc_host;     // pinned host
 };
 
+// Iterations enqueued between two reads of the stopping state.  The kernels of iterations
+// after the stop are no-ops except the operator's own, so at most kChunk - 1 vmults are spent
+// past convergence while the host never waits inside a chunk.
+constexpr int kChunk = 32;
+
+// One FP64 dot product (two fixed-order reduction passes), read back synchronously.
 template <typename T>
-uf_status dots(SolveCtx &c, const T *a, const T *b, bool two, double &ab, double &aa) {
-  k_dot_partial<T><<<kDotBlocks, kDotThreads, 0, c.s>>>(a, b, c.n, c.dot_part, two ? 1 : 0);
+uf_status host_dot(SolveCtx &c, const T *a, const T *b, double &ab) {
+  k_dot_partial<T><<<kDotBlocks, kDotThreads, 0, c.s>>>(a, b, c.n, c.dot_part, 0);
   k_dot_final<<<1, kDotThreads, 0, c.s>>>(c.dot_part, c.dot_out);
   cudaError_t err = cudaMemcpyAsync(c.dot_host, c.dot_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.s);
   if (err == cudaSuccess) err = cudaStreamSynchronize(c.s);
   if (err != cudaSuccess) return fail(UF_ECUDA, std::string("reduction: ") + cudaGetErrorString(err));
   ab = c.dot_host[0];
-  aa = c.dot_host[1];
   return UF_OK;
 }
 
 // Jacobi-preconditioned CG on A x = r (x starts at zero, r is overwritten by the residual) until
-// ||r|| <= rtol ||r_0|| or `maxit` iterations; returns the iterations done in *its.
+// ||r|| <= rtol ||r_0|| or `maxit` iterations; *its = iterations done, *rel = ||r|| / ||r_0|| of
+// the recursive residual.  alpha, beta and the dot products stay on the device (PcgScalars).
 template <typename T>
 uf_status pcg(SolveCtx &c, int precision, const T *invd, T *x, T *r, T *z, T *p, T *q, double rtol,
               int maxit, int *its, double *rel) {
@@ -351,32 +487,34 @@ uf_status pcg(SolveCtx &c, int precision, const T *invd, T *x, T *r, T *z, T *p,
   k_fill<T><<<nblk(n), 256, 0, c.s>>>(x, T(0), n);
   k_jacobi<T><<<nblk(n), 256, 0, c.s>>>(z, r, invd, n);
   cudaMemcpyAsync(p, z, n * sizeof(T), cudaMemcpyDeviceToDevice, c.s);
-  double rz, rr;
-  uf_status st = dots<T>(c, r, z, true, rz, rr);
-  if (st != UF_OK) return st;
-  const double r0 = std::sqrt(rr);
+  k_dot_partial<T><<<kDotBlocks, kDotThreads, 0, c.s>>>(r, z, n, c.dot_part, 1);
+  k_pcg_init_final<<<1, kDotThreads, 0, c.s>>>(c.dot_part, c.sc, rtol);
   *its = 0;
   *rel = 1.0;
-  if (r0 == 0.0) return UF_OK;
-  for (int it = 1; it <= maxit; ++it) {
-    st = vmult_launch(c.op, precision, q, p, c.s, false);
-    if (st != UF_OK) return st;
-    double pq, dummy;
-    st = dots<T>(c, p, q, false, pq, dummy);
-    if (st != UF_OK) return st;
-    if (!(pq > 0.0)) return fail(UF_EINVAL, "CG breakdown: the operator is not positive definite");
-    const double alpha = rz / pq;
-    k_update_xr<T><<<nblk(n), 256, 0, c.s>>>(x, r, p, q, (T)alpha, n);
-    k_jacobi<T><<<nblk(n), 256, 0, c.s>>>(z, r, invd, n);
-    double rz_new;
-    st = dots<T>(c, r, z, true, rz_new, rr);
-    if (st != UF_OK) return st;
-    *its = it;
-    *rel = std::sqrt(rr) / r0;
-    if (*rel <= rtol) break;
-    const double beta = rz_new / rz;
-    rz = rz_new;
-    k_update_p<T><<<nblk(n), 256, 0, c.s>>>(p, z, (T)beta, n);
+  double rr0 = 0.0;
+  bool started = false;  // the first pass only reads the state after the start
+  for (int launched = 0;;) {
+    const int chunk = started ? std::min(kChunk, maxit - launched) : 0;
+    for (int i = 0; i < chunk; ++i) {
+      uf_status st = vmult_launch(c.op, precision, q, p, c.s, false);
+      if (st != UF_OK) return st;
+      k_pcg_pq<T><<<kDotBlocks, kDotThreads, 0, c.s>>>(p, q, n, c.dot_part, c.sc);
+      k_pcg_alpha<<<1, kDotThreads, 0, c.s>>>(c.dot_part, c.sc);
+      k_pcg_update<T><<<kDotBlocks, kDotThreads, 0, c.s>>>(x, r, z, p, q, invd, n, c.dot_part, c.sc);
+      k_pcg_beta<<<1, kDotThreads, 0, c.s>>>(c.dot_part, c.sc);
+      k_pcg_direction<T><<<nblk(n), 256, 0, c.s>>>(p, z, n, c.sc);
+    }
+    launched += chunk;
+    cudaError_t err = cudaMemcpyAsync(c.sc_host, c.sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, c.s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(c.s);
+    if (err != cudaSuccess) return fail(UF_ECUDA, std::string("PCG: ") + cudaGetErrorString(err));
+    const PcgScalars &h = *c.sc_host;
+    if (!started) rr0 = h.rr;
+    started = true;
+    *its = h.its;
+    *rel = rr0 > 0.0 ? std::sqrt(h.rr / rr0) : 0.0;
+    if (h.status == 2) return fail(UF_EINVAL, "CG breakdown: the operator is not positive definite");
+    if (h.status == 1 || launched >= maxit) break;
   }
   return UF_OK;
 }
@@ -399,15 +537,15 @@ extern "C" uf_status uf_solve(uf_operator *op, const uf_solve_params *prm, doubl
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int64_t n = op->host.n_cg;
   uf::CgSolveData &w = op->cgs;
-  uf::SolveCtx c{op, s, n, w.dot_part, w.dot_out, w.dot_host};
+  uf::SolveCtx c{op, s, n, w.dot_part, w.dot_out, w.dot_host, w.sc, w.sc_host};
   std::memset(stats, 0, sizeof(*stats));
   cudaEvent_t t0, t1;
   cudaEventCreate(&t0);
   cudaEventCreate(&t1);
   cudaEventRecord(t0, s);
   uf_status st = UF_OK;
-  double bb, dummy;
-  st = uf::dots<double>(c, b, b, false, bb, dummy);
+  double bb = 0.0;
+  st = uf::host_dot<double>(c, b, b, bb);
   const double bnorm = std::sqrt(bb);
   auto residual64 = [&]() -> uf_status {  // r64 = b - A x (FP64)
     uf_status s2 = uf::vmult_launch(op, UF_FP64, w.q64, x, s, false);
@@ -415,47 +553,42 @@ extern "C" uf_status uf_solve(uf_operator *op, const uf_solve_params *prm, doubl
     uf::k_residual<<<uf::nblk(n), 256, 0, s>>>(w.r64, b, w.q64, n);
     return UF_OK;
   };
+  const bool ir = prm->mode == UF_SOLVE_IR;
   int total_it = 0, outer = 0;
   double rel = 1.0;
   if (st == UF_OK && bnorm == 0.0) {
     uf::k_fill<double><<<uf::nblk(n), 256, 0, s>>>(x, 0.0, n);
     rel = 0.0;
-  } else if (st == UF_OK && prm->mode == UF_SOLVE_FP64) {
-    // FP64 PCG for the correction of the initial guess: A d = b - A x, x += d
-    st = residual64();
-    int its = 0;
-    double rr, rn;
-    if (st == UF_OK) st = uf::dots<double>(c, w.r64, w.r64, false, rr, dummy);
-    rn = std::sqrt(rr);
-    if (st == UF_OK && rn > prm->tol * bnorm) {
-      st = uf::pcg<double>(c, UF_FP64, w.invd64, w.d64, w.r64, w.z64, w.p64, w.q64,
-                           prm->tol * bnorm / rn, prm->max_iter, &its, &rel);
-      if (st == UF_OK) uf::k_add<<<uf::nblk(n), 256, 0, s>>>(x, w.d64, n);
-    }
-    total_it = its;
-    outer = 1;
-    if (st == UF_OK) st = residual64();
-    if (st == UF_OK) st = uf::dots<double>(c, w.r64, w.r64, false, rr, dummy);
-    rel = std::sqrt(rr) / bnorm;
   } else if (st == UF_OK) {
-    // FP32 inner PCG inside FP64 iterative refinement
+    // Correction steps on the FP64 residual r = b - A x:
+    //   FP64 mode: PCG in FP64 on A d = r to the remaining reduction tol ||b|| / ||r||, x += d;
+    //     it is repeated (restarted CG) while the recursive residual of the PCG has drifted
+    //     from the true one, so both modes stop on the same true FP64 residual;
+    //   IR mode: PCG in FP32 on A d = r / ||r|| to inner_tol, x += ||r|| d.
     st = residual64();
     for (outer = 0; st == UF_OK && outer < std::max(prm->max_outer, 1); ++outer) {
-      double rr;
-      st = uf::dots<double>(c, w.r64, w.r64, false, rr, dummy);
+      double rr = 0.0;
+      st = uf::host_dot<double>(c, w.r64, w.r64, rr);
       if (st != UF_OK) break;
       const double rn = std::sqrt(rr);
       rel = rn / bnorm;
       if (rel <= prm->tol || total_it >= prm->max_iter) break;
-      uf::k_scale_to_f32<<<uf::nblk(n), 256, 0, s>>>(w.r32, w.r64, 1.0 / rn, n);
       int its = 0;
-      double rel_in;
-      st = uf::pcg<float>(c, UF_FP32, w.invd32, w.d32, w.r32, w.z32, w.p32, w.q32,
-                          prm->inner_tol > 0.0 ? prm->inner_tol : 1e-4, prm->max_iter - total_it,
-                          &its, &rel_in);
-      if (st != UF_OK) break;
+      double rel_in = 1.0;
+      if (ir) {
+        uf::k_scale_to_f32<<<uf::nblk(n), 256, 0, s>>>(w.r32, w.r64, 1.0 / rn, n);
+        st = uf::pcg<float>(c, UF_FP32, w.invd32, w.d32, w.r32, w.z32, w.p32, w.q32,
+                            prm->inner_tol > 0.0 ? prm->inner_tol : 1e-4, prm->max_iter - total_it,
+                            &its, &rel_in);
+        if (st != UF_OK) break;
+        uf::k_refine<<<uf::nblk(n), 256, 0, s>>>(x, w.d32, rn, n);
+      } else {
+        st = uf::pcg<double>(c, UF_FP64, w.invd64, w.d64, w.r64, w.z64, w.p64, w.q64,
+                             prm->tol * bnorm / rn, prm->max_iter - total_it, &its, &rel_in);
+        if (st != UF_OK) break;
+        uf::k_add<<<uf::nblk(n), 256, 0, s>>>(x, w.d64, n);
+      }
       total_it += its;
-      uf::k_refine<<<uf::nblk(n), 256, 0, s>>>(x, w.d32, rn, n);
       st = residual64();
     }
   }
@@ -500,7 +633,9 @@ uf_status cg_alloc(uf_operator *op) {
   }
   A((void **)&w.dot_part, 2 * kDotBlocks * sizeof(double));
   A((void **)&w.dot_out, 2 * sizeof(double));
+  A((void **)&w.sc, sizeof(PcgScalars));
   if (err == cudaSuccess) err = cudaMallocHost((void **)&w.dot_host, 2 * sizeof(double));
+  if (err == cudaSuccess) err = cudaMallocHost((void **)&w.sc_host, sizeof(PcgScalars));
   if (err != cudaSuccess) return fail(UF_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(err));
   return cg_upload_diag(op);
 }
@@ -524,10 +659,11 @@ uf_status cg_upload_diag(uf_operator *op) {
 void cg_free(uf_operator *op) {
   CgSolveData &w = op->cgs;
   void *ptrs[] = {w.r64, w.q64, w.d64, w.z64, w.p64, w.invd64, w.r32, w.q32, w.d32,
-                  w.z32, w.p32, w.invd32, w.dot_part, w.dot_out};
+                  w.z32, w.p32, w.invd32, w.dot_part, w.dot_out, w.sc};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (w.dot_host) cudaFreeHost(w.dot_host);
+  if (w.sc_host) cudaFreeHost(w.sc_host);
   w = CgSolveData{};
 }
 

@@ -34,6 +34,17 @@ struct PrecisionData {
   T *x_loc = nullptr, *y_loc = nullptr;
 };
 
+// Scalars of one PCG run, kept in device memory so that the iterations need no host round trip.
+struct PcgScalars {
+  double rz;       // r . z of the current iterate
+  double pq;       // p . A p
+  double rr;       // r . r
+  double alpha, beta;
+  double rr_stop;  // converged once rr <= rr_stop
+  int status;      // 0 running, 1 converged, 2 breakdown (p . A p <= 0)
+  int its;         // iterations completed
+};
+
 // Work vectors of the CG solvers (continuous operators).
 struct CgSolveData {
   bool ready = false;
@@ -42,6 +53,7 @@ struct CgSolveData {
   float *r32 = nullptr, *q32 = nullptr, *d32 = nullptr, *z32 = nullptr, *p32 = nullptr;
   float *invd32 = nullptr;
   double *dot_part = nullptr, *dot_out = nullptr, *dot_host = nullptr;
+  PcgScalars *sc = nullptr, *sc_host = nullptr;  // device / pinned host copy
 };
 
 struct ProfSlot {
