@@ -93,8 +93,14 @@ typedef struct {
   double flops;
   /* Per kernel (index 0 = structured terms of all cells, 1 = unstructured terms of cut cells):
    * algorithmic bytes for FP64 / FP32 data and algorithmic floating-point operations (model
-   * above) of one launch, and the floating-point operations the kernels execute as built. */
+   * above) of one launch, and the floating-point operations the kernels execute as built: the
+   * FP64 kernels read the 1D basis at lines and points from tables, the FP32 kernels evaluate
+   * it (kernel_flops_built_fp32). */
   double kernel_bytes_fp64[2], kernel_bytes_fp32[2], kernel_flops[2], kernel_flops_built[2];
+  double kernel_flops_built_fp32[2];
+  /* Groups of volume lines (3D): lines of a cut cell along one axis that share one outer
+   * coordinate; the cut-cell kernel contracts along that coordinate once per group. */
+  int64_t n_vol_groups;
 } uf_info;
 
 /* Per-kernel device times collected between uf_profile_begin and uf_profile_end, indexed
@@ -231,14 +237,17 @@ uf_status uf_export_cg(const uf_operator *op, int32_t *l2g, double *rhs, double 
 /* Solve A x = b for a continuous (UF_CG) operator with Jacobi-preconditioned CG (the solver of
  * the paper's Sec. 3.5 is a PCG; its multigrid preconditioner is out of scope):
  *   UF_SOLVE_FP64  PCG in FP64 on the correction of the initial guess until
- *                  ||b - A x|| <= tol ||b||;
+ *                  ||b - A x|| <= tol ||b||, restarted from the true FP64 residual while the
+ *                  recursive residual of the PCG has drifted below it (outer counts the runs);
  *   UF_SOLVE_IR    iterative refinement: FP64 residual r = b - A x, FP32 PCG on A d = r / ||r||
  *                  to a relative reduction inner_tol, FP64 update x += ||r|| d, repeated until
  *                  the FP64 relative residual is <= tol (FP64 only for the outer residual and the
  *                  update; the FP32 operator carries the Nitsche and ghost-penalty terms).
- * x (in: initial guess, out: solution) and b are FP64 device vectors [n_dofs].  Synchronous: the
- * dot products (deterministic two-pass reductions) are read back every iteration.  max_iter caps
- * the CG iterations (all inner iterations in IR mode), max_outer the refinement steps.
+ * x (in: initial guess, out: solution) and b are FP64 device vectors [n_dofs].  Synchronous on
+ * return.  The dot products (deterministic two-pass FP64 reductions), alpha and beta stay in
+ * device memory; the host reads the stopping state once per 32 iterations, so up to 31 operator
+ * applications run past the stop (their updates are skipped).  max_iter caps the CG iterations
+ * (all inner iterations in IR mode), max_outer the refinement steps / restarts.
  * Work vectors are allocated at creation; no allocation here.  Errors: UF_EINVAL (not a UF_CG
  * operator, missing precision, bad parameters, breakdown), UF_ENODEVICE, UF_ECUDA. */
 enum { UF_SOLVE_FP64 = 0, UF_SOLVE_IR = 1 };

@@ -57,7 +57,8 @@ class uf_info(ctypes.Structure):
         ("quad_order", ctypes.c_int32), ("h", ctypes.c_double), ("bytes_fp64", ctypes.c_double),
         ("bytes_fp32", ctypes.c_double), ("flops", ctypes.c_double),
         ("kernel_bytes_fp64", ctypes.c_double * 2), ("kernel_bytes_fp32", ctypes.c_double * 2),
-        ("kernel_flops", ctypes.c_double * 2), ("kernel_flops_built", ctypes.c_double * 2)]
+        ("kernel_flops", ctypes.c_double * 2), ("kernel_flops_built", ctypes.c_double * 2),
+        ("kernel_flops_built_fp32", ctypes.c_double * 2), ("n_vol_groups", ctypes.c_int64)]
 
 
 class uf_kernel_times(ctypes.Structure):

@@ -139,6 +139,64 @@ void variant_tables(const uf::HostOperator &op, const std::vector<double> &m,
             (full ? M(8, s)[i] + M(10, s)[i] + M(12, s)[i] : 0.0) + M(14, s)[i];
 }
 
+// Outer reference coordinate `which` (0: lower other axis, 1: upper) of a line along axis k.
+double line_outer(const uf::HostOperator &H, const uf::QLine &ln, int which) {
+  const int d = H.dim, k = ln.k;
+  int ob = (k == 0) ? 1 : 0, oc = (k == 2) ? 1 : 2;
+  if (d == 2) ob = 1 - k;
+  if (which == 1 && d == 2) return 0.0;
+  const bool from_vol = ln.vcnt > 0;
+  const int64_t p0 = from_vol ? ln.vbeg : ln.sidx;
+  const std::vector<double> *xi = from_vol ? H.vol_xi : H.surf_xi;
+  return xi[which == 0 ? ob : oc][p0];
+}
+
+// Groups of the lines of one cut cell along one axis (3D): lines that share one outer
+// coordinate (the points of one line of the (d-1)-dimensional outer rule) form a group, so the
+// contraction along the shared axis is done once per group.  The shared axis is the one with
+// fewer distinct values; `lines` is reordered so that groups are contiguous, and
+// group_start[i] = index in `lines` of the first line of line i's group.  Returns 1 if the
+// lines share the lower outer coordinate, 0 if the upper one (2D: no groups, returns 0).
+int group_lines(const uf::HostOperator &H, std::vector<const uf::QLine *> &lines,
+                std::vector<int> &group_start) {
+  group_start.resize(lines.size());
+  if (H.dim != 3 || lines.empty()) {
+    for (size_t i = 0; i < lines.size(); ++i) group_start[i] = (int)i;
+    return 0;
+  }
+  auto distinct = [&](int which) {
+    std::vector<double> v;
+    for (const uf::QLine *l : lines) v.push_back(line_outer(H, *l, which));
+    std::sort(v.begin(), v.end());
+    return std::unique(v.begin(), v.end()) - v.begin();
+  };
+  const int shared_lo = distinct(0) < distinct(1) ? 1 : 0;
+  const int which = shared_lo ? 0 : 1;
+  std::stable_sort(lines.begin(), lines.end(), [&](const uf::QLine *a, const uf::QLine *b) {
+    return line_outer(H, *a, which) < line_outer(H, *b, which);
+  });
+  for (size_t i = 0; i < lines.size(); ++i)
+    group_start[i] = (i > 0 && line_outer(H, *lines[i], which) == line_outer(H, *lines[i - 1], which))
+                         ? group_start[i - 1]
+                         : (int)i;
+  return shared_lo;
+}
+
+// Number of line groups of all cut cells (group_lines), for the as-built operation count.
+int64_t count_line_groups(const uf::HostOperator &H) {
+  int64_t groups = 0;
+  std::vector<int> gs;
+  for (int64_t c = 0; c < H.n_cut; ++c)
+    for (int k = 0; k < H.dim; ++k) {
+      std::vector<const uf::QLine *> lk;
+      for (int64_t li = H.vline_off[c]; li < H.vline_off[c + 1]; ++li)
+        if (H.vol_lines[li].k == k) lk.push_back(&H.vol_lines[li]);
+      group_lines(H, lk, gs);
+      for (size_t i = 0; i < gs.size(); ++i) groups += (gs[i] == (int)i) ? 1 : 0;
+    }
+  return groups;
+}
+
 bool kappa_is_uniform(const std::vector<double> &k) {
   for (double v : k)
     if (v != k[0]) return false;
@@ -170,7 +228,7 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   }
 
   // ---- line-structured point data (lines of a cell sorted by axis)
-  std::vector<int32_t> vline_koff(nc * 4), vpt_off, lsurf, fline_koff(nc * nf * 3), fpt_off;
+  std::vector<int32_t> vline_koff(nc * 4), vpt_off, lsurf, fline_koff(nc * nf * 3), fpt_off, vline_grp;
   std::vector<double> vline_o0, vline_o1, vpt_t, vpt_w, spt_t, spt_w, spt_n[3];
   std::vector<double> fline_o, fpt_t, fpt_w;
   vpt_off.push_back(0);
@@ -181,30 +239,32 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
     std::stable_sort(ls.begin(), ls.end(), [](const uf::QLine &a, const uf::QLine &b) { return a.k < b.k; });
     for (int k = 0; k < 4; ++k) {
       vline_koff[c * 4 + k] = (int32_t)lsurf.size();
+      std::vector<const uf::QLine *> lk;
       if (k < d)
-        for (const uf::QLine &ln : ls) {
-          if (ln.k != k) continue;
-          int ob = (k == 0) ? 1 : 0, oc = (k == 2) ? 1 : 2;
-          if (d == 2) ob = 1 - k;
-          const bool from_vol = ln.vcnt > 0;
-          const int64_t p0 = from_vol ? ln.vbeg : ln.sidx;
-          const std::vector<double> *xi = from_vol ? H.vol_xi : H.surf_xi;
-          vline_o0.push_back(xi[ob][p0]);
-          vline_o1.push_back(d == 3 ? xi[oc][p0] : 0.0);
-          for (int64_t p = ln.vbeg; p < ln.vbeg + ln.vcnt; ++p) {
-            vpt_t.push_back(H.vol_xi[k][p]);
-            vpt_w.push_back(H.vol_w[p]);
-          }
-          vpt_off.push_back((int32_t)vpt_t.size());
-          if (ln.sidx >= 0) {
-            lsurf.push_back((int32_t)spt_t.size());
-            spt_t.push_back(H.surf_xi[k][ln.sidx]);
-            spt_w.push_back(H.surf_w[ln.sidx]);
-            for (int a = 0; a < 3; ++a) spt_n[a].push_back(a < d ? H.surf_n[a][ln.sidx] : 0.0);
-          } else {
-            lsurf.push_back(-1);
-          }
+        for (const uf::QLine &ln : ls)
+          if (ln.k == k) lk.push_back(&ln);
+      std::vector<int> gstart;
+      const int shared_lo = group_lines(H, lk, gstart);
+      const int32_t first = (int32_t)lsurf.size();
+      for (size_t i = 0; i < lk.size(); ++i) {
+        const uf::QLine &ln = *lk[i];
+        vline_grp.push_back(((first + gstart[i]) << 1) | shared_lo);
+        vline_o0.push_back(line_outer(H, ln, 0));
+        vline_o1.push_back(line_outer(H, ln, 1));
+        for (int64_t p = ln.vbeg; p < ln.vbeg + ln.vcnt; ++p) {
+          vpt_t.push_back(H.vol_xi[k][p]);
+          vpt_w.push_back(H.vol_w[p]);
         }
+        vpt_off.push_back((int32_t)vpt_t.size());
+        if (ln.sidx >= 0) {
+          lsurf.push_back((int32_t)spt_t.size());
+          spt_t.push_back(H.surf_xi[k][ln.sidx]);
+          spt_w.push_back(H.surf_w[ln.sidx]);
+          for (int a = 0; a < 3; ++a) spt_n[a].push_back(a < d ? H.surf_n[a][ln.sidx] : 0.0);
+        } else {
+          lsurf.push_back(-1);
+        }
+      }
     }
     for (int f = 0; f < nf; ++f) {
       std::vector<uf::QLine> fls(H.face_lines.begin() + H.fline_off[c * nf + f],
@@ -240,6 +300,7 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   const size_t o_vo1 = L.take(sizeof(T) * std::max<int64_t>(nvl, 1));
   const size_t o_vpo = L.take(sizeof(int32_t) * (nvl + 1));
   const size_t o_lsf = L.take(sizeof(int32_t) * std::max<int64_t>(nvl, 1));
+  const size_t o_vlg = L.take(sizeof(int32_t) * std::max<int64_t>(nvl, 1));
   const size_t o_vpt = L.take(sizeof(T) * std::max<int64_t>(nv, 1));
   const size_t o_vpw = L.take(sizeof(T) * std::max<int64_t>(nv, 1));
   const size_t o_spt = L.take(sizeof(T) * std::max<int64_t>(ns, 1));
@@ -324,6 +385,7 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   put_t(o_vo1, vline_o1);
   put_i(o_vpo, vpt_off);
   put_i(o_lsf, lsurf);
+  put_i(o_vlg, vline_grp);
   put_t(o_vpt, vpt_t);
   put_t(o_vpw, vpt_w);
   put_t(o_spt, spt_t);
@@ -382,6 +444,7 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   A.vline_o1 = TP(o_vo1);
   A.vpt_off = I32(o_vpo);
   A.lsurf = I32(o_lsf);
+  A.vline_grp = I32(o_vlg);
   A.vpt_t = TP(o_vpt);
   A.vpt_w = TP(o_vpw);
   A.spt_t = TP(o_spt);
@@ -601,6 +664,7 @@ uf_status uf_get_info(const uf_operator *op, uf_info *info) {
   info->n_face_points = H.n_face_points_unique;
   info->n_vol_lines = (int64_t)H.vol_lines.size();
   info->n_face_lines = (int64_t)H.face_lines.size();
+  info->n_vol_groups = count_line_groups(H);
   info->dim = H.dim;
   info->degree = H.p;
   info->dofs_per_cell = H.ndof;
@@ -653,25 +717,34 @@ uf_status uf_get_info(const uf_operator *op, uf_info *info) {
                             (double)gp_faces_cell * sweep) +
                      (double)H.n_active * d * nd + (double)r2_faces_cell * nline * (4 * n + 8);
   if (!uni) fl_struct += (double)H.n_active * d * n * n * 2.0 * 13.0;
-  // cut-cell kernel: 1D basis (values and derivatives) 14n - 8, values only 6n - 4 flops
-  const double fb = 14 * n - 8, fbv = 6 * n - 4;
+  // cut-cell kernel: 1D basis (values and derivatives) 14n - 8, values only 6n - 4 flops when
+  // evaluated (FP32); the FP64 kernels read them from tables (fb = fbv = 0)
   const double vlines = (double)H.vol_lines.size(), flines = (double)H.face_lines.size();
-  double fl_cut = 0.0;
-  if (d == 3) {
-    fl_cut += vlines * (2 * fb + 2 * (2 * n * n * n + 3 * n * n) + 4 * n * n + 4 * n * n * n);
-    fl_cut += (double)info->n_vol_points * (fb + 2 * 3 * n + 4 + 2 * 3 * n);
-    fl_cut += (double)info->n_surf_points * (fb + 2 * 4 * n + 16 + 2 * 3 * n + 6);
-    fl_cut += flines * (fbv + 2 * 4 * n * n + 2 * 2 * n * n);
-  } else {
-    fl_cut += vlines * (fb + 2 * 2 * n * n + 2 * 2 * n * n);
-    fl_cut += (double)info->n_vol_points * (fb + 2 * 2 * n + 3 + 2 * 2 * n);
-    fl_cut += (double)info->n_surf_points * (fb + 2 * 3 * n + 12 + 2 * 2 * n + 4);
-    fl_cut += flines * (2 * 2 * n);
-  }
-  fl_cut += 2.0 * (double)info->n_face_points * (fbv + 2 * 4 * n + 10 + 2 * 2 * n);
-  fl_cut += 2.0 * (double)H.n_faces_cut * (2 * 4 * nd + 4 * nd);  // traces and expansion
+  const double vgroups = (double)info->n_vol_groups;
+  auto cut_flops = [&](bool tables) {
+    const double fb = tables ? 0.0 : 14 * n - 8, fbv = tables ? 0.0 : 6 * n - 4;
+    double fl = 0.0;
+    if (d == 3) {
+      // per group: contraction along the shared axis and expansion back (2 n^3 FMA each);
+      // per line: its own outer axis, evaluation and integration (3 n^2 FMA each)
+      fl += vgroups * (fb + 8 * n * n * n) + vlines * (fb + 12 * n * n);
+      fl += (double)info->n_vol_points * (fb + 2 * 3 * n + 4 + 2 * 3 * n);
+      fl += (double)info->n_surf_points * (fb + 2 * 4 * n + 16 + 2 * 3 * n + 6);
+      fl += flines * (fbv + 2 * 4 * n * n + 2 * 2 * n * n);
+    } else {
+      fl += vlines * (fb + 2 * 2 * n * n + 2 * 2 * n * n);
+      fl += (double)info->n_vol_points * (fb + 2 * 2 * n + 3 + 2 * 2 * n);
+      fl += (double)info->n_surf_points * (fb + 2 * 3 * n + 12 + 2 * 2 * n + 4);
+      fl += flines * (2 * 2 * n);
+    }
+    fl += 2.0 * (double)info->n_face_points * (fbv + 2 * 4 * n + 10 + 2 * 2 * n);
+    fl += 2.0 * (double)H.n_faces_cut * (2 * 4 * nd + 4 * nd);  // traces and expansion
+    return fl;
+  };
   info->kernel_flops_built[0] = fl_struct;
-  info->kernel_flops_built[1] = fl_cut;
+  info->kernel_flops_built[1] = cut_flops(true);
+  info->kernel_flops_built_fp32[0] = fl_struct;
+  info->kernel_flops_built_fp32[1] = cut_flops(false);
 
   // Algorithmic FMAs from the paper's complexity model (evaluation + integration = x2).
   const double k = n;

@@ -75,6 +75,10 @@ struct DevArrays {
   const T *vline_o0, *vline_o1;  // outer reference coordinates (lower, upper other axis)
   const int32_t *vpt_off;     // [n_vlines + 1]
   const int32_t *lsurf;       // [n_vlines]
+  // [n_vlines] (first line of the line's group) << 1 | shared_lo: the lines of a group are
+  // contiguous and share the outer coordinate along the lower (shared_lo = 1) or upper other
+  // axis, so the kernel contracts along that axis once per group (3D)
+  const int32_t *vline_grp;
   const T *vpt_t, *vpt_w;     // [n_vol_points] coordinate along the line, weight
   const T *spt_t, *spt_w, *spt_n[3];  // [n_surf_points]
   // cut-face lines

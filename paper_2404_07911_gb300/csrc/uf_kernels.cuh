@@ -396,9 +396,236 @@ struct CutSmem {
   static constexpr int ldb = lvb + CH * N;       // [CH][N] (derivatives)
   static constexpr int tr = ldb + CH * N;        // [NF][4][NL] traces of every cut face
   static constexpr int ft = tr + NF * 4 * NL;    // [NF][2][NL] face accumulators
-  static constexpr int total = ft + NF * 2 * NL;
-  static constexpr size_t bytes = (size_t)total * sizeof(T) + CH * sizeof(int);
+  static constexpr int zz = ft + NF * 2 * NL;    // [3][CH][N] per line point integrals (3D)
+  static constexpr int gcv = zz + 3 * CH * N;    // [CH][N] per group shared-axis basis (3D)
+  static constexpr int gcd = gcv + CH * N;
+  static constexpr int total = gcd + CH * N;
+  // ints after the T data: line tags (faces) [CH], group of each line [CH], first line of
+  // each group [CH + 1], shared axis of each group [CH]
+  static constexpr size_t bytes = (size_t)total * sizeof(T) + (4 * CH + 1) * sizeof(int);
 };
+
+// Volume (Poisson) and surface (Nitsche) points of a 3D cut cell (Eq. unstructured_cell), in a
+// two-level hierarchy of the dimension-reduction rule: a line holds the points that share both
+// outer coordinates, and a group holds the lines that share one of them (the points of one
+// line of the 2D outer rule).  Per chunk of CH lines (one thread per line):
+//   A  (per group)  P0 = (phi_c x I x I) u, P1 = (phi_c' x I x I) u along the shared axis c;
+//   B  (per line)   w0, w1, w2 = (phi_b | phi_b') contractions of P0 / P1 along the line's own
+//                   outer axis b, then values and gradients at the line's points and the
+//                   integration back along the line (z0, z1, z2);
+//   C1 (per group)  Q0 = sum_lines phi_b z0 + phi_b' z1, Q1 = sum_lines phi_b z2;
+//   C2 (per DoF)    acc += sum_groups phi_c Q0 + phi_c' Q1.
+// Per line this costs 6 n^2 FMA and per group 4 n^3, against 4 n^3 + 6 n^2 per line when
+// every line contracts both outer axes itself.
+template <typename T, int N>
+__device__ __forceinline__ void cut_volume_3d(const PointTables<T, N> &pt, const DevArrays<T> &d,
+                                              const Scalars<T> &sc, unsigned char *smem_raw, int ci,
+                                              T kap) {
+  using G = Geo<3, N>;
+  using SM = CutSmem<T, 3, N>;
+  constexpr int ND = G::ND, NL = G::NL;
+  constexpr int CH = SM::CH;
+  constexpr unsigned kMask = (CH == 32) ? 0xffffffffu : ((1u << CH) - 1u);
+  T *sm = reinterpret_cast<T *>(smem_raw);
+  const T *s_u = sm + SM::u;
+  T *s_acc = sm + SM::acc;
+  T (*s_p0)[NL] = reinterpret_cast<T (*)[NL]>(sm + SM::lt0);  // P0, then Q0
+  T (*s_p1)[NL] = reinterpret_cast<T (*)[NL]>(sm + SM::lt1);  // P1, then Q1
+  T (*s_vb)[N] = reinterpret_cast<T (*)[N]>(sm + SM::lvb);
+  T (*s_db)[N] = reinterpret_cast<T (*)[N]>(sm + SM::ldb);
+  T (*s_z)[CH][N] = reinterpret_cast<T (*)[CH][N]>(sm + SM::zz);
+  T (*s_gcv)[N] = reinterpret_cast<T (*)[N]>(sm + SM::gcv);
+  T (*s_gcd)[N] = reinterpret_cast<T (*)[N]>(sm + SM::gcd);
+  int *s_lgrp = reinterpret_cast<int *>(sm + SM::total) + CH;
+  int *s_gline = s_lgrp + CH;
+  int *s_gax = s_gline + CH + 1;
+  const int tid = threadIdx.x;
+
+#pragma unroll 1
+  for (int k = 0; k < 3; ++k) {
+    const int lbeg = __ldg(d.vline_koff + ci * 4 + k);
+    const int lend = __ldg(d.vline_koff + ci * 4 + k + 1);
+    int ob, oc;
+    other_axes(k, ob, oc);
+    const int sk = stride_of<N>(k), sob = stride_of<N>(ob), soc = stride_of<N>(oc);
+#pragma unroll 1
+    for (int l0 = lbeg; l0 < lend; l0 += CH) {
+      const int nl = min(CH, lend - l0);
+      const int line = l0 + tid;
+      const bool act = tid < nl;
+      const int gword = act ? __ldg(d.vline_grp + line) : 0;
+      const int shared_lo = gword & 1;  // the group shares the coordinate along ob
+      // groups of this chunk (a group cut by the chunk boundary restarts at its first thread)
+      const bool start = act && (tid == 0 || (gword >> 1) == line);
+      const unsigned starts = __ballot_sync(kMask, start);
+      const int ng = __popc(starts);
+      const int gl = __popc(starts & ((2u << tid) - 1u)) - 1;
+      if (start) {
+        s_gline[gl] = tid;
+        s_gax[gl] = shared_lo;
+        T cv[N], cd[N];
+        if constexpr (kPrecomputedBasis<T>) {
+          const T *bp = d.vline_b + (size_t)line * 4 * N + (shared_lo ? 0 : 2 * N);
+#pragma unroll
+          for (int i = 0; i < N; ++i) {
+            cv[i] = __ldg(bp + i);
+            cd[i] = __ldg(bp + N + i);
+          }
+        } else {
+          basis_1d<T, N>(pt, __ldg((shared_lo ? d.vline_o0 : d.vline_o1) + line), cv, cd);
+        }
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          s_gcv[gl][i] = cv[i];
+          s_gcd[gl][i] = cd[i];
+        }
+      }
+      if (tid == 0) s_gline[ng] = nl;
+      if (act) s_lgrp[tid] = gl;
+      __syncthreads();
+      // A: contraction along the shared axis, per group; P[g][ib * N + m], ib along the
+      // group's line axis, m along k
+      for (int item = tid; item < ng * NL; item += CH) {
+        const int g = item / NL, r = item % NL, ib = r / N, m = r % N;
+        const int lo = s_gax[g];
+        const int sb = lo ? soc : sob, scs = lo ? sob : soc;
+        const T *up = s_u + ib * sb + m * sk;
+        T p0 = T(0), p1 = T(0);
+#pragma unroll
+        for (int ic = 0; ic < N; ++ic) {
+          const T v = up[ic * scs];
+          p0 = fma(s_gcv[g][ic], v, p0);
+          p1 = fma(s_gcd[g][ic], v, p1);
+        }
+        s_p0[g][r] = p0;
+        s_p1[g][r] = p1;
+      }
+      __syncthreads();
+      // B: one thread per line
+      if (act) {
+        const int ab = shared_lo ? oc : ob;  // the line's own outer axis
+        const int ac = shared_lo ? ob : oc;  // the shared one
+        T vb[N], db[N];
+        if constexpr (kPrecomputedBasis<T>) {
+          const T *bp = d.vline_b + (size_t)line * 4 * N + (shared_lo ? 2 * N : 0);
+#pragma unroll
+          for (int i = 0; i < N; ++i) {
+            vb[i] = __ldg(bp + i);
+            db[i] = __ldg(bp + N + i);
+          }
+        } else {
+          basis_1d<T, N>(pt, __ldg((shared_lo ? d.vline_o1 : d.vline_o0) + line), vb, db);
+        }
+        // w0 = phi_b phi_c u, w1 = phi_b' phi_c u, w2 = phi_b phi_c' u along the line
+        T w0[N], w1[N], w2[N];
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+          T a0 = T(0), a1 = T(0), a2 = T(0);
+#pragma unroll
+          for (int ib = 0; ib < N; ++ib) {
+            const T q0 = s_p0[gl][ib * N + m];
+            a0 = fma(vb[ib], q0, a0);
+            a1 = fma(db[ib], q0, a1);
+            a2 = fma(vb[ib], s_p1[gl][ib * N + m], a2);
+          }
+          w0[m] = a0;
+          w1[m] = a1;
+          w2[m] = a2;
+        }
+        T z0[N], z1[N], z2[N];
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+          z0[m] = T(0);
+          z1[m] = T(0);
+          z2[m] = T(0);
+        }
+        const int pb = __ldg(d.vpt_off + line), pe = __ldg(d.vpt_off + line + 1);
+        const T cfv = kap * sc.inv_h2;
+#pragma unroll 1
+        for (int p = pb; p < pe; ++p) {
+          T cv[N], cd[N];
+          point_basis<T, N>(pt, d.vpt_b, d.vpt_t, p, cv, cd);
+          T gk = T(0), gb = T(0), gc = T(0);
+#pragma unroll
+          for (int m = 0; m < N; ++m) {
+            gk = fma(cd[m], w0[m], gk);
+            gb = fma(cv[m], w1[m], gb);
+            gc = fma(cv[m], w2[m], gc);
+          }
+          // kappa int grad v . grad u: reference gradients carry 1/h each
+          const T cf = cfv * __ldg(d.vpt_w + p);
+          gk *= cf;
+          gb *= cf;
+          gc *= cf;
+#pragma unroll
+          for (int m = 0; m < N; ++m) {
+            z0[m] = fma(gk, cd[m], z0[m]);
+            z1[m] = fma(gb, cv[m], z1[m]);
+            z2[m] = fma(gc, cv[m], z2[m]);
+          }
+        }
+        const int sp = __ldg(d.lsurf + line);
+        if (sp >= 0) {
+          // kappa int_Gamma [ -d_n v u - v d_n u + tau/h v u ]
+          T cv[N], cd[N];
+          point_basis<T, N>(pt, d.spt_b, d.spt_t, sp, cv, cd);
+          T u = T(0), gk = T(0), gb = T(0), gc = T(0);
+#pragma unroll
+          for (int m = 0; m < N; ++m) {
+            u = fma(cv[m], w0[m], u);
+            gk = fma(cd[m], w0[m], gk);
+            gb = fma(cv[m], w1[m], gb);
+            gc = fma(cv[m], w2[m], gc);
+          }
+          const T nk = __ldg(d.spt_n[k] + sp), nb = __ldg(d.spt_n[ab] + sp), nc = __ldg(d.spt_n[ac] + sp);
+          const T wk = kap * __ldg(d.spt_w + sp);
+          const T dn = (nk * gk + nb * gb + nc * gc) * sc.inv_h;
+          const T cval = wk * (sc.nitsche_over_h * u - dn);
+          const T cu = -wk * u * sc.inv_h;
+#pragma unroll
+          for (int m = 0; m < N; ++m) {
+            z0[m] = fma(cval, cv[m], fma(cu * nk, cd[m], z0[m]));
+            z1[m] = fma(cu * nb, cv[m], z1[m]);
+            z2[m] = fma(cu * nc, cv[m], z2[m]);
+          }
+        }
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+          s_z[0][tid][m] = z0[m];
+          s_z[1][tid][m] = z1[m];
+          s_z[2][tid][m] = z2[m];
+          s_vb[tid][m] = vb[m];
+          s_db[tid][m] = db[m];
+        }
+      }
+      __syncthreads();
+      // C1: sum over the lines of each group, Q[g][ib * N + m] (P is no longer read)
+      for (int item = tid; item < ng * NL; item += CH) {
+        const int g = item / NL, r = item % NL, ib = r / N, m = r % N;
+        T q0 = T(0), q1 = T(0);
+        for (int t = s_gline[g]; t < s_gline[g + 1]; ++t) {
+          q0 = fma(s_vb[t][ib], s_z[0][t][m], fma(s_db[t][ib], s_z[1][t][m], q0));
+          q1 = fma(s_vb[t][ib], s_z[2][t][m], q1);
+        }
+        s_p0[g][r] = q0;
+        s_p1[g][r] = q1;
+      }
+      __syncthreads();
+      // C2: expansion along the shared axis into the cell's rows
+      for (int l = tid; l < ND; l += CH) {
+        const int im = (l / sk) % N, iob = (l / sob) % N, ioc = (l / soc) % N;
+        T acc = T(0);
+        for (int g = 0; g < ng; ++g) {
+          const int lo = s_gax[g];
+          const int ib = lo ? ioc : iob, ic = lo ? iob : ioc;
+          acc = fma(s_gcv[g][ic], s_p0[g][ib * N + im], fma(s_gcd[g][ic], s_p1[g][ib * N + im], acc));
+        }
+        s_acc[l] += acc;
+      }
+      __syncthreads();
+    }
+  }
+}
 
 template <typename T, int DIM, int N>
 __global__ void __launch_bounds__(cut_chunk<N>()) cut_kernel(const __grid_constant__ PointTables<T, N> pt,
@@ -436,157 +663,161 @@ __global__ void __launch_bounds__(cut_chunk<N>()) cut_kernel(const __grid_consta
   }
   __syncthreads();
 
-  // ---- volume (Poisson) and surface (Nitsche) points, line by line (Eq. unstructured_cell:
-  // the contractions along the two outer axes are shared by every point of a line)
-#pragma unroll 1
-  for (int k = 0; k < DIM; ++k) {
-    const int lbeg = __ldg(d.vline_koff + ci * 4 + k);
-    const int lend = __ldg(d.vline_koff + ci * 4 + k + 1);
-    int ob = 0, oc = 0;
-    if constexpr (DIM == 3) {
-      other_axes(k, ob, oc);
-    } else {
-      ob = 1 - k;
-    }
-    const int sk = stride_of<N>(k), sb = stride_of<N>(ob), scc = stride_of<N>(oc);
-#pragma unroll 1
-    for (int l0 = lbeg; l0 < lend; l0 += CH) {
-      const int line = l0 + tid;
-      if (line < lend) {
-        T vb[N], db[N], vc[N], dc[N];
-        if constexpr (kPrecomputedBasis<T>) {
-          const T *bp = d.vline_b + (size_t)line * 4 * N;
-#pragma unroll
-          for (int i = 0; i < N; ++i) {
-            vb[i] = __ldg(bp + i);
-            db[i] = __ldg(bp + N + i);
-            if constexpr (DIM == 3) {
-              vc[i] = __ldg(bp + 2 * N + i);
-              dc[i] = __ldg(bp + 3 * N + i);
-            }
-          }
-        } else {
-          basis_1d<T, N>(pt, __ldg(d.vline_o0 + line), vb, db);
-          if constexpr (DIM == 3) basis_1d<T, N>(pt, __ldg(d.vline_o1 + line), vc, dc);
-        }
-        // w0 = (phi_b phi_c) u, w1 = (phi_b' phi_c) u, w2 = (phi_b phi_c') u along the line
-        T w0[N], w1[N], w2[N];
-#pragma unroll
-        for (int m = 0; m < N; ++m) {
-          w0[m] = T(0);
-          w1[m] = T(0);
-          w2[m] = T(0);
-        }
-        constexpr int NC = (DIM == 3) ? N : 1;
-#pragma unroll
-        for (int m = 0; m < N; ++m) {
-#pragma unroll
-          for (int ic = 0; ic < NC; ++ic) {
-            T s0 = T(0), s1 = T(0);
-#pragma unroll
-            for (int ib = 0; ib < N; ++ib) {
-              const T v = s_u[ib * sb + ic * scc + m * sk];
-              s0 = fma(vb[ib], v, s0);
-              s1 = fma(db[ib], v, s1);
-            }
-            if constexpr (DIM == 3) {
-              w0[m] = fma(vc[ic], s0, w0[m]);
-              w1[m] = fma(vc[ic], s1, w1[m]);
-              w2[m] = fma(dc[ic], s0, w2[m]);
-            } else {
-              w0[m] = s0;
-              w1[m] = s1;
-            }
-          }
-        }
-        T z0[N], z1[N], z2[N];
-#pragma unroll
-        for (int m = 0; m < N; ++m) {
-          z0[m] = T(0);
-          z1[m] = T(0);
-          z2[m] = T(0);
-        }
-        const int pb = __ldg(d.vpt_off + line), pe = __ldg(d.vpt_off + line + 1);
-        const T cfv = kap * sc.inv_h2;
-#pragma unroll 1
-        for (int p = pb; p < pe; ++p) {
-          T cv[N], cd[N];
-          point_basis<T, N>(pt, d.vpt_b, d.vpt_t, p, cv, cd);
-          T gk = T(0), gb = T(0), gc = T(0);
-#pragma unroll
-          for (int m = 0; m < N; ++m) {
-            gk = fma(cd[m], w0[m], gk);
-            gb = fma(cv[m], w1[m], gb);
-            if constexpr (DIM == 3) gc = fma(cv[m], w2[m], gc);
-          }
-          // kappa int grad v . grad u: reference gradients carry 1/h each
-          const T cf = cfv * __ldg(d.vpt_w + p);
-          gk *= cf;
-          gb *= cf;
-          gc *= cf;
-#pragma unroll
-          for (int m = 0; m < N; ++m) {
-            z0[m] = fma(gk, cd[m], z0[m]);
-            z1[m] = fma(gb, cv[m], z1[m]);
-            if constexpr (DIM == 3) z2[m] = fma(gc, cv[m], z2[m]);
-          }
-        }
-        const int sp = __ldg(d.lsurf + line);
-        if (sp >= 0) {
-          // kappa int_Gamma [ -d_n v u - v d_n u + tau/h v u ]
-          T cv[N], cd[N];
-          point_basis<T, N>(pt, d.spt_b, d.spt_t, sp, cv, cd);
-          T u = T(0), gk = T(0), gb = T(0), gc = T(0);
-#pragma unroll
-          for (int m = 0; m < N; ++m) {
-            u = fma(cv[m], w0[m], u);
-            gk = fma(cd[m], w0[m], gk);
-            gb = fma(cv[m], w1[m], gb);
-            if constexpr (DIM == 3) gc = fma(cv[m], w2[m], gc);
-          }
-          const T nk = __ldg(d.spt_n[k] + sp), nb = __ldg(d.spt_n[ob] + sp);
-          const T nc = (DIM == 3) ? __ldg(d.spt_n[oc] + sp) : T(0);
-          const T wk = kap * __ldg(d.spt_w + sp);
-          const T dn = (nk * gk + nb * gb + nc * gc) * sc.inv_h;
-          const T cval = wk * (sc.nitsche_over_h * u - dn);
-          const T cu = -wk * u * sc.inv_h;
-#pragma unroll
-          for (int m = 0; m < N; ++m) {
-            z0[m] = fma(cval, cv[m], fma(cu * nk, cd[m], z0[m]));
-            z1[m] = fma(cu * nb, cv[m], z1[m]);
-            if constexpr (DIM == 3) z2[m] = fma(cu * nc, cv[m], z2[m]);
-          }
-        }
-        // partial integration along the upper other axis; the lower one is done by the DoFs
-#pragma unroll
-        for (int ic = 0; ic < NC; ++ic)
-#pragma unroll
-          for (int m = 0; m < N; ++m) {
-            if constexpr (DIM == 3) {
-              s_lt0[tid][ic * N + m] = fma(vc[ic], z0[m], dc[ic] * z2[m]);
-              s_lt1[tid][ic * N + m] = vc[ic] * z1[m];
-            } else {
-              s_lt0[tid][m] = z0[m];
-              s_lt1[tid][m] = z1[m];
-            }
-          }
-#pragma unroll
-        for (int ib = 0; ib < N; ++ib) {
-          s_lvb[tid][ib] = vb[ib];
-          s_ldb[tid][ib] = db[ib];
-        }
+  if constexpr (DIM == 3) {
+    cut_volume_3d<T, N>(pt, d, sc, smem_raw, ci, kap);
+  } else {
+    // ---- volume (Poisson) and surface (Nitsche) points, line by line (Eq. unstructured_cell:
+    // the contractions along the two outer axes are shared by every point of a line)
+  #pragma unroll 1
+    for (int k = 0; k < DIM; ++k) {
+      const int lbeg = __ldg(d.vline_koff + ci * 4 + k);
+      const int lend = __ldg(d.vline_koff + ci * 4 + k + 1);
+      int ob = 0, oc = 0;
+      if constexpr (DIM == 3) {
+        other_axes(k, ob, oc);
+      } else {
+        ob = 1 - k;
       }
-      __syncthreads();
-      const int nlines = min(CH, lend - l0);
-      for (int l = tid; l < ND; l += CH) {
-        const int ib = (l / sb) % N, m = (l / sk) % N;
-        const int col = (DIM == 3) ? (((l / scc) % N) * N + m) : m;
-        T acc = T(0);
-        for (int q = 0; q < nlines; ++q)
-          acc = fma(s_lvb[q][ib], s_lt0[q][col], fma(s_ldb[q][ib], s_lt1[q][col], acc));
-        s_acc[l] += acc;
+      const int sk = stride_of<N>(k), sb = stride_of<N>(ob), scc = stride_of<N>(oc);
+  #pragma unroll 1
+      for (int l0 = lbeg; l0 < lend; l0 += CH) {
+        const int line = l0 + tid;
+        if (line < lend) {
+          T vb[N], db[N], vc[N], dc[N];
+          if constexpr (kPrecomputedBasis<T>) {
+            const T *bp = d.vline_b + (size_t)line * 4 * N;
+  #pragma unroll
+            for (int i = 0; i < N; ++i) {
+              vb[i] = __ldg(bp + i);
+              db[i] = __ldg(bp + N + i);
+              if constexpr (DIM == 3) {
+                vc[i] = __ldg(bp + 2 * N + i);
+                dc[i] = __ldg(bp + 3 * N + i);
+              }
+            }
+          } else {
+            basis_1d<T, N>(pt, __ldg(d.vline_o0 + line), vb, db);
+            if constexpr (DIM == 3) basis_1d<T, N>(pt, __ldg(d.vline_o1 + line), vc, dc);
+          }
+          // w0 = (phi_b phi_c) u, w1 = (phi_b' phi_c) u, w2 = (phi_b phi_c') u along the line
+          T w0[N], w1[N], w2[N];
+  #pragma unroll
+          for (int m = 0; m < N; ++m) {
+            w0[m] = T(0);
+            w1[m] = T(0);
+            w2[m] = T(0);
+          }
+          constexpr int NC = (DIM == 3) ? N : 1;
+  #pragma unroll
+          for (int m = 0; m < N; ++m) {
+  #pragma unroll
+            for (int ic = 0; ic < NC; ++ic) {
+              T s0 = T(0), s1 = T(0);
+  #pragma unroll
+              for (int ib = 0; ib < N; ++ib) {
+                const T v = s_u[ib * sb + ic * scc + m * sk];
+                s0 = fma(vb[ib], v, s0);
+                s1 = fma(db[ib], v, s1);
+              }
+              if constexpr (DIM == 3) {
+                w0[m] = fma(vc[ic], s0, w0[m]);
+                w1[m] = fma(vc[ic], s1, w1[m]);
+                w2[m] = fma(dc[ic], s0, w2[m]);
+              } else {
+                w0[m] = s0;
+                w1[m] = s1;
+              }
+            }
+          }
+          T z0[N], z1[N], z2[N];
+  #pragma unroll
+          for (int m = 0; m < N; ++m) {
+            z0[m] = T(0);
+            z1[m] = T(0);
+            z2[m] = T(0);
+          }
+          const int pb = __ldg(d.vpt_off + line), pe = __ldg(d.vpt_off + line + 1);
+          const T cfv = kap * sc.inv_h2;
+  #pragma unroll 1
+          for (int p = pb; p < pe; ++p) {
+            T cv[N], cd[N];
+            point_basis<T, N>(pt, d.vpt_b, d.vpt_t, p, cv, cd);
+            T gk = T(0), gb = T(0), gc = T(0);
+  #pragma unroll
+            for (int m = 0; m < N; ++m) {
+              gk = fma(cd[m], w0[m], gk);
+              gb = fma(cv[m], w1[m], gb);
+              if constexpr (DIM == 3) gc = fma(cv[m], w2[m], gc);
+            }
+            // kappa int grad v . grad u: reference gradients carry 1/h each
+            const T cf = cfv * __ldg(d.vpt_w + p);
+            gk *= cf;
+            gb *= cf;
+            gc *= cf;
+  #pragma unroll
+            for (int m = 0; m < N; ++m) {
+              z0[m] = fma(gk, cd[m], z0[m]);
+              z1[m] = fma(gb, cv[m], z1[m]);
+              if constexpr (DIM == 3) z2[m] = fma(gc, cv[m], z2[m]);
+            }
+          }
+          const int sp = __ldg(d.lsurf + line);
+          if (sp >= 0) {
+            // kappa int_Gamma [ -d_n v u - v d_n u + tau/h v u ]
+            T cv[N], cd[N];
+            point_basis<T, N>(pt, d.spt_b, d.spt_t, sp, cv, cd);
+            T u = T(0), gk = T(0), gb = T(0), gc = T(0);
+  #pragma unroll
+            for (int m = 0; m < N; ++m) {
+              u = fma(cv[m], w0[m], u);
+              gk = fma(cd[m], w0[m], gk);
+              gb = fma(cv[m], w1[m], gb);
+              if constexpr (DIM == 3) gc = fma(cv[m], w2[m], gc);
+            }
+            const T nk = __ldg(d.spt_n[k] + sp), nb = __ldg(d.spt_n[ob] + sp);
+            const T nc = (DIM == 3) ? __ldg(d.spt_n[oc] + sp) : T(0);
+            const T wk = kap * __ldg(d.spt_w + sp);
+            const T dn = (nk * gk + nb * gb + nc * gc) * sc.inv_h;
+            const T cval = wk * (sc.nitsche_over_h * u - dn);
+            const T cu = -wk * u * sc.inv_h;
+  #pragma unroll
+            for (int m = 0; m < N; ++m) {
+              z0[m] = fma(cval, cv[m], fma(cu * nk, cd[m], z0[m]));
+              z1[m] = fma(cu * nb, cv[m], z1[m]);
+              if constexpr (DIM == 3) z2[m] = fma(cu * nc, cv[m], z2[m]);
+            }
+          }
+          // partial integration along the upper other axis; the lower one is done by the DoFs
+  #pragma unroll
+          for (int ic = 0; ic < NC; ++ic)
+  #pragma unroll
+            for (int m = 0; m < N; ++m) {
+              if constexpr (DIM == 3) {
+                s_lt0[tid][ic * N + m] = fma(vc[ic], z0[m], dc[ic] * z2[m]);
+                s_lt1[tid][ic * N + m] = vc[ic] * z1[m];
+              } else {
+                s_lt0[tid][m] = z0[m];
+                s_lt1[tid][m] = z1[m];
+              }
+            }
+  #pragma unroll
+          for (int ib = 0; ib < N; ++ib) {
+            s_lvb[tid][ib] = vb[ib];
+            s_ldb[tid][ib] = db[ib];
+          }
+        }
+        __syncthreads();
+        const int nlines = min(CH, lend - l0);
+        for (int l = tid; l < ND; l += CH) {
+          const int ib = (l / sb) % N, m = (l / sk) % N;
+          const int col = (DIM == 3) ? (((l / scc) % N) * N + m) : m;
+          T acc = T(0);
+          for (int q = 0; q < nlines; ++q)
+            acc = fma(s_lvb[q][ib], s_lt0[q][col], fma(s_ldb[q][ib], s_lt1[q][col], acc));
+          s_acc[l] += acc;
+        }
+        __syncthreads();
       }
-      __syncthreads();
     }
   }
 

@@ -66,3 +66,13 @@ def test_benchmark_workload_setup():
     assert (i["n_faces"], i["n_faces_full"], i["n_faces_cut"], i["n_faces_gp"]) == (
         245746, 219390, 26356, 38904)
     assert i["n_vol_points"] > 64 * i["n_cut"] and i["n_surf_points"] > 10 * i["n_cut"]
+
+
+def test_line_groups():
+    """Lines of the dimension-reduction rule that share one outer coordinate are grouped in 3D
+    (each line of the 2D outer rule carries q points, so about q lines per group); 2D lines
+    stay single."""
+    i3 = UnfittedOperator(workloads.cfg_3d_q3(), device=-1).info
+    assert i3["n_vol_lines"] / i3["n_vol_groups"] > 3.0
+    i2 = UnfittedOperator(workloads.small(p=3, N=10, dim=2), device=-1).info
+    assert i2["n_vol_groups"] == i2["n_vol_lines"]
