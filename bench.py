@@ -485,8 +485,12 @@ def run_sweep(args, local):
             op.vmult(x64, y64, stream)
             op.vmult(x32, y32, stream)
         K = 20
+        op.profile_begin(2 * K)
         ms64 = _event_ms(lambda: op.vmult(x64, y64, stream), K, stream, flush)
         ms32 = _event_ms(lambda: op.vmult(x32, y32, stream), K, stream, flush)
+        kt = op.profile_end()
+        kernels = {f"{kern}_{prec}": round(tot / cnt, 4)
+                   for (prec, kern, _), (tot, cnt) in sorted(kt.items())}
         o = forms.Oracle(mesh.problem_from_dict(cfg))
         cut = np.nonzero(o.mesh.active_type == mesh.CUT)[0]
         ins = np.nonzero(o.mesh.active_type == mesh.INSIDE)[0]
@@ -507,7 +511,7 @@ def run_sweep(args, local):
             "fp32": {"ms": round(ms32, 4), "gdofs": round(n / ms32 / 1e6, 3),
                      "rel_err_vs_rounded_input": float(np.max(np.abs(g32 - ref32)) / sc),
                      "rel_err_vs_fp64_oracle": float(np.max(np.abs(g32 - ref)) / sc)},
-            "l2": "flushed before every launch"}), flush=True)
+            "kernel_ms": kernels, "l2": "flushed before every launch"}), flush=True)
         op.close()
         del x64, x32, y64, y32
         torch.cuda.empty_cache()

@@ -82,14 +82,14 @@ __host__ __device__ constexpr int struct_cells_per_block() {
 //   3D: y = M_z (M_y W_x + M_x W_y) + M_y M_x W_z     (5 sweeps instead of 6)
 //   2D: y = M_y W_x + M_x W_y
 template <typename T, int N>
-__device__ __forceinline__ void apply_line(const T *__restrict__ Lm, T scale, const T *u, T *w,
-                                           bool transpose, bool accumulate) {
+__device__ __forceinline__ void apply_line(const T *__restrict__ Lm, const T *u, T *w, bool transpose,
+                                           bool accumulate) {
 #pragma unroll
   for (int r = 0; r < N; ++r) {
-    T acc = T(0);
+    T acc = accumulate ? w[r] : T(0);
 #pragma unroll
     for (int m = 0; m < N; ++m) acc = fma(Lm[transpose ? (m * N + r) : (r * N + m)], u[m], acc);
-    w[r] = accumulate ? fma(scale, acc, w[r]) : scale * acc;
+    w[r] = acc;
   }
 }
 
@@ -158,6 +158,18 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
     }
   }
   const bool inside = has_cell && !(fl & 1u);
+  // Uniform kappa: every structured term scales with it, so the lines are computed for kappa = 1
+  // and the cell's rows are scaled once at the end (not at all when kappa = 1).
+  const T yscale = uniform ? kap : T(1);
+  if (uniform) {
+    kap = T(1);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      knb[f] = T(1);
+      kavg[f] = T(1);
+    }
+  }
+  const bool scale_rows = yscale != T(1);
 
   if (!uniform && has_cell) {
     // per-cell 1D matrices from the constant ones and kappa
@@ -209,9 +221,9 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
         v |= bit(fl, bit_gp(2 * a)) ? 4 : 0;
         v |= bit(fl, bit_full(2 * a + 1)) ? 8 : 0;
         v |= bit(fl, bit_gp(2 * a + 1)) ? 16 : 0;
-        apply_line<T, N>(d.lself + v * NN, kap, u, w, ADJ, false);
+        apply_line<T, N>(d.lself + v * NN, u, w, ADJ, false);
       } else {
-        apply_line<T, N>(s_l[c][a][0], T(1), u, w, false, false);
+        apply_line<T, N>(s_l[c][a][0], u, w, false, false);
       }
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
@@ -228,9 +240,9 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
           if (uniform) {
             // transpose of the neighbour's table entry (its face 1 - s) for the adjoint
             const T *Lg = d.lnbgp + (2 * (ADJ ? 1 - s : s) + (full ? 1 : 0)) * NN;
-            apply_line<T, N>(Lg, kap, un, w, ADJ, true);
+            apply_line<T, N>(Lg, un, w, ADJ, true);
           } else {
-            apply_line<T, N>(s_l[c][a][1 + s], T(1), un, w, false, true);
+            apply_line<T, N>(s_l[c][a][1 + s], un, w, false, true);
           }
         } else {
           // rank-2 SIPG coupling (the transposed coupling of a symmetric flux is the same form)
@@ -262,8 +274,10 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
       // y = W_x + W_y; thread t writes the x-line t
       const int base = line_base<DIM, N>(0, t);
 #pragma unroll
-      for (int r = 0; r < N; ++r)
-        y[(size_t)e * ND + base + r] = s_w[0][c][base + r] + s_w[1][c][base + r];
+      for (int r = 0; r < N; ++r) {
+        const T v = s_w[0][c][base + r] + s_w[1][c][base + r];
+        y[(size_t)e * ND + base + r] = scale_rows ? yscale * v : v;
+      }
     }
   } else {
     if (has_cell) {
@@ -298,7 +312,7 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
         T acc = s_w[2][c][bz + r * N * N];
 #pragma unroll
         for (int m = 0; m < N; ++m) acc = fma(M[r * N + m], a[m], acc);
-        y[(size_t)e * ND + bz + r * N * N] = acc;
+        y[(size_t)e * ND + bz + r * N * N] = scale_rows ? yscale * acc : acc;
       }
     }
   }
@@ -394,8 +408,8 @@ struct CutSmem {
   static constexpr int lt1 = lt0 + CH * NL;
   static constexpr int lvb = lt1 + CH * NL;      // [CH][N] per line outer basis (values)
   static constexpr int ldb = lvb + CH * N;       // [CH][N] (derivatives)
-  static constexpr int tr = ldb + CH * N;        // [NF][4][NL] traces of every cut face
-  static constexpr int ft = tr + NF * 4 * NL;    // [NF][2][NL] face accumulators
+  static constexpr int tr = ldb + CH * N;        // [NF][2][NL] trace jump and flux of every cut face
+  static constexpr int ft = tr + NF * 2 * NL;    // [NF][2][NL] face accumulators
   static constexpr int zz = ft + NF * 2 * NL;    // [3][CH][N] per line point integrals (3D)
   static constexpr int gcv = zz + 3 * CH * N;    // [CH][N] per group shared-axis basis (3D)
   static constexpr int gcd = gcv + CH * N;
@@ -645,7 +659,7 @@ __global__ void __launch_bounds__(cut_chunk<N>()) cut_kernel(const __grid_consta
   T (*s_lt1)[NL] = reinterpret_cast<T (*)[NL]>(sm + SM::lt1);
   T (*s_lvb)[N] = reinterpret_cast<T (*)[N]>(sm + SM::lvb);
   T (*s_ldb)[N] = reinterpret_cast<T (*)[N]>(sm + SM::ldb);
-  T (*s_tr)[4][NL] = reinterpret_cast<T (*)[4][NL]>(sm + SM::tr);
+  T (*s_tr)[2][NL] = reinterpret_cast<T (*)[2][NL]>(sm + SM::tr);
   T (*s_ft)[2][NL] = reinterpret_cast<T (*)[2][NL]>(sm + SM::ft);
   int *s_tag = reinterpret_cast<int *>(sm + SM::total);
 
@@ -829,31 +843,28 @@ __global__ void __launch_bounds__(cut_chunk<N>()) cut_kernel(const __grid_consta
   for (int f = 0; f < NF; ++f)
     if (bit(fl, bit_cut(f))) cfl[ncf++] = f;
   if (ncf > 0) {
-    // traces on each cut face: values (delta property of the Lobatto basis) and
-    // n_K-derivatives, indexed by the in-face DoF tl = i_b' + n i_c' (b' < c' in-face axes);
-    // the neighbour's lines are read from global memory (L2)
+    // per cut face, indexed by the in-face DoF tl = i_b' + n i_c' (b' < c' in-face axes): the
+    // jump of the traces [u] = u_K - u_nb (the trace of a Lobatto basis is its face-node value)
+    // and the average normal flux {kappa d_n u} along the own outward normal; the neighbour's
+    // lines are read from global memory (L2)
     for (int item = tid; item < ncf * NL; item += CH) {
       const int fi = item / NL, tl = item % NL;
       const int f = cfl[fi], axis = f / 2, side = f % 2;
       const int nbe = __ldg(d.nbr + (size_t)e * NF + f);
+      const T knb = __ldg(d.kappa + nbe);
       const int base = line_base<DIM, N>(axis, tl);
       const int st = stride_of<N>(axis);
       const T *xn = x + (size_t)nbe * ND + base;
-      T ov = T(0), od = T(0), nv = T(0), nd = T(0);
+      const int end_own = side ? N - 1 : 0, end_nb = side ? 0 : N - 1;
+      T od = T(0), nd = T(0);
 #pragma unroll
       for (int m = 0; m < N; ++m) {
-        const T uo = s_u[base + m * st];
-        const T un = __ldg(xn + m * st);
-        ov = fma(pt.end_val[side][m], uo, ov);
-        od = fma(pt.end_der[side][m], uo, od);
-        nv = fma(pt.end_val[1 - side][m], un, nv);
-        nd = fma(pt.end_der[1 - side][m], un, nd);
+        od = fma(pt.end_der[side][m], s_u[base + m * st], od);
+        nd = fma(pt.end_der[1 - side][m], __ldg(xn + m * st), nd);
       }
       const T sgn = side ? T(1) : T(-1);
-      s_tr[fi][0][tl] = ov;
-      s_tr[fi][1][tl] = sgn * sc.inv_h * od;
-      s_tr[fi][2][tl] = nv;
-      s_tr[fi][3][tl] = sgn * sc.inv_h * nd;
+      s_tr[fi][0][tl] = s_u[base + end_own * st] - __ldg(xn + end_nb * st);
+      s_tr[fi][1][tl] = (T(0.5) * sgn * sc.inv_h) * fma(kap, od, knb * nd);
       s_ft[fi][0][tl] = T(0);
       s_ft[fi][1][tl] = T(0);
     }
@@ -890,12 +901,12 @@ __global__ void __launch_bounds__(cut_chunk<N>()) cut_kernel(const __grid_consta
             basis_1d_val<T, N>(pt, __ldg(d.fline_o + line), vo);
           }
         }
-        // traces contracted along the outer in-face axis
-        T r[4][N];
+        // jump and flux contracted along the outer in-face axis
+        T r[2][N];
 #pragma unroll
         for (int m = 0; m < N; ++m) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
+          for (int q = 0; q < 2; ++q) {
             if constexpr (DIM == 3) {
               T acc = T(0);
 #pragma unroll
@@ -922,14 +933,13 @@ __global__ void __launch_bounds__(cut_chunk<N>()) cut_kernel(const __grid_consta
           } else {
             basis_1d_val<T, N>(pt, __ldg(d.fpt_t + p), cv);
           }
-          T ev[4] = {T(0), T(0), T(0), T(0)};
+          T jump = T(0), avg = T(0);
 #pragma unroll
-          for (int m = 0; m < N; ++m)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) ev[q] = fma(cv[m], r[q][m], ev[q]);
+          for (int m = 0; m < N; ++m) {
+            jump = fma(cv[m], r[0][m], jump);
+            avg = fma(cv[m], r[1][m], avg);
+          }
           const T w = __ldg(d.fpt_w + p);
-          const T jump = ev[0] - ev[2];
-          const T avg = T(0.5) * (kap * ev[1] + knb * ev[3]);
           // coefficients of the own trace value and own normal derivative of the test function
           const T cvv = w * (sc.sipg_over_h * kavg * jump - avg);
           const T cdd = w * (T(-0.5) * kap * jump);
@@ -986,8 +996,8 @@ __global__ void __launch_bounds__(cut_chunk<N>()) cut_kernel(const __grid_consta
           const int i0 = l % N, i1 = (l / N) % N, i2 = l / (N * N);
           tl = (axis == 0) ? (i1 + N * i2) : (axis == 1) ? (i0 + N * i2) : (i0 + N * i1);
         }
-        add += pt.end_val[side][ia] * s_ft[fi][0][tl] +
-               sgn * sc.inv_h * pt.end_der[side][ia] * s_ft[fi][1][tl];
+        add = fma(sgn * sc.inv_h * pt.end_der[side][ia], s_ft[fi][1][tl], add);
+        if (ia == (side ? N - 1 : 0)) add += s_ft[fi][0][tl];
       }
       s_acc[l] += add;
     }
