@@ -482,6 +482,9 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   pd.struct_tables.assign(sizeof(T) * mats.size(), 0);
   T *st = reinterpret_cast<T *>(pd.struct_tables.data());
   for (size_t i = 0; i < mats.size(); ++i) st[i] = (T)mats[i];
+  // dow, dnb (after the 16 matrices) carry h^{d-1} / 2 in the device copy
+  const double half_hf = 0.5 * std::pow(H.h, d - 1);
+  for (int i = 0; i < 4 * n; ++i) st[16 * n * n + i] = (T)(half_hf * mats[16 * n * n + i]);
   pd.point_tables.assign(sizeof(T) * 6 * n, 0);
   T *ptab = reinterpret_cast<T *>(pd.point_tables.data());
   for (int i = 0; i < n; ++i) {
@@ -498,6 +501,7 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   pd.scalars.sipg_over_h = (T)(H.params.sipg_gamma / H.h);
   pd.scalars.nitsche_over_h = (T)(H.params.nitsche_gamma / H.h);
   pd.scalars.hf = (T)std::pow(H.h, d - 1);
+  pd.scalars.hf_sigma = (T)(std::pow(H.h, d - 1) * H.params.sipg_gamma / H.h);
   pd.present = true;
   return UF_OK;
 }
@@ -713,9 +717,12 @@ uf_status uf_get_info(const uf_operator *op, uf_info *info) {
     }
   const double sweep = nline * n * n;  // FMA per line sweep of a cell
   const bool uni = kappa_is_uniform(H.kappa);
+  // uniform kappa: lines for kappa = 1, rows scaled once (not at all for kappa = 1); rank-2
+  // couplings 2n FMA + 2 per line (the face factors are folded into the 1D trace tables)
   double fl_struct = 2.0 * ((double)H.n_active * (d * sweep + (d == 3 ? 5 : 2) * sweep) +
                             (double)gp_faces_cell * sweep) +
-                     (double)H.n_active * d * nd + (double)r2_faces_cell * nline * (4 * n + 8);
+                     (double)r2_faces_cell * nline * (uni ? 4 * n + 3 : 4 * n + 6);
+  if (uni && H.kappa[0] != 1.0) fl_struct += (double)H.n_active * nd;
   if (!uni) fl_struct += (double)H.n_active * d * n * n * 2.0 * 13.0;
   // cut-cell kernel: 1D basis (values and derivatives) 14n - 8, values only 6n - 4 flops when
   // evaluated (FP32); the FP64 kernels read them from tables (fb = fbv = 0)
@@ -730,15 +737,16 @@ uf_status uf_get_info(const uf_operator *op, uf_info *info) {
       fl += vgroups * (fb + 8 * n * n * n) + vlines * (fb + 12 * n * n);
       fl += (double)info->n_vol_points * (fb + 2 * 3 * n + 4 + 2 * 3 * n);
       fl += (double)info->n_surf_points * (fb + 2 * 4 * n + 16 + 2 * 3 * n + 6);
-      fl += flines * (fbv + 2 * 4 * n * n + 2 * 2 * n * n);
+      fl += flines * (fbv + 2 * 2 * n * n + 2 * 2 * n * n);
     } else {
       fl += vlines * (fb + 2 * 2 * n * n + 2 * 2 * n * n);
       fl += (double)info->n_vol_points * (fb + 2 * 2 * n + 3 + 2 * 2 * n);
       fl += (double)info->n_surf_points * (fb + 2 * 3 * n + 12 + 2 * 2 * n + 4);
       fl += flines * (2 * 2 * n);
     }
-    fl += 2.0 * (double)info->n_face_points * (fbv + 2 * 4 * n + 10 + 2 * 2 * n);
-    fl += 2.0 * (double)H.n_faces_cut * (2 * 4 * nd + 4 * nd);  // traces and expansion
+    fl += 2.0 * (double)info->n_face_points * (fbv + 2 * 2 * n + 8 + 2 * 2 * n);
+    // traces (jump and flux; Lobatto face values need no arithmetic) and expansion
+    fl += 2.0 * (double)H.n_faces_cut * (2 * 2 * nd + 4 * nd / n + 2 * nd + nd / n);
     return fl;
   };
   info->kernel_flops_built[0] = fl_struct;

@@ -21,12 +21,12 @@ constexpr int kMaxNdev = 9;
 //   qn[s]   SIPG penalty, own-neighbour                (x {kappa})
 //   hn[s]   ghost penalty, own-neighbour               (x {kappa})
 // Face matrices carry the face measure h^{d-1} and the normal-derivative scalings 1/h^j.
-//   dow[s]  sgn_s phi'(s) / h          (own outward normal derivative at the face)
-//   dnb[s]  sgn_s phi'(1 - s) / h      (neighbour's derivative along the own outward normal)
+//   dow[s]  h^{d-1}/2 sgn_s phi'(s) / h       (own outward normal derivative at the face)
+//   dnb[s]  h^{d-1}/2 sgn_s phi'(1 - s) / h   (neighbour's derivative along the own normal)
 // A full face without ghost penalty couples to the neighbour through rank 2 only:
 //   (kappa_K b + kappa_nb c + {kappa} qn) u_nb
-//     = h^{d-1} [ kappa_K/2 dow (u_nb at its face node) - e_own (kappa_nb/2 dnb.u_nb
-//                 + sigma/h {kappa} u_nb at its face node) ]   (delta property of the basis).
+//     = kappa_K dow (u_nb at its face node) - e_own (kappa_nb dnb.u_nb
+//       + h^{d-1} sigma/h {kappa} u_nb at its face node)   (delta property of the basis).
 template <typename T, int N>
 struct StructTables {
   T kv[N * N];
@@ -52,6 +52,7 @@ struct Scalars {
   T sipg_over_h;     // sigma / h
   T nitsche_over_h;  // tau / h
   T hf;              // face measure scaling h^{d-1}
+  T hf_sigma;        // h^{d-1} sigma / h
 };
 
 // Pointers into device memory (one allocation per precision).

@@ -109,7 +109,7 @@ __device__ __forceinline__ void mass_line(const T *__restrict__ M, T *v, int bas
   for (int r = 0; r < N; ++r) v[base + r * st] = b[r];
 }
 
-template <typename T, int DIM, int N, bool ADJ>
+template <typename T, int DIM, int N, bool ADJ, bool UNI>
 __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ StructTables<T, N> tab,
                                                      const DevArrays<T> d, const Scalars<T> sc,
                                                      T *__restrict__ y, const T *__restrict__ x) {
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
   const bool active_thread = (c < CPB);
   const int e = first + c;
   const bool has_cell = active_thread && (e < d.n_active);
-  const bool uniform = d.kappa_uniform != 0;
+  constexpr bool uniform = UNI;  // kappa uniform (d.kappa_uniform != 0)
 
   {
     const int ncell = min(CPB, d.n_active - first);
@@ -245,15 +245,20 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
             apply_line<T, N>(s_l[c][a][1 + s], un, w, false, true);
           }
         } else {
-          // rank-2 SIPG coupling (the transposed coupling of a symmetric flux is the same form)
+          // rank-2 SIPG coupling (the transposed coupling of a symmetric flux is the same form);
+          // the device copies of dow and dnb carry the factor h^{d-1} / 2
           const T alpha = un[s ? 0 : N - 1];
           T beta = T(0);
 #pragma unroll
           for (int m = 0; m < N; ++m) beta = fma(tab.dnb[s][m], un[m], beta);
-          const T ca = T(0.5) * sc.hf * kap * alpha;
+          const T ca = uniform ? alpha : kap * alpha;
 #pragma unroll
           for (int r = 0; r < N; ++r) w[r] = fma(ca, tab.dow[s][r], w[r]);
-          w[s ? N - 1 : 0] -= sc.hf * (T(0.5) * knb[f] * beta + sc.sipg_over_h * kavg[f] * alpha);
+          if constexpr (uniform) {
+            w[s ? N - 1 : 0] -= fma(sc.hf_sigma, alpha, beta);
+          } else {
+            w[s ? N - 1 : 0] -= fma(knb[f], beta, (sc.hf_sigma * kavg[f]) * alpha);
+          }
         }
       }
 #pragma unroll
@@ -384,11 +389,16 @@ __device__ __forceinline__ void point_basis(const PointTables<T, N> &pt, const T
   }
 }
 
-// Lines per chunk (= threads per CTA) of the cut-cell kernel; bounded by the per-line shared
-// memory (2 n^{d-1} + 2 n values per line).
+// Lines per chunk (= threads per CTA = one warp) of the cut-cell kernel, and the most line
+// groups one chunk of the 3D volume part holds (a chunk ends early at the next group start once
+// it has that many; the per-group partial contractions take GMAX n^2 values each).
 template <int N>
 __host__ __device__ constexpr int cut_chunk() {
-  return (N <= 6) ? 32 : 16;
+  return 32;
+}
+template <int N>
+__host__ __device__ constexpr int cut_gmax() {
+  return (N <= 5) ? 16 : 8;
 }
 
 // Other axes of a line along axis k (lower first) in 3D.
@@ -397,26 +407,35 @@ __device__ __forceinline__ void other_axes(int k, int &b, int &c) {
   c = (k == 2) ? 1 : 2;
 }
 
-// Dynamic shared memory of the cut-cell kernel (offsets in elements of T, then CH ints).
+// Dynamic shared memory of the cut-cell kernel (offsets in elements of T, then ints).  The
+// volume phase and the cut-face phase run one after the other, so the per-group partial
+// contractions (3D), the per-line partial integrals (2D) and the face arrays share one region.
 template <typename T, int DIM, int N>
 struct CutSmem {
   static constexpr int ND = Geo<DIM, N>::ND, NL = Geo<DIM, N>::NL, NF = Geo<DIM, N>::NF;
   static constexpr int CH = cut_chunk<N>();
+  static constexpr int GMAX = cut_gmax<N>();
+  static constexpr int cmax(int a, int b) { return a > b ? a : b; }
   static constexpr int u = 0;                    // [ND] the cell's DoFs
   static constexpr int acc = u + ND;             // [ND] accumulated output rows
-  static constexpr int lt0 = acc + ND;           // [CH][NL] per line partial integrals
-  static constexpr int lt1 = lt0 + CH * NL;
-  static constexpr int lvb = lt1 + CH * NL;      // [CH][N] per line outer basis (values)
+  static constexpr int shared = acc + ND;        // region of size `region`:
+  //   3D volume: P0, P1 = [GMAX][NL] per group (then Q0, Q1)
+  //   2D volume: lt0, lt1 = [CH][NL] per line partial integrals
+  //   faces:     tr = [NF][2][NL] trace jump and flux, ft = [NF][2][NL] face accumulators
+  static constexpr int region = cmax(cmax(2 * GMAX * NL, 2 * CH * NL * (DIM == 2 ? 1 : 0)), 4 * NF * NL);
+  static constexpr int p0 = shared, p1 = shared + GMAX * NL;
+  static constexpr int lt0 = shared, lt1 = shared + CH * NL;
+  static constexpr int tr = shared, ft = shared + 2 * NF * NL;
+  static constexpr int lvb = shared + region;    // [CH][N] per line basis (values)
   static constexpr int ldb = lvb + CH * N;       // [CH][N] (derivatives)
-  static constexpr int tr = ldb + CH * N;        // [NF][2][NL] trace jump and flux of every cut face
-  static constexpr int ft = tr + NF * 2 * NL;    // [NF][2][NL] face accumulators
-  static constexpr int zz = ft + NF * 2 * NL;    // [3][CH][N] per line point integrals (3D)
-  static constexpr int gcv = zz + 3 * CH * N;    // [CH][N] per group shared-axis basis (3D)
-  static constexpr int gcd = gcv + CH * N;
-  static constexpr int total = gcd + CH * N;
+  static constexpr int zz = ldb + CH * N;        // [3][CH][N] per line point integrals
+  static constexpr int gcv = zz + 3 * CH * N;    // [GMAX][N] per group shared-axis basis (3D)
+  static constexpr int gcd = gcv + GMAX * N;
+  static constexpr int total = gcd + GMAX * N;
   // ints after the T data: line tags (faces) [CH], group of each line [CH], first line of
-  // each group [CH + 1], shared axis of each group [CH]
-  static constexpr size_t bytes = (size_t)total * sizeof(T) + (4 * CH + 1) * sizeof(int);
+  // each group [GMAX + 1], shared axis of each group [GMAX]
+  static constexpr int itag = 0, ilgrp = CH, igline = 2 * CH, igax = 2 * CH + GMAX + 1;
+  static constexpr size_t bytes = (size_t)total * sizeof(T) + (2 * CH + 2 * GMAX + 1) * sizeof(int);
 };
 
 // Volume (Poisson) and surface (Nitsche) points of a 3D cut cell (Eq. unstructured_cell), in a
@@ -438,21 +457,23 @@ __device__ __forceinline__ void cut_volume_3d(const PointTables<T, N> &pt, const
   using G = Geo<3, N>;
   using SM = CutSmem<T, 3, N>;
   constexpr int ND = G::ND, NL = G::NL;
-  constexpr int CH = SM::CH;
-  constexpr unsigned kMask = (CH == 32) ? 0xffffffffu : ((1u << CH) - 1u);
+  constexpr int CH = SM::CH, GMAX = SM::GMAX;
+  constexpr unsigned kMask = 0xffffffffu;
+  static_assert(CH == 32, "one warp per cut cell");
   T *sm = reinterpret_cast<T *>(smem_raw);
   const T *s_u = sm + SM::u;
   T *s_acc = sm + SM::acc;
-  T (*s_p0)[NL] = reinterpret_cast<T (*)[NL]>(sm + SM::lt0);  // P0, then Q0
-  T (*s_p1)[NL] = reinterpret_cast<T (*)[NL]>(sm + SM::lt1);  // P1, then Q1
+  T (*s_p0)[NL] = reinterpret_cast<T (*)[NL]>(sm + SM::p0);  // P0, then Q0
+  T (*s_p1)[NL] = reinterpret_cast<T (*)[NL]>(sm + SM::p1);  // P1, then Q1
   T (*s_vb)[N] = reinterpret_cast<T (*)[N]>(sm + SM::lvb);
   T (*s_db)[N] = reinterpret_cast<T (*)[N]>(sm + SM::ldb);
   T (*s_z)[CH][N] = reinterpret_cast<T (*)[CH][N]>(sm + SM::zz);
   T (*s_gcv)[N] = reinterpret_cast<T (*)[N]>(sm + SM::gcv);
   T (*s_gcd)[N] = reinterpret_cast<T (*)[N]>(sm + SM::gcd);
-  int *s_lgrp = reinterpret_cast<int *>(sm + SM::total) + CH;
-  int *s_gline = s_lgrp + CH;
-  int *s_gax = s_gline + CH + 1;
+  int *s_ints = reinterpret_cast<int *>(sm + SM::total);
+  int *s_lgrp = s_ints + SM::ilgrp;
+  int *s_gline = s_ints + SM::igline;
+  int *s_gax = s_ints + SM::igax;
   const int tid = threadIdx.x;
 
 #pragma unroll 1
@@ -462,18 +483,23 @@ __device__ __forceinline__ void cut_volume_3d(const PointTables<T, N> &pt, const
     int ob, oc;
     other_axes(k, ob, oc);
     const int sk = stride_of<N>(k), sob = stride_of<N>(ob), soc = stride_of<N>(oc);
+    int nl = 0;
 #pragma unroll 1
-    for (int l0 = lbeg; l0 < lend; l0 += CH) {
-      const int nl = min(CH, lend - l0);
+    for (int l0 = lbeg; l0 < lend; l0 += nl) {
       const int line = l0 + tid;
-      const bool act = tid < nl;
-      const int gword = act ? __ldg(d.vline_grp + line) : 0;
+      const bool in_range = tid < min(CH, lend - l0);
+      const int gword = in_range ? __ldg(d.vline_grp + line) : 0;
       const int shared_lo = gword & 1;  // the group shares the coordinate along ob
-      // groups of this chunk (a group cut by the chunk boundary restarts at its first thread)
-      const bool start = act && (tid == 0 || (gword >> 1) == line);
-      const unsigned starts = __ballot_sync(kMask, start);
-      const int ng = __popc(starts);
-      const int gl = __popc(starts & ((2u << tid) - 1u)) - 1;
+      // groups of this chunk (a group cut by the chunk boundary restarts at its first thread);
+      // the chunk ends before the start of group GMAX
+      const bool start0 = in_range && (tid == 0 || (gword >> 1) == line);
+      const unsigned starts0 = __ballot_sync(kMask, start0);
+      const int gl = __popc(starts0 & ((2u << tid) - 1u)) - 1;
+      const unsigned over = __ballot_sync(kMask, start0 && gl >= GMAX);
+      nl = over ? (__ffs(over) - 1) : min(CH, lend - l0);
+      const bool act = tid < nl;
+      const bool start = start0 && act;
+      const int ng = __popc(starts0 & ((nl >= 32) ? 0xffffffffu : ((1u << nl) - 1u)));
       if (start) {
         s_gline[gl] = tid;
         s_gax[gl] = shared_lo;
@@ -661,7 +687,8 @@ __global__ void __launch_bounds__(cut_chunk<N>()) cut_kernel(const __grid_consta
   T (*s_ldb)[N] = reinterpret_cast<T (*)[N]>(sm + SM::ldb);
   T (*s_tr)[2][NL] = reinterpret_cast<T (*)[2][NL]>(sm + SM::tr);
   T (*s_ft)[2][NL] = reinterpret_cast<T (*)[2][NL]>(sm + SM::ft);
-  int *s_tag = reinterpret_cast<int *>(sm + SM::total);
+  T (*s_fz)[CH][N] = reinterpret_cast<T (*)[CH][N]>(sm + SM::zz);  // face lines: zv, zd
+  int *s_tag = reinterpret_cast<int *>(sm + SM::total) + SM::itag;
 
   const int tid = threadIdx.x;
   const int slot = blockIdx.x;
@@ -951,8 +978,8 @@ __global__ void __launch_bounds__(cut_chunk<N>()) cut_kernel(const __grid_consta
         }
 #pragma unroll
         for (int m = 0; m < N; ++m) {
-          s_lt0[tid][m] = zv[m];
-          s_lt1[tid][m] = zd[m];
+          s_fz[0][tid][m] = zv[m];
+          s_fz[1][tid][m] = zd[m];
           s_lvb[tid][m] = (DIM == 3) ? vo[m] : T(1);
         }
       }
@@ -974,8 +1001,8 @@ __global__ void __launch_bounds__(cut_chunk<N>()) cut_kernel(const __grid_consta
             m = tl;
             io = 0;
           }
-          av = fma(s_lvb[q][io], s_lt0[q][m], av);
-          ad = fma(s_lvb[q][io], s_lt1[q][m], ad);
+          av = fma(s_lvb[q][io], s_fz[0][q][m], av);
+          ad = fma(s_lvb[q][io], s_fz[1][q][m], ad);
         }
         s_ft[fi][0][tl] += av;
         s_ft[fi][1][tl] += ad;
@@ -1020,10 +1047,15 @@ int launch_vmult_t(const DevArrays<T> &d, const void *tables_struct, const void 
   const auto &tab = *reinterpret_cast<const StructTables<T, N> *>(tables_struct);
   if (ev) cudaEventRecord(static_cast<cudaEvent_t>(ev[0]), stream);
   if (blocks > 0) {
-    if (adjoint)
-      struct_kernel<T, DIM, N, true><<<blocks, threads, 0, stream>>>(tab, d, s, y, x);
+    const bool uni = d.kappa_uniform != 0;
+    if (adjoint && uni)
+      struct_kernel<T, DIM, N, true, true><<<blocks, threads, 0, stream>>>(tab, d, s, y, x);
+    else if (adjoint)
+      struct_kernel<T, DIM, N, true, false><<<blocks, threads, 0, stream>>>(tab, d, s, y, x);
+    else if (uni)
+      struct_kernel<T, DIM, N, false, true><<<blocks, threads, 0, stream>>>(tab, d, s, y, x);
     else
-      struct_kernel<T, DIM, N, false><<<blocks, threads, 0, stream>>>(tab, d, s, y, x);
+      struct_kernel<T, DIM, N, false, false><<<blocks, threads, 0, stream>>>(tab, d, s, y, x);
   }
   if (ev) cudaEventRecord(static_cast<cudaEvent_t>(ev[1]), stream);
   cudaError_t err = cudaGetLastError();
