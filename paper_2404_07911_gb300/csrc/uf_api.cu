@@ -317,6 +317,17 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   variant_tables(H, mats, lself, lnbgp);
   const size_t o_lself = L.take(sizeof(T) * lself.size());
   const size_t o_lnbgp = L.take(sizeof(T) * lnbgp.size());
+  auto transposed = [&](const std::vector<double> &m) {
+    std::vector<double> t(m.size());
+    const int nn = n * n;
+    for (size_t b = 0; b < m.size() / nn; ++b)
+      for (int r = 0; r < n; ++r)
+        for (int c2 = 0; c2 < n; ++c2) t[b * nn + r * n + c2] = m[b * nn + c2 * n + r];
+    return t;
+  };
+  const std::vector<double> lselfT = transposed(lself), lnbgpT = transposed(lnbgp);
+  const size_t o_lselfT = L.take(sizeof(T) * lselfT.size());
+  const size_t o_lnbgpT = L.take(sizeof(T) * lnbgpT.size());
   // FP64: the 1D basis at every line and point (the FP64 pipe is the bottleneck there, HBM is not)
   const bool pre = sizeof(T) == sizeof(double);
   std::vector<double> vline_b, vpt_b, spt_b, fline_b, fpt_b;
@@ -398,6 +409,8 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   put_t(o_fpw, fpt_w);
   put_t(o_lself, lself);
   put_t(o_lnbgp, lnbgp);
+  put_t(o_lselfT, lselfT);
+  put_t(o_lnbgpT, lnbgpT);
   if (pre) {
     put_t(o_vlb, vline_b);
     put_t(o_vpb, vpt_b);
@@ -457,6 +470,8 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   A.fpt_w = TP(o_fpw);
   A.lself = TP(o_lself);
   A.lnbgp = TP(o_lnbgp);
+  A.lselfT = TP(o_lselfT);
+  A.lnbgpT = TP(o_lnbgpT);
   A.vline_b = pre ? TP(o_vlb) : nullptr;
   A.vpt_b = pre ? TP(o_vpb) : nullptr;
   A.spt_b = pre ? TP(o_spb) : nullptr;

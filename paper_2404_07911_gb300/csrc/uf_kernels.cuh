@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "uf_device.h"
 
@@ -54,6 +55,67 @@ __device__ __forceinline__ int line_base(int axis, int t) {
   }
 }
 
+// Shared-memory layout of a cell in the structured kernel: element (i, j, k) at i + P j + P n k
+// with the odd line stride P = n | 1, so that the lanes of a warp working on neighbouring x-lines
+// (and the two cells a warp holds for n = 4) fall into different banks.
+template <int N>
+__host__ __device__ constexpr int spad() {
+  return N | 1;
+}
+template <int DIM, int N>
+__host__ __device__ constexpr int snd() {
+  return (DIM == 2) ? spad<N>() * N : spad<N>() * N * N;
+}
+template <int N>
+__device__ __forceinline__ int sstride(int axis) {
+  return axis == 0 ? 1 : (axis == 1 ? spad<N>() : spad<N>() * N);
+}
+template <int DIM, int N>
+__device__ __forceinline__ int sline_base(int axis, int t) {
+  constexpr int P = spad<N>();
+  if constexpr (DIM == 2) {
+    return (axis == 0) ? t * P : t;
+  } else {
+    const int tb = t % N, tc = t / N;
+    if (axis == 0) return tb * P + tc * P * N;
+    if (axis == 1) return tb + tc * P * N;
+    return tb + tc * P;
+  }
+}
+
+// Row of an n x n row-major matrix whose rows start on multiples of n elements of a 16-byte
+// aligned table: loaded with the widest vector the row length allows.
+__device__ __forceinline__ void unpack(const float4 &v, float *o) {
+  o[0] = v.x;
+  o[1] = v.y;
+  o[2] = v.z;
+  o[3] = v.w;
+}
+__device__ __forceinline__ void unpack(const float2 &v, float *o) {
+  o[0] = v.x;
+  o[1] = v.y;
+}
+__device__ __forceinline__ void unpack(const double2 &v, double *o) {
+  o[0] = v.x;
+  o[1] = v.y;
+}
+template <typename T, int N>
+__device__ __forceinline__ void load_row(const T *row, T *out) {
+  constexpr int B = N * (int)sizeof(T);
+  if constexpr (B % 16 == 0) {
+    using V = typename std::conditional<sizeof(T) == 8, double2, float4>::type;
+    constexpr int W = 16 / (int)sizeof(T);
+#pragma unroll
+    for (int i = 0; i < N / W; ++i) unpack(reinterpret_cast<const V *>(row)[i], out + W * i);
+  } else if constexpr (sizeof(T) == 4 && B % 8 == 0) {
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) unpack(reinterpret_cast<const float2 *>(row)[i], out + 2 * i);
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) out[i] = row[i];
+  }
+}
+
 __device__ __forceinline__ bool bit(uint32_t f, uint32_t b) { return (f & b) != 0u; }
 __device__ __forceinline__ uint32_t bit_full(int f) { return 1u << (1 + 3 * f); }
 __device__ __forceinline__ uint32_t bit_cut(int f) { return 1u << (2 + 3 * f); }
@@ -66,7 +128,8 @@ __host__ __device__ constexpr int struct_cells_per_block() {
   constexpr int ND = (DIM == 2) ? N * N : N * N * N;
   constexpr int NL = (DIM == 2) ? N : N * N;
   constexpr int by_threads = (NL >= 128) ? 1 : (128 / NL);
-  constexpr int cell_bytes = (int)sizeof(T) * (ND * (1 + DIM) + DIM * 3 * N * N);
+  constexpr int SND = (DIM == 2) ? (N | 1) * N : (N | 1) * N * N;
+  constexpr int cell_bytes = (int)sizeof(T) * (SND * (1 + DIM) + DIM * 3 * N * N);
   constexpr int by_smem = 40960 / cell_bytes;
   constexpr int cpb = by_threads < by_smem ? by_threads : by_smem;
   return cpb < 1 ? 1 : cpb;
@@ -82,13 +145,14 @@ __host__ __device__ constexpr int struct_cells_per_block() {
 //   3D: y = M_z (M_y W_x + M_x W_y) + M_y M_x W_z     (5 sweeps instead of 6)
 //   2D: y = M_y W_x + M_x W_y
 template <typename T, int N>
-__device__ __forceinline__ void apply_line(const T *__restrict__ Lm, const T *u, T *w, bool transpose,
-                                           bool accumulate) {
+__device__ __forceinline__ void apply_line(const T *__restrict__ Lm, const T *u, T *w, bool accumulate) {
 #pragma unroll
   for (int r = 0; r < N; ++r) {
+    T lr[N];
+    load_row<T, N>(Lm + r * N, lr);
     T acc = accumulate ? w[r] : T(0);
 #pragma unroll
-    for (int m = 0; m < N; ++m) acc = fma(Lm[transpose ? (m * N + r) : (r * N + m)], u[m], acc);
+    for (int m = 0; m < N; ++m) acc = fma(lr[m], u[m], acc);
     w[r] = acc;
   }
 }
@@ -117,10 +181,11 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
   constexpr int ND = G::ND, NL = G::NL, NF = G::NF, NN = N * N;
   constexpr int CPB = struct_cells_per_block<T, DIM, N>();
   constexpr int TPC = NL;
+  constexpr int P = spad<N>(), SND = snd<DIM, N>();
 
-  __shared__ T s_u[CPB][ND];
-  __shared__ T s_w[DIM][CPB][ND];
-  __shared__ T s_l[CPB][DIM][3][NN];  // per-cell matrices when kappa is not uniform
+  __shared__ __align__(16) T s_u[CPB][SND];
+  __shared__ __align__(16) T s_w[DIM][CPB][SND];
+  __shared__ __align__(16) T s_l[CPB][DIM][3][NN];  // per-cell matrices when kappa is not uniform
 
   const int tid = threadIdx.x;
   const int first = blockIdx.x * CPB;
@@ -134,7 +199,10 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
   {
     const int ncell = min(CPB, d.n_active - first);
     const T *src = x + (size_t)first * ND;
-    for (int i = tid; i < ncell * ND; i += blockDim.x) (&s_u[0][0])[i] = src[i];
+    for (int i = tid; i < ncell * ND; i += blockDim.x) {
+      const int l = i % ND;
+      s_u[i / ND][l + (P - N) * (l / N)] = src[i];
+    }
   }
 
   uint32_t fl = 0;
@@ -210,20 +278,22 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
   if (has_cell) {
 #pragma unroll 1
     for (int a = 0; a < DIM; ++a) {
-      const int base = line_base<DIM, N>(a, t);
+      const int base = line_base<DIM, N>(a, t);  // global layout (neighbour lines)
       const int st = stride_of<N>(a);
+      const int sb = sline_base<DIM, N>(a, t);   // shared-memory layout
+      const int ss = sstride<N>(a);
       T u[N], w[N];
 #pragma unroll
-      for (int m = 0; m < N; ++m) u[m] = s_u[c][base + m * st];
+      for (int m = 0; m < N; ++m) u[m] = s_u[c][sb + m * ss];
       if (uniform) {
         int v = inside ? 1 : 0;
         v |= bit(fl, bit_full(2 * a)) ? 2 : 0;
         v |= bit(fl, bit_gp(2 * a)) ? 4 : 0;
         v |= bit(fl, bit_full(2 * a + 1)) ? 8 : 0;
         v |= bit(fl, bit_gp(2 * a + 1)) ? 16 : 0;
-        apply_line<T, N>(d.lself + v * NN, u, w, ADJ, false);
+        apply_line<T, N>((ADJ ? d.lselfT : d.lself) + v * NN, u, w, false);
       } else {
-        apply_line<T, N>(s_l[c][a][0], u, w, false, false);
+        apply_line<T, N>(s_l[c][a][0], u, w, false);
       }
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
@@ -239,10 +309,11 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
         if (gp) {
           if (uniform) {
             // transpose of the neighbour's table entry (its face 1 - s) for the adjoint
-            const T *Lg = d.lnbgp + (2 * (ADJ ? 1 - s : s) + (full ? 1 : 0)) * NN;
-            apply_line<T, N>(Lg, un, w, ADJ, true);
+            const T *Lg = ADJ ? d.lnbgpT + (2 * (1 - s) + (full ? 1 : 0)) * NN
+                              : d.lnbgp + (2 * s + (full ? 1 : 0)) * NN;
+            apply_line<T, N>(Lg, un, w, true);
           } else {
-            apply_line<T, N>(s_l[c][a][1 + s], un, w, false, true);
+            apply_line<T, N>(s_l[c][a][1 + s], un, w, true);
           }
         } else {
           // rank-2 SIPG coupling (the transposed coupling of a symmetric flux is the same form);
@@ -262,7 +333,7 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
         }
       }
 #pragma unroll
-      for (int r = 0; r < N; ++r) s_w[a][c][base + r * st] = w[r];
+      for (int r = 0; r < N; ++r) s_w[a][c][sb + r * ss] = w[r];
     }
   }
   __syncthreads();
@@ -271,28 +342,28 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
   const T *M = tab.mass;
   if constexpr (DIM == 2) {
     if (has_cell) {
-      mass_line<T, N>(M, s_w[0][c], line_base<DIM, N>(1, t), N);  // M_y W_x
-      mass_line<T, N>(M, s_w[1][c], line_base<DIM, N>(0, t), 1);  // M_x W_y
+      mass_line<T, N>(M, s_w[0][c], sline_base<DIM, N>(1, t), P);  // M_y W_x
+      mass_line<T, N>(M, s_w[1][c], sline_base<DIM, N>(0, t), 1);  // M_x W_y
     }
     __syncthreads();
     if (has_cell) {
       // y = W_x + W_y; thread t writes the x-line t
-      const int base = line_base<DIM, N>(0, t);
+      const int base = line_base<DIM, N>(0, t), sb = sline_base<DIM, N>(0, t);
 #pragma unroll
       for (int r = 0; r < N; ++r) {
-        const T v = s_w[0][c][base + r] + s_w[1][c][base + r];
+        const T v = s_w[0][c][sb + r] + s_w[1][c][sb + r];
         y[(size_t)e * ND + base + r] = scale_rows ? yscale * v : v;
       }
     }
   } else {
     if (has_cell) {
-      mass_line<T, N>(M, s_w[0][c], line_base<DIM, N>(1, t), N);  // W_x <- M_y W_x
-      mass_line<T, N>(M, s_w[2][c], line_base<DIM, N>(0, t), 1);  // W_z <- M_x W_z
+      mass_line<T, N>(M, s_w[0][c], sline_base<DIM, N>(1, t), P);  // W_x <- M_y W_x
+      mass_line<T, N>(M, s_w[2][c], sline_base<DIM, N>(0, t), 1);  // W_z <- M_x W_z
     }
     __syncthreads();
     if (has_cell) {
       // W_x += M_x W_y (x-lines)
-      const int bx = line_base<DIM, N>(0, t);
+      const int bx = sline_base<DIM, N>(0, t);
       T a[N];
 #pragma unroll
       for (int m = 0; m < N; ++m) a[m] = s_w[1][c][bx + m];
@@ -303,18 +374,18 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
         for (int m = 0; m < N; ++m) acc = fma(M[r * N + m], a[m], acc);
         s_w[0][c][bx + r] = acc;
       }
-      mass_line<T, N>(M, s_w[2][c], line_base<DIM, N>(1, t), N);  // W_z <- M_y W_z
+      mass_line<T, N>(M, s_w[2][c], sline_base<DIM, N>(1, t), P);  // W_z <- M_y W_z
     }
     __syncthreads();
     if (has_cell) {
       // y = M_z W_x + W_z along z-lines
-      const int bz = line_base<DIM, N>(2, t);
+      const int bz = line_base<DIM, N>(2, t), sbz = sline_base<DIM, N>(2, t);
       T a[N];
 #pragma unroll
-      for (int m = 0; m < N; ++m) a[m] = s_w[0][c][bz + m * N * N];
+      for (int m = 0; m < N; ++m) a[m] = s_w[0][c][sbz + m * P * N];
 #pragma unroll
       for (int r = 0; r < N; ++r) {
-        T acc = s_w[2][c][bz + r * N * N];
+        T acc = s_w[2][c][sbz + r * P * N];
 #pragma unroll
         for (int m = 0; m < N; ++m) acc = fma(M[r * N + m], a[m], acc);
         y[(size_t)e * ND + bz + r * N * N] = scale_rows ? yscale * acc : acc;
