@@ -5,10 +5,13 @@ level set phi; the physical domain is Omega = {phi < 0}.  Sec. 2.3 classifies ce
 (structured quadrature), cut (unstructured quadrature) or outside (dropped), and interior faces as
 inside faces (structured) or cut faces (unstructured).
 
-Level set: the sphere phi(x) = |x - c| - R.  Its classification of a closed box is exact through
-the squared minimum / maximum distance from c to the box:
-    inside  <=>  dmax^2 <= R^2,     outside  <=>  dmin^2 >= R^2,     cut otherwise.
-Squared distances are summed over the coordinate directions in increasing index order.
+Level sets: the sphere phi(x) = |x - c| - R, classified exactly through the squared minimum /
+maximum distance from c to the closed box:
+    inside  <=>  dmax^2 <= R^2,     outside  <=>  dmin^2 >= R^2,     cut otherwise;
+and the plane phi(x) = n . x - off, classified exactly through its minimum / maximum over the box
+(the corner chosen per direction by the sign of n_a):
+    inside  <=>  max phi <= 0,      outside  <=>  min phi >= 0,      cut otherwise.
+Sums are taken over the coordinate directions in increasing index order.
 
 Active cells (inside + cut) are numbered lexicographically with the x index fastest; the DoFs of
 active cell e are e * n^d + l with l = i + n j + n^2 k (Sec. 3.2).
@@ -22,6 +25,8 @@ A face carries the face-based ghost penalty iff at least one of its two cells is
 from dataclasses import dataclass, field
 
 import numpy as np
+
+from . import saye
 
 INSIDE, CUT, OUTSIDE = 0, 1, 2
 FACE_FULL, FACE_CUT, FACE_EMPTY = 0, 1, 2
@@ -50,9 +55,26 @@ def classify_box(c, R, lo, hi):
     return CUT
 
 
+def classify_plane_box(n, off, lo, hi):
+    mn, mx = saye.lin_range(n, off, lo, hi)
+    if mx <= 0.0:
+        return INSIDE
+    if mn >= 0.0:
+        return OUTSIDE
+    return CUT
+
+
+def classify(prob, lo, hi):
+    """Type of the closed box [lo, hi] against the level set of `prob`."""
+    if prob.ls_kind == "plane":
+        return classify_plane_box(prob.normal, prob.offset, lo, hi)
+    return classify_box(prob.center, prob.radius, lo, hi)
+
+
 @dataclass
 class Problem:
-    """One unfitted DG Poisson problem (sphere domain, uniform Cartesian background grid)."""
+    """One unfitted Poisson problem (sphere or half-space domain, uniform Cartesian background
+    grid).  ls_kind "sphere": |x - center| < radius; "plane": normal . x < offset."""
 
     dim: int
     degree: int
@@ -67,6 +89,9 @@ class Problem:
     gp_max_order: int      # J: ghost penalty on jumps of d^j/dn^j, j = 1..J
     gp_gamma: float        # gamma_j = gp_gamma * h^(2j-1) / (j!)^2
     kappa: np.ndarray = None  # per active cell diffusion coefficient (None = 1)
+    ls_kind: str = "sphere"
+    normal: tuple = None      # plane: phi(x) = normal . x - offset
+    offset: float = 0.0
     # derived
     h: float = field(init=False)
 
@@ -76,6 +101,13 @@ class Problem:
         self.lo = tuple(float(v) for v in self.lo[:d])
         self.hi = tuple(float(v) for v in self.hi[:d])
         self.center = tuple(float(v) for v in self.center[:d])
+        if self.ls_kind not in ("sphere", "plane"):
+            raise ValueError("ls_kind must be 'sphere' or 'plane'")
+        if self.ls_kind == "plane":
+            self.normal = tuple(float(v) for v in self.normal[:d])
+            self.offset = float(self.offset)
+            if not any(v != 0.0 for v in self.normal):
+                raise ValueError("the plane normal must not vanish")
         hs = [(self.hi[a] - self.lo[a]) / self.n_cells[a] for a in range(d)]
         if max(hs) - min(hs) > 1e-14 * max(hs):
             raise ValueError("the oracle needs a uniform (isotropic) background grid")
@@ -94,7 +126,8 @@ class Problem:
 def problem_from_dict(cfg, kappa=None):
     keys = ["dim", "degree", "n_cells", "lo", "hi", "center", "radius", "quad_order",
             "sipg_gamma", "nitsche_gamma", "gp_max_order", "gp_gamma"]
-    return Problem(**{k: cfg[k] for k in keys}, kappa=kappa)
+    extra = {k: cfg[k] for k in ("ls_kind", "normal", "offset") if k in cfg}
+    return Problem(**{k: cfg[k] for k in keys}, kappa=kappa, **extra)
 
 
 def cell_box(prob, idx):
@@ -119,17 +152,28 @@ class Mesh:
             idx = np.arange(N[a], dtype=np.float64)
             lo = prob.lo[a] + idx * prob.hvec[a]
             hi = prob.lo[a] + (idx + 1) * prob.hvec[a]
+            bshape = [1] * d
+            bshape[d - 1 - a] = N[a]
+            if prob.ls_kind == "plane":
+                # (min, max) of n . x over the cell, as in saye.lin_range
+                na = prob.normal[a]
+                lo_t, hi_t = (na * lo, na * hi) if na >= 0.0 else (na * hi, na * lo)
+                dmin2 = dmin2 + lo_t.reshape(bshape)
+                dmax2 = dmax2 + hi_t.reshape(bshape)
+                continue
             dl = lo - prob.center[a]
             dh = hi - prob.center[a]
             e = np.maximum(np.maximum(dl, 0.0), -dh)
-            bshape = [1] * d
-            bshape[d - 1 - a] = N[a]
             dmin2 = dmin2 + (e * e).reshape(bshape)
             dmax2 = dmax2 + np.maximum(dl * dl, dh * dh).reshape(bshape)
-        r2 = prob.radius * prob.radius
         t = np.full(shape, CUT, dtype=np.int8)
-        t[dmin2 >= r2] = OUTSIDE
-        t[dmax2 <= r2] = INSIDE
+        if prob.ls_kind == "plane":
+            t[dmin2 - prob.offset >= 0.0] = OUTSIDE
+            t[dmax2 - prob.offset <= 0.0] = INSIDE
+        else:
+            r2 = prob.radius * prob.radius
+            t[dmin2 >= r2] = OUTSIDE
+            t[dmax2 <= r2] = INSIDE
         self.cell_type = t
         act = np.nonzero(t.reshape(-1) != OUTSIDE)[0]
         self.id_map = np.full(t.size, -1, dtype=np.int64)
@@ -175,7 +219,7 @@ class Mesh:
 
     def face_type(self, e_minus, axis):
         lo, hi = self.face_box(e_minus, axis)
-        t = classify_box(self.prob.center, self.prob.radius, lo, hi)
+        t = classify(self.prob, lo, hi)
         return {INSIDE: FACE_FULL, CUT: FACE_CUT, OUTSIDE: FACE_EMPTY}[t]
 
     def interior_faces(self):

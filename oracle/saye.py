@@ -1,4 +1,5 @@
-"""Dimension-reduction quadrature for sphere level sets (oracle; test infrastructure only).
+"""Dimension-reduction quadrature for sphere and plane level sets (oracle; test infrastructure
+only).
 
 The paper generates the cut-cell (volume, surface) and cut-face rules with the dimension
 reduction method of Saye (2015) (Sec. 1, Sec. 2.3) and adds uniform subdivision when needed
@@ -259,18 +260,167 @@ def sphere_rules(lo, hi, c, rho, q, depth=0, surface=True):
     return vol, surf
 
 
+# ------------------------------------------------------------------------------------------
+# Plane level sets psi(x) = sum_a n_a x_a - off (n != 0; Omega = {psi < 0})
+# ------------------------------------------------------------------------------------------
+#
+# The same method for a linear level set: psi is monotone along every direction with n_k != 0,
+# so no bisection is needed.  Height direction k = argmax |n_i| (lowest index on ties); the
+# restriction of psi to x_k = v is linear again, (n without k, off - n_k v); the root on the
+# line through x' is t = (off - s) / n_k with s = sum_{a != k} n_a x'_a (increasing a); a
+# surface point has weight w' |n| / |n_k| (= w' |grad phi| / |d_k phi|) and normal n / |n|.
+# Sums run over coordinate directions in increasing index order.
+
+
+def lin_range(n, off, lo, hi):
+    """(min, max) of sum_a n_a x_a - off over the closed box [lo, hi]."""
+    mn = 0.0
+    mx = 0.0
+    for a in range(len(n)):
+        if n[a] >= 0.0:
+            mn += n[a] * lo[a]
+            mx += n[a] * hi[a]
+        else:
+            mn += n[a] * hi[a]
+            mx += n[a] * lo[a]
+    return mn - off, mx - off
+
+
+def _lin_height(n):
+    k = 0
+    best = -1.0
+    for i in range(len(n)):
+        v = abs(n[i])
+        if v > best:
+            best = v
+            k = i
+    return k
+
+
+def _lin_sum_excl(n, k, xp):
+    """sum_{a != k} n_a x'_a, x' = the coordinates without direction k, increasing a."""
+    s = 0.0
+    j = 0
+    for a in range(len(n)):
+        if a == k:
+            continue
+        s += n[a] * xp[j]
+        j += 1
+    return s
+
+
+def full_rule_linear(lo, hi, fns, q):
+    """Rule for the whole box [lo, hi] whose pieces break at the zero sets of the linear
+    functions `fns` (list of (n, off), all with the same n)."""
+    m = len(lo)
+    keep = []
+    for (n, off) in fns:
+        mn, mx = lin_range(n, off, lo, hi)
+        if not (mn >= 0.0 or mx <= 0.0):
+            keep.append((n, off))
+    if not keep:
+        return tensor_gauss(lo, hi, q)
+    g, w = gauss01(q)
+    n = keep[0][0]
+    if m == 1:
+        roots = []
+        for (nf, off) in keep:
+            t = off / nf[0]
+            if lo[0] < t < hi[0]:
+                roots.append(t)
+        out = []
+        for (a, b) in _pieces(lo[0], hi[0], roots):
+            for i in range(q):
+                out.append(((a + (b - a) * g[i],), (b - a) * w[i]))
+        return out
+    k = _lin_height(n)
+    nsub = _drop(n, k)
+    fns2 = []
+    for (nf, off) in keep:
+        fns2.append((nsub, off - n[k] * lo[k]))
+        fns2.append((nsub, off - n[k] * hi[k]))
+    outer = full_rule_linear(_drop(lo, k), _drop(hi, k), fns2, q)
+    out = []
+    for (xp, wp) in outer:
+        s = _lin_sum_excl(n, k, xp)
+        roots = []
+        for (nf, off) in keep:
+            t = (off - s) / n[k]
+            if lo[k] < t < hi[k]:
+                roots.append(t)
+        for (a, b) in _pieces(lo[k], hi[k], roots):
+            for i in range(q):
+                out.append((_insert(xp, k, a + (b - a) * g[i]), wp * ((b - a) * w[i])))
+    return out
+
+
+def plane_rules(lo, hi, n, off, q, surface=True):
+    """Volume rule for {psi < 0} cap [lo, hi] and (if `surface`) the surface rule for {psi = 0},
+    psi(x) = sum_a n_a x_a - off.  Returns (volume, surface) as sphere_rules does."""
+    m = len(lo)
+    mn, mx = lin_range(n, off, lo, hi)
+    if mx <= 0.0:
+        return tensor_gauss(lo, hi, q), []
+    if mn >= 0.0:
+        return [], []
+    g, w = gauss01(q)
+    nn = 0.0
+    for a in range(m):
+        nn += n[a] * n[a]
+    nn = math.sqrt(nn)
+    if m == 1:
+        t = off / n[0]
+        roots = [t] if lo[0] < t < hi[0] else []
+        vol = []
+        for (a, b) in _pieces(lo[0], hi[0], roots):
+            mid = 0.5 * (a + b)
+            if n[0] * mid - off < 0.0:
+                for i in range(q):
+                    vol.append(((a + (b - a) * g[i],), (b - a) * w[i]))
+        surf = [((t,), 1.0, (1.0 if n[0] > 0.0 else -1.0,)) for t in roots] if surface else []
+        return vol, surf
+    k = _lin_height(n)
+    nsub = _drop(n, k)
+    outer = full_rule_linear(_drop(lo, k), _drop(hi, k),
+                             [(nsub, off - n[k] * lo[k]), (nsub, off - n[k] * hi[k])], q)
+    vol = []
+    surf = []
+    for (xp, wp) in outer:
+        s = _lin_sum_excl(n, k, xp)
+        tt = (off - s) / n[k]
+        t = tt if lo[k] < tt < hi[k] else None
+        for (a, b) in _pieces(lo[k], hi[k], [] if t is None else [t]):
+            mid = 0.5 * (a + b)
+            if (s + n[k] * mid) - off < 0.0:
+                for i in range(q):
+                    vol.append((_insert(xp, k, a + (b - a) * g[i]), wp * ((b - a) * w[i])))
+        if surface and t is not None:
+            x = _insert(xp, k, t)
+            normal = tuple(n[i] / nn for i in range(m))
+            surf.append((x, wp * (nn / abs(n[k])), normal))
+    return vol, surf
+
+
 def cell_rules(prob, lo, hi, q=None):
-    """Volume and surface rule of the cell [lo, hi] cut by the sphere of `prob`."""
+    """Volume and surface rule of the cell [lo, hi] cut by the level set of `prob`."""
+    q = prob.quad_order if q is None else q
+    if prob.ls_kind == "plane":
+        return plane_rules(lo, hi, prob.normal, prob.offset, q)
     R = prob.radius
-    return sphere_rules(lo, hi, prob.center, R * R, prob.quad_order if q is None else q)
+    return sphere_rules(lo, hi, prob.center, R * R, q)
 
 
 def face_rule(prob, face_lo, face_hi, axis, q=None):
     """Rule for F cap Omega on the face x_axis = face_lo[axis] (a (d-1)-dimensional box)."""
-    R = prob.radius
+    q = prob.quad_order if q is None else q
     xa = face_lo[axis]
-    da = xa - prob.center[axis]
-    rho = R * R - da * da
-    vol, _ = sphere_rules(_drop(face_lo, axis), _drop(face_hi, axis), _drop(prob.center, axis),
-                          rho, prob.quad_order if q is None else q, surface=False)
+    if prob.ls_kind == "plane":
+        vol, _ = plane_rules(_drop(face_lo, axis), _drop(face_hi, axis), _drop(prob.normal, axis),
+                             prob.offset - prob.normal[axis] * xa, q, surface=False)
+    else:
+        R = prob.radius
+        da = xa - prob.center[axis]
+        rho = R * R - da * da
+        vol, _ = sphere_rules(_drop(face_lo, axis), _drop(face_hi, axis), _drop(prob.center, axis),
+                              rho, q, surface=False)
     return [(_insert(x, axis, xa), wt) for (x, wt) in vol]

@@ -170,3 +170,105 @@ def test_subdivision_path():
                      abs(sum(w for _, w, _ in surf) / (4.0 * math.pi * R ** 2) - 1.0)))
     assert errs[0][0] < 1e-5 and errs[0][1] < 5e-3
     assert errs[2][0] < errs[0][0] / 10 and errs[2][1] < errs[0][1] / 100
+
+
+# ------------------------------------------------------------------------------------------
+# Plane level sets: the region below a plane in a box is a polytope, and every dimension-
+# reduction piece is split exactly at the plane, so the rules integrate polynomials of degree
+# <= 2q - 1 per direction exactly: closed forms hold to rounding.
+# ------------------------------------------------------------------------------------------
+
+def _plane_prob(dim, N, q, normal, offset):
+    return mesh.Problem(dim, 2, (N,) * dim, (0.0,) * dim, (1.0,) * dim, (0.0,) * dim, 1.0, q, 1, 1,
+                        1, 0.5, ls_kind="plane", normal=normal, offset=offset)
+
+
+def _height(normal, offset):
+    """The plane as a graph over the first d-1 coordinates: x_d = offset - sum a_i x_i."""
+    nd = normal[-1]
+    return lambda xs: (offset - sum(normal[i] * xs[i] for i in range(len(xs)))) / nd
+
+
+@pytest.mark.parametrize("dim,normal,offset", [
+    (2, (-0.1, 1.0), 0.43),
+    (3, (-0.1, -0.05, 1.0), 0.43),
+    (3, (0.2, -0.3, 0.9), 0.31),     # tilted enough that cut cells stack along the last axis
+    (3, (0.0, 0.0, 1.0), 0.5),       # on a grid plane: the cut is a layer of full faces
+])
+def test_plane_rules_closed_forms(dim, normal, offset):
+    import scipy.integrate as si
+
+    prob = _plane_prob(dim, 5, 3, normal, offset)
+    vx, vw, sx, sw, sn = _all_rules(prob)
+    f = _height(normal, offset)
+    nrm = math.sqrt(sum(v * v for v in normal))
+    # the plane stays inside the box over the whole footprint for these cases
+    if dim == 2:
+        vol = si.quad(lambda x: f((x,)), 0, 1, epsabs=1e-15)[0]
+        mom = si.quad(lambda x: x * f((x,)) ** 2 / 2, 0, 1, epsabs=1e-15)[0]
+    else:
+        vol = si.dblquad(lambda y, x: f((x, y)), 0, 1, 0, 1, epsabs=1e-15)[0]
+        mom = si.dblquad(lambda y, x: x * f((x, y)) ** 2 / 2, 0, 1, 0, 1, epsabs=1e-15)[0]
+    area = nrm / abs(normal[-1])  # the plane over the unit footprint
+    assert abs(vw.sum() - vol) < 1e-14
+    assert abs(sw.sum() - area) < 1e-14
+    # int_Gamma n = projected area along every axis = normal / |normal_d|
+    assert np.abs((sw[:, None] * sn).sum(axis=0) - np.array(normal) / abs(normal[-1])).max() < 1e-14
+    # int x_0 x_d (degree 2, exact for q = 3)
+    assert abs(vw @ (vx[:, 0] * vx[:, -1]) - mom) < 1e-14
+    # every surface point lies on the plane, with the unit normal
+    assert np.abs(sx @ np.array(normal) - offset).max() < 1e-14
+    assert np.abs(sn - np.array(normal) / nrm).max() < 1e-15
+
+
+def test_plane_divergence_theorem_per_cut_cell_exact():
+    """Per cut cell, divergence theorem with the face rules; exact for a cubic field (q = 4)."""
+    prob = _plane_prob(3, 4, 4, (0.2, -0.3, 0.9), 0.31)
+    m = mesh.Mesh(prob)
+
+    def F(x):
+        return np.array([x[0] ** 2 * x[1], x[1] * x[2] ** 2 + x[0], x[0] * x[1] * x[2]])
+
+    def divF(x):
+        return 2 * x[0] * x[1] + x[2] ** 2 + x[0] * x[1]
+
+    worst = 0.0
+    n_cut = 0
+    for e in range(m.n_active):
+        if m.active_type[e] != mesh.CUT:
+            continue
+        n_cut += 1
+        lo, hi = mesh.cell_box(prob, m.index_of(e))
+        vol, surf = saye.cell_rules(prob, lo, hi)
+        lhs = sum(w * divF(x) for x, w in vol)
+        rhs = sum(w * F(x) @ np.array(nn) for x, w, nn in surf)
+        for axis in range(3):
+            for side, sign in ((0, -1.0), (1, 1.0)):
+                flo = list(lo)
+                fhi = list(hi)
+                if side == 0:
+                    fhi[axis] = lo[axis]
+                else:
+                    flo[axis] = hi[axis]
+                for x, w in saye.face_rule(prob, tuple(flo), tuple(fhi), axis):
+                    rhs += sign * w * F(x)[axis]
+        worst = max(worst, abs(lhs - rhs))
+    assert n_cut > 10
+    assert worst < 1e-14
+
+
+def test_plane_classification_against_sampling():
+    """Inside / cut / outside of every cell against a dense sampling of the plane's sign."""
+    normal, offset = (0.2, -0.3, 0.9), 0.31
+    prob = _plane_prob(3, 6, 2, normal, offset)
+    m = mesh.Mesh(prob)
+    t = np.linspace(0.0, 1.0, 9)
+    for flat in range(6 ** 3):
+        idx = (flat % 6, (flat // 6) % 6, flat // 36)
+        lo, hi = mesh.cell_box(prob, idx)
+        g = np.stack(np.meshgrid(*[lo[a] + t * (hi[a] - lo[a]) for a in range(3)]), -1).reshape(-1, 3)
+        phi = g @ np.array(normal) - offset
+        want = mesh.INSIDE if phi.max() <= 0 else (mesh.OUTSIDE if phi.min() >= 0 else mesh.CUT)
+        e = m.id_map[idx[::-1]]
+        got = mesh.OUTSIDE if e < 0 else m.active_type[e]
+        assert got == want

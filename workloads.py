@@ -22,6 +22,10 @@ benchmark configurations:
   * ``cfg_cg_q4``      3D continuous Q4 on an 80^3 background, ball of radius 1 at the origin,
                        Nitsche u = 0, ghost penalty orders 1..4, f = 1 (the solve workload).
   * ``small(...)``     reduced grids of the same geometry for tests the oracle finishes in seconds.
+  * ``plane(...)``     half-space below a slightly tilted plane in a box of cubes (the paper's plane
+                       benchmark, Sec. 5.3, positions the plane to set the ratio of cut cells);
+                       ``cfg_plane(kind, ratio)`` sizes the box so that the cut layer is a fraction
+                       ``ratio`` of the active cells.
 
 Vectors are drawn with ``numpy.random.default_rng(seed)`` in DoF order (active cells
 lexicographic with x fastest, local index i + n j + n^2 k).
@@ -99,3 +103,43 @@ def x_and_b(n, seed=5):
     """x then b ~ U[-1, 1] from one generator."""
     rng = np.random.default_rng(seed)
     return rng.uniform(-1.0, 1.0, n), rng.uniform(-1.0, 1.0, n)
+
+
+PLANE_NORMAL = (-0.04, -0.03, 1.0)
+
+
+def plane(p=2, N=5, dim=3, layers=None, offset_cells=None, discretization="dg", quad_order=None,
+          seed=9, normal=None):
+    """Half-space normal . x < offset in the box [0, 1]^(d-1) x [0, layers h], h = 1 / N: the
+    plane is tilted by a few per cent against the last axis and crosses the box at about
+    offset_cells cells above the bottom.  Penalties as for the ball workloads."""
+    layers = N if layers is None else layers
+    nrm = tuple((normal or PLANE_NORMAL)[3 - dim:]) if dim == 2 else tuple(normal or PLANE_NORMAL)
+    h = 1.0 / N
+    oc = (layers - 0.45) if offset_cells is None else offset_cells
+    n_cells = (N,) * (dim - 1) + (layers,)
+    lo = (0.0,) * dim
+    hi = (1.0,) * (dim - 1) + (layers * h,)
+    pad = (0.0,) * (3 - dim)
+    c = dict(name=f"{dim}d_{discretization}_q{p}_plane_{N}x{layers}", dim=dim, degree=p,
+             n_cells=n_cells + (1,) * (3 - dim), lo=lo + pad, hi=hi + pad, center=(0.0, 0.0, 0.0),
+             radius=1.0, ls_kind="plane", normal=nrm + pad, offset=oc * h,
+             quad_order=quad_order if quad_order is not None else p + 1, seed=seed,
+             discretization=discretization, **_penalties(p))
+    return c
+
+
+def cfg_plane(discretization, p, ratio, n_dofs=2.0e7):
+    """Plane benchmark: the active cells are `layers` cell layers of an N x N footprint with the
+    plane in the top one, so that about 1 / layers of the active cells are cut; `ratio` = 0
+    puts the plane above the box (no cut cell).  N is chosen for about n_dofs unknowns."""
+    layers = 1 if ratio >= 1.0 else (100 if ratio <= 0.0 else int(round(1.0 / ratio)))
+    per_cell = (p + 1) ** 3 if discretization == "dg" else p ** 3
+    N = max(4, int(round((n_dofs / per_cell / layers) ** 0.5)))
+    # the plane rises by h / 2 across the box, so it stays inside the top cell layer
+    oc = layers + 10.0 if ratio <= 0.0 else layers - 0.75
+    c = plane(p=p, N=N, dim=3, layers=layers, offset_cells=oc, discretization=discretization,
+              seed=10, normal=(-0.3 / N, -0.2 / N, 1.0))
+    c["name"] = f"3d_{discretization}_q{p}_plane_ratio_{ratio:g}"
+    return c
+
