@@ -59,10 +59,11 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-csr", action="store_true",
                     help="skip the assembled-matrix (CSR SpMV) comparison")
-    ap.add_argument("--config", choices=("q3", "solve", "sweep", "kappa"), default="q3",
+    ap.add_argument("--config", choices=("q3", "solve", "sweep", "kappa", "plane"), default="q3",
                     help="q3: the headline step (default); solve: CG Q4 time to solution, IR vs "
                          "FP64; sweep: degree sweep p = 1..8 at ~2e7 DoFs; kappa: forward vs "
-                         "forward + backward of the differentiable operator")
+                         "forward + backward of the differentiable operator; plane: throughput "
+                         "against the ratio of cut cells (DG Q1, CG Q3)")
     return ap.parse_args()
 
 
@@ -429,6 +430,66 @@ def _event_ms(fn, K, stream, flush=None):
     return statistics.median(a.elapsed_time(b) for a, b in ev)
 
 
+def run_plane(args, local):
+    """Plane benchmark: throughput of A x against the ratio of cut to active cells (1, 0.5, 0.1,
+    0.01, 0) for DG Q1 and continuous Q3 at about 2e7 DoFs, FP64 and FP32; DG rows of cut and
+    inside cells sampled against the oracle."""
+    import torch
+
+    from oracle import forms, mesh
+    from paper_2404_07911_gb300 import UF_FP32, UF_FP64, UnfittedOperator
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for disc, p in (("dg", 1), ("cg", 3)):
+        for ratio in (1.0, 0.5, 0.1, 0.01, 0.0):
+            cfg = workloads.cfg_plane(disc, p, ratio)
+            t0 = time.perf_counter()
+            op = UnfittedOperator(cfg, precisions=UF_FP64 | UF_FP32, device=local)
+            t_setup = time.perf_counter() - t0
+            n = op.n_dofs
+            xh = workloads.uniform_vector(n, cfg["seed"])
+            x64 = torch.from_numpy(xh).cuda()
+            x32 = x64.float()
+            y64 = torch.empty_like(x64)
+            y32 = torch.empty_like(x32)
+            for _ in range(3):
+                op.vmult(x64, y64, stream)
+                op.vmult(x32, y32, stream)
+            K = 20
+            op.profile_begin(2 * K)
+            ms64 = _event_ms(lambda: op.vmult(x64, y64, stream), K, stream, flush)
+            ms32 = _event_ms(lambda: op.vmult(x32, y32, stream), K, stream, flush)
+            kt = op.profile_end()
+            info = op.info
+            rec = {"metric": "plane benchmark: MDoF/s of A x against the ratio of cut cells",
+                   "discretization": disc, "degree": p, "ratio_target": ratio,
+                   "config": {"workload": cfg["name"], "n_cells": list(cfg["n_cells"]), "n_dofs": n,
+                              "n_active": info["n_active"], "n_cut": info["n_cut"],
+                              "cut_ratio": round(info["n_cut"] / info["n_active"], 5),
+                              "setup_s": round(t_setup, 2)},
+                   "fp64": {"ms": round(ms64, 4), "mdofs": round(n / ms64 / 1e3, 1)},
+                   "fp32": {"ms": round(ms32, 4), "mdofs": round(n / ms32 / 1e3, 1)},
+                   "kernel_ms": {f"{kern}_{prec}": round(tot / cnt, 4)
+                                 for (prec, kern, _), (tot, cnt) in sorted(kt.items())},
+                   "l2": "flushed before every launch"}
+            if disc == "dg":
+                o = forms.Oracle(mesh.problem_from_dict(cfg))
+                cut = np.nonzero(o.mesh.active_type == mesh.CUT)[0]
+                ins = np.nonzero(o.mesh.active_type == mesh.INSIDE)[0]
+                rng = np.random.default_rng(p)
+                cells = sorted(set(int(c) for c in list(rng.choice(cut, min(4, len(cut)), replace=False))
+                                   + list(rng.choice(ins, min(2, len(ins)), replace=False))))
+                nd = info["dofs_per_cell"]
+                ref = o.apply_rows(xh, cells)
+                g64 = y64.cpu().numpy().reshape(-1, nd)[cells]
+                rec["fp64"]["rel_err"] = float(np.max(np.abs(g64 - ref)) / np.max(np.abs(ref)))
+            print(json.dumps(rec), flush=True)
+            op.close()
+            del x64, x32, y64, y32
+
+
 def run_solve(args, local):
     """CG Q4 ball solve: FP32 PCG inside FP64 refinement vs all-FP64 PCG, same final residual."""
     import torch
@@ -605,6 +666,8 @@ def main():
         run_sweep(args, local)
     elif args.config == "kappa":
         run_kappa(args, local)
+    elif args.config == "plane":
+        run_plane(args, local)
     else:
         run_ours(args, rank, world, local)
 

@@ -46,7 +46,7 @@ typedef enum {
 } uf_status;
 
 enum { UF_FP64 = 1, UF_FP32 = 2 };     /* precision flags (bit mask in uf_params.precisions) */
-enum { UF_LS_SPHERE = 0 };             /* level set kinds */
+enum { UF_LS_SPHERE = 0, UF_LS_PLANE = 1 };  /* level set kinds */
 enum { UF_DG = 0, UF_CG = 1 };         /* discretizations (uf_params.discretization) */
 
 /* Parameters of uf_create_unfitted_operator.  Penalties follow the paper's forms:
@@ -57,7 +57,8 @@ typedef struct {
   int degree;             /* polynomial degree p, 1..8 */
   int n_cells[3];         /* background cells per direction (entries >= dim ignored) */
   double lo[3], hi[3];    /* background box; cells must be cubes (isotropic h) */
-  int ls_kind;            /* UF_LS_SPHERE: phi(x) = |x - ls_center| - ls_radius */
+  int ls_kind;            /* UF_LS_SPHERE: phi(x) = |x - ls_center| - ls_radius;
+                             UF_LS_PLANE: phi(x) = ls_normal . x - ls_offset (fields at the end) */
   double ls_center[3];
   double ls_radius;
   int quad_order;         /* q: Gauss points per interval of the cut-cell / cut-face rules */
@@ -71,6 +72,8 @@ typedef struct {
   int discretization;     /* UF_DG: SIPG (Eq. bilinear_dg), DoFs per cell; UF_CG: continuous Q_p
                              (Eq. bilinear_cg, no SIPG), DoFs on the Gauss-Lobatto lattice points of
                              the active cells numbered lexicographically (x fastest) */
+  double ls_normal[3];    /* UF_LS_PLANE: normal (any length > 0; entries >= dim ignored) */
+  double ls_offset;       /* UF_LS_PLANE: the domain is ls_normal . x < ls_offset */
 } uf_params;
 
 /* Sizes and algorithmic traffic of an operator (uf_get_info). */

@@ -14,6 +14,7 @@ from . import build as _build
 UF_OK, UF_EINVAL, UF_ENOMEM, UF_ECUDA, UF_EUNSUPPORTED, UF_EGEOMETRY, UF_ENODEVICE = range(7)
 UF_FP64, UF_FP32 = 1, 2
 UF_LS_SPHERE = 0
+UF_LS_PLANE = 1
 UF_DG, UF_CG = 0, 1
 
 _STATUS = {0: "UF_OK", 1: "UF_EINVAL", 2: "UF_ENOMEM", 3: "UF_ECUDA", 4: "UF_EUNSUPPORTED",
@@ -45,6 +46,8 @@ class uf_params(ctypes.Structure):
         ("device", ctypes.c_int),
         ("kappa", ctypes.POINTER(ctypes.c_double)),
         ("discretization", ctypes.c_int),
+        ("ls_normal", ctypes.c_double * 3),
+        ("ls_offset", ctypes.c_double),
     ]
 
 
@@ -154,6 +157,11 @@ def make_params(cfg, precisions=UF_FP64 | UF_FP32, device=0, kappa=None):
         p.ls_center[a] = float(cfg["center"][a]) if a < len(cfg["center"]) else 0.0
     p.ls_kind = UF_LS_SPHERE
     p.ls_radius = float(cfg["radius"])
+    if cfg.get("ls_kind", "sphere") == "plane":
+        p.ls_kind = UF_LS_PLANE
+        for a in range(3):
+            p.ls_normal[a] = float(cfg["normal"][a]) if a < len(cfg["normal"]) else 0.0
+        p.ls_offset = float(cfg["offset"])
     p.quad_order = int(cfg["quad_order"])
     p.sipg_gamma = float(cfg["sipg_gamma"])
     p.nitsche_gamma = float(cfg["nitsche_gamma"])

@@ -64,6 +64,9 @@ struct HostOperator {
   double h = 0;
   double center[kMaxDim] = {0, 0, 0};
   double radius = 0;
+  int ls_kind = 0;                      // UF_LS_SPHERE or UF_LS_PLANE
+  double normal[kMaxDim] = {0, 0, 0};   // plane: phi = normal . x - offset
+  double offset = 0;
 
   Tables1D t;
 

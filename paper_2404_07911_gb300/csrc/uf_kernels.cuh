@@ -125,7 +125,6 @@ __device__ __forceinline__ uint32_t bit_gp(int f) { return 1u << (3 + 3 * f); }
 // threads, and the shared memory of the cells (u, W per axis, per-cell matrices) under 40 KB.
 template <typename T, int DIM, int N>
 __host__ __device__ constexpr int struct_cells_per_block() {
-  constexpr int ND = (DIM == 2) ? N * N : N * N * N;
   constexpr int NL = (DIM == 2) ? N : N * N;
   constexpr int by_threads = (NL >= 128) ? 1 : (128 / NL);
   constexpr int SND = (DIM == 2) ? (N | 1) * N : (N | 1) * N * N;

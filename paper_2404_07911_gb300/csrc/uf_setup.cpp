@@ -416,6 +416,199 @@ void sphere_box_rules(const Box &b, const double *c, double rho, const Gauss1 &g
   }
 }
 
+// ------------------------------------------------------------------------------------------
+// Dimension-reduction quadrature for a plane psi = n . x - off
+// ------------------------------------------------------------------------------------------
+// psi is monotone along every direction with n_k != 0, so no bisection is needed: the height
+// direction maximises |n_k| (first index on ties), the restriction of psi to x_k = v is linear
+// again (n without k, off - n_k v), the root on the line through x' is (off - s) / n_k with
+// s = sum_{a != k} n_a x'_a, and a surface point has weight w' |n| / |n_k| and normal n / |n|.
+
+struct LinFn {
+  double n[kMaxDim];
+  double off;
+};
+
+// minimum and maximum of n . x - off over the closed box
+void lin_range(const double *n, double off, const Box &b, double &mn, double &mx) {
+  mn = 0.0;
+  mx = 0.0;
+  for (int a = 0; a < b.m; ++a) {
+    if (n[a] >= 0.0) {
+      mn += n[a] * b.lo[a];
+      mx += n[a] * b.hi[a];
+    } else {
+      mn += n[a] * b.hi[a];
+      mx += n[a] * b.lo[a];
+    }
+  }
+  mn -= off;
+  mx -= off;
+}
+
+int lin_height(const double *n, int m) {
+  int k = 0;
+  double best = -1.0;
+  for (int i = 0; i < m; ++i)
+    if (std::fabs(n[i]) > best) {
+      best = std::fabs(n[i]);
+      k = i;
+    }
+  return k;
+}
+
+// sum over a != k of n_a x'_a, with x' the m - 1 coordinates other than k
+double lin_sum_excl(const double *n, int m, int k, const double *xp) {
+  double s = 0.0;
+  for (int a = 0, j = 0; a < m; ++a)
+    if (a != k) s += n[a] * xp[j++];
+  return s;
+}
+
+void full_box_rule_lin(const Box &b, const std::vector<LinFn> &fns, const Gauss1 &g,
+                       std::vector<QPoint> &out) {
+  std::vector<LinFn> keep;
+  for (const LinFn &f : fns) {
+    double mn, mx;
+    lin_range(f.n, f.off, b, mn, mx);
+    if (!(mn >= 0.0 || mx <= 0.0)) keep.push_back(f);
+  }
+  if (keep.empty()) {
+    tensor_rule(b, g, out);
+    return;
+  }
+  const double *n = keep[0].n;  // kept functions are restrictions of one plane: same n
+  if (b.m == 1) {
+    double roots[16];
+    int nr = 0;
+    for (const LinFn &f : keep) {
+      const double t = f.off / f.n[0];
+      if (b.lo[0] < t && t < b.hi[0]) roots[nr++] = t;
+    }
+    double pa[16], pb[16];
+    const int np = make_pieces(b.lo[0], b.hi[0], roots, nr, pa, pb);
+    for (int ip = 0; ip < np; ++ip)
+      for (int i = 0; i < g.q; ++i) {
+        QPoint p{};
+        p.x[0] = pa[ip] + (pb[ip] - pa[ip]) * g.x[i];
+        p.w = (pb[ip] - pa[ip]) * g.w[i];
+        out.push_back(p);
+      }
+    return;
+  }
+  const int k = lin_height(n, b.m);
+  std::vector<LinFn> fns2;
+  for (const LinFn &f : keep) {
+    LinFn lo_f{}, hi_f{};
+    drop_vec(n, b.m, k, lo_f.n);
+    drop_vec(n, b.m, k, hi_f.n);
+    lo_f.off = f.off - n[k] * b.lo[k];
+    hi_f.off = f.off - n[k] * b.hi[k];
+    fns2.push_back(lo_f);
+    fns2.push_back(hi_f);
+  }
+  std::vector<QPoint> outer;
+  full_box_rule_lin(drop_dim(b, k), fns2, g, outer);
+  for (const QPoint &op : outer) {
+    const double s = lin_sum_excl(n, b.m, k, op.x);
+    double roots[16];
+    int nr = 0;
+    for (const LinFn &f : keep) {
+      const double t = (f.off - s) / n[k];
+      if (b.lo[k] < t && t < b.hi[k]) roots[nr++] = t;
+    }
+    double pa[16], pb[16];
+    const int np = make_pieces(b.lo[k], b.hi[k], roots, nr, pa, pb);
+    for (int ip = 0; ip < np; ++ip)
+      for (int i = 0; i < g.q; ++i) {
+        QPoint p{};
+        insert_coord(op.x, b.m, k, pa[ip] + (pb[ip] - pa[ip]) * g.x[i], p.x);
+        p.w = op.w * ((pb[ip] - pa[ip]) * g.w[i]);
+        out.push_back(p);
+      }
+  }
+}
+
+void plane_box_rules(const Box &b, const double *n, double off, const Gauss1 &g, bool surface,
+                     std::vector<QPoint> &vol, std::vector<QPoint> &surf,
+                     std::vector<QLine> *lines = nullptr) {
+  double mn, mx;
+  lin_range(n, off, b, mn, mx);
+  if (mx <= 0.0) {
+    tensor_rule(b, g, vol, lines);
+    return;
+  }
+  if (mn >= 0.0) return;
+  double nn = 0.0;
+  for (int a = 0; a < b.m; ++a) nn += n[a] * n[a];
+  nn = std::sqrt(nn);
+  if (b.m == 1) {
+    const double t = off / n[0];
+    double roots[1] = {t};
+    const bool has_root = b.lo[0] < t && t < b.hi[0];
+    double pa[4], pb[4];
+    const int np = make_pieces(b.lo[0], b.hi[0], roots, has_root ? 1 : 0, pa, pb);
+    const int64_t vbeg = (int64_t)vol.size();
+    for (int ip = 0; ip < np; ++ip) {
+      const double mid = 0.5 * (pa[ip] + pb[ip]);
+      if (n[0] * mid - off < 0.0)
+        for (int i = 0; i < g.q; ++i) {
+          QPoint p{};
+          p.x[0] = pa[ip] + (pb[ip] - pa[ip]) * g.x[i];
+          p.w = (pb[ip] - pa[ip]) * g.w[i];
+          vol.push_back(p);
+        }
+    }
+    if (lines && (int64_t)vol.size() > vbeg)
+      lines->push_back(QLine{0, vbeg, (int64_t)vol.size() - vbeg, -1});
+    if (surface && has_root) {
+      QPoint p{};
+      p.x[0] = t;
+      p.w = 1.0;
+      p.nrm[0] = n[0] > 0.0 ? 1.0 : -1.0;
+      surf.push_back(p);
+    }
+    return;
+  }
+  const int k = lin_height(n, b.m);
+  std::vector<LinFn> fns(2);
+  drop_vec(n, b.m, k, fns[0].n);
+  drop_vec(n, b.m, k, fns[1].n);
+  fns[0].off = off - n[k] * b.lo[k];
+  fns[1].off = off - n[k] * b.hi[k];
+  std::vector<QPoint> outer;
+  full_box_rule_lin(drop_dim(b, k), fns, g, outer);
+  for (const QPoint &op : outer) {
+    const double s = lin_sum_excl(n, b.m, k, op.x);
+    const double t = (off - s) / n[k];
+    const bool has_root = b.lo[k] < t && t < b.hi[k];
+    double roots[1] = {t};
+    double pa[4], pb[4];
+    const int np = make_pieces(b.lo[k], b.hi[k], roots, has_root ? 1 : 0, pa, pb);
+    const int64_t vbeg = (int64_t)vol.size();
+    const int64_t sidx = (surface && has_root) ? (int64_t)surf.size() : -1;
+    for (int ip = 0; ip < np; ++ip) {
+      const double mid = 0.5 * (pa[ip] + pb[ip]);
+      if ((s + n[k] * mid) - off < 0.0)
+        for (int i = 0; i < g.q; ++i) {
+          QPoint p{};
+          insert_coord(op.x, b.m, k, pa[ip] + (pb[ip] - pa[ip]) * g.x[i], p.x);
+          p.w = op.w * ((pb[ip] - pa[ip]) * g.w[i]);
+          vol.push_back(p);
+        }
+    }
+    if (surface && has_root) {
+      QPoint p{};
+      insert_coord(op.x, b.m, k, t, p.x);
+      for (int a = 0; a < b.m; ++a) p.nrm[a] = n[a] / nn;
+      p.w = op.w * (nn / std::fabs(n[k]));
+      surf.push_back(p);
+    }
+    if (lines && ((int64_t)vol.size() > vbeg || sidx >= 0))
+      lines->push_back(QLine{k, vbeg, (int64_t)vol.size() - vbeg, sidx});
+  }
+}
+
 }  // namespace
 
 void lagrange_values(const Tables1D &t, double x, double *val, double *der) {
@@ -486,13 +679,24 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
     msg = "gp_max_order must be in 0..degree";
     return UF_EINVAL;
   }
-  if (prm.ls_kind != UF_LS_SPHERE) {
-    msg = "only the sphere level set is supported";
+  if (prm.ls_kind != UF_LS_SPHERE && prm.ls_kind != UF_LS_PLANE) {
+    msg = "ls_kind must be UF_LS_SPHERE or UF_LS_PLANE";
     return UF_EUNSUPPORTED;
   }
-  if (!(prm.ls_radius > 0.0)) {
+  if (prm.ls_kind == UF_LS_SPHERE && !(prm.ls_radius > 0.0)) {
     msg = "ls_radius must be positive";
     return UF_EINVAL;
+  }
+  if (prm.ls_kind == UF_LS_PLANE) {
+    bool nonzero = false, finite = std::isfinite(prm.ls_offset);
+    for (int a = 0; a < d; ++a) {
+      finite = finite && std::isfinite(prm.ls_normal[a]);
+      if (prm.ls_normal[a] != 0.0) nonzero = true;
+    }
+    if (!nonzero || !finite) {
+      msg = "the plane needs a finite, non-zero ls_normal and a finite ls_offset";
+      return UF_EINVAL;
+    }
   }
   if (prm.discretization != UF_DG && prm.discretization != UF_CG) {
     msg = "discretization must be UF_DG or UF_CG";
@@ -515,6 +719,7 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
     op.N[a] = prm.n_cells[a];
     op.lo[a] = prm.lo[a];
     op.center[a] = prm.ls_center[a];
+    op.normal[a] = prm.ls_normal[a];
     hv[a] = (prm.hi[a] - prm.lo[a]) / (double)prm.n_cells[a];
     total *= op.N[a];
   }
@@ -533,10 +738,22 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
   }
   op.h = hv[0];
   op.radius = prm.ls_radius;
+  op.ls_kind = prm.ls_kind;
+  op.offset = prm.ls_offset;
+  // type of a closed box (d-dimensional, possibly a face): 0 inside, 1 cut, 2 outside
+  auto classify = [&](const Box &b) {
+    double lo_v, hi_v;
+    if (op.ls_kind == UF_LS_PLANE) {
+      lin_range(op.normal, op.offset, b, lo_v, hi_v);
+      return hi_v <= 0.0 ? 0 : (lo_v >= 0.0 ? 2 : 1);
+    }
+    box_dist2(op.center, b, lo_v, hi_v);
+    const double r2 = op.radius * op.radius;
+    return hi_v <= r2 ? 0 : (lo_v >= r2 ? 2 : 1);
+  };
   build_tables_1d(op.p, op.t);
 
   // ---- classification and numbering (x index fastest)
-  const double r2 = op.radius * op.radius;
   op.n_background = total;
   op.id_map.assign(total, -1);
   std::vector<int8_t> bg_type(total);
@@ -550,9 +767,7 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
       b.lo[a] = op.lo[a] + (double)I * hv[a];
       b.hi[a] = op.lo[a] + (double)(I + 1) * hv[a];
     }
-    double dmin2, dmax2;
-    box_dist2(op.center, b, dmin2, dmax2);
-    bg_type[flat] = dmax2 <= r2 ? 0 : (dmin2 >= r2 ? 2 : 1);
+    bg_type[flat] = (int8_t)classify(b);
   }
   for (int64_t flat = 0; flat < total; ++flat) {
     if (bg_type[flat] == 2) continue;
@@ -622,10 +837,7 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
         const int f = 2 * axis + side;
         op.nbr[e * nf + f] = nb;
         const int64_t e_minus = side ? e : nb;
-        Box fb = face_box(e_minus, axis);
-        double dmin2, dmax2;
-        box_dist2(op.center, fb, dmin2, dmax2);
-        const int ftype = dmax2 <= r2 ? 0 : (dmin2 >= r2 ? 2 : 1);  // full, cut, empty
+        const int ftype = classify(face_box(e_minus, axis));  // full, cut, empty
         const bool gp = use_gp && (op.act_type[e] == 1 || op.act_type[nb] == 1);
         // the continuous space has no SIPG term
         if (ftype == 0 && !op.cg) op.flags[e] |= face_bit_sipg_full(f);
@@ -669,7 +881,10 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
       vol.clear();
       surf.clear();
       lines.clear();
-      sphere_box_rules(b, op.center, op.radius * op.radius, g, 0, true, vol, surf, &lines);
+      if (op.ls_kind == UF_LS_PLANE)
+        plane_box_rules(b, op.normal, op.offset, g, true, vol, surf, &lines);
+      else
+        sphere_box_rules(b, op.center, op.radius * op.radius, g, 0, true, vol, surf, &lines);
       const int64_t vbase = (int64_t)op.vol_w.size(), sbase = (int64_t)op.surf_w.size();
       for (const QLine &ln : lines)
         op.vol_lines.push_back(QLine{ln.k, vbase + ln.vbeg, ln.vcnt, ln.sidx >= 0 ? sbase + ln.sidx : -1});
@@ -693,15 +908,21 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
           const int64_t e_minus = side ? e : op.nbr[e * nf + f];
           Box fb = face_box(e_minus, axis);
           const double xa = fb.lo[axis];
-          const double da = xa - op.center[axis];
-          const double rho = op.radius * op.radius - da * da;
           Box sub = drop_dim(fb, axis);
-          double csub[kMaxDim];
-          drop_vec(op.center, d, axis, csub);
           fq.clear();
           lines.clear();
           std::vector<QPoint> dummy;
-          sphere_box_rules(sub, csub, rho, g, 0, false, fq, dummy, &lines);
+          if (op.ls_kind == UF_LS_PLANE) {
+            double nsub[kMaxDim];
+            drop_vec(op.normal, d, axis, nsub);
+            plane_box_rules(sub, nsub, op.offset - op.normal[axis] * xa, g, false, fq, dummy, &lines);
+          } else {
+            const double da = xa - op.center[axis];
+            const double rho = op.radius * op.radius - da * da;
+            double csub[kMaxDim];
+            drop_vec(op.center, d, axis, csub);
+            sphere_box_rules(sub, csub, rho, g, 0, false, fq, dummy, &lines);
+          }
           const int64_t fbase = (int64_t)op.cface_w.size();
           for (const QLine &ln : lines) op.face_lines.push_back(QLine{ln.k, fbase + ln.vbeg, ln.vcnt, -1});
           Box sb = drop_dim(b, axis);

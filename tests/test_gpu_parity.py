@@ -55,6 +55,12 @@ SMALL = {
     "3d_q4_6": workloads.small(p=4, N=6),
     "3d_q3_center_on_grid": workloads.small(p=3, N=6, center=(0.0, 0.0, 0.0)),
     "3d_q6_4": workloads.small(p=6, N=4),
+    # half-spaces below tilted planes (the plane benchmark's geometry)
+    "2d_plane_q2_7": workloads.plane(p=2, N=7, dim=2),
+    "3d_plane_q1_6": workloads.plane(p=1, N=6, dim=3),
+    "3d_plane_q3_5_steep": workloads.plane(p=3, N=5, dim=3, normal=(0.2, -0.3, 0.9), offset_cells=1.55),
+    "3d_plane_q2_4_one_layer": workloads.plane(p=2, N=4, dim=3, layers=1, offset_cells=0.25,
+                                               normal=(-0.075, -0.05, 1.0)),
 }
 
 

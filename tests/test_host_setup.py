@@ -14,6 +14,10 @@ CASES = {
     "2d_q4": workloads.small(p=4, N=12, dim=2),
     "3d_q3_8": workloads.small(p=3, N=8),
     "3d_q2_center_on_grid": workloads.small(p=2, N=10, center=(0.0, 0.0, 0.0)),
+    "2d_plane_q2": workloads.plane(p=2, N=7, dim=2),
+    "3d_plane_q2": workloads.plane(p=2, N=5, dim=3),
+    "3d_plane_steep_q3": workloads.plane(p=3, N=5, dim=3, normal=(0.2, -0.3, 0.9), offset_cells=1.55),
+    "3d_plane_on_axis_q1": workloads.plane(p=1, N=4, dim=3, normal=(0.0, 0.0, 1.0), offset_cells=2.5),
 }
 
 
