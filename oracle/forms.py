@@ -294,13 +294,33 @@ class Oracle:
         return (P.T @ self.assemble() @ P).tocsr()
 
     def load_vector(self, f=1.0):
-        """b_l = int_{K cap Omega} f phi_l for every cell-local DoF (constant f)."""
+        """b_l = int_{K cap Omega} f phi_l for every cell-local DoF; f is a constant or a function
+        of the points (array [m, d] -> [m])."""
         out = np.zeros((self.mesh.n_active, self.ndof))
         for e in range(self.mesh.n_active):
             vx, vw, _, _, _ = self.cell_quadrature(e)
             if len(vw):
-                out[e] = f * (vw @ self.basis_at(e, vx))
+                fv = f(vx) if callable(f) else f
+                out[e] = (vw * fv) @ self.basis_at(e, vx)
         return out.reshape(-1)
+
+    def l2_error(self, x, u):
+        """(||u_h - u||_{L2(Omega)}, ||u||_{L2(Omega)}) for the discrete function with DoF values
+        x (cell-local for "dg", global for "cg") and the function u of the points, on the cell
+        quadrature of every active cell."""
+        xl = self.cg_prolongation() @ x if self.discretization == "cg" else np.asarray(x)
+        xl = xl.reshape(self.mesh.n_active, self.ndof)
+        err2 = 0.0
+        nrm2 = 0.0
+        for e in range(self.mesh.n_active):
+            vx, vw, _, _, _ = self.cell_quadrature(e)
+            if not len(vw):
+                continue
+            uh = self.basis_at(e, vx) @ xl[e]
+            ue = u(vx)
+            err2 += vw @ ((uh - ue) ** 2)
+            nrm2 += vw @ (ue ** 2)
+        return math.sqrt(err2), math.sqrt(nrm2)
 
     def cg_load_vector(self, f=1.0):
         return self.cg_prolongation().T @ self.load_vector(f)

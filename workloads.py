@@ -105,6 +105,16 @@ def x_and_b(n, seed=5):
     return rng.uniform(-1.0, 1.0, n), rng.uniform(-1.0, 1.0, n)
 
 
+def accuracy(p, N, dim=3):
+    """Sphere accuracy benchmark (paper Sec. 4): unit ball at the origin in the background box
+    [-1.035, 1.035]^d with N cells per direction, q = p + 1, penalties as for the ball workloads;
+    the right-hand side and exact solution are the manufactured pair of that section."""
+    pad = (0.0,) * (3 - dim)
+    return dict(name=f"{dim}d_q{p}_{N}_accuracy", dim=dim, degree=p, n_cells=(N,) * dim + (1,) * (3 - dim),
+                lo=(-1.035,) * dim + pad, hi=(1.035,) * dim + pad, center=(0.0, 0.0, 0.0), radius=1.0,
+                quad_order=p + 1, seed=0, **_penalties(p))
+
+
 PLANE_NORMAL = (-0.04, -0.03, 1.0)
 
 
