@@ -59,11 +59,13 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-csr", action="store_true",
                     help="skip the assembled-matrix (CSR SpMV) comparison")
-    ap.add_argument("--config", choices=("q3", "solve", "sweep", "kappa", "plane"), default="q3",
+    ap.add_argument("--config", choices=("q3", "solve", "sweep", "kappa", "plane", "accuracy"),
+                    default="q3",
                     help="q3: the headline step (default); solve: CG Q4 time to solution, IR vs "
                          "FP64; sweep: degree sweep p = 1..8 at ~2e7 DoFs; kappa: forward vs "
                          "forward + backward of the differentiable operator; plane: throughput "
-                         "against the ratio of cut cells (DG Q1, CG Q3)")
+                         "against the ratio of cut cells (DG Q1, CG Q3); accuracy: convergence of "
+                         "the sphere accuracy benchmark (CG, DG, p = 1..4)")
     return ap.parse_args()
 
 
@@ -490,6 +492,38 @@ def run_plane(args, local):
             del x64, x32, y64, y32
 
 
+def run_accuracy(args, local):
+    """Sphere accuracy benchmark: the manufactured problem (omega = 2 pi) solved with Jacobi-PCG
+    in FP64 on refined grids, relative L2 error and observed order, CG and DG, p = 1..4."""
+    import torch
+
+    from paper_2404_07911_gb300 import UF_FP64, UnfittedOperator
+
+    torch.cuda.set_device(local)
+    omega = 2.0 * np.pi
+    levels = {1: (12, 24, 48, 96), 2: (12, 24, 48, 96), 3: (12, 24, 48), 4: (12, 24, 48)}
+    for disc in ("cg", "dg"):
+        for p in (1, 2, 3, 4):
+            prev = None
+            for N in levels[p]:
+                cfg = dict(workloads.accuracy(p, N), discretization=disc)
+                op = UnfittedOperator(cfg, precisions=UF_FP64, device=local)
+                b = torch.from_numpy(op.manufactured_rhs(omega)).cuda()
+                x, st = op.solve(b, mode="fp64", tol=1e-13, max_iter=400000, max_outer=20)
+                err, nrm = op.l2_error(omega, x.cpu().numpy())
+                rel = err / nrm
+                rate = None if prev is None else round(float(np.log2(prev / rel)), 3)
+                prev = rel
+                print(json.dumps({
+                    "metric": "sphere accuracy benchmark: relative L2 error of the PCG solution",
+                    "discretization": disc, "degree": p, "N": N, "h_over_L": round(2.07 / N, 6),
+                    "n_dofs": op.n_dofs, "rel_l2_error": rel, "observed_order": rate,
+                    "solver": {k: st[k] for k in ("converged", "outer", "iterations", "rel_residual",
+                                                  "seconds")},
+                    "omega": omega}), flush=True)
+                op.close()
+
+
 def run_solve(args, local):
     """CG Q4 ball solve: FP32 PCG inside FP64 refinement vs all-FP64 PCG, same final residual."""
     import torch
@@ -668,6 +702,8 @@ def main():
         run_kappa(args, local)
     elif args.config == "plane":
         run_plane(args, local)
+    elif args.config == "accuracy":
+        run_accuracy(args, local)
     else:
         run_ours(args, rank, world, local)
 

@@ -104,6 +104,9 @@ typedef struct {
   /* Groups of volume lines (3D): lines of a cut cell along one axis that share one outer
    * coordinate; the cut-cell kernel contracts along that coordinate once per group. */
   int64_t n_vol_groups;
+  /* Lanes of a warp that work on one cut cell in the cut-cell kernel (32, 16 or 8; several cut
+   * cells share a warp when their rules have few lines), chosen at creation. */
+  int32_t cut_lanes;
 } uf_info;
 
 /* Per-kernel device times collected between uf_profile_begin and uf_profile_end, indexed
@@ -237,8 +240,11 @@ uf_status uf_export_cut_face_rule(const uf_operator *op, int64_t e, int axis, in
  * FP64.  Any pointer may be NULL.  Errors: UF_EINVAL (NULL op, not a UF_CG operator). */
 uf_status uf_export_cg(const uf_operator *op, int32_t *l2g, double *rhs, double *diag);
 
-/* Solve A x = b for a continuous (UF_CG) operator with Jacobi-preconditioned CG (the solver of
- * the paper's Sec. 3.5 is a PCG; its multigrid preconditioner is out of scope):
+/* Solve A x = b with Jacobi-preconditioned CG (the solver of the paper's Sec. 3.5 is a PCG; its
+ * multigrid preconditioner is out of scope), for a continuous (UF_CG) or a discontinuous (UF_DG)
+ * operator.  The Jacobi diagonal is computed on the host in FP64 (for UF_DG, and the work
+ * vectors with it, on the first call: that call allocates device memory) and follows
+ * uf_set_kappa, not uf_set_kappa_device:
  *   UF_SOLVE_FP64  PCG in FP64 on the correction of the initial guess until
  *                  ||b - A x|| <= tol ||b||, restarted from the true FP64 residual while the
  *                  recursive residual of the PCG has drifted below it (outer counts the runs);
@@ -251,8 +257,8 @@ uf_status uf_export_cg(const uf_operator *op, int32_t *l2g, double *rhs, double 
  * device memory; the host reads the stopping state once per 32 iterations, so up to 31 operator
  * applications run past the stop (their updates are skipped).  max_iter caps the CG iterations
  * (all inner iterations in IR mode), max_outer the refinement steps / restarts.
- * Work vectors are allocated at creation; no allocation here.  Errors: UF_EINVAL (not a UF_CG
- * operator, missing precision, bad parameters, breakdown), UF_ENODEVICE, UF_ECUDA. */
+ * UF_CG: work vectors are allocated at creation; UF_DG: on the first call.  Errors: UF_EINVAL
+ * (missing precision, bad parameters, breakdown), UF_ENOMEM, UF_ENODEVICE, UF_ECUDA. */
 enum { UF_SOLVE_FP64 = 0, UF_SOLVE_IR = 1 };
 typedef struct {
   int mode;
@@ -268,6 +274,20 @@ typedef struct {
 } uf_solve_stats;
 uf_status uf_solve(uf_operator *op, const uf_solve_params *params, double *x, const double *b,
                    uf_solve_stats *stats, void *stream);
+
+/* Sphere accuracy benchmark (paper Sec. 4).  On the operator's ball (radius R = ls_radius around
+ * ls_center), with r = |x - ls_center| and d = dim,
+ *   u(r) = cos(omega R) - cos(omega r),   f(r) = -omega^2 (cos(omega r) + (d - 1) sin(omega r) / (omega r)),
+ * solve -Lap u = f with u = 0 on the sphere (the Dirichlet data g = 0 of the Nitsche terms).
+ * uf_manufactured_rhs writes b_i = int_Omega f phi_i (host FP64 [n_dofs]); uf_l2_error returns
+ * ||u_h - u||_L2(Omega) and ||u||_L2(Omega) for the discrete function with DoF values x (host FP64
+ * [n_dofs]).  Both integrate on the operator's own quadrature (tensor Gauss with p + 1 points per
+ * direction on inside cells, the cut-cell rules on cut cells), in FP64 on the host; they are
+ * set-up and post-processing of the accuracy study, not part of the operator's evaluation.
+ * Errors: UF_EINVAL (NULL, non-finite omega), UF_EUNSUPPORTED (not a sphere level set). */
+uf_status uf_manufactured_rhs(const uf_operator *op, double omega, double *b);
+uf_status uf_l2_error(const uf_operator *op, double omega, const double *x, double *err,
+                      double *norm);
 
 /* Release every host and device resource of op.  NULL is accepted (no-op).  The caller must
  * make sure no stream still runs work of op. */

@@ -61,7 +61,8 @@ class uf_info(ctypes.Structure):
         ("bytes_fp32", ctypes.c_double), ("flops", ctypes.c_double),
         ("kernel_bytes_fp64", ctypes.c_double * 2), ("kernel_bytes_fp32", ctypes.c_double * 2),
         ("kernel_flops", ctypes.c_double * 2), ("kernel_flops_built", ctypes.c_double * 2),
-        ("kernel_flops_built_fp32", ctypes.c_double * 2), ("n_vol_groups", ctypes.c_int64)]
+        ("kernel_flops_built_fp32", ctypes.c_double * 2), ("n_vol_groups", ctypes.c_int64),
+        ("cut_lanes", ctypes.c_int32)]
 
 
 class uf_kernel_times(ctypes.Structure):
@@ -85,7 +86,7 @@ EXPORTED = ["uf_create_unfitted_operator", "uf_get_info", "uf_vmult", "uf_vmult_
             "uf_set_kappa", "uf_export_cells", "uf_export_cut_cell_rule",
             "uf_export_cut_face_rule", "uf_assemble_csr", "uf_csr_info", "uf_csr_spmv",
             "uf_export_csr", "uf_release_csr", "uf_kappa_gradient", "uf_kappa_gradient_noalloc",
-            "uf_set_kappa_device", "uf_export_cg", "uf_solve",
+            "uf_set_kappa_device", "uf_export_cg", "uf_solve", "uf_manufactured_rhs", "uf_l2_error",
             "uf_destroy", "uf_last_error"]
 
 _lib = None
@@ -128,6 +129,9 @@ def load_library(path=None):
     lib.uf_set_kappa_device.argtypes = [P, P, P]
     lib.uf_export_cg.argtypes = [P, P, P, P]
     lib.uf_solve.argtypes = [P, ctypes.POINTER(uf_solve_params), P, P, ctypes.POINTER(uf_solve_stats), P]
+    lib.uf_manufactured_rhs.argtypes = [P, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    lib.uf_l2_error.argtypes = [P, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     lib.uf_destroy.argtypes = [P]
     lib.uf_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -363,7 +367,8 @@ class UnfittedOperator:
 
     def solve(self, b, x=None, mode="ir", tol=1e-10, inner_tol=1e-4, max_iter=100000,
               max_outer=50, stream=None):
-        """Solve A x = b (continuous operators); b, x float64 CUDA tensors.  Returns (x, stats)."""
+        """Solve A x = b with Jacobi-PCG (FP64, or FP32 inside FP64 refinement); b, x float64
+        CUDA tensors.  Returns (x, stats)."""
         import torch
 
         if x is None:
@@ -375,6 +380,25 @@ class UnfittedOperator:
                              ctypes.c_void_p(b.contiguous().data_ptr()), ctypes.byref(st),
                              self._stream_ptr(stream)))
         return x, {name: getattr(st, name) for name, _ in uf_solve_stats._fields_}
+
+    def manufactured_rhs(self, omega):
+        """Load vector of the sphere accuracy benchmark's right-hand side (host float64)."""
+        b = np.zeros(self.n_dofs)
+        _check(_lib.uf_manufactured_rhs(self._h, float(omega),
+                                        b.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return b
+
+    def l2_error(self, omega, x):
+        """(||u_h - u||_L2, ||u||_L2) of the discrete function x (host float64) against the
+        benchmark's exact solution."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        if x.shape != (self.n_dofs,):
+            raise ValueError("x must have n_dofs entries")
+        err = ctypes.c_double()
+        nrm = ctypes.c_double()
+        _check(_lib.uf_l2_error(self._h, float(omega), x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                ctypes.byref(err), ctypes.byref(nrm)))
+        return err.value, nrm.value
 
     def export_cg(self):
         """(l2g[n_active, n^d], rhs[n_dofs], diag[n_dofs]) of a continuous operator."""

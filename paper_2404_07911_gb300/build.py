@@ -13,7 +13,8 @@ LIB = os.path.join(HERE, "libunfitted.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["uf_kernels_f64.cu", "uf_kernels_f32.cu", "uf_api.cu", "uf_csr.cu", "uf_kgrad.cu", "uf_cg.cu"]
+CU_SOURCES = ["uf_kernels_f64.cu", "uf_kernels_f32.cu", "uf_api.cu", "uf_csr.cu", "uf_kgrad.cu", "uf_cg.cu",
+              "uf_accuracy.cu"]
 CPP_SOURCES = ["uf_setup.cpp"]
 
 

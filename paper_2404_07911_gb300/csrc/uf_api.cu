@@ -490,6 +490,11 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   A.kappa_uniform = kappa_is_uniform(H.kappa) ? 1 : 0;
   A.n_active = (int32_t)na;
   A.n_cut = (int32_t)nc;
+  {
+    // lanes per cut cell from the average number of volume and cut-face lines of a cut cell
+    const double vl = nc ? (double)nvl / (double)nc : 0.0, fl = nc ? (double)nfl / (double)nc : 0.0;
+    A.cut_lanes = uf::cut_lanes_for(n, vl > fl ? vl : fl);
+  }
   pd.n_vlines = nvl;
   pd.n_flines = nfl;
 
@@ -684,6 +689,12 @@ uf_status uf_get_info(const uf_operator *op, uf_info *info) {
   info->n_vol_lines = (int64_t)H.vol_lines.size();
   info->n_face_lines = (int64_t)H.face_lines.size();
   info->n_vol_groups = count_line_groups(H);
+  {
+    const double nc = (double)H.n_cut;
+    const double vl = nc > 0 ? (double)H.vol_lines.size() / nc : 0.0;
+    const double fl = nc > 0 ? (double)H.face_lines.size() / nc : 0.0;
+    info->cut_lanes = uf::cut_lanes_for(H.n, vl > fl ? vl : fl);
+  }
   info->dim = H.dim;
   info->degree = H.p;
   info->dofs_per_cell = H.ndof;
@@ -891,6 +902,7 @@ uf_status uf_set_kappa(uf_operator *op, const double *kappa_host) {
       return fail(UF_EINVAL, "kappa must be positive and finite");
   std::copy(kappa_host, kappa_host + op->host.n_active, op->host.kappa.begin());
   if (op->host.cg) uf::cg_host_vectors(op->host);
+  if (!op->host.cg && op->cgs.ready) uf::dg_host_diagonal(op->host);
   const int32_t uni = kappa_is_uniform(op->host.kappa) ? 1 : 0;
   op->f64.arrays.kappa_uniform = uni;
   op->f32.arrays.kappa_uniform = uni;
@@ -906,7 +918,7 @@ uf_status uf_set_kappa(uf_operator *op, const double *kappa_host) {
     cudaError_t err = cudaMemcpy(op->f32.kappa_dev, k32.data(), sizeof(float) * na, cudaMemcpyHostToDevice);
     if (err != cudaSuccess) return fail(UF_ECUDA, cudaGetErrorString(err));
   }
-  if (op->host.cg && op->cgs.ready) return uf::cg_upload_diag(op);
+  if (op->cgs.ready) return uf::cg_upload_diag(op);
   return UF_OK;
 }
 

@@ -22,7 +22,12 @@ namespace uf {
 // ------------------------------------------------------------------------------------------
 // Host: load vector (f = 1) and diagonal of A, FP64
 // ------------------------------------------------------------------------------------------
-void cg_host_vectors(HostOperator &op) {
+// Cell-local load vector (f = 1) and diagonal of the cell-local operator of every active cell.
+// discontinuous = false: the continuous space, where the couplings across a face act on the shared
+// face nodes (they enter the diagonal); true: the discontinuous space, whose diagonal carries the
+// SIPG self terms of full and cut faces and no neighbour coupling.
+void local_vectors(const HostOperator &op, bool discontinuous, std::vector<double> &bloc,
+                   std::vector<double> &dloc) {
   const int d = op.dim, n = op.n, nd = op.ndof, nf = 2 * d, nn = n * n;
   const Tables1D &t = op.t;
   const double h = op.h;
@@ -39,7 +44,8 @@ void cg_host_vectors(HostOperator &op) {
       wi[i] += t.gauss_w[q] * v[i];
     }
   const double hd = std::pow(h, d);
-  std::vector<double> bloc((size_t)op.n_active * nd, 0.0), dloc((size_t)op.n_active * nd, 0.0);
+  bloc.assign((size_t)op.n_active * nd, 0.0);
+  dloc.assign((size_t)op.n_active * nd, 0.0);
   auto idx3 = [&](int l, int *ia) {
     for (int a = 0; a < 3; ++a) {
       ia[a] = (a < d) ? l % n : 0;
@@ -84,8 +90,9 @@ void cg_host_vectors(HostOperator &op) {
         for (int bb = 0; bb < d; ++bb)
           if (bb != a) mm *= M[ia[bb] * n + ia[bb]];
         acc += Lself[a][ia[a] * n + ia[a]] * mm;
-        for (int s = 0; s < 2; ++s)
-          if (ia[a] == (s ? n - 1 : 0)) acc += cross[a][s] * mm;
+        if (!discontinuous)
+          for (int s = 0; s < 2; ++s)
+            if (ia[a] == (s ? n - 1 : 0)) acc += cross[a][s] * mm;
       }
       dg[l] = acc;
       if (inside) {
@@ -151,7 +158,47 @@ void cg_host_vectors(HostOperator &op) {
             }
       }
     }
+    if (!discontinuous) continue;
+    // ---- SIPG on the cut faces of a cut cell (own-own terms): at a face point only the DoFs on
+    // the own face-node layer are non-zero; with sgn = +1 on the upper face (own cell K^-) and
+    // -1 on the lower one, a(phi, phi) += w (-sgn kappa_K d_axis phi phi + sigma/h {kappa} phi^2)
+    for (int f = 0; f < nf; ++f) {
+      if (!(fl & face_bit_sipg_cut(f))) continue;
+      const int axis = f / 2, side = f % 2;
+      const int nb = op.nbr[e * nf + f];
+      const double kavg = 0.5 * (kap + op.kappa[nb]);
+      const double sgn = side ? 1.0 : -1.0, sig = op.params.sipg_gamma / h;
+      const int end = side ? n - 1 : 0;
+      const double dend = t.deriv_end[side][1][end] / h;
+      int oa[2] = {0, 0}, no = 0;
+      for (int a = 0; a < d; ++a)
+        if (a != axis) oa[no++] = a;
+      for (int64_t p = op.cface_off[c * nf + f]; p < op.cface_off[c * nf + f + 1]; ++p) {
+        double V[2][kMaxN], Dv[kMaxN];
+        for (int j = 0; j < no; ++j) lagrange_values(t, op.cface_eta[j][p], V[j], Dv);
+        const double w = op.cface_w[p];
+        for (int l = 0; l < nd; ++l) {
+          int ia[3];
+          idx3(l, ia);
+          if (ia[axis] != end) continue;
+          double prod = 1.0;
+          for (int j = 0; j < no; ++j) prod *= V[j][ia[oa[j]]];
+          const double phi = prod, dphi = dend * prod;
+          dg[l] += w * (-sgn * kap * dphi * phi + sig * kavg * phi * phi);
+        }
+      }
+    }
   }
+}
+
+void dg_host_diagonal(HostOperator &op) {
+  std::vector<double> bloc;
+  local_vectors(op, true, bloc, op.dg_diag);
+}
+
+void cg_host_vectors(HostOperator &op) {
+  std::vector<double> bloc, dloc;
+  local_vectors(op, false, bloc, dloc);
   op.cg_rhs.assign(op.n_cg, 0.0);
   op.cg_diag.assign(op.n_cg, 0.0);
   for (int64_t g = 0; g < op.n_cg; ++g)
@@ -528,14 +575,24 @@ extern "C" uf_status uf_solve(uf_operator *op, const uf_solve_params *prm, doubl
                               uf_solve_stats *stats, void *stream) {
   if (!op || !prm || !x || !b || !stats) return fail(UF_EINVAL, "NULL argument");
   if (op->device < 0) return fail(UF_ENODEVICE, "operator was created host-only");
-  if (!op->host.cg || !op->cgs.ready) return fail(UF_EINVAL, "uf_solve needs a continuous (UF_CG) operator");
+  if (!op->host.cg && !op->cgs.ready) {
+    // discontinuous operators: Jacobi diagonal and work vectors on the first solve
+    uf::DeviceGuard g0(op->device);
+    uf::dg_host_diagonal(op->host);
+    const uf_status st0 = uf::cg_alloc(op);
+    if (st0 != UF_OK) {
+      uf::cg_free(op);
+      return st0;
+    }
+  }
+  if (!op->cgs.ready) return fail(UF_EINVAL, "the solver's work vectors are missing");
   if (prm->mode != UF_SOLVE_FP64 && prm->mode != UF_SOLVE_IR) return fail(UF_EINVAL, "bad solve mode");
   if (prm->mode == UF_SOLVE_IR && !op->f32.present) return fail(UF_EINVAL, "IR needs the FP32 operator");
   if (!op->f64.present) return fail(UF_EINVAL, "uf_solve needs the FP64 operator");
   if (!(prm->tol > 0.0) || prm->max_iter < 1) return fail(UF_EINVAL, "bad tolerance or iteration cap");
   uf::DeviceGuard guard(op->device);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const int64_t n = op->host.n_cg;
+  const int64_t n = uf::solve_size(op->host);
   uf::CgSolveData &w = op->cgs;
   uf::SolveCtx c{op, s, n, w.dot_part, w.dot_out, w.dot_host, w.sc, w.sc_host};
   std::memset(stats, 0, sizeof(*stats));
@@ -608,9 +665,11 @@ extern "C" uf_status uf_solve(uf_operator *op, const uf_solve_params *prm, doubl
 
 namespace uf {
 
+int64_t solve_size(const HostOperator &h) { return h.cg ? h.n_cg : h.n_active * h.ndof; }
+
 uf_status cg_alloc(uf_operator *op) {
   CgSolveData &w = op->cgs;
-  const int64_t n = op->host.n_cg;
+  const int64_t n = solve_size(op->host);
   cudaError_t err = cudaSuccess;
   auto A = [&](void **p, size_t bytes) {
     if (err == cudaSuccess) err = cudaMalloc(p, bytes);
@@ -642,9 +701,10 @@ uf_status cg_alloc(uf_operator *op) {
 
 uf_status cg_upload_diag(uf_operator *op) {
   CgSolveData &w = op->cgs;
-  const int64_t n = op->host.n_cg;
+  const int64_t n = solve_size(op->host);
+  const std::vector<double> &diag = op->host.cg ? op->host.cg_diag : op->host.dg_diag;
   std::vector<double> inv(n);
-  for (int64_t i = 0; i < n; ++i) inv[i] = 1.0 / op->host.cg_diag[i];
+  for (int64_t i = 0; i < n; ++i) inv[i] = 1.0 / diag[i];
   cudaError_t err = cudaSuccess;
   if (w.invd64) err = cudaMemcpy(w.invd64, inv.data(), n * 8, cudaMemcpyHostToDevice);
   if (err == cudaSuccess && w.invd32) {

@@ -99,7 +99,15 @@ struct DevArrays {
   const T *vline_b, *vpt_b, *spt_b, *fline_b, *fpt_b;
   int32_t kappa_uniform;
   int32_t n_active, n_cut;
+  int32_t cut_lanes;  // lanes per cut cell in the cut-cell kernel: 32, 16 or 8
 };
+
+// Lanes per cut cell in the cut-cell kernel for an operator whose cut cells carry on average
+// `lines` volume or cut-face lines (the larger of the two): groups of 8 or 16 lanes (several cut
+// cells per warp) only for n <= 5, whose rules have few lines per cell.
+inline int cut_lanes_for(int n, double lines) {
+  return (n > 5 || lines > 20.0) ? 32 : (lines > 10.0 ? 16 : 8);
+}
 
 // Launchers (uf_kernels_*.cu).  Return cudaError_t as int.
 // ev: optional events recorded around the structured kernel (ev[0], ev[1]) and the cut-cell

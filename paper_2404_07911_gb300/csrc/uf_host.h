@@ -105,6 +105,7 @@ struct HostOperator {
   std::vector<int32_t> cg_own_off;        // [n_cg + 1]
   std::vector<int32_t> cg_own_idx;        // [n_active * n^d]
   std::vector<double> cg_rhs, cg_diag;    // [n_cg]
+  std::vector<double> dg_diag;            // DG: diagonal of A [n_active * ndof], built on demand
 
   // counts
   int64_t n_faces = 0, n_faces_full = 0, n_faces_cut = 0, n_faces_empty = 0, n_faces_gp = 0;

@@ -459,17 +459,15 @@ __device__ __forceinline__ void point_basis(const PointTables<T, N> &pt, const T
   }
 }
 
-// Lines per chunk (= threads per CTA = one warp) of the cut-cell kernel, and the most line
-// groups one chunk of the 3D volume part holds (a chunk ends early at the next group start once
+// The cut-cell kernel runs one warp per CTA; each cut cell is handled by a group of S lanes
+// (S = 32, 16 or 8: the CTA then holds 32 / S cells), and S lines form a chunk.  A chunk of the
+// 3D volume part holds at most cut_gmax line groups (it ends early at the next group start once
 // it has that many; the per-group partial contractions take GMAX n^2 values each).
-template <int N>
-__host__ __device__ constexpr int cut_chunk() {
-  return 32;
-}
 template <int N>
 __host__ __device__ constexpr int cut_gmax() {
   return (N <= 5) ? 16 : 8;
 }
+
 
 // Other axes of a line along axis k (lower first) in 3D.
 __device__ __forceinline__ void other_axes(int k, int &b, int &c) {
@@ -480,11 +478,11 @@ __device__ __forceinline__ void other_axes(int k, int &b, int &c) {
 // Dynamic shared memory of the cut-cell kernel (offsets in elements of T, then ints).  The
 // volume phase and the cut-face phase run one after the other, so the per-group partial
 // contractions (3D), the per-line partial integrals (2D) and the face arrays share one region.
-template <typename T, int DIM, int N>
+template <typename T, int DIM, int N, int S>
 struct CutSmem {
   static constexpr int ND = Geo<DIM, N>::ND, NL = Geo<DIM, N>::NL, NF = Geo<DIM, N>::NF;
-  static constexpr int CH = cut_chunk<N>();
-  static constexpr int GMAX = cut_gmax<N>();
+  static constexpr int CH = S;
+  static constexpr int GMAX = cut_gmax<N>() < S ? cut_gmax<N>() : S;
   static constexpr int cmax(int a, int b) { return a > b ? a : b; }
   static constexpr int u = 0;                    // [ND] the cell's DoFs
   static constexpr int acc = u + ND;             // [ND] accumulated output rows
@@ -506,6 +504,7 @@ struct CutSmem {
   // each group [GMAX + 1], shared axis of each group [GMAX]
   static constexpr int itag = 0, ilgrp = CH, igline = 2 * CH, igax = 2 * CH + GMAX + 1;
   static constexpr size_t bytes = (size_t)total * sizeof(T) + (2 * CH + 2 * GMAX + 1) * sizeof(int);
+  static constexpr size_t stride = (bytes + 15) / 16 * 16;  // per cell in the CTA
 };
 
 // Volume (Poisson) and surface (Nitsche) points of a 3D cut cell (Eq. unstructured_cell), in a
@@ -520,16 +519,14 @@ struct CutSmem {
 //   C2 (per DoF)    acc += sum_groups phi_c Q0 + phi_c' Q1.
 // Per line this costs 6 n^2 FMA and per group 4 n^3, against 4 n^3 + 6 n^2 per line when
 // every line contracts both outer axes itself.
-template <typename T, int N>
+template <typename T, int N, int S>
 __device__ __forceinline__ void cut_volume_3d(const PointTables<T, N> &pt, const DevArrays<T> &d,
                                               const Scalars<T> &sc, unsigned char *smem_raw, int ci,
-                                              T kap) {
+                                              T kap, int tid, unsigned gmask, int gshift) {
   using G = Geo<3, N>;
-  using SM = CutSmem<T, 3, N>;
+  using SM = CutSmem<T, 3, N, S>;
   constexpr int ND = G::ND, NL = G::NL;
   constexpr int CH = SM::CH, GMAX = SM::GMAX;
-  constexpr unsigned kMask = 0xffffffffu;
-  static_assert(CH == 32, "one warp per cut cell");
   T *sm = reinterpret_cast<T *>(smem_raw);
   const T *s_u = sm + SM::u;
   T *s_acc = sm + SM::acc;
@@ -544,7 +541,6 @@ __device__ __forceinline__ void cut_volume_3d(const PointTables<T, N> &pt, const
   int *s_lgrp = s_ints + SM::ilgrp;
   int *s_gline = s_ints + SM::igline;
   int *s_gax = s_ints + SM::igax;
-  const int tid = threadIdx.x;
 
 #pragma unroll 1
   for (int k = 0; k < 3; ++k) {
@@ -563,9 +559,9 @@ __device__ __forceinline__ void cut_volume_3d(const PointTables<T, N> &pt, const
       // groups of this chunk (a group cut by the chunk boundary restarts at its first thread);
       // the chunk ends before the start of group GMAX
       const bool start0 = in_range && (tid == 0 || (gword >> 1) == line);
-      const unsigned starts0 = __ballot_sync(kMask, start0);
+      const unsigned starts0 = __ballot_sync(gmask, start0) >> gshift;  // bits of this group
       const int gl = __popc(starts0 & ((2u << tid) - 1u)) - 1;
-      const unsigned over = __ballot_sync(kMask, start0 && gl >= GMAX);
+      const unsigned over = __ballot_sync(gmask, start0 && gl >= GMAX) >> gshift;
       nl = over ? (__ffs(over) - 1) : min(CH, lend - l0);
       const bool act = tid < nl;
       const bool start = start0 && act;
@@ -592,7 +588,7 @@ __device__ __forceinline__ void cut_volume_3d(const PointTables<T, N> &pt, const
       }
       if (tid == 0) s_gline[ng] = nl;
       if (act) s_lgrp[tid] = gl;
-      __syncthreads();
+      __syncwarp(gmask);
       // A: contraction along the shared axis, per group; P[g][ib * N + m], ib along the
       // group's line axis, m along k
       for (int item = tid; item < ng * NL; item += CH) {
@@ -610,7 +606,7 @@ __device__ __forceinline__ void cut_volume_3d(const PointTables<T, N> &pt, const
         s_p0[g][r] = p0;
         s_p1[g][r] = p1;
       }
-      __syncthreads();
+      __syncwarp(gmask);
       // B: one thread per line
       if (act) {
         const int ab = shared_lo ? oc : ob;  // the line's own outer axis
@@ -708,7 +704,7 @@ __device__ __forceinline__ void cut_volume_3d(const PointTables<T, N> &pt, const
           s_db[tid][m] = db[m];
         }
       }
-      __syncthreads();
+      __syncwarp(gmask);
       // C1: sum over the lines of each group, Q[g][ib * N + m] (P is no longer read)
       for (int item = tid; item < ng * NL; item += CH) {
         const int g = item / NL, r = item % NL, ib = r / N, m = r % N;
@@ -720,7 +716,7 @@ __device__ __forceinline__ void cut_volume_3d(const PointTables<T, N> &pt, const
         s_p0[g][r] = q0;
         s_p1[g][r] = q1;
       }
-      __syncthreads();
+      __syncwarp(gmask);
       // C2: expansion along the shared axis into the cell's rows
       for (int l = tid; l < ND; l += CH) {
         const int im = (l / sk) % N, iob = (l / sob) % N, ioc = (l / soc) % N;
@@ -732,22 +728,27 @@ __device__ __forceinline__ void cut_volume_3d(const PointTables<T, N> &pt, const
         }
         s_acc[l] += acc;
       }
-      __syncthreads();
+      __syncwarp(gmask);
     }
   }
 }
 
-template <typename T, int DIM, int N>
-__global__ void __launch_bounds__(cut_chunk<N>()) cut_kernel(const __grid_constant__ PointTables<T, N> pt,
-                                                            const DevArrays<T> d, const Scalars<T> sc,
-                                                            T *__restrict__ y,
-                                                            const T *__restrict__ x) {
+template <typename T, int DIM, int N, int S>
+__global__ void __launch_bounds__(32) cut_kernel(const __grid_constant__ PointTables<T, N> pt,
+                                                 const DevArrays<T> d, const Scalars<T> sc,
+                                                 T *__restrict__ y, const T *__restrict__ x) {
   using G = Geo<DIM, N>;
-  using SM = CutSmem<T, DIM, N>;
+  using SM = CutSmem<T, DIM, N, S>;
   constexpr int ND = G::ND, NL = G::NL, NF = G::NF;
   constexpr int CH = SM::CH;
+  constexpr int CPW = 32 / S;  // cut cells per CTA
 
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // lane group of this thread: lanes [gshift, gshift + S) work on one cut cell
+  const int grp = threadIdx.x / S;
+  const int gshift = grp * S;
+  const unsigned gmask = (S == 32) ? 0xffffffffu : (((1u << S) - 1u) << gshift);
+  extern __shared__ __align__(16) unsigned char smem_all[];
+  unsigned char *smem_raw = smem_all + grp * SM::stride;
   T *sm = reinterpret_cast<T *>(smem_raw);
   T *s_u = sm + SM::u;
   T *s_acc = sm + SM::acc;
@@ -760,9 +761,9 @@ __global__ void __launch_bounds__(cut_chunk<N>()) cut_kernel(const __grid_consta
   T (*s_fz)[CH][N] = reinterpret_cast<T (*)[CH][N]>(sm + SM::zz);  // face lines: zv, zd
   int *s_tag = reinterpret_cast<int *>(sm + SM::total) + SM::itag;
 
-  const int tid = threadIdx.x;
-  const int slot = blockIdx.x;
-  if (slot >= d.n_cut) return;
+  const int tid = threadIdx.x - gshift;
+  const int slot = blockIdx.x * CPW + grp;
+  if (slot >= d.n_cut) return;  // a whole lane group leaves together
   const int e = __ldg(d.cut_list + slot);
   const int ci = __ldg(d.cut_idx + slot);
   const T kap = __ldg(d.kappa + e);
@@ -772,10 +773,10 @@ __global__ void __launch_bounds__(cut_chunk<N>()) cut_kernel(const __grid_consta
     s_u[i] = __ldg(x + (size_t)e * ND + i);
     s_acc[i] = T(0);
   }
-  __syncthreads();
+  __syncwarp(gmask);
 
   if constexpr (DIM == 3) {
-    cut_volume_3d<T, N>(pt, d, sc, smem_raw, ci, kap);
+    cut_volume_3d<T, N, S>(pt, d, sc, smem_raw, ci, kap, tid, gmask, gshift);
   } else {
     // ---- volume (Poisson) and surface (Nitsche) points, line by line (Eq. unstructured_cell:
     // the contractions along the two outer axes are shared by every point of a line)
@@ -917,7 +918,7 @@ __global__ void __launch_bounds__(cut_chunk<N>()) cut_kernel(const __grid_consta
             s_ldb[tid][ib] = db[ib];
           }
         }
-        __syncthreads();
+        __syncwarp(gmask);
         const int nlines = min(CH, lend - l0);
         for (int l = tid; l < ND; l += CH) {
           const int ib = (l / sb) % N, m = (l / sk) % N;
@@ -927,7 +928,7 @@ __global__ void __launch_bounds__(cut_chunk<N>()) cut_kernel(const __grid_consta
             acc = fma(s_lvb[q][ib], s_lt0[q][col], fma(s_ldb[q][ib], s_lt1[q][col], acc));
           s_acc[l] += acc;
         }
-        __syncthreads();
+        __syncwarp(gmask);
       }
     }
   }
@@ -965,7 +966,7 @@ __global__ void __launch_bounds__(cut_chunk<N>()) cut_kernel(const __grid_consta
       s_ft[fi][0][tl] = T(0);
       s_ft[fi][1][tl] = T(0);
     }
-    __syncthreads();
+    __syncwarp(gmask);
     const int *koff_cell = d.fline_koff + (size_t)ci * NF * 3;
     const int fl_beg = __ldg(koff_cell);
     const int fl_end = __ldg(koff_cell + (NF - 1) * 3 + 2);
@@ -1054,7 +1055,7 @@ __global__ void __launch_bounds__(cut_chunk<N>()) cut_kernel(const __grid_consta
         }
       }
       s_tag[tid] = tag;
-      __syncthreads();
+      __syncwarp(gmask);
       const int nlines = min(CH, fl_end - l0);
       for (int item = tid; item < ncf * NL; item += CH) {
         const int fi = item / NL, tl = item % NL;
@@ -1077,7 +1078,7 @@ __global__ void __launch_bounds__(cut_chunk<N>()) cut_kernel(const __grid_consta
         s_ft[fi][0][tl] += av;
         s_ft[fi][1][tl] += ad;
       }
-      __syncthreads();
+      __syncwarp(gmask);
     }
     // expand the face accumulators into the cell: phi_l = phi_{i_a}(side) x in-face product
     for (int l = tid; l < ND; l += CH) {
@@ -1106,6 +1107,22 @@ __global__ void __launch_bounds__(cut_chunk<N>()) cut_kernel(const __grid_consta
 // ------------------------------------------------------------------------------------------
 // Launch
 // ------------------------------------------------------------------------------------------
+template <typename T, int DIM, int N, int S>
+int launch_cut(const PointTables<T, N> &ptab, const DevArrays<T> &d, const Scalars<T> &s, T *y,
+               const T *x, cudaStream_t stream, void *const *ev) {
+  using SM = CutSmem<T, DIM, N, S>;
+  constexpr int CPW = 32 / S;
+  constexpr size_t smem = CPW * SM::stride;
+  if (smem > 48 * 1024) {
+    const cudaError_t err = cudaFuncSetAttribute(cut_kernel<T, DIM, N, S>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return (int)err;
+  }
+  cut_kernel<T, DIM, N, S><<<(d.n_cut + CPW - 1) / CPW, 32, smem, stream>>>(ptab, d, s, y, x);
+  if (ev) cudaEventRecord(static_cast<cudaEvent_t>(ev[3]), stream);
+  return (int)cudaGetLastError();
+}
+
 template <typename T, int DIM, int N>
 int launch_vmult_t(const DevArrays<T> &d, const void *tables_struct, const void *tables_point,
                    const Scalars<T> &s, T *y, const T *x, bool adjoint, cudaStream_t stream,
@@ -1133,13 +1150,11 @@ int launch_vmult_t(const DevArrays<T> &d, const void *tables_struct, const void 
   if (ev) cudaEventRecord(static_cast<cudaEvent_t>(ev[2]), stream);
   if (d.n_cut > 0) {
     const auto &ptab = *reinterpret_cast<const PointTables<T, N> *>(tables_point);
-    constexpr size_t smem = CutSmem<T, DIM, N>::bytes;
-    if (smem > 48 * 1024) {
-      err = cudaFuncSetAttribute(cut_kernel<T, DIM, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-      if (err != cudaSuccess) return (int)err;
+    if constexpr (N <= 5) {
+      if (d.cut_lanes == 8) return launch_cut<T, DIM, N, 8>(ptab, d, s, y, x, stream, ev);
+      if (d.cut_lanes == 16) return launch_cut<T, DIM, N, 16>(ptab, d, s, y, x, stream, ev);
     }
-    cut_kernel<T, DIM, N><<<d.n_cut, cut_chunk<N>(), smem, stream>>>(ptab, d, s, y, x);
+    return launch_cut<T, DIM, N, 32>(ptab, d, s, y, x, stream, ev);
   }
   if (ev) cudaEventRecord(static_cast<cudaEvent_t>(ev[3]), stream);
   return (int)cudaGetLastError();

@@ -111,6 +111,9 @@ void kgrad_tables(int n, const std::vector<double> &m, std::vector<double> &out)
 void structured_matrices(const HostOperator &op, std::vector<double> &out);
 // Continuous Q_p: load vector (f = 1) and diagonal of A on the host, FP64 (uf_cg.cu).
 void cg_host_vectors(HostOperator &op);
+// Discontinuous space: diagonal of A on the host, FP64, into op.dg_diag (uf_cg.cu).
+void dg_host_diagonal(HostOperator &op);
+int64_t solve_size(const HostOperator &h);  // unknowns of the linear system (CG: nodes)
 uf_status cg_alloc(uf_operator *op);        // solver work vectors + Jacobi diagonal upload
 uf_status cg_upload_diag(uf_operator *op);  // (re)upload 1 / diag(A)
 void cg_free(uf_operator *op);

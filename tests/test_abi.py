@@ -16,7 +16,7 @@ HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "un
 
 def _declared_functions():
     text = open(HEADER).read()
-    return sorted(set(re.findall(r"\b(uf_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(uf_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_library_exports_every_declared_symbol():
