@@ -501,7 +501,7 @@ def run_accuracy(args, local):
 
     torch.cuda.set_device(local)
     omega = 2.0 * np.pi
-    levels = {1: (12, 24, 48, 96), 2: (12, 24, 48, 96), 3: (12, 24, 48), 4: (12, 24, 48)}
+    levels = {1: (12, 24, 48, 96), 2: (12, 24, 48), 3: (12, 24, 48), 4: (12, 24, 48)}
     for disc in ("cg", "dg"):
         for p in (1, 2, 3, 4):
             prev = None
@@ -509,7 +509,7 @@ def run_accuracy(args, local):
                 cfg = dict(workloads.accuracy(p, N), discretization=disc)
                 op = UnfittedOperator(cfg, precisions=UF_FP64, device=local)
                 b = torch.from_numpy(op.manufactured_rhs(omega)).cuda()
-                x, st = op.solve(b, mode="fp64", tol=1e-13, max_iter=400000, max_outer=20)
+                x, st = op.solve(b, mode="fp64", tol=1e-12, max_iter=400000, max_outer=20)
                 err, nrm = op.l2_error(omega, x.cpu().numpy())
                 rel = err / nrm
                 rate = None if prev is None else round(float(np.log2(prev / rel)), 3)
