@@ -159,11 +159,67 @@ class Oracle:
                                        + sig * kavg * sgn[s] * sgn[t] * (V[s].T @ (Wt * V[t])))
         return blocks
 
+    def volume_gp_patches(self):
+        """Faces (e_minus, axis) of the volume ghost penalty's patches, stable-neighbour strategy
+        (Sec. 2.2): every cut cell is paired across one face with its active face neighbour of
+        largest physical volume fraction |K cap Omega| / h^d (inside cells: 1; fractions compared
+        after rounding to 12 decimals; the first face in the order axis 0 lower, axis 0 upper,
+        axis 1 lower, ... wins ties); a pair chosen from both sides is one patch."""
+        if getattr(self, "_patches", None) is None:
+            m = self.mesh
+            d = self.prob.dim
+            frac = np.ones(m.n_active)
+            for e in range(m.n_active):
+                if m.active_type[e] == mesh.CUT:
+                    frac[e] = self.cell_quadrature(e)[1].sum() / self.prob.h ** d
+            key = np.floor(frac * 1e12 + 0.5)
+            patches = set()
+            for e in range(m.n_active):
+                if m.active_type[e] != mesh.CUT:
+                    continue
+                best = None
+                for axis in range(d):
+                    for side in range(2):
+                        nb = m.neighbor(e, axis, side)
+                        if nb >= 0 and (best is None or key[nb] > key[best[0]]):
+                            best = (nb, axis, side)
+                if best is not None:
+                    nb, axis, side = best
+                    patches.add((e if side == 1 else nb, axis))
+            self._patches = patches
+        return self._patches
+
+    def volume_gp_blocks(self, e_minus, axis):
+        """Blocks of the volume ghost penalty tau_v / h^2 {kappa} int_P [v]_P [u]_P on the patch
+        P = K- cup K+ (Sec. 2.2, Eq. volume_based_gp): on each cell of the patch [u]_P is the own
+        polynomial minus the other cell's polynomial extended to it (Sec. 3.4), integrated with the
+        tensor Gauss rule of the full cell."""
+        prob = self.prob
+        cells, kap, kavg = self._face_setup(e_minus, axis)
+        blocks = {(s, t): np.zeros((self.ndof, self.ndof)) for s in range(2) for t in range(2)}
+        c = prob.gp_tau / prob.h ** 2 * kavg
+        for owner in range(2):
+            lo, hi = mesh.cell_box(prob, self.mesh.index_of(cells[owner]))
+            pts = saye.tensor_gauss(lo, hi, self.n)
+            X = np.array([x for x, _ in pts])
+            w = np.array([wt for _, wt in pts])
+            V = [self.basis_at(cells[s], X) for s in range(2)]  # extrapolated for s != owner
+            sg = [1.0 if s == owner else -1.0 for s in range(2)]
+            for s in range(2):
+                for t in range(2):
+                    blocks[(s, t)] += c * sg[s] * sg[t] * (V[s].T @ (w[:, None] * V[t]))
+        return blocks
+
     def gp_blocks(self, e_minus, axis):
-        """Blocks of the face-based ghost penalty sum_j gamma_j {kappa} int_F [d_n^j v][d_n^j u]
-        on the full face (zero unless one of the two cells is cut)."""
+        """Blocks of the ghost penalty of one interior face: face-based, sum_j gamma_j {kappa}
+        int_F [d_n^j v][d_n^j u] on the full face (zero unless one of the two cells is cut); or
+        volume-based on the patches of volume_gp_patches."""
         prob = self.prob
         m = self.mesh
+        if prob.gp_kind == "volume":
+            if prob.gp_max_order > 0 and (e_minus, axis) in self.volume_gp_patches():
+                return self.volume_gp_blocks(e_minus, axis)
+            return {(s, t): np.zeros((self.ndof, self.ndof)) for s in range(2) for t in range(2)}
         cells, kap, kavg = self._face_setup(e_minus, axis)
         sgn = (1.0, -1.0)
         xi_face = (1.0, 0.0)

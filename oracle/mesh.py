@@ -92,6 +92,8 @@ class Problem:
     ls_kind: str = "sphere"
     normal: tuple = None      # plane: phi(x) = normal . x - offset
     offset: float = 0.0
+    gp_kind: str = "face"     # "face": jumps of normal derivatives on faces; "volume": patch jumps
+    gp_tau: float = 1.0       # volume ghost penalty parameter tau_v
     # derived
     h: float = field(init=False)
 
@@ -101,6 +103,8 @@ class Problem:
         self.lo = tuple(float(v) for v in self.lo[:d])
         self.hi = tuple(float(v) for v in self.hi[:d])
         self.center = tuple(float(v) for v in self.center[:d])
+        if self.gp_kind not in ("face", "volume"):
+            raise ValueError("gp_kind must be 'face' or 'volume'")
         if self.ls_kind not in ("sphere", "plane"):
             raise ValueError("ls_kind must be 'sphere' or 'plane'")
         if self.ls_kind == "plane":
@@ -126,7 +130,7 @@ class Problem:
 def problem_from_dict(cfg, kappa=None):
     keys = ["dim", "degree", "n_cells", "lo", "hi", "center", "radius", "quad_order",
             "sipg_gamma", "nitsche_gamma", "gp_max_order", "gp_gamma"]
-    extra = {k: cfg[k] for k in ("ls_kind", "normal", "offset") if k in cfg}
+    extra = {k: cfg[k] for k in ("ls_kind", "normal", "offset", "gp_kind", "gp_tau") if k in cfg}
     return Problem(**{k: cfg[k] for k in keys}, kappa=kappa, **extra)
 
 

@@ -362,3 +362,68 @@ def test_kappa_linearity():
     A12 = _oracle(cfg, k1 + k2).assemble()
     assert abs(A12 - A1 - A2).max() < 1e-13 * abs(A12).max()
     assert abs(A1 - A1.T).max() < 1e-14 * abs(A1).max()
+
+
+# ------------------------------------------------------------------------------------------
+# Volume-based ghost penalty (Sec. 2.2, stable-neighbour patches)
+# ------------------------------------------------------------------------------------------
+
+def _gp_matrix(o):
+    """The ghost-penalty part alone, assembled from the oracle's face blocks."""
+    import scipy.sparse as sp
+
+    nd = o.ndof
+    rows, cols, vals = [], [], []
+    for e in range(o.mesh.n_active):
+        for axis in range(o.prob.dim):
+            ep = o.mesh.neighbor(e, axis, 1)
+            if ep < 0:
+                continue
+            cells = (e, ep)
+            for (s, t), blk in o.gp_blocks(e, axis).items():
+                rows.append(np.repeat(np.arange(nd) + cells[s] * nd, nd))
+                cols.append(np.tile(np.arange(nd) + cells[t] * nd, nd))
+                vals.append(blk.reshape(-1))
+    n = o.mesh.n_dofs
+    return sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(n, n)).tocsr()
+
+
+@pytest.mark.parametrize("dim,p", [(2, 2), (3, 2)])
+def test_volume_ghost_penalty_pins(dim, p):
+    cfg = dict(workloads.small(p=p, N=6, dim=dim), gp_kind="volume", gp_tau=0.7)
+    if dim == 2:
+        cfg["center"] = (0.03, 0.02, 0.0)
+    rng = np.random.default_rng(2)
+    kappa = rng.lognormal(0.0, 0.5, mesh.Mesh(mesh.problem_from_dict(cfg)).n_active)
+    o = _oracle(cfg, kappa)
+    G = _gp_matrix(o)
+    patches = o.volume_gp_patches()
+    # every cut cell belongs to a patch; only patch faces carry the penalty
+    in_patch = set()
+    for (em, axis) in patches:
+        in_patch.add(em)
+        in_patch.add(o.mesh.neighbor(em, axis, 1))
+    cut = set(int(e) for e in np.nonzero(o.mesh.active_type == mesh.CUT)[0])
+    assert cut <= in_patch
+    # symmetric positive semi-definite
+    assert abs(G - G.T).max() <= 1e-14 * abs(G).max()
+    ev = np.linalg.eigvalsh(G.toarray())
+    assert ev.min() > -1e-12 * ev.max()
+    # consistency: the extension of a global polynomial of degree p is the polynomial itself
+    f = _poly3d if dim == 3 else _poly2d
+    if p < 3 and dim == 3:
+        f = lambda X: 0.3 + X[:, 0] - 2 * X[:, 1] * X[:, 2] + 0.5 * X[:, 2] ** 2  # noqa: E731
+    u = _interp(o, f)
+    assert np.abs(G @ u).max() <= 1e-12 * abs(G).max() * np.abs(u).max()
+    # one cell's indicator: its patch jump is 1 on both cells of each of its patches
+    h = o.prob.h
+    for e in sorted(in_patch)[:6]:
+        ind = np.zeros(o.mesh.n_dofs)
+        ind[e * o.ndof:(e + 1) * o.ndof] = 1.0
+        want = 0.0
+        for (em, axis) in patches:
+            ep = o.mesh.neighbor(em, axis, 1)
+            if e in (em, ep):
+                want += 2.0 * cfg["gp_tau"] * h ** (dim - 2) * 0.5 * (kappa[em] + kappa[ep])
+        assert abs(ind @ G @ ind - want) <= 1e-12 * want
