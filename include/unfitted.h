@@ -48,6 +48,7 @@ typedef enum {
 enum { UF_FP64 = 1, UF_FP32 = 2 };     /* precision flags (bit mask in uf_params.precisions) */
 enum { UF_LS_SPHERE = 0, UF_LS_PLANE = 1 };  /* level set kinds */
 enum { UF_DG = 0, UF_CG = 1 };         /* discretizations (uf_params.discretization) */
+enum { UF_GP_FACE = 0, UF_GP_VOLUME = 1 }; /* ghost penalties (uf_params.gp_kind) */
 
 /* Parameters of uf_create_unfitted_operator.  Penalties follow the paper's forms:
  * SIPG penalty sigma/h (Eq. bilinear_dg), Nitsche penalty tau/h (Eq. bilinear_cg), ghost
@@ -74,6 +75,13 @@ typedef struct {
                              the active cells numbered lexicographically (x fastest) */
   double ls_normal[3];    /* UF_LS_PLANE: normal (any length > 0; entries >= dim ignored) */
   double ls_offset;       /* UF_LS_PLANE: the domain is ls_normal . x < ls_offset */
+  int gp_kind;            /* UF_GP_FACE: sum_j gamma_j {kappa} int_F [d^j u/dn^j][d^j v/dn^j] on every
+                             face of a cut cell; UF_GP_VOLUME: gp_tau / h^2 {kappa} int_P [u]_P [v]_P on
+                             stable-neighbour patches P (paper Sec. 2.2, Eq. volume_based_gp): every
+                             cut cell with its active face neighbour of largest volume fraction, [u]_P
+                             the own polynomial minus the neighbour's extended one (Sec. 3.4).  Either
+                             is off when gp_max_order = 0. */
+  double gp_tau;          /* tau_v of UF_GP_VOLUME */
 } uf_params;
 
 /* Sizes and algorithmic traffic of an operator (uf_get_info). */

@@ -16,6 +16,7 @@ UF_FP64, UF_FP32 = 1, 2
 UF_LS_SPHERE = 0
 UF_LS_PLANE = 1
 UF_DG, UF_CG = 0, 1
+UF_GP_FACE, UF_GP_VOLUME = 0, 1
 
 _STATUS = {0: "UF_OK", 1: "UF_EINVAL", 2: "UF_ENOMEM", 3: "UF_ECUDA", 4: "UF_EUNSUPPORTED",
            5: "UF_EGEOMETRY", 6: "UF_ENODEVICE"}
@@ -48,6 +49,8 @@ class uf_params(ctypes.Structure):
         ("discretization", ctypes.c_int),
         ("ls_normal", ctypes.c_double * 3),
         ("ls_offset", ctypes.c_double),
+        ("gp_kind", ctypes.c_int),
+        ("gp_tau", ctypes.c_double),
     ]
 
 
@@ -161,6 +164,8 @@ def make_params(cfg, precisions=UF_FP64 | UF_FP32, device=0, kappa=None):
         p.ls_center[a] = float(cfg["center"][a]) if a < len(cfg["center"]) else 0.0
     p.ls_kind = UF_LS_SPHERE
     p.ls_radius = float(cfg["radius"])
+    p.gp_kind = UF_GP_VOLUME if cfg.get("gp_kind", "face") == "volume" else UF_GP_FACE
+    p.gp_tau = float(cfg.get("gp_tau", 1.0))
     if cfg.get("ls_kind", "sphere") == "plane":
         p.ls_kind = UF_LS_PLANE
         for a in range(3):

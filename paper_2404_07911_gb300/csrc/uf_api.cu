@@ -107,6 +107,32 @@ void uf::structured_matrices(const uf::HostOperator &op, std::vector<double> &ou
         G[k] = hf * g;
         H[k] = -hf * hh;
       }
+    if (op.params.gp_kind == UF_GP_VOLUME && op.params.gp_max_order > 0) {
+      // Volume ghost penalty on the patch with the neighbour across face s (Kronecker form: the
+      // in-face mass sweeps supply the other axes).  Along the axis, with the neighbour's cell at
+      // xi + sigma (sigma = +-1) and Gauss points x_q of [0, 1]:
+      //   own-own  tau h^{d-2} (M + sum_q w_q phi_r(x_q + sigma) phi_m(x_q + sigma))
+      //   own-nb  -tau h^{d-2} (sum_q w_q phi_r(x_q) phi_m(x_q - sigma)
+      //                         + sum_q w_q phi_r(x_q + sigma) phi_m(x_q))
+      const double sigma = s ? 1.0 : -1.0, c = op.params.gp_tau * std::pow(h, d - 2);
+      double vq[uf::kMaxN][uf::kMaxN], vp[uf::kMaxN][uf::kMaxN], vm[uf::kMaxN][uf::kMaxN], dd[uf::kMaxN];
+      for (int q = 0; q < n; ++q) {
+        uf::lagrange_values(t, t.gauss_x[q], vq[q], dd);
+        uf::lagrange_values(t, t.gauss_x[q] + sigma, vp[q], dd);
+        uf::lagrange_values(t, t.gauss_x[q] - sigma, vm[q], dd);
+      }
+      for (int r = 0; r < n; ++r)
+        for (int m = 0; m < n; ++m) {
+          double ee = 0.0, x1 = 0.0, x2 = 0.0;
+          for (int q = 0; q < n; ++q) {
+            ee += t.gauss_w[q] * vp[q][r] * vp[q][m];
+            x1 += t.gauss_w[q] * vq[q][r] * vm[q][m];
+            x2 += t.gauss_w[q] * vp[q][r] * vq[q][m];
+          }
+          G[r * n + m] = c * (t.mass[r * n + m] + ee);
+          H[r * n + m] = -c * (x1 + x2);
+        }
+    }
   }
 }
 

@@ -698,6 +698,14 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
       return UF_EINVAL;
     }
   }
+  if (prm.gp_kind != UF_GP_FACE && prm.gp_kind != UF_GP_VOLUME) {
+    msg = "gp_kind must be UF_GP_FACE or UF_GP_VOLUME";
+    return UF_EINVAL;
+  }
+  if (prm.gp_kind == UF_GP_VOLUME && prm.gp_max_order > 0 && !(prm.gp_tau > 0.0)) {
+    msg = "gp_tau must be positive";
+    return UF_EINVAL;
+  }
   if (prm.discretization != UF_DG && prm.discretization != UF_CG) {
     msg = "discretization must be UF_DG or UF_CG";
     return UF_EINVAL;
@@ -809,6 +817,7 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
     }
   }
   const bool use_gp = prm.gp_max_order > 0;
+  const bool volume_gp = use_gp && prm.gp_kind == UF_GP_VOLUME;  // patches chosen after quadrature
   auto face_box = [&](int64_t e_minus, int axis) {
     Box b;
     b.m = d;
@@ -838,7 +847,7 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
         op.nbr[e * nf + f] = nb;
         const int64_t e_minus = side ? e : nb;
         const int ftype = classify(face_box(e_minus, axis));  // full, cut, empty
-        const bool gp = use_gp && (op.act_type[e] == 1 || op.act_type[nb] == 1);
+        const bool gp = use_gp && !volume_gp && (op.act_type[e] == 1 || op.act_type[nb] == 1);
         // the continuous space has no SIPG term
         if (ftype == 0 && !op.cg) op.flags[e] |= face_bit_sipg_full(f);
         if (ftype == 1 && !op.cg) op.flags[e] |= face_bit_sipg_cut(f);
@@ -939,6 +948,32 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
   } catch (const QuadError &) {
     msg = "quadrature subdivision depth exceeded";
     return UF_EGEOMETRY;
+  }
+  if (volume_gp) {
+    // stable-neighbour patches: every cut cell pairs with its active face neighbour of largest
+    // volume fraction (inside cells 1; compared after rounding to 12 decimals; first face in
+    // the order axis 0 lower, axis 0 upper, ... on ties); a pair chosen twice is one patch
+    const double hd = std::pow(op.h, d);
+    std::vector<double> key(op.n_active, std::floor(1.0 * 1e12 + 0.5));
+    for (int64_t c = 0; c < op.n_cut; ++c) {
+      double vol = 0.0;
+      for (int64_t p = op.vol_off[c]; p < op.vol_off[c + 1]; ++p) vol += op.vol_w[p];
+      key[op.cut_cells[c]] = std::floor(vol / hd * 1e12 + 0.5);
+    }
+    for (int64_t c = 0; c < op.n_cut; ++c) {
+      const int64_t e = op.cut_cells[c];
+      int best_f = -1;
+      for (int f = 0; f < nf; ++f) {
+        const int32_t nb = op.nbr[e * nf + f];
+        if (nb >= 0 && (best_f < 0 || key[nb] > key[op.nbr[e * nf + best_f]])) best_f = f;
+      }
+      if (best_f < 0) continue;
+      const int32_t nb = op.nbr[e * nf + best_f];
+      const int f_nb = best_f ^ 1;  // the same face seen from the neighbour
+      if (!(op.flags[e] & face_bit_gp(best_f))) ++op.n_faces_gp;
+      op.flags[e] |= face_bit_gp(best_f);
+      op.flags[nb] |= face_bit_gp(f_nb);
+    }
   }
   if (op.cg) {
     // lattice point p I_a + i_a of every cell-local DoF; used points numbered in lexicographic

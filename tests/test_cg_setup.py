@@ -9,7 +9,10 @@ from paper_2404_07911_gb300.binding import UnfittedOperator
 
 
 @pytest.mark.parametrize("cfg", [workloads.small(p=2, N=6), workloads.small(p=4, N=5),
-                                 workloads.small(p=3, N=10, dim=2)], ids=["3d_q2", "3d_q4", "2d_q3"])
+                                 workloads.small(p=3, N=10, dim=2),
+                                 dict(workloads.small(p=3, N=6), gp_kind="volume", gp_tau=0.7),
+                                 dict(workloads.small(p=2, N=10, dim=2), gp_kind="volume", gp_tau=1.3)],
+                         ids=["3d_q2", "3d_q4", "2d_q3", "3d_q3_volume_gp", "2d_q2_volume_gp"])
 def test_cg_numbering_rhs_diag_match_oracle(cfg):
     cfg = dict(cfg, discretization="cg")
     op = UnfittedOperator(cfg, device=-1)
@@ -33,3 +36,14 @@ def test_cg_with_kappa():
     d_ref = forms.Oracle(mesh.problem_from_dict(cfg, kappa), "cg").cg_matrix().diagonal()
     _, _, diag = op.export_cg()
     assert np.max(np.abs(diag - d_ref)) <= 1e-12 * np.max(np.abs(d_ref))
+
+
+@pytest.mark.parametrize("cfg", [dict(workloads.small(p=3, N=6), gp_kind="volume"),
+                                 dict(workloads.plane(p=2, N=5, dim=3), gp_kind="volume")],
+                         ids=["ball", "plane"])
+def test_volume_gp_patch_count(cfg):
+    """The library's stable-neighbour patches of the volume ghost penalty against the oracle's."""
+    op = UnfittedOperator(cfg, device=-1)
+    o = forms.Oracle(mesh.problem_from_dict(cfg))
+    assert op.info["n_faces_gp"] == len(o.volume_gp_patches())
+    op.close()

@@ -16,6 +16,7 @@ CASES = {
     "3d_q4_5": workloads.small(p=4, N=5),
     "2d_q3_10": workloads.small(p=3, N=10, dim=2),
     "3d_plane_q3_4": workloads.plane(p=3, N=4, dim=3),
+    "3d_q3_5_volume_gp": dict(workloads.small(p=3, N=5), gp_kind="volume", gp_tau=0.7),
 }
 
 

@@ -55,6 +55,9 @@ SMALL = {
     "3d_q4_6": workloads.small(p=4, N=6),
     "3d_q3_center_on_grid": workloads.small(p=3, N=6, center=(0.0, 0.0, 0.0)),
     "3d_q6_4": workloads.small(p=6, N=4),
+    # volume-based ghost penalty on stable-neighbour patches
+    "3d_q3_6_volume_gp": dict(workloads.small(p=3, N=6), gp_kind="volume", gp_tau=0.7),
+    "2d_q2_10_volume_gp": dict(workloads.small(p=2, N=10, dim=2), gp_kind="volume"),
     # half-spaces below tilted planes (the plane benchmark's geometry)
     "2d_plane_q2_7": workloads.plane(p=2, N=7, dim=2),
     "3d_plane_q1_6": workloads.plane(p=1, N=6, dim=3),
@@ -205,3 +208,16 @@ def test_host_buffer_path_matches_device(full):
     y_host32 = op.vmult_host(x.astype(np.float32))
     y_dev32 = _apply(op, x, dtype=torch.float32)
     assert np.array_equal(y_host32.astype(np.float64), y_dev32)
+
+
+def test_parity_volume_gp_with_kappa():
+    """Volume ghost penalty with a log-normal coefficient: {kappa} on the patches, the general
+    per-cell path of the structured kernel, vmult and adjoint."""
+    cfg = dict(workloads.small(p=2, N=7), gp_kind="volume", gp_tau=0.7)
+    o0 = forms.Oracle(mesh.problem_from_dict(cfg))
+    kappa = workloads.kappa_vector(o0.mesh.n_active, seed=4)
+    A = forms.Oracle(mesh.problem_from_dict(cfg, kappa)).assemble()
+    op = _gpu_op(cfg, kappa=kappa)
+    x = workloads.uniform_vector(op.n_dofs, 5)
+    assert _rel(_apply(op, x), A @ x) <= TOL64
+    assert _rel(_apply(op, x, adjoint=True), A.T @ x) <= TOL64
