@@ -57,6 +57,9 @@ def parse_args():
     ap.add_argument("--cpu-sample-cells", type=int, default=120,
                     help="cells of the oracle's bounded sample (cpu_baseline / reference arm)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--gp", choices=("face", "volume"), default="face",
+                    help="ghost penalty of the headline workload: face-based (default) or the "
+                         "paper's volume-based one on stable-neighbour patches (tau_v = 1)")
     ap.add_argument("--no-csr", action="store_true",
                     help="skip the assembled-matrix (CSR SpMV) comparison")
     ap.add_argument("--config", choices=("q3", "solve", "sweep", "kappa", "plane", "accuracy"),
@@ -234,6 +237,8 @@ def run_ours(args, rank, world, local):
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     cfg = workloads.cfg_3d_q3()
+    if args.gp == "volume":
+        cfg = dict(cfg, gp_kind="volume", gp_tau=1.0, name=cfg["name"] + "_volume_gp")
     op = UnfittedOperator(cfg, precisions=UF_FP64 | UF_FP32, device=local)
     info = op.info
     n = info["n_dofs"]
