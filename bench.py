@@ -58,8 +58,9 @@ def parse_args():
                     help="cells of the oracle's bounded sample (cpu_baseline / reference arm)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--gp", choices=("face", "volume"), default="face",
-                    help="ghost penalty of the headline workload: face-based (default) or the "
-                         "paper's volume-based one on stable-neighbour patches (tau_v = 1)")
+                    help="ghost penalty of the headline and accuracy workloads: face-based "
+                         "(default) or the paper's volume-based one on stable-neighbour patches "
+                         "(tau_v = 1)")
     ap.add_argument("--no-csr", action="store_true",
                     help="skip the assembled-matrix (CSR SpMV) comparison")
     ap.add_argument("--config", choices=("q3", "solve", "sweep", "kappa", "plane", "accuracy"),
@@ -512,6 +513,8 @@ def run_accuracy(args, local):
             prev = None
             for N in levels[p]:
                 cfg = dict(workloads.accuracy(p, N), discretization=disc)
+                if args.gp == "volume":
+                    cfg.update(gp_kind="volume", gp_tau=1.0)
                 op = UnfittedOperator(cfg, precisions=UF_FP64, device=local)
                 b = torch.from_numpy(op.manufactured_rhs(omega)).cuda()
                 x, st = op.solve(b, mode="fp64", tol=1e-12, max_iter=400000, max_outer=20)
@@ -522,6 +525,7 @@ def run_accuracy(args, local):
                 print(json.dumps({
                     "metric": "sphere accuracy benchmark: relative L2 error of the PCG solution",
                     "discretization": disc, "degree": p, "N": N, "h_over_L": round(2.07 / N, 6),
+                    "ghost_penalty": args.gp,
                     "n_dofs": op.n_dofs, "rel_l2_error": rel, "observed_order": rate,
                     "solver": {k: st[k] for k in ("converged", "outer", "iterations", "rel_residual",
                                                   "seconds")},
