@@ -80,3 +80,11 @@ def test_line_groups():
     assert i3["n_vol_lines"] / i3["n_vol_groups"] > 3.0
     i2 = UnfittedOperator(workloads.small(p=3, N=10, dim=2), device=-1).info
     assert i2["n_vol_groups"] == i2["n_vol_lines"]
+
+
+def test_gpu_parity_cases_cover_every_lane_group():
+    """The GPU parity cases run the cut-cell kernel with 8, 16 and 32 lanes per cut cell."""
+    import test_gpu_parity
+
+    lanes = {UnfittedOperator(cfg, device=-1).info["cut_lanes"] for cfg in test_gpu_parity.SMALL.values()}
+    assert lanes == {8, 16, 32}
