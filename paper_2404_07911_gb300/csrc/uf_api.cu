@@ -340,6 +340,13 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   const size_t o_fpw = L.take(sizeof(T) * std::max<int64_t>(nfp, 1));
   std::vector<double> mats, lself, lnbgp;
   structured_matrices(H, mats);
+  // the device copy of the structured tables: dow, dnb (after the 16 matrices) carry h^{d-1} / 2
+  std::vector<double> smat = mats;
+  {
+    const double half_hf = 0.5 * std::pow(H.h, d - 1);
+    for (int i = 0; i < 4 * n; ++i) smat[16 * n * n + i] = half_hf * mats[16 * n * n + i];
+  }
+  const size_t o_smat = L.take(sizeof(T) * smat.size());
   variant_tables(H, mats, lself, lnbgp);
   const size_t o_lself = L.take(sizeof(T) * lself.size());
   const size_t o_lnbgp = L.take(sizeof(T) * lnbgp.size());
@@ -434,6 +441,7 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   put_t(o_fpt, fpt_t);
   put_t(o_fpw, fpt_w);
   put_t(o_lself, lself);
+  put_t(o_smat, smat);
   put_t(o_lnbgp, lnbgp);
   put_t(o_lselfT, lselfT);
   put_t(o_lnbgpT, lnbgpT);
@@ -495,6 +503,7 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   A.fpt_t = TP(o_fpt);
   A.fpt_w = TP(o_fpw);
   A.lself = TP(o_lself);
+  A.smat = TP(o_smat);
   A.lnbgp = TP(o_lnbgp);
   A.lselfT = TP(o_lselfT);
   A.lnbgpT = TP(o_lnbgpT);
@@ -525,12 +534,9 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   pd.n_flines = nfl;
 
   // constant tables
-  pd.struct_tables.assign(sizeof(T) * mats.size(), 0);
+  pd.struct_tables.assign(sizeof(T) * smat.size(), 0);
   T *st = reinterpret_cast<T *>(pd.struct_tables.data());
-  for (size_t i = 0; i < mats.size(); ++i) st[i] = (T)mats[i];
-  // dow, dnb (after the 16 matrices) carry h^{d-1} / 2 in the device copy
-  const double half_hf = 0.5 * std::pow(H.h, d - 1);
-  for (int i = 0; i < 4 * n; ++i) st[16 * n * n + i] = (T)(half_hf * mats[16 * n * n + i]);
+  for (size_t i = 0; i < smat.size(); ++i) st[i] = (T)smat[i];
   pd.point_tables.assign(sizeof(T) * 6 * n, 0);
   T *ptab = reinterpret_cast<T *>(pd.point_tables.data());
   for (int i = 0; i < n; ++i) {

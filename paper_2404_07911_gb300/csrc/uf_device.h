@@ -93,6 +93,8 @@ struct DevArrays {
   // (kappa_uniform != 0) every structured term scales with that value.
   const T *lself, *lnbgp;
   const T *lselfT, *lnbgpT;  // the same tables transposed (adjoint)
+  // the StructTables in global memory (flat, same layout), for reads with a per-thread index
+  const T *smat;
   // FP64 only (null otherwise): the 1D basis at every line and point, precomputed at creation
   // (values and derivatives; faces values only): vline_b [line][4n] = phi, phi' of the lower and
   // upper outer coordinate; vpt_b / spt_b [point][2n]; fline_b [face line][n]; fpt_b [point][n].

@@ -239,12 +239,15 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
   const bool scale_rows = yscale != T(1);
 
   if (!uniform && has_cell) {
-    // per-cell 1D matrices from the constant ones and kappa
+    // per-cell 1D matrices from the constant ones and kappa; the constant matrices are read from
+    // their global-memory copy (each thread reads its own entry: coalesced through L1), matrix
+    // `which` (kv 0, mass 1, a 2, pen 4, gp 6, b 8, c 10, qn 12, hn 14, + side) at which * NN
+    const T *Q = d.smat;
     for (int a = 0; a < DIM; ++a)
       for (int idx = t; idx < NN; idx += TPC) {
         const int r = idx / N, m = idx % N;
         const int tr = ADJ ? (m * N + r) : idx;
-        T self = inside ? kap * tab.kv[tr] : T(0);
+        T self = inside ? kap * __ldg(Q + tr) : T(0);
         T ln[2] = {T(0), T(0)};
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
@@ -252,17 +255,21 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
           if (nb[f] < 0) continue;
           const bool full = bit(fl, bit_full(f));
           const bool gp = bit(fl, bit_gp(f));
-          if (full) self += kap * tab.a[s][tr] + kavg[f] * tab.pen[s][tr];
-          if (gp) self += kavg[f] * tab.gp[s][tr];
+          if (full) self += kap * __ldg(Q + (2 + s) * NN + tr) + kavg[f] * __ldg(Q + (4 + s) * NN + tr);
+          if (gp) self += kavg[f] * __ldg(Q + (6 + s) * NN + tr);
           if (gp) {
             if (!ADJ) {
-              if (full) ln[s] += kap * tab.b[s][idx] + knb[f] * tab.c[s][idx] + kavg[f] * tab.qn[s][idx];
-              ln[s] += kavg[f] * tab.hn[s][idx];
+              if (full)
+                ln[s] += kap * __ldg(Q + (8 + s) * NN + idx) + knb[f] * __ldg(Q + (10 + s) * NN + idx) +
+                         kavg[f] * __ldg(Q + (12 + s) * NN + idx);
+              ln[s] += kavg[f] * __ldg(Q + (14 + s) * NN + idx);
             } else {
               // transpose of the neighbour's coupling toward this cell (its face 1 - s)
               const int so = 1 - s;
-              if (full) ln[s] += knb[f] * tab.b[so][tr] + kap * tab.c[so][tr] + kavg[f] * tab.qn[so][tr];
-              ln[s] += kavg[f] * tab.hn[so][tr];
+              if (full)
+                ln[s] += knb[f] * __ldg(Q + (8 + so) * NN + tr) + kap * __ldg(Q + (10 + so) * NN + tr) +
+                         kavg[f] * __ldg(Q + (12 + so) * NN + tr);
+              ln[s] += kavg[f] * __ldg(Q + (14 + so) * NN + tr);
             }
           }
         }

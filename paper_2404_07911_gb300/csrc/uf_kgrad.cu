@@ -182,6 +182,146 @@ __global__ void __launch_bounds__(128) kgrad_struct_kernel(const double *__restr
   }
 }
 
+// Volume and surface integrands of r^T (dA/dkappa_K) x on a 3D cut cell, with the two-level line
+// groups of the cut-cell rule (as in the operator's cut-cell kernel): per chunk of 32 lines, the
+// contraction of x and r along each group's shared outer axis (2 n^3 FMA per field and group),
+// then per line along its own outer axis (3 n^2 per field), then the points on the line.
+template <int N>
+__device__ __forceinline__ void kgrad_volume_grouped(const PointTables<double, N> &pt,
+                                                     const DevArrays<double> &d,
+                                                     const Scalars<double> &sc, int ci, int lane,
+                                                     const double *s_x, const double *s_r,
+                                                     double &p_self) {
+  constexpr int NL = N * N, GMAX = 16;
+  __shared__ double s_p[4][GMAX][NL];  // P0 x, P1 x, P0 r, P1 r per group
+  __shared__ double s_gcv[GMAX][N], s_gcd[GMAX][N];
+  __shared__ int s_gax[GMAX];
+#pragma unroll 1
+  for (int k = 0; k < 3; ++k) {
+    const int lbeg = __ldg(d.vline_koff + ci * 4 + k);
+    const int lend = __ldg(d.vline_koff + ci * 4 + k + 1);
+    int ob, oc;
+    other_axes(k, ob, oc);
+    const int sk = stride_of<N>(k), sob = stride_of<N>(ob), soc = stride_of<N>(oc);
+    int nl = 0;
+#pragma unroll 1
+    for (int l0 = lbeg; l0 < lend; l0 += nl) {
+      const int line = l0 + lane;
+      const bool in_range = lane < min(32, lend - l0);
+      const int gword = in_range ? __ldg(d.vline_grp + line) : 0;
+      const int shared_lo = gword & 1;  // the group shares the coordinate along ob
+      const bool start0 = in_range && (lane == 0 || (gword >> 1) == line);
+      const unsigned starts0 = __ballot_sync(0xffffffffu, start0);
+      const int gl = __popc(starts0 & ((2u << lane) - 1u)) - 1;
+      const unsigned over = __ballot_sync(0xffffffffu, start0 && gl >= GMAX);
+      nl = over ? (__ffs(over) - 1) : min(32, lend - l0);
+      const bool act = lane < nl;
+      const int ng = __popc(starts0 & ((nl >= 32) ? 0xffffffffu : ((1u << nl) - 1u)));
+      if (start0 && act) {
+        s_gax[gl] = shared_lo;
+        const double *bp = d.vline_b + (size_t)line * 4 * N + (shared_lo ? 0 : 2 * N);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          s_gcv[gl][i] = __ldg(bp + i);
+          s_gcd[gl][i] = __ldg(bp + N + i);
+        }
+      }
+      __syncwarp();
+      for (int item = lane; item < ng * NL; item += 32) {
+        const int g = item / NL, rr = item % NL, ib = rr / N, m = rr % N;
+        const int lo = s_gax[g];
+        const int sb = lo ? soc : sob, scs = lo ? sob : soc;
+        double px0 = 0.0, px1 = 0.0, pr0 = 0.0, pr1 = 0.0;
+#pragma unroll
+        for (int ic = 0; ic < N; ++ic) {
+          const int idx = ib * sb + ic * scs + m * sk;
+          px0 = fma(s_gcv[g][ic], s_x[idx], px0);
+          px1 = fma(s_gcd[g][ic], s_x[idx], px1);
+          pr0 = fma(s_gcv[g][ic], s_r[idx], pr0);
+          pr1 = fma(s_gcd[g][ic], s_r[idx], pr1);
+        }
+        s_p[0][g][rr] = px0;
+        s_p[1][g][rr] = px1;
+        s_p[2][g][rr] = pr0;
+        s_p[3][g][rr] = pr1;
+      }
+      __syncwarp();
+      if (act) {
+        const int ab = shared_lo ? oc : ob, ac = shared_lo ? ob : oc;
+        double vb[N], db[N];
+        const double *bp = d.vline_b + (size_t)line * 4 * N + (shared_lo ? 2 * N : 0);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          vb[i] = __ldg(bp + i);
+          db[i] = __ldg(bp + N + i);
+        }
+        // w[0] value, w[1] derivative along the own outer axis ab, w[2] along the shared one ac
+        double wx[3][N], wr[3][N];
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+          double a0 = 0.0, a1 = 0.0, a2 = 0.0, b0 = 0.0, b1 = 0.0, b2 = 0.0;
+#pragma unroll
+          for (int ib = 0; ib < N; ++ib) {
+            const double qx = s_p[0][gl][ib * N + m], qr = s_p[2][gl][ib * N + m];
+            a0 = fma(vb[ib], qx, a0);
+            a1 = fma(db[ib], qx, a1);
+            a2 = fma(vb[ib], s_p[1][gl][ib * N + m], a2);
+            b0 = fma(vb[ib], qr, b0);
+            b1 = fma(db[ib], qr, b1);
+            b2 = fma(vb[ib], s_p[3][gl][ib * N + m], b2);
+          }
+          wx[0][m] = a0;
+          wx[1][m] = a1;
+          wx[2][m] = a2;
+          wr[0][m] = b0;
+          wr[1][m] = b1;
+          wr[2][m] = b2;
+        }
+        const int pb = __ldg(d.vpt_off + line), pe = __ldg(d.vpt_off + line + 1);
+#pragma unroll 1
+        for (int p = pb; p < pe; ++p) {
+          double cv[N], cd[N];
+          point_basis<double, N>(pt, d.vpt_b, d.vpt_t, p, cv, cd);
+          double gx[3] = {0, 0, 0}, gr[3] = {0, 0, 0};
+#pragma unroll
+          for (int m = 0; m < N; ++m) {
+            gx[0] = fma(cd[m], wx[0][m], gx[0]);
+            gx[1] = fma(cv[m], wx[1][m], gx[1]);
+            gx[2] = fma(cv[m], wx[2][m], gx[2]);
+            gr[0] = fma(cd[m], wr[0][m], gr[0]);
+            gr[1] = fma(cv[m], wr[1][m], gr[1]);
+            gr[2] = fma(cv[m], wr[2][m], gr[2]);
+          }
+          p_self += __ldg(d.vpt_w + p) * sc.inv_h2 * (gx[0] * gr[0] + gx[1] * gr[1] + gx[2] * gr[2]);
+        }
+        const int sp = __ldg(d.lsurf + line);
+        if (sp >= 0) {
+          double cv[N], cd[N];
+          point_basis<double, N>(pt, d.spt_b, d.spt_t, sp, cv, cd);
+          double ux = 0.0, ur = 0.0, gx[3] = {0, 0, 0}, gr[3] = {0, 0, 0};
+#pragma unroll
+          for (int m = 0; m < N; ++m) {
+            ux = fma(cv[m], wx[0][m], ux);
+            ur = fma(cv[m], wr[0][m], ur);
+            gx[0] = fma(cd[m], wx[0][m], gx[0]);
+            gx[1] = fma(cv[m], wx[1][m], gx[1]);
+            gx[2] = fma(cv[m], wx[2][m], gx[2]);
+            gr[0] = fma(cd[m], wr[0][m], gr[0]);
+            gr[1] = fma(cv[m], wr[1][m], gr[1]);
+            gr[2] = fma(cv[m], wr[2][m], gr[2]);
+          }
+          const double nk = __ldg(d.spt_n[k] + sp), nb = __ldg(d.spt_n[ab] + sp);
+          const double nc = __ldg(d.spt_n[ac] + sp);
+          const double dnx = (nk * gx[0] + nb * gx[1] + nc * gx[2]) * sc.inv_h;
+          const double dnr = (nk * gr[0] + nb * gr[1] + nc * gr[2]) * sc.inv_h;
+          p_self += __ldg(d.spt_w + sp) * (-dnr * ux - ur * dnx + sc.nitsche_over_h * ur * ux);
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
 // Cut cells: one warp per cut cell, adds its unstructured partials to S.
 template <int DIM, int N>
 __global__ void __launch_bounds__(32) kgrad_cut_kernel(const __grid_constant__ PointTables<double, N> pt,
@@ -210,111 +350,116 @@ __global__ void __launch_bounds__(32) kgrad_cut_kernel(const __grid_constant__ P
 #pragma unroll
   for (int f = 0; f < NF; ++f) p_face[f] = 0.0;
 
-  // volume and surface points, line by line
-#pragma unroll 1
-  for (int k = 0; k < DIM; ++k) {
-    const int lbeg = __ldg(d.vline_koff + ci * 4 + k);
-    const int lend = __ldg(d.vline_koff + ci * 4 + k + 1);
-    int ob = 0, oc = 0;
-    if constexpr (DIM == 3) {
-      other_axes(k, ob, oc);
-    } else {
-      ob = 1 - k;
-    }
-    const int sk = stride_of<N>(k), sb = stride_of<N>(ob), scc = stride_of<N>(oc);
-    constexpr int NC = (DIM == 3) ? N : 1;
-#pragma unroll 1
-    for (int line = lbeg + lane; line < lend; line += 32) {
-      double vb[N], db[N], vc[N], dc[N];
-      {
-        const double *bp = d.vline_b + (size_t)line * 4 * N;  // precomputed at creation (FP64)
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-          vb[i] = __ldg(bp + i);
-          db[i] = __ldg(bp + N + i);
-          if constexpr (DIM == 3) {
-            vc[i] = __ldg(bp + 2 * N + i);
-            dc[i] = __ldg(bp + 3 * N + i);
-          }
-        }
+  // volume and surface points
+  if constexpr (DIM == 3 && N <= 6) {
+    kgrad_volume_grouped<N>(pt, d, sc, ci, lane, s_x, s_r, p_self);
+  } else {
+    // volume and surface points, line by line
+  #pragma unroll 1
+    for (int k = 0; k < DIM; ++k) {
+      const int lbeg = __ldg(d.vline_koff + ci * 4 + k);
+      const int lend = __ldg(d.vline_koff + ci * 4 + k + 1);
+      int ob = 0, oc = 0;
+      if constexpr (DIM == 3) {
+        other_axes(k, ob, oc);
+      } else {
+        ob = 1 - k;
       }
-      double wx[3][N], wr[3][N];
-#pragma unroll
-      for (int m = 0; m < N; ++m)
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          wx[q][m] = 0.0;
-          wr[q][m] = 0.0;
-        }
-#pragma unroll
-      for (int m = 0; m < N; ++m)
-#pragma unroll
-        for (int ic = 0; ic < NC; ++ic) {
-          double sx0 = 0.0, sx1 = 0.0, sr0 = 0.0, sr1 = 0.0;
-#pragma unroll
-          for (int ib = 0; ib < N; ++ib) {
-            const int idx = ib * sb + ic * scc + m * sk;
-            sx0 = fma(vb[ib], s_x[idx], sx0);
-            sx1 = fma(db[ib], s_x[idx], sx1);
-            sr0 = fma(vb[ib], s_r[idx], sr0);
-            sr1 = fma(db[ib], s_r[idx], sr1);
-          }
-          if constexpr (DIM == 3) {
-            wx[0][m] = fma(vc[ic], sx0, wx[0][m]);
-            wx[1][m] = fma(vc[ic], sx1, wx[1][m]);
-            wx[2][m] = fma(dc[ic], sx0, wx[2][m]);
-            wr[0][m] = fma(vc[ic], sr0, wr[0][m]);
-            wr[1][m] = fma(vc[ic], sr1, wr[1][m]);
-            wr[2][m] = fma(dc[ic], sr0, wr[2][m]);
-          } else {
-            wx[0][m] = sx0;
-            wx[1][m] = sx1;
-            wr[0][m] = sr0;
-            wr[1][m] = sr1;
+      const int sk = stride_of<N>(k), sb = stride_of<N>(ob), scc = stride_of<N>(oc);
+      constexpr int NC = (DIM == 3) ? N : 1;
+  #pragma unroll 1
+      for (int line = lbeg + lane; line < lend; line += 32) {
+        double vb[N], db[N], vc[N], dc[N];
+        {
+          const double *bp = d.vline_b + (size_t)line * 4 * N;  // precomputed at creation (FP64)
+  #pragma unroll
+          for (int i = 0; i < N; ++i) {
+            vb[i] = __ldg(bp + i);
+            db[i] = __ldg(bp + N + i);
+            if constexpr (DIM == 3) {
+              vc[i] = __ldg(bp + 2 * N + i);
+              dc[i] = __ldg(bp + 3 * N + i);
+            }
           }
         }
-      const int pb = __ldg(d.vpt_off + line), pe = __ldg(d.vpt_off + line + 1);
-#pragma unroll 1
-      for (int p = pb; p < pe; ++p) {
-        double cv[N], cd[N];
-        point_basis<double, N>(pt, d.vpt_b, d.vpt_t, p, cv, cd);
-        double gx[3] = {0, 0, 0}, gr[3] = {0, 0, 0};
-#pragma unroll
-        for (int m = 0; m < N; ++m) {
-          gx[0] = fma(cd[m], wx[0][m], gx[0]);
-          gx[1] = fma(cv[m], wx[1][m], gx[1]);
-          gr[0] = fma(cd[m], wr[0][m], gr[0]);
-          gr[1] = fma(cv[m], wr[1][m], gr[1]);
-          if constexpr (DIM == 3) {
-            gx[2] = fma(cv[m], wx[2][m], gx[2]);
-            gr[2] = fma(cv[m], wr[2][m], gr[2]);
+        double wx[3][N], wr[3][N];
+  #pragma unroll
+        for (int m = 0; m < N; ++m)
+  #pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            wx[q][m] = 0.0;
+            wr[q][m] = 0.0;
           }
-        }
-        p_self += __ldg(d.vpt_w + p) * sc.inv_h2 * (gx[0] * gr[0] + gx[1] * gr[1] + gx[2] * gr[2]);
-      }
-      const int sp = __ldg(d.lsurf + line);
-      if (sp >= 0) {
-        double cv[N], cd[N];
-        point_basis<double, N>(pt, d.spt_b, d.spt_t, sp, cv, cd);
-        double ux = 0.0, ur = 0.0, gx[3] = {0, 0, 0}, gr[3] = {0, 0, 0};
-#pragma unroll
-        for (int m = 0; m < N; ++m) {
-          ux = fma(cv[m], wx[0][m], ux);
-          ur = fma(cv[m], wr[0][m], ur);
-          gx[0] = fma(cd[m], wx[0][m], gx[0]);
-          gx[1] = fma(cv[m], wx[1][m], gx[1]);
-          gr[0] = fma(cd[m], wr[0][m], gr[0]);
-          gr[1] = fma(cv[m], wr[1][m], gr[1]);
-          if constexpr (DIM == 3) {
-            gx[2] = fma(cv[m], wx[2][m], gx[2]);
-            gr[2] = fma(cv[m], wr[2][m], gr[2]);
+  #pragma unroll
+        for (int m = 0; m < N; ++m)
+  #pragma unroll
+          for (int ic = 0; ic < NC; ++ic) {
+            double sx0 = 0.0, sx1 = 0.0, sr0 = 0.0, sr1 = 0.0;
+  #pragma unroll
+            for (int ib = 0; ib < N; ++ib) {
+              const int idx = ib * sb + ic * scc + m * sk;
+              sx0 = fma(vb[ib], s_x[idx], sx0);
+              sx1 = fma(db[ib], s_x[idx], sx1);
+              sr0 = fma(vb[ib], s_r[idx], sr0);
+              sr1 = fma(db[ib], s_r[idx], sr1);
+            }
+            if constexpr (DIM == 3) {
+              wx[0][m] = fma(vc[ic], sx0, wx[0][m]);
+              wx[1][m] = fma(vc[ic], sx1, wx[1][m]);
+              wx[2][m] = fma(dc[ic], sx0, wx[2][m]);
+              wr[0][m] = fma(vc[ic], sr0, wr[0][m]);
+              wr[1][m] = fma(vc[ic], sr1, wr[1][m]);
+              wr[2][m] = fma(dc[ic], sr0, wr[2][m]);
+            } else {
+              wx[0][m] = sx0;
+              wx[1][m] = sx1;
+              wr[0][m] = sr0;
+              wr[1][m] = sr1;
+            }
           }
+        const int pb = __ldg(d.vpt_off + line), pe = __ldg(d.vpt_off + line + 1);
+  #pragma unroll 1
+        for (int p = pb; p < pe; ++p) {
+          double cv[N], cd[N];
+          point_basis<double, N>(pt, d.vpt_b, d.vpt_t, p, cv, cd);
+          double gx[3] = {0, 0, 0}, gr[3] = {0, 0, 0};
+  #pragma unroll
+          for (int m = 0; m < N; ++m) {
+            gx[0] = fma(cd[m], wx[0][m], gx[0]);
+            gx[1] = fma(cv[m], wx[1][m], gx[1]);
+            gr[0] = fma(cd[m], wr[0][m], gr[0]);
+            gr[1] = fma(cv[m], wr[1][m], gr[1]);
+            if constexpr (DIM == 3) {
+              gx[2] = fma(cv[m], wx[2][m], gx[2]);
+              gr[2] = fma(cv[m], wr[2][m], gr[2]);
+            }
+          }
+          p_self += __ldg(d.vpt_w + p) * sc.inv_h2 * (gx[0] * gr[0] + gx[1] * gr[1] + gx[2] * gr[2]);
         }
-        const double nk = __ldg(d.spt_n[k] + sp), nb = __ldg(d.spt_n[ob] + sp);
-        const double nc = (DIM == 3) ? __ldg(d.spt_n[oc] + sp) : 0.0;
-        const double dnx = (nk * gx[0] + nb * gx[1] + nc * gx[2]) * sc.inv_h;
-        const double dnr = (nk * gr[0] + nb * gr[1] + nc * gr[2]) * sc.inv_h;
-        p_self += __ldg(d.spt_w + sp) * (-dnr * ux - ur * dnx + sc.nitsche_over_h * ur * ux);
+        const int sp = __ldg(d.lsurf + line);
+        if (sp >= 0) {
+          double cv[N], cd[N];
+          point_basis<double, N>(pt, d.spt_b, d.spt_t, sp, cv, cd);
+          double ux = 0.0, ur = 0.0, gx[3] = {0, 0, 0}, gr[3] = {0, 0, 0};
+  #pragma unroll
+          for (int m = 0; m < N; ++m) {
+            ux = fma(cv[m], wx[0][m], ux);
+            ur = fma(cv[m], wr[0][m], ur);
+            gx[0] = fma(cd[m], wx[0][m], gx[0]);
+            gx[1] = fma(cv[m], wx[1][m], gx[1]);
+            gr[0] = fma(cd[m], wr[0][m], gr[0]);
+            gr[1] = fma(cv[m], wr[1][m], gr[1]);
+            if constexpr (DIM == 3) {
+              gx[2] = fma(cv[m], wx[2][m], gx[2]);
+              gr[2] = fma(cv[m], wr[2][m], gr[2]);
+            }
+          }
+          const double nk = __ldg(d.spt_n[k] + sp), nb = __ldg(d.spt_n[ob] + sp);
+          const double nc = (DIM == 3) ? __ldg(d.spt_n[oc] + sp) : 0.0;
+          const double dnx = (nk * gx[0] + nb * gx[1] + nc * gx[2]) * sc.inv_h;
+          const double dnr = (nk * gr[0] + nb * gr[1] + nc * gr[2]) * sc.inv_h;
+          p_self += __ldg(d.spt_w + sp) * (-dnr * ux - ur * dnx + sc.nitsche_over_h * ur * ux);
+        }
       }
     }
   }
