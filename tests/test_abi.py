@@ -52,6 +52,10 @@ def test_destroy_null_is_ok():
     (dict(radius=-1.0), binding.UF_EINVAL),
     (dict(n_cells=(16, 8, 1)), binding.UF_EUNSUPPORTED),   # anisotropic cells
     (dict(center=(10.0, 10.0, 0.0)), binding.UF_EGEOMETRY),  # no active cell
+    (dict(ls_kind="plane", normal=(0.0, 0.0, 0.0), offset=0.5), binding.UF_EINVAL),  # zero normal
+    (dict(ls_kind="plane", normal=(0.0, 1.0, 0.0), offset=-5.0), binding.UF_EGEOMETRY),  # plane below the box
+    (dict(gp_kind="volume", gp_tau=0.0), binding.UF_EINVAL),
+    (dict(n_cells=(40000, 40000, 1)), binding.UF_EUNSUPPORTED),  # background grid > 2^30 cells
 ])
 def test_invalid_parameters(change, status):
     cfg = workloads.cfg_2d_q1()
