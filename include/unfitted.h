@@ -112,9 +112,10 @@ typedef struct {
   /* Groups of volume lines (3D): lines of a cut cell along one axis that share one outer
    * coordinate; the cut-cell kernel contracts along that coordinate once per group. */
   int64_t n_vol_groups;
-  /* Lanes of a warp that work on one cut cell in the cut-cell kernel (32, 16 or 8; several cut
-   * cells share a warp when their rules have few lines), chosen at creation. */
-  int32_t cut_lanes;
+  /* Cut cells that the cut-cell kernel handles with 32, 16 and 8 lanes of a warp (a cell's
+   * group is the smallest that holds all its volume lines and all its cut-face lines in one
+   * chunk; several small cut cells share a warp), chosen at creation. */
+  int64_t cut_lane_classes[3];
 } uf_info;
 
 /* Per-kernel device times collected between uf_profile_begin and uf_profile_end, indexed

@@ -65,7 +65,7 @@ class uf_info(ctypes.Structure):
         ("kernel_bytes_fp64", ctypes.c_double * 2), ("kernel_bytes_fp32", ctypes.c_double * 2),
         ("kernel_flops", ctypes.c_double * 2), ("kernel_flops_built", ctypes.c_double * 2),
         ("kernel_flops_built_fp32", ctypes.c_double * 2), ("n_vol_groups", ctypes.c_int64),
-        ("cut_lanes", ctypes.c_int32)]
+        ("cut_lane_classes", ctypes.c_int64 * 3)]
 
 
 class uf_kernel_times(ctypes.Structure):

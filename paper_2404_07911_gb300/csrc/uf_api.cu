@@ -242,11 +242,18 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   // cut cells ordered by decreasing work (points of volume, surface and cut faces)
   std::vector<int32_t> order(nc);
   std::iota(order.begin(), order.end(), 0);
+  // lane class of a cut cell (32, 16 or 8 lanes: the class's chunk holds all its volume lines and
+  // all its cut-face lines), then decreasing work within a class; classes are contiguous
   std::vector<int64_t> cost(nc);
-  for (int64_t c = 0; c < nc; ++c)
+  std::vector<int> lanes(nc);
+  for (int64_t c = 0; c < nc; ++c) {
     cost[c] = (H.vol_off[c + 1] - H.vol_off[c]) + (H.surf_off[c + 1] - H.surf_off[c]) +
               (H.cface_off[(c + 1) * nf] - H.cface_off[c * nf]);
-  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
+    lanes[c] = uf::cut_lanes_of_cell(H, c);
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    return lanes[a] != lanes[b] ? lanes[a] > lanes[b] : cost[a] > cost[b];
+  });
   std::vector<int32_t> cut_list(nc), cut_idx(nc);
   for (int64_t i = 0; i < nc; ++i) {
     cut_idx[i] = order[i];
@@ -526,9 +533,15 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   A.n_active = (int32_t)na;
   A.n_cut = (int32_t)nc;
   {
-    // lanes per cut cell from the average number of volume and cut-face lines of a cut cell
-    const double vl = nc ? (double)nvl / (double)nc : 0.0, fl = nc ? (double)nfl / (double)nc : 0.0;
-    A.cut_lanes = uf::cut_lanes_for(n, vl > fl ? vl : fl);
+    // cut_list ranges of the three lane classes (32, then 16, then 8 lanes per cut cell)
+    int32_t split[2] = {(int32_t)nc, (int32_t)nc};
+    for (int64_t i = nc - 1; i >= 0; --i) {
+      const int l = lanes[order[i]];
+      if (l <= 16) split[0] = (int32_t)i;
+      if (l <= 8) split[1] = (int32_t)i;
+    }
+    A.cut_split[0] = split[0];
+    A.cut_split[1] = split[1];
   }
   pd.n_vlines = nvl;
   pd.n_flines = nfl;
@@ -721,11 +734,10 @@ uf_status uf_get_info(const uf_operator *op, uf_info *info) {
   info->n_vol_lines = (int64_t)H.vol_lines.size();
   info->n_face_lines = (int64_t)H.face_lines.size();
   info->n_vol_groups = count_line_groups(H);
-  {
-    const double nc = (double)H.n_cut;
-    const double vl = nc > 0 ? (double)H.vol_lines.size() / nc : 0.0;
-    const double fl = nc > 0 ? (double)H.face_lines.size() / nc : 0.0;
-    info->cut_lanes = uf::cut_lanes_for(H.n, vl > fl ? vl : fl);
+  for (int k = 0; k < 3; ++k) info->cut_lane_classes[k] = 0;
+  for (int64_t c = 0; c < H.n_cut; ++c) {
+    const int l = uf::cut_lanes_of_cell(H, c);
+    ++info->cut_lane_classes[l == 32 ? 0 : (l == 16 ? 1 : 2)];
   }
   info->dim = H.dim;
   info->degree = H.p;

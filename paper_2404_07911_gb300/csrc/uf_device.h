@@ -101,14 +101,16 @@ struct DevArrays {
   const T *vline_b, *vpt_b, *spt_b, *fline_b, *fpt_b;
   int32_t kappa_uniform;
   int32_t n_active, n_cut;
-  int32_t cut_lanes;  // lanes per cut cell in the cut-cell kernel: 32, 16 or 8
+  // the cut-cell kernel gives cut_list[0 .. cut_split[0]) 32 lanes per cell, [cut_split[0] ..
+  // cut_split[1]) 16 lanes (2 cells per warp) and the rest 8 lanes (4 cells per warp)
+  int32_t cut_split[2];
 };
 
-// Lanes per cut cell in the cut-cell kernel for an operator whose cut cells carry on average
-// `lines` volume or cut-face lines (the larger of the two): groups of 8 or 16 lanes (several cut
-// cells per warp) only for n <= 5, whose rules have few lines per cell.
-inline int cut_lanes_for(int n, double lines) {
-  return (n > 5 || lines > 20.0) ? 32 : (lines > 10.0 ? 16 : 8);
+// Lanes of the cut-cell kernel for one cut cell: the smallest group (8, 16 or 32 lanes) whose
+// chunk holds all volume lines and all cut-face lines of the cell, so that small cut cells share
+// a warp; groups of 8 or 16 only for n <= 5.
+inline int cut_lanes_for(int n, int64_t lines) {
+  return (n > 5 || lines > 16) ? 32 : (lines > 8 ? 16 : 8);
 }
 
 // Launchers (uf_kernels_*.cu).  Return cudaError_t as int.

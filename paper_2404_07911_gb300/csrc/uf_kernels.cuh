@@ -743,7 +743,8 @@ __device__ __forceinline__ void cut_volume_3d(const PointTables<T, N> &pt, const
 template <typename T, int DIM, int N, int S>
 __global__ void __launch_bounds__(32) cut_kernel(const __grid_constant__ PointTables<T, N> pt,
                                                  const DevArrays<T> d, const Scalars<T> sc,
-                                                 T *__restrict__ y, const T *__restrict__ x) {
+                                                 T *__restrict__ y, const T *__restrict__ x,
+                                                 int slot_begin, int slot_end) {
   using G = Geo<DIM, N>;
   using SM = CutSmem<T, DIM, N, S>;
   constexpr int ND = G::ND, NL = G::NL, NF = G::NF;
@@ -769,8 +770,8 @@ __global__ void __launch_bounds__(32) cut_kernel(const __grid_constant__ PointTa
   int *s_tag = reinterpret_cast<int *>(sm + SM::total) + SM::itag;
 
   const int tid = threadIdx.x - gshift;
-  const int slot = blockIdx.x * CPW + grp;
-  if (slot >= d.n_cut) return;  // a whole lane group leaves together
+  const int slot = slot_begin + blockIdx.x * CPW + grp;  // cut_list range of this lane class
+  if (slot >= slot_end) return;  // a whole lane group leaves together
   const int e = __ldg(d.cut_list + slot);
   const int ci = __ldg(d.cut_idx + slot);
   const T kap = __ldg(d.kappa + e);
@@ -1116,7 +1117,8 @@ __global__ void __launch_bounds__(32) cut_kernel(const __grid_constant__ PointTa
 // ------------------------------------------------------------------------------------------
 template <typename T, int DIM, int N, int S>
 int launch_cut(const PointTables<T, N> &ptab, const DevArrays<T> &d, const Scalars<T> &s, T *y,
-               const T *x, cudaStream_t stream, void *const *ev) {
+               const T *x, cudaStream_t stream, int begin, int end) {
+  if (end <= begin) return 0;
   using SM = CutSmem<T, DIM, N, S>;
   constexpr int CPW = 32 / S;
   constexpr size_t smem = CPW * SM::stride;
@@ -1125,8 +1127,7 @@ int launch_cut(const PointTables<T, N> &ptab, const DevArrays<T> &d, const Scala
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return (int)err;
   }
-  cut_kernel<T, DIM, N, S><<<(d.n_cut + CPW - 1) / CPW, 32, smem, stream>>>(ptab, d, s, y, x);
-  if (ev) cudaEventRecord(static_cast<cudaEvent_t>(ev[3]), stream);
+  cut_kernel<T, DIM, N, S><<<(end - begin + CPW - 1) / CPW, 32, smem, stream>>>(ptab, d, s, y, x, begin, end);
   return (int)cudaGetLastError();
 }
 
@@ -1157,11 +1158,13 @@ int launch_vmult_t(const DevArrays<T> &d, const void *tables_struct, const void 
   if (ev) cudaEventRecord(static_cast<cudaEvent_t>(ev[2]), stream);
   if (d.n_cut > 0) {
     const auto &ptab = *reinterpret_cast<const PointTables<T, N> *>(tables_point);
+    // the three lane classes are contiguous in cut_list (32, 16, 8 lanes per cell)
+    int e2 = launch_cut<T, DIM, N, 32>(ptab, d, s, y, x, stream, 0, d.cut_split[0]);
     if constexpr (N <= 5) {
-      if (d.cut_lanes == 8) return launch_cut<T, DIM, N, 8>(ptab, d, s, y, x, stream, ev);
-      if (d.cut_lanes == 16) return launch_cut<T, DIM, N, 16>(ptab, d, s, y, x, stream, ev);
+      if (e2 == 0) e2 = launch_cut<T, DIM, N, 16>(ptab, d, s, y, x, stream, d.cut_split[0], d.cut_split[1]);
+      if (e2 == 0) e2 = launch_cut<T, DIM, N, 8>(ptab, d, s, y, x, stream, d.cut_split[1], d.n_cut);
     }
-    return launch_cut<T, DIM, N, 32>(ptab, d, s, y, x, stream, ev);
+    if (e2 != 0) return e2;
   }
   if (ev) cudaEventRecord(static_cast<cudaEvent_t>(ev[3]), stream);
   return (int)cudaGetLastError();

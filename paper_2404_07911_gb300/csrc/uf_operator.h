@@ -101,6 +101,13 @@ struct uf_operator {
 };
 
 namespace uf {
+// Lanes of the cut-cell kernel for cut cell c (cut_lanes_for of its volume / cut-face lines).
+inline int cut_lanes_of_cell(const HostOperator &H, int64_t c) {
+  const int nf = 2 * H.dim;
+  const int64_t vl = H.vline_off[c + 1] - H.vline_off[c];
+  const int64_t fl = H.fline_off[(c + 1) * nf] - H.fline_off[c * nf];
+  return cut_lanes_for(H.n, vl > fl ? vl : fl);
+}
 // Launch y = A x (or A^T x) of the operator's kernels on `stream` (no argument checks).
 uf_status vmult_launch(uf_operator *op, int precision, void *y, const void *x, void *stream,
                        bool adjoint);

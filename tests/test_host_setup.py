@@ -83,8 +83,12 @@ def test_line_groups():
 
 
 def test_gpu_parity_cases_cover_every_lane_group():
-    """The GPU parity cases run the cut-cell kernel with 8, 16 and 32 lanes per cut cell."""
+    """The GPU parity cases run the cut-cell kernel with 8, 16 and 32 lanes per cut cell, and
+    with all three classes in one operator."""
     import test_gpu_parity
 
-    lanes = {UnfittedOperator(cfg, device=-1).info["cut_lanes"] for cfg in test_gpu_parity.SMALL.values()}
-    assert lanes == {8, 16, 32}
+    classes = [tuple(UnfittedOperator(cfg, device=-1).info["cut_lane_classes"])
+               for cfg in test_gpu_parity.SMALL.values()]
+    for k in range(3):
+        assert any(c[k] > 0 for c in classes)
+    assert any(all(v > 0 for v in c) for c in classes)
