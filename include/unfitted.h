@@ -112,9 +112,10 @@ typedef struct {
   /* Groups of volume lines (3D): lines of a cut cell along one axis that share one outer
    * coordinate; the cut-cell kernel contracts along that coordinate once per group. */
   int64_t n_vol_groups;
-  /* Cut cells that the cut-cell kernel handles with 32, 16 and 8 lanes of a warp (a cell's
+  /* Cut cells that the FP64 cut-cell kernel handles with 32, 16 and 8 lanes of a warp (a cell's
    * group is the smallest that holds all its volume lines and all its cut-face lines in one
-   * chunk; several small cut cells share a warp), chosen at creation. */
+   * chunk; several small cut cells share a warp), chosen at creation.  The FP32 kernel uses the
+   * same classes except that the 16-lane class runs with 32 lanes. */
   int64_t cut_lane_classes[3];
 } uf_info;
 
