@@ -22,6 +22,7 @@ Interior faces: a face between two active cells K- (lower index along the axis) 
   cut   otherwise                                     (SIPG on F cap Omega, unstructured rule).
 A face carries the face-based ghost penalty iff at least one of its two cells is cut.
 """
+import math
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -64,10 +65,33 @@ def classify_plane_box(n, off, lo, hi):
     return CUT
 
 
+def crossing_spheres(prob, lo, hi):
+    """Union of balls: (inside, crossing) for the closed box: inside if one ball contains it,
+    crossing = indices of the spheres whose surface meets it."""
+    inside = False
+    crossing = []
+    for i, (c, R) in enumerate(prob.spheres):
+        t = classify_box(c, R, lo, hi)
+        if t == INSIDE:
+            inside = True
+        elif t == CUT:
+            crossing.append(i)
+    return inside, crossing
+
+
 def classify(prob, lo, hi):
-    """Type of the closed box [lo, hi] against the level set of `prob`."""
+    """Type of the closed box [lo, hi] against the level set of `prob`.  A union of balls is
+    classified box by box: inside if one ball contains it, outside if it lies outside every
+    ball, cut otherwise (the spheres must be separated: a cut box meets exactly one sphere)."""
     if prob.ls_kind == "plane":
         return classify_plane_box(prob.normal, prob.offset, lo, hi)
+    if prob.ls_kind == "spheres":
+        inside, crossing = crossing_spheres(prob, lo, hi)
+        if inside:
+            return INSIDE
+        if len(crossing) > 1:
+            raise ValueError("a box meets two spheres: the union's rules need separated spheres")
+        return CUT if crossing else OUTSIDE
     return classify_box(prob.center, prob.radius, lo, hi)
 
 
@@ -94,6 +118,7 @@ class Problem:
     offset: float = 0.0
     gp_kind: str = "face"     # "face": jumps of normal derivatives on faces; "volume": patch jumps
     gp_tau: float = 1.0       # volume ghost penalty parameter tau_v
+    spheres: tuple = None     # "spheres": ((cx, cy, cz, R), ...), the union of separated balls
     # derived
     h: float = field(init=False)
 
@@ -105,8 +130,10 @@ class Problem:
         self.center = tuple(float(v) for v in self.center[:d])
         if self.gp_kind not in ("face", "volume"):
             raise ValueError("gp_kind must be 'face' or 'volume'")
-        if self.ls_kind not in ("sphere", "plane"):
-            raise ValueError("ls_kind must be 'sphere' or 'plane'")
+        if self.ls_kind not in ("sphere", "plane", "spheres"):
+            raise ValueError("ls_kind must be 'sphere', 'plane' or 'spheres'")
+        if self.ls_kind == "spheres":
+            self.spheres = tuple((tuple(float(v) for v in sp[:d]), float(sp[3])) for sp in self.spheres)
         if self.ls_kind == "plane":
             self.normal = tuple(float(v) for v in self.normal[:d])
             self.offset = float(self.offset)
@@ -130,7 +157,8 @@ class Problem:
 def problem_from_dict(cfg, kappa=None):
     keys = ["dim", "degree", "n_cells", "lo", "hi", "center", "radius", "quad_order",
             "sipg_gamma", "nitsche_gamma", "gp_max_order", "gp_gamma"]
-    extra = {k: cfg[k] for k in ("ls_kind", "normal", "offset", "gp_kind", "gp_tau") if k in cfg}
+    extra = {k: cfg[k] for k in ("ls_kind", "normal", "offset", "gp_kind", "gp_tau", "spheres")
+             if k in cfg}
     return Problem(**{k: cfg[k] for k in keys}, kappa=kappa, **extra)
 
 
@@ -170,8 +198,13 @@ class Mesh:
             e = np.maximum(np.maximum(dl, 0.0), -dh)
             dmin2 = dmin2 + (e * e).reshape(bshape)
             dmax2 = dmax2 + np.maximum(dl * dl, dh * dh).reshape(bshape)
-        t = np.full(shape, CUT, dtype=np.int8)
-        if prob.ls_kind == "plane":
+        if prob.ls_kind == "spheres":
+            t = self._classify_spheres(prob)
+        else:
+            t = np.full(shape, CUT, dtype=np.int8)
+        if prob.ls_kind == "spheres":
+            pass
+        elif prob.ls_kind == "plane":
             t[dmin2 - prob.offset >= 0.0] = OUTSIDE
             t[dmax2 - prob.offset <= 0.0] = INSIDE
         else:
@@ -193,6 +226,48 @@ class Mesh:
         else:
             self.kappa = np.asarray(prob.kappa, dtype=np.float64)
             assert self.kappa.shape == (self.n_active,)
+
+    @staticmethod
+    def _classify_spheres(prob):
+        """Cell types of a union of separated balls: each ball updates the cells of its bounding
+        box with the arithmetic of classify_box."""
+        d = prob.dim
+        N = prob.n_cells
+        shape = tuple(N[::-1])
+        inside = np.zeros(shape, dtype=bool)
+        count = np.zeros(shape, dtype=np.int32)
+        for (c, R) in prob.spheres:
+            rng = []
+            for a in range(d):
+                i0 = max(0, int(math.floor((c[a] - R - prob.lo[a]) / prob.hvec[a])) - 1)
+                i1 = min(N[a], int(math.floor((c[a] + R - prob.lo[a]) / prob.hvec[a])) + 2)
+                rng.append((i0, i1))
+            if any(i1 <= i0 for i0, i1 in rng):
+                continue
+            sub = tuple(i1 - i0 for i0, i1 in rng)[::-1]
+            dmin2 = np.zeros(sub)
+            dmax2 = np.zeros(sub)
+            for a in range(d):
+                idx = np.arange(rng[a][0], rng[a][1], dtype=np.float64)
+                lo = prob.lo[a] + idx * prob.hvec[a]
+                hi = prob.lo[a] + (idx + 1) * prob.hvec[a]
+                dl = lo - c[a]
+                dh = hi - c[a]
+                e = np.maximum(np.maximum(dl, 0.0), -dh)
+                bshape = [1] * d
+                bshape[d - 1 - a] = len(idx)
+                dmin2 = dmin2 + (e * e).reshape(bshape)
+                dmax2 = dmax2 + np.maximum(dl * dl, dh * dh).reshape(bshape)
+            sl = tuple(slice(i0, i1) for i0, i1 in rng)[::-1]
+            r2 = R * R
+            inside[sl] |= dmax2 <= r2
+            count[sl] += ((dmin2 < r2) & (dmax2 > r2)).astype(np.int32)
+        if np.any((count > 1) & ~inside):
+            raise ValueError("a cell meets two spheres: the union's rules need separated spheres")
+        t = np.full(shape, OUTSIDE, dtype=np.int8)
+        t[count == 1] = CUT
+        t[inside] = INSIDE
+        return t
 
     @property
     def active(self):

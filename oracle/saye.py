@@ -401,11 +401,27 @@ def plane_rules(lo, hi, n, off, q, surface=True):
     return vol, surf
 
 
+def _crossing_sphere(prob, lo, hi):
+    """Union of separated balls: the one sphere whose surface meets the closed box."""
+    hits = []
+    for (c, R) in prob.spheres:
+        dmin2, dmax2 = _box_dist2(c, lo, hi)
+        if dmin2 < R * R < dmax2:
+            hits.append((c, R))
+    if len(hits) != 1:
+        raise QuadratureError("a cut box must meet exactly one sphere of the union")
+    return hits[0]
+
+
 def cell_rules(prob, lo, hi, q=None):
-    """Volume and surface rule of the cell [lo, hi] cut by the level set of `prob`."""
+    """Volume and surface rule of the cell [lo, hi] cut by the level set of `prob` (for a union
+    of separated balls: by the one sphere that meets the cell)."""
     q = prob.quad_order if q is None else q
     if prob.ls_kind == "plane":
         return plane_rules(lo, hi, prob.normal, prob.offset, q)
+    if prob.ls_kind == "spheres":
+        c, R = _crossing_sphere(prob, lo, hi)
+        return sphere_rules(lo, hi, c, R * R, q)
     R = prob.radius
     return sphere_rules(lo, hi, prob.center, R * R, q)
 
@@ -418,9 +434,10 @@ def face_rule(prob, face_lo, face_hi, axis, q=None):
         vol, _ = plane_rules(_drop(face_lo, axis), _drop(face_hi, axis), _drop(prob.normal, axis),
                              prob.offset - prob.normal[axis] * xa, q, surface=False)
     else:
-        R = prob.radius
-        da = xa - prob.center[axis]
+        c, R = _crossing_sphere(prob, face_lo, face_hi) if prob.ls_kind == "spheres" else \
+            (prob.center, prob.radius)
+        da = xa - c[axis]
         rho = R * R - da * da
-        vol, _ = sphere_rules(_drop(face_lo, axis), _drop(face_hi, axis), _drop(prob.center, axis),
+        vol, _ = sphere_rules(_drop(face_lo, axis), _drop(face_hi, axis), _drop(c, axis),
                               rho, q, surface=False)
     return [(_insert(x, axis, xa), wt) for (x, wt) in vol]

@@ -272,3 +272,54 @@ def test_plane_classification_against_sampling():
         e = m.id_map[idx[::-1]]
         got = mesh.OUTSIDE if e < 0 else m.active_type[e]
         assert got == want
+
+
+# ------------------------------------------------------------------------------------------
+# Union of separated balls: each cut cell meets one sphere, whose rule it uses
+# ------------------------------------------------------------------------------------------
+
+_EIGHT = [(0.25 + 0.5 * i, 0.26 + 0.5 * j, 0.24 + 0.5 * k, 0.2 - 0.01 * (i + j + k))
+          for k in range(2) for j in range(2) for i in range(2)]
+
+
+def _spheres_prob(N, q, spheres=_EIGHT):
+    return mesh.Problem(3, 2, (N,) * 3, (0.0,) * 3, (1.0,) * 3, (0.0,) * 3, 1.0, q, 1, 1, 1, 0.5,
+                        ls_kind="spheres", spheres=spheres)
+
+
+def test_union_of_separated_balls_converges():
+    vol = sum(4.0 / 3.0 * math.pi * R ** 3 for *_, R in _EIGHT)
+    area = sum(4.0 * math.pi * R ** 2 for *_, R in _EIGHT)
+    errs = []
+    for N in (10, 20, 40):
+        _, vw, sx, sw, sn = _all_rules(_spheres_prob(N, 4))
+        errs.append((abs(vw.sum() - vol) / vol, abs(sw.sum() - area) / area))
+        assert np.abs(np.linalg.norm(sn, axis=1) - 1.0).max() < 1e-14
+    assert errs[-1][0] < 1e-8 and errs[-1][1] < 1e-7
+    # high order: at least h^4 per halving over two halvings
+    assert errs[0][0] / errs[2][0] > 16 ** 2 and errs[0][1] / errs[2][1] > 16 ** 2
+
+
+def test_union_classification_against_sampling():
+    prob = _spheres_prob(12, 2)
+    m = mesh.Mesh(prob)
+    t = np.linspace(0.0, 1.0, 7)
+    for flat in range(0, 12 ** 3, 5):
+        idx = (flat % 12, (flat // 12) % 12, flat // 144)
+        lo, hi = mesh.cell_box(prob, idx)
+        g = np.stack(np.meshgrid(*[lo[a] + t * (hi[a] - lo[a]) for a in range(3)]), -1).reshape(-1, 3)
+        phi = np.min([np.linalg.norm(g - np.array(c[:3]), axis=1) - R for *c, R in _EIGHT], axis=0)
+        e = m.id_map[idx[::-1]]
+        got = mesh.OUTSIDE if e < 0 else m.active_type[e]
+        if phi.max() < 0:
+            assert got == mesh.INSIDE
+        elif phi.min() > 0:
+            assert got == mesh.OUTSIDE
+        else:
+            assert got == mesh.CUT
+
+
+def test_union_rejects_a_cell_that_meets_two_spheres():
+    touching = [(0.3, 0.5, 0.5, 0.21), (0.72, 0.5, 0.5, 0.2)]
+    with pytest.raises(ValueError):
+        mesh.Mesh(_spheres_prob(8, 2, touching))
