@@ -63,13 +63,15 @@ def parse_args():
                          "(tau_v = 1)")
     ap.add_argument("--no-csr", action="store_true",
                     help="skip the assembled-matrix (CSR SpMV) comparison")
-    ap.add_argument("--config", choices=("q3", "solve", "sweep", "kappa", "plane", "accuracy"),
+    ap.add_argument("--config", choices=("q3", "solve", "sweep", "kappa", "plane", "accuracy",
+                                         "spheres"),
                     default="q3",
                     help="q3: the headline step (default); solve: CG Q4 time to solution, IR vs "
                          "FP64; sweep: degree sweep p = 1..8 at ~2e7 DoFs; kappa: forward vs "
                          "forward + backward of the differentiable operator; plane: throughput "
                          "against the ratio of cut cells (DG Q1, CG Q3); accuracy: convergence of "
-                         "the sphere accuracy benchmark (CG, DG, p = 1..4)")
+                         "the sphere accuracy benchmark (CG, DG, p = 1..4); spheres: the "
+                         "regular 1000-spheres benchmark (DG Q1)")
     return ap.parse_args()
 
 
@@ -533,6 +535,60 @@ def run_accuracy(args, local):
                 op.close()
 
 
+def run_spheres(args, local):
+    """Regular-spheres benchmark: 1000 separated balls, 192^3 background cells, DG Q1 (about
+    1.5e7 DoFs, cut-cell ratio 0.48): MDoF/s of A x in FP64 and FP32, rows of cut and inside
+    cells sampled against the oracle."""
+    import torch
+
+    from oracle import forms, mesh
+    from paper_2404_07911_gb300 import UF_FP32, UF_FP64, UnfittedOperator
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    cfg = workloads.cfg_spheres_regular()
+    t0 = time.perf_counter()
+    op = UnfittedOperator(cfg, precisions=UF_FP64 | UF_FP32, device=local)
+    t_setup = time.perf_counter() - t0
+    n = op.n_dofs
+    xh = workloads.uniform_vector(n, cfg["seed"])
+    x64 = torch.from_numpy(xh).cuda()
+    x32 = x64.float()
+    y64 = torch.empty_like(x64)
+    y32 = torch.empty_like(x32)
+    for _ in range(3):
+        op.vmult(x64, y64, stream)
+        op.vmult(x32, y32, stream)
+    K = 20
+    op.profile_begin(2 * K)
+    ms64 = _event_ms(lambda: op.vmult(x64, y64, stream), K, stream, flush)
+    ms32 = _event_ms(lambda: op.vmult(x32, y32, stream), K, stream, flush)
+    kt = op.profile_end()
+    info = op.info
+    o = forms.Oracle(mesh.problem_from_dict(cfg))
+    cut = np.nonzero(o.mesh.active_type == mesh.CUT)[0]
+    ins = np.nonzero(o.mesh.active_type == mesh.INSIDE)[0]
+    rng = np.random.default_rng(1)
+    cells = sorted(set(int(c) for c in list(rng.choice(cut, 4, replace=False)) +
+                       list(rng.choice(ins, 2, replace=False))))
+    nd = info["dofs_per_cell"]
+    ref = o.apply_rows(xh, cells)
+    g64 = y64.cpu().numpy().reshape(-1, nd)[cells]
+    print(json.dumps({
+        "metric": "regular spheres benchmark: MDoF/s of A x",
+        "config": {"workload": cfg["name"], "n_dofs": n, "n_active": info["n_active"],
+                   "n_cut": info["n_cut"], "cut_ratio": round(info["n_cut"] / info["n_active"], 4),
+                   "lane_classes": list(info["cut_lane_classes"]), "setup_s": round(t_setup, 2)},
+        "fp64": {"ms": round(ms64, 4), "mdofs": round(n / ms64 / 1e3, 1),
+                 "rel_err": float(np.max(np.abs(g64 - ref)) / np.max(np.abs(ref)))},
+        "fp32": {"ms": round(ms32, 4), "mdofs": round(n / ms32 / 1e3, 1)},
+        "kernel_ms": {f"{kern}_{prec}": round(tot / cnt, 4)
+                      for (prec, kern, _), (tot, cnt) in sorted(kt.items())},
+        "l2": "flushed before every launch"}), flush=True)
+    op.close()
+
+
 def run_solve(args, local):
     """CG Q4 ball solve: FP32 PCG inside FP64 refinement vs all-FP64 PCG, same final residual."""
     import torch
@@ -713,6 +769,8 @@ def main():
         run_plane(args, local)
     elif args.config == "accuracy":
         run_accuracy(args, local)
+    elif args.config == "spheres":
+        run_spheres(args, local)
     else:
         run_ours(args, rank, world, local)
 

@@ -46,7 +46,7 @@ typedef enum {
 } uf_status;
 
 enum { UF_FP64 = 1, UF_FP32 = 2 };     /* precision flags (bit mask in uf_params.precisions) */
-enum { UF_LS_SPHERE = 0, UF_LS_PLANE = 1 };  /* level set kinds */
+enum { UF_LS_SPHERE = 0, UF_LS_PLANE = 1, UF_LS_SPHERES = 2 };  /* level set kinds */
 enum { UF_DG = 0, UF_CG = 1 };         /* discretizations (uf_params.discretization) */
 enum { UF_GP_FACE = 0, UF_GP_VOLUME = 1 }; /* ghost penalties (uf_params.gp_kind) */
 
@@ -82,6 +82,11 @@ typedef struct {
                              the own polynomial minus the neighbour's extended one (Sec. 3.4).  Either
                              is off when gp_max_order = 0. */
   double gp_tau;          /* tau_v of UF_GP_VOLUME */
+  const double *ls_spheres;  /* UF_LS_SPHERES: host array [ls_n_spheres][4] = (cx, cy, cz, R), copied
+                                at creation; the domain is the union of the balls, which must be
+                                separated so that no cell or face meets two spheres (UF_EGEOMETRY
+                                otherwise): each cut cell / face uses the rule of its one sphere */
+  int ls_n_spheres;
 } uf_params;
 
 /* Sizes and algorithmic traffic of an operator (uf_get_info). */

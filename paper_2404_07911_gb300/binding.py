@@ -15,6 +15,7 @@ UF_OK, UF_EINVAL, UF_ENOMEM, UF_ECUDA, UF_EUNSUPPORTED, UF_EGEOMETRY, UF_ENODEVI
 UF_FP64, UF_FP32 = 1, 2
 UF_LS_SPHERE = 0
 UF_LS_PLANE = 1
+UF_LS_SPHERES = 2
 UF_DG, UF_CG = 0, 1
 UF_GP_FACE, UF_GP_VOLUME = 0, 1
 
@@ -51,6 +52,8 @@ class uf_params(ctypes.Structure):
         ("ls_offset", ctypes.c_double),
         ("gp_kind", ctypes.c_int),
         ("gp_tau", ctypes.c_double),
+        ("ls_spheres", ctypes.POINTER(ctypes.c_double)),
+        ("ls_n_spheres", ctypes.c_int),
     ]
 
 
@@ -193,6 +196,12 @@ class UnfittedOperator:
         if kappa is not None:
             self._keep = np.ascontiguousarray(kappa, dtype=np.float64)
             params.kappa = self._keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        spheres = None
+        if cfg.get("ls_kind", "sphere") == "spheres":
+            spheres = np.ascontiguousarray(np.asarray(cfg["spheres"], dtype=np.float64).reshape(-1, 4))
+            params.ls_kind = UF_LS_SPHERES
+            params.ls_spheres = spheres.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            params.ls_n_spheres = len(spheres)
         handle = ctypes.c_void_p()
         _check(lib.uf_create_unfitted_operator(ctypes.byref(params), ctypes.byref(handle)))
         self._h = handle

@@ -67,6 +67,8 @@ struct HostOperator {
   int ls_kind = 0;                      // UF_LS_SPHERE or UF_LS_PLANE
   double normal[kMaxDim] = {0, 0, 0};   // plane: phi = normal . x - offset
   double offset = 0;
+  std::vector<double> spheres;          // union of separated balls: [n][4] = (cx, cy, cz, R)
+  std::vector<int32_t> cut_sphere;      // [n_cut] the one sphere that meets each cut cell
 
   Tables1D t;
 

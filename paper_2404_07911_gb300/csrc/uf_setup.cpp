@@ -659,6 +659,53 @@ void build_tables_1d(int p, Tables1D &t) {
     }
 }
 
+namespace {
+
+// Union of separated balls: the spheres of the cut cells among the two cells of a face.
+int union_face_candidates(const HostOperator &op, int64_t e, int64_t nb, int32_t *cand) {
+  int n = 0;
+  for (int64_t c : {e, nb}) {
+    if (c < 0 || op.act_type[c] != 1) continue;
+    const int32_t s = op.cut_sphere[op.cut_of[c]];
+    if (n == 0 || cand[0] != s) cand[n++] = s;
+  }
+  return n;
+}
+
+// Type of a face of the union of separated balls: 0 full (in a ball), 1 cut, 2 empty, -1 if it
+// meets two spheres.  A face of an inside cell lies in that cell's ball; otherwise every ball that
+// contains or meets the face meets both (cut) cells, so their spheres are the only candidates.
+int union_face_type(const HostOperator &op, const Box &fb, int64_t e, int64_t nb) {
+  if (op.act_type[e] == 0 || op.act_type[nb] == 0) return 0;
+  int32_t cand[2];
+  const int n = union_face_candidates(op, e, nb, cand);
+  int crossing = 0;
+  for (int i = 0; i < n; ++i) {
+    const double *sp = &op.spheres[4 * (size_t)cand[i]];
+    double dmin2, dmax2;
+    box_dist2(sp, fb, dmin2, dmax2);
+    const double r2 = sp[3] * sp[3];
+    if (dmax2 <= r2) return 0;
+    if (dmin2 < r2 && dmax2 > r2) ++crossing;
+  }
+  return crossing == 0 ? 2 : (crossing == 1 ? 1 : -1);
+}
+
+// The one sphere that meets a cut face of the union.
+const double *union_face_sphere(const HostOperator &op, const Box &fb, int64_t e, int64_t nb) {
+  int32_t cand[2];
+  const int n = union_face_candidates(op, e, nb, cand);
+  for (int i = 0; i < n; ++i) {
+    const double *sp = &op.spheres[4 * (size_t)cand[i]];
+    double dmin2, dmax2;
+    box_dist2(sp, fb, dmin2, dmax2);
+    if (dmin2 < sp[3] * sp[3] && dmax2 > sp[3] * sp[3]) return sp;
+  }
+  return &op.spheres[4 * (size_t)cand[0]];  // not reached for a cut face
+}
+
+}  // namespace
+
 uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::string &msg) {
   op.params = prm;
   op.params.kappa = nullptr;
@@ -679,9 +726,23 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
     msg = "gp_max_order must be in 0..degree";
     return UF_EINVAL;
   }
-  if (prm.ls_kind != UF_LS_SPHERE && prm.ls_kind != UF_LS_PLANE) {
-    msg = "ls_kind must be UF_LS_SPHERE or UF_LS_PLANE";
+  if (prm.ls_kind != UF_LS_SPHERE && prm.ls_kind != UF_LS_PLANE && prm.ls_kind != UF_LS_SPHERES) {
+    msg = "ls_kind must be UF_LS_SPHERE, UF_LS_PLANE or UF_LS_SPHERES";
     return UF_EUNSUPPORTED;
+  }
+  if (prm.ls_kind == UF_LS_SPHERES) {
+    if (!prm.ls_spheres || prm.ls_n_spheres < 1) {
+      msg = "UF_LS_SPHERES needs ls_spheres and ls_n_spheres >= 1";
+      return UF_EINVAL;
+    }
+    for (int i = 0; i < prm.ls_n_spheres; ++i) {
+      bool ok = prm.ls_spheres[4 * i + 3] > 0.0 && std::isfinite(prm.ls_spheres[4 * i + 3]);
+      for (int a = 0; a < 3; ++a) ok = ok && std::isfinite(prm.ls_spheres[4 * i + a]);
+      if (!ok) {
+        msg = "every sphere needs a finite centre and a positive radius";
+        return UF_EINVAL;
+      }
+    }
   }
   if (prm.ls_kind == UF_LS_SPHERE && !(prm.ls_radius > 0.0)) {
     msg = "ls_radius must be positive";
@@ -748,6 +809,10 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
   op.radius = prm.ls_radius;
   op.ls_kind = prm.ls_kind;
   op.offset = prm.ls_offset;
+  if (op.ls_kind == UF_LS_SPHERES) {
+    op.spheres.assign(prm.ls_spheres, prm.ls_spheres + 4 * (size_t)prm.ls_n_spheres);
+    op.params.ls_spheres = nullptr;  // the caller's array is not kept
+  }
   // type of a closed box (d-dimensional, possibly a face): 0 inside, 1 cut, 2 outside
   auto classify = [&](const Box &b) {
     double lo_v, hi_v;
@@ -765,17 +830,66 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
   op.n_background = total;
   op.id_map.assign(total, -1);
   std::vector<int8_t> bg_type(total);
-  for (int64_t flat = 0; flat < total; ++flat) {
-    Box b;
-    b.m = d;
-    int64_t rem = flat;
-    for (int a = 0; a < d; ++a) {
-      const int64_t I = rem % op.N[a];
-      rem /= op.N[a];
-      b.lo[a] = op.lo[a] + (double)I * hv[a];
-      b.hi[a] = op.lo[a] + (double)(I + 1) * hv[a];
+  std::vector<int32_t> bg_sphere;  // union of balls: the one sphere that meets a cut cell
+  if (op.ls_kind == UF_LS_SPHERES) {
+    // every ball updates the cells of its bounding box (cells beyond it lie outside the ball)
+    std::vector<uint8_t> inside(total, 0), crossings(total, 0);
+    bg_sphere.assign(total, -1);
+    const int ns = (int)(op.spheres.size() / 4);
+    for (int i = 0; i < ns; ++i) {
+      const double *c = &op.spheres[4 * i];
+      const double R = c[3], r2 = R * R;
+      int64_t i0[kMaxDim] = {0, 0, 0}, i1[kMaxDim] = {1, 1, 1};
+      bool empty = false;
+      for (int a = 0; a < d; ++a) {
+        i0[a] = std::max<int64_t>(0, (int64_t)std::floor((c[a] - R - op.lo[a]) / hv[a]) - 1);
+        i1[a] = std::min<int64_t>(op.N[a], (int64_t)std::floor((c[a] + R - op.lo[a]) / hv[a]) + 2);
+        empty = empty || i1[a] <= i0[a];
+      }
+      if (empty) continue;
+      for (int64_t k = i0[2]; k < i1[2]; ++k)
+        for (int64_t j = i0[1]; j < i1[1]; ++j)
+          for (int64_t ii = i0[0]; ii < i1[0]; ++ii) {
+            const int64_t I[3] = {ii, j, k};
+            Box b;
+            b.m = d;
+            int64_t flat = 0, stride = 1;
+            for (int a = 0; a < d; ++a) {
+              b.lo[a] = op.lo[a] + (double)I[a] * hv[a];
+              b.hi[a] = op.lo[a] + (double)(I[a] + 1) * hv[a];
+              flat += I[a] * stride;
+              stride *= op.N[a];
+            }
+            double dmin2, dmax2;
+            box_dist2(c, b, dmin2, dmax2);
+            if (dmax2 <= r2) {
+              inside[flat] = 1;
+            } else if (dmin2 < r2 && dmax2 > r2) {
+              if (crossings[flat] < 255) ++crossings[flat];
+              bg_sphere[flat] = i;
+            }
+          }
     }
-    bg_type[flat] = (int8_t)classify(b);
+    for (int64_t flat = 0; flat < total; ++flat) {
+      if (!inside[flat] && crossings[flat] > 1) {
+        msg = "a cell meets two spheres: UF_LS_SPHERES needs separated spheres";
+        return UF_EGEOMETRY;
+      }
+      bg_type[flat] = inside[flat] ? 0 : (crossings[flat] == 1 ? 1 : 2);
+    }
+  } else {
+    for (int64_t flat = 0; flat < total; ++flat) {
+      Box b;
+      b.m = d;
+      int64_t rem = flat;
+      for (int a = 0; a < d; ++a) {
+        const int64_t I = rem % op.N[a];
+        rem /= op.N[a];
+        b.lo[a] = op.lo[a] + (double)I * hv[a];
+        b.hi[a] = op.lo[a] + (double)(I + 1) * hv[a];
+      }
+      bg_type[flat] = (int8_t)classify(b);
+    }
   }
   for (int64_t flat = 0; flat < total; ++flat) {
     if (bg_type[flat] == 2) continue;
@@ -812,6 +926,14 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
       op.flags[e] |= kCellCut;
       op.cut_of[e] = (int32_t)op.n_cut++;
       op.cut_cells.push_back((int32_t)e);
+      if (op.ls_kind == UF_LS_SPHERES) {
+        int64_t flat = 0, stride = 1;
+        for (int a = 0; a < d; ++a) {
+          flat += (int64_t)op.act_index[e * 3 + a] * stride;
+          stride *= op.N[a];
+        }
+        op.cut_sphere.push_back(bg_sphere[flat]);
+      }
     } else {
       ++op.n_inside;
     }
@@ -846,7 +968,18 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
         const int f = 2 * axis + side;
         op.nbr[e * nf + f] = nb;
         const int64_t e_minus = side ? e : nb;
-        const int ftype = classify(face_box(e_minus, axis));  // full, cut, empty
+        int ftype;  // 0 full, 1 cut, 2 empty
+        if (op.ls_kind == UF_LS_SPHERES) {
+          // a face lies in a closed inside cell, or meets (or lies in) only the spheres of its two
+          // cut cells
+          ftype = union_face_type(op, face_box(e_minus, axis), e, nb);
+          if (ftype < 0) {
+            msg = "a face meets two spheres: UF_LS_SPHERES needs separated spheres";
+            return UF_EGEOMETRY;
+          }
+        } else {
+          ftype = classify(face_box(e_minus, axis));
+        }
         const bool gp = use_gp && !volume_gp && (op.act_type[e] == 1 || op.act_type[nb] == 1);
         // the continuous space has no SIPG term
         if (ftype == 0 && !op.cg) op.flags[e] |= face_bit_sipg_full(f);
@@ -890,10 +1023,14 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
       vol.clear();
       surf.clear();
       lines.clear();
-      if (op.ls_kind == UF_LS_PLANE)
+      if (op.ls_kind == UF_LS_PLANE) {
         plane_box_rules(b, op.normal, op.offset, g, true, vol, surf, &lines);
-      else
+      } else if (op.ls_kind == UF_LS_SPHERES) {
+        const double *sp = &op.spheres[4 * (size_t)op.cut_sphere[c]];
+        sphere_box_rules(b, sp, sp[3] * sp[3], g, 0, true, vol, surf, &lines);
+      } else {
         sphere_box_rules(b, op.center, op.radius * op.radius, g, 0, true, vol, surf, &lines);
+      }
       const int64_t vbase = (int64_t)op.vol_w.size(), sbase = (int64_t)op.surf_w.size();
       for (const QLine &ln : lines)
         op.vol_lines.push_back(QLine{ln.k, vbase + ln.vbeg, ln.vcnt, ln.sidx >= 0 ? sbase + ln.sidx : -1});
@@ -926,10 +1063,17 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
             drop_vec(op.normal, d, axis, nsub);
             plane_box_rules(sub, nsub, op.offset - op.normal[axis] * xa, g, false, fq, dummy, &lines);
           } else {
-            const double da = xa - op.center[axis];
-            const double rho = op.radius * op.radius - da * da;
+            const double *cen = op.center;
+            double R = op.radius;
+            if (op.ls_kind == UF_LS_SPHERES) {
+              const double *sp = union_face_sphere(op, fb, e, op.nbr[e * nf + f]);
+              cen = sp;
+              R = sp[3];
+            }
+            const double da = xa - cen[axis];
+            const double rho = R * R - da * da;
             double csub[kMaxDim];
-            drop_vec(op.center, d, axis, csub);
+            drop_vec(cen, d, axis, csub);
             sphere_box_rules(sub, csub, rho, g, 0, false, fq, dummy, &lines);
           }
           const int64_t fbase = (int64_t)op.cface_w.size();

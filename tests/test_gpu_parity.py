@@ -58,6 +58,9 @@ SMALL = {
     # volume-based ghost penalty on stable-neighbour patches
     "3d_q3_6_volume_gp": dict(workloads.small(p=3, N=6), gp_kind="volume", gp_tau=0.7),
     "2d_q2_10_volume_gp": dict(workloads.small(p=2, N=10, dim=2), gp_kind="volume"),
+    # unions of separated balls
+    "3d_spheres_q2_10": workloads.spheres(p=2, N=10, m=2, R=0.2),
+    "2d_spheres_q3_16": workloads.spheres(p=3, N=16, m=3, R=0.12, dim=2),
     # half-spaces below tilted planes (the plane benchmark's geometry)
     "2d_plane_q2_7": workloads.plane(p=2, N=7, dim=2),
     "3d_plane_q1_6": workloads.plane(p=1, N=6, dim=3),

@@ -153,3 +153,34 @@ def cfg_plane(discretization, p, ratio, n_dofs=2.0e7):
     c["name"] = f"3d_{discretization}_q{p}_plane_ratio_{ratio:g}"
     return c
 
+
+def sphere_lattice(m, R, dim=3):
+    """m^d balls of radius R centred on the lattice (i + 1/2) / m of the unit box."""
+    out = []
+    for k in range(m if dim == 3 else 1):
+        for j in range(m):
+            for i in range(m):
+                out.append(((i + 0.5) / m, (j + 0.5) / m, (k + 0.5) / m if dim == 3 else 0.0, R))
+    return out
+
+
+def spheres(p=2, N=12, m=2, R=0.2, dim=3, discretization="dg", quad_order=None, seed=11):
+    """Union of m^d separated balls of radius R on a lattice in [0, 1]^d, N cells per direction;
+    penalties as for the ball workloads."""
+    pad = (0.0,) * (3 - dim)
+    return dict(name=f"{dim}d_{discretization}_q{p}_{m}^{dim}_spheres_{N}", dim=dim, degree=p,
+                n_cells=(N,) * dim + (1,) * (3 - dim), lo=(0.0,) * dim + pad, hi=(1.0,) * dim + pad,
+                center=(0.0, 0.0, 0.0), radius=1.0, ls_kind="spheres",
+                spheres=sphere_lattice(m, R, dim), quad_order=quad_order if quad_order else p + 1,
+                seed=seed, discretization=discretization, **_penalties(p))
+
+
+def cfg_spheres_regular(p=1, discretization="dg"):
+    """The paper's regular-spheres benchmark (Sec. 6): 1000 balls on a regular pattern; their
+    radius and placement are not given, so: the 10^3 lattice of the unit cube, radius 0.0362
+    (fitted to the printed DoF count and cut-cell ratio), 12^3 background cells refined four
+    times (192^3), DG Q1."""
+    c = spheres(p=p, N=192, m=10, R=0.0362, discretization=discretization, seed=12)
+    c["name"] = f"3d_{discretization}_q{p}_1000_spheres_192^3"
+    return c
+
