@@ -81,16 +81,15 @@ def crossing_spheres(prob, lo, hi):
 
 def classify(prob, lo, hi):
     """Type of the closed box [lo, hi] against the level set of `prob`.  A union of balls is
-    classified box by box: inside if one ball contains it, outside if it lies outside every
-    ball, cut otherwise (the spheres must be separated: a cut box meets exactly one sphere)."""
+    classified box by box: inside if one ball contains it, cut if a sphere meets it, outside
+    otherwise (a box covered by several balls but by none alone is cut, with a full volume
+    rule and no surface points)."""
     if prob.ls_kind == "plane":
         return classify_plane_box(prob.normal, prob.offset, lo, hi)
     if prob.ls_kind == "spheres":
         inside, crossing = crossing_spheres(prob, lo, hi)
         if inside:
             return INSIDE
-        if len(crossing) > 1:
-            raise ValueError("a box meets two spheres: the union's rules need separated spheres")
         return CUT if crossing else OUTSIDE
     return classify_box(prob.center, prob.radius, lo, hi)
 
@@ -118,7 +117,7 @@ class Problem:
     offset: float = 0.0
     gp_kind: str = "face"     # "face": jumps of normal derivatives on faces; "volume": patch jumps
     gp_tau: float = 1.0       # volume ghost penalty parameter tau_v
-    spheres: tuple = None     # "spheres": ((cx, cy, cz, R), ...), the union of separated balls
+    spheres: tuple = None     # "spheres": ((cx, cy, cz, R), ...), the union of these balls
     # derived
     h: float = field(init=False)
 
@@ -229,8 +228,9 @@ class Mesh:
 
     @staticmethod
     def _classify_spheres(prob):
-        """Cell types of a union of separated balls: each ball updates the cells of its bounding
-        box with the arithmetic of classify_box."""
+        """Cell types of a union of balls: each ball updates the cells of its bounding box with
+        the arithmetic of classify_box (inside if one ball contains the cell, cut if a sphere
+        meets it)."""
         d = prob.dim
         N = prob.n_cells
         shape = tuple(N[::-1])
@@ -262,10 +262,8 @@ class Mesh:
             r2 = R * R
             inside[sl] |= dmax2 <= r2
             count[sl] += ((dmin2 < r2) & (dmax2 > r2)).astype(np.int32)
-        if np.any((count > 1) & ~inside):
-            raise ValueError("a cell meets two spheres: the union's rules need separated spheres")
         t = np.full(shape, OUTSIDE, dtype=np.int8)
-        t[count == 1] = CUT
+        t[count >= 1] = CUT
         t[inside] = INSIDE
         return t
 

@@ -319,7 +319,128 @@ def test_union_classification_against_sampling():
             assert got == mesh.CUT
 
 
-def test_union_rejects_a_cell_that_meets_two_spheres():
-    touching = [(0.3, 0.5, 0.5, 0.21), (0.72, 0.5, 0.5, 0.2)]
-    with pytest.raises(ValueError):
-        mesh.Mesh(_spheres_prob(8, 2, touching))
+# Intersecting balls: two with a lens, three meeting at triple points (generic positions)
+_TWO = [(0.43, 0.47, 0.52, 0.26), (0.71, 0.58, 0.46, 0.19)]
+_THREE = [(0.41, 0.45, 0.5, 0.24), (0.66, 0.52, 0.47, 0.21), (0.52, 0.71, 0.55, 0.205)]
+
+
+def _union_two_closed_forms(balls):
+    """Volume and area of the union of two intersecting balls (lens by two spherical caps)."""
+    (x1, y1, z1, R1), (x2, y2, z2, R2) = balls
+    D = math.sqrt((x2 - x1) ** 2 + (y2 - y1) ** 2 + (z2 - z1) ** 2)
+    a1 = (D * D + R1 * R1 - R2 * R2) / (2 * D)
+    h1 = R1 - a1
+    h2 = R2 - (D - a1)
+    cap = lambda R, h: math.pi * h * h * (3 * R - h) / 3.0
+    vol = 4.0 / 3.0 * math.pi * (R1 ** 3 + R2 ** 3) - cap(R1, h1) - cap(R2, h2)
+    area = 4.0 * math.pi * (R1 * R1 + R2 * R2) - 2.0 * math.pi * (R1 * h1 + R2 * h2)
+    return vol, area
+
+
+def test_union_of_two_intersecting_balls_converges():
+    vol, area = _union_two_closed_forms(_TWO)
+    errs = []
+    for N in (8, 16, 32):
+        _, vw, sx, sw, sn = _all_rules(_spheres_prob(N, 4, _TWO))
+        errs.append((abs(vw.sum() - vol) / vol, abs(sw.sum() - area) / area))
+        assert np.abs(np.linalg.norm(sn, axis=1) - 1.0).max() < 1e-14
+    assert errs[-1][0] < 1e-9 and errs[-1][1] < 5e-8
+    assert errs[0][0] / errs[2][0] > 16 ** 2 and errs[0][1] / errs[2][1] > 16 ** 2
+
+
+def test_union_of_two_intersecting_discs():
+    (x1, y1, _, R1), (x2, y2, _, R2) = _TWO
+    D = math.hypot(x2 - x1, y2 - y1)
+    lens = (R1 * R1 * math.acos((D * D + R1 * R1 - R2 * R2) / (2 * D * R1))
+            + R2 * R2 * math.acos((D * D + R2 * R2 - R1 * R1) / (2 * D * R2))
+            - 0.5 * math.sqrt((-D + R1 + R2) * (D + R1 - R2) * (D - R1 + R2) * (D + R1 + R2)))
+    area = math.pi * (R1 * R1 + R2 * R2) - lens
+    # perimeter: each circle minus its arc inside the other disc
+    t1 = math.acos((D * D + R1 * R1 - R2 * R2) / (2 * D * R1))
+    t2 = math.acos((D * D + R2 * R2 - R1 * R1) / (2 * D * R2))
+    per = 2 * R1 * (math.pi - t1) + 2 * R2 * (math.pi - t2)
+    prob = mesh.Problem(2, 2, (24, 24), (0.0, 0.0), (1.0, 1.0), (0.0, 0.0), 1.0, 8, 1, 1, 1, 0.5,
+                        ls_kind="spheres", spheres=_TWO)
+    _, vw, sx, sw, sn = _all_rules(prob)
+    assert abs(vw.sum() - area) < 1e-13 and abs(sw.sum() - per) < 1e-12
+
+
+def _divergence_residuals(prob, F, divF):
+    m = mesh.Mesh(prob)
+    d = prob.dim
+    res = []
+    for e in range(m.n_active):
+        if m.active_type[e] != mesh.CUT:
+            continue
+        lo, hi = mesh.cell_box(prob, m.index_of(e))
+        vol, surf = saye.cell_rules(prob, lo, hi)
+        lhs = sum(w * divF(x) for x, w in vol)
+        rhs = sum(w * F(x) @ np.array(nn) for x, w, nn in surf)
+        for axis in range(d):
+            for side, sign in ((0, -1.0), (1, 1.0)):
+                flo = list(lo)
+                fhi = list(hi)
+                if side == 0:
+                    fhi[axis] = lo[axis]
+                else:
+                    flo[axis] = hi[axis]
+                for x, w in saye.face_rule(prob, tuple(flo), tuple(fhi), axis):
+                    rhs += sign * w * F(x)[axis]
+        res.append(abs(lhs - rhs))
+    return np.array(res)
+
+
+def test_union_of_three_balls_divergence_theorem_per_cell():
+    """Cells that hold intersection circles and triple points, q = 8: every cell's residual
+    stays at the level of the single-sphere cells (<= 5e-9 here; dropping the intersection
+    circles as break curves gives 6e-5, dropping the break points on the cell faces and the
+    triple points 2e-6)."""
+    prob = _spheres_prob(16, 8, _THREE)
+
+    def F(x):
+        return np.array([x[0] ** 2 * x[1], x[1] * x[2] ** 2 + x[0], x[0] * x[1] * x[2]])
+
+    def divF(x):
+        return 2 * x[0] * x[1] + x[2] ** 2 + x[0] * x[1]
+
+    res = _divergence_residuals(prob, F, divF)
+    assert len(res) > 300 and res.max() < 3e-8
+
+
+def test_union_of_three_discs_divergence_theorem_per_cell():
+    """Dropping the circles' intersection points as break points gives 3e-3."""
+    prob = mesh.Problem(2, 2, (16, 16), (0.0, 0.0), (1.0, 1.0), (0.0, 0.0), 1.0, 8, 1, 1, 1, 0.5,
+                        ls_kind="spheres", spheres=_THREE)
+    res = _divergence_residuals(prob, lambda x: np.array([x[0] ** 3 * x[1], x[1] ** 2 + x[0]]),
+                                lambda x: 3 * x[0] ** 2 * x[1] + 2 * x[1])
+    assert len(res) > 40 and res.max() < 1e-11
+
+
+def test_union_intersecting_classification_against_sampling():
+    prob = _spheres_prob(10, 2, _THREE)
+    m = mesh.Mesh(prob)
+    t = np.linspace(0.0, 1.0, 9)
+    for flat in range(10 ** 3):
+        idx = (flat % 10, (flat // 10) % 10, flat // 100)
+        lo, hi = mesh.cell_box(prob, idx)
+        g = np.stack(np.meshgrid(*[lo[a] + t * (hi[a] - lo[a]) for a in range(3)]), -1).reshape(-1, 3)
+        phis = [np.linalg.norm(g - np.array(c[:3]), axis=1) - R for *c, R in _THREE]
+        e = m.id_map[idx[::-1]]
+        got = mesh.OUTSIDE if e < 0 else m.active_type[e]
+        if any(p.max() < 0 for p in phis):
+            assert got == mesh.INSIDE
+        elif np.min(phis) > 0:
+            assert got == mesh.OUTSIDE
+        elif any(p.min() < 0 < p.max() for p in phis):
+            assert got == mesh.CUT
+
+
+def test_box_covered_by_two_balls_but_by_neither():
+    """A cell inside the union but inside no single ball is cut, with the full volume and no
+    surface points."""
+    balls = [(0.2, 0.5, 0.5, 0.33), (0.8, 0.5, 0.5, 0.33)]
+    lo, hi = (0.45, 0.45, 0.45), (0.55, 0.55, 0.55)
+    prob = _spheres_prob(10, 3, balls)
+    assert mesh.classify(prob, lo, hi) == mesh.CUT
+    vol, surf = saye.cell_rules(prob, lo, hi)
+    assert surf == [] and abs(sum(w for _, w in vol) - 1e-3) < 1e-17
