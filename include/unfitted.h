@@ -83,9 +83,11 @@ typedef struct {
                              is off when gp_max_order = 0. */
   double gp_tau;          /* tau_v of UF_GP_VOLUME */
   const double *ls_spheres;  /* UF_LS_SPHERES: host array [ls_n_spheres][4] = (cx, cy, cz, R), copied
-                                at creation; the domain is the union of the balls, which must be
-                                separated so that no cell or face meets two spheres (UF_EGEOMETRY
-                                otherwise): each cut cell / face uses the rule of its one sphere */
+                                at creation; the domain is the union of the balls, level set
+                                min_i (|x - c_i| - R_i) (paper Sec. 6).  Balls may intersect: a cell
+                                or face met by several spheres gets a rule split at their
+                                intersection circles; a cell inside the union but inside no single
+                                ball is a cut cell with a full volume rule and no surface points */
   int ls_n_spheres;
 } uf_params;
 

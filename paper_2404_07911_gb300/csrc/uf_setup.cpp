@@ -417,6 +417,500 @@ void sphere_box_rules(const Box &b, const double *c, double rho, const Gauss1 &g
 }
 
 // ------------------------------------------------------------------------------------------
+// Unions of balls: psi = min_i (|x - c_i|^2 - rho_i) (Sec. 6), balls may intersect
+// ------------------------------------------------------------------------------------------
+// Along a coordinate line the union is the merged union of the balls' intervals (exact inner
+// integrals).  The outer integration splits where an interval meets the box (the circles
+// psi_i(., lo_k) = 0, psi_i(., hi_k) = 0), where two spheres' endpoints meet (their intersection
+// circle seen along k) and at the 3D points where such events coincide (intersection circles on
+// the planes x_k = lo_k, hi_k; triple points of three spheres), all in closed form.  Decisions:
+//  * box status: contained in one ball -> tensor Gauss; S = balls whose sphere meets the closed
+//    box; |S| = 0 -> nothing; |S| = 1 -> sphere_box_rules; m = 1 -> split at all roots, pieces
+//    whose midpoint lies in a ball get Gauss points.
+//  * height direction k: no centre with lo_k < c_ik < hi_k; among those the one maximising
+//    min_i |mid_k - c_ik| (first on ties); none -> bisect (depth <= 8), at depth 8 the same
+//    maximum without the test.
+//  * outer rule, m = 2: split at the roots of psi_i(., lo_k), psi_i(., hi_k), at the pair
+//    intersection points and (invalid k) at the silhouettes c_i' +- R_i.  m = 3: rectangle
+//    rule with circles in 2D and intersection circles in 3D as break curves and the coincidence
+//    points as break points; its line direction is the one whose curves' points with tangent
+//    along it lie outside the open rectangle, farthest from it (squared distance, first on
+//    ties); none -> bisect the rectangle (depth <= 8, then direction 0).
+//  * each outer line: intervals sorted by start (ball order on ties), merged when they touch;
+//    merged ends inside (lo_k, hi_k) are surface points of the ball that starts / first reaches
+//    them, weight w' R_i / |t - c_ik|.  A line with two surface points is stored as two lines
+//    (the second one without volume points).
+
+using Pieces = std::vector<std::pair<double, double>>;
+
+Pieces pieces_of(double a, double b, std::vector<double> &roots) {
+  std::sort(roots.begin(), roots.end());
+  Pieces out;
+  double prev = a;
+  for (double r : roots) {
+    if (r > prev) out.emplace_back(prev, r);
+    prev = std::max(prev, r);
+  }
+  if (b > prev) out.emplace_back(prev, b);
+  return out;
+}
+
+double dot3(const double *u, const double *v) {
+  double r = 0.0;
+  for (int a = 0; a < 3; ++a) r += u[a] * v[a];
+  return r;
+}
+
+struct Circle3 {  // circle of centre q, unit normal nu, radius^2 rc2 (3D)
+  double q[3], nu[3], rc2;
+};
+
+bool pair_circle(const Fn &bi, const Fn &bj, Circle3 &out) {
+  double dv[3];
+  for (int a = 0; a < 3; ++a) dv[a] = bj.c[a] - bi.c[a];
+  const double D2 = dot3(dv, dv);
+  if (D2 == 0.0) return false;
+  const double D = std::sqrt(D2);
+  for (int a = 0; a < 3; ++a) out.nu[a] = dv[a] / D;
+  const double a0 = (D2 + bi.rho - bj.rho) / (2.0 * D);
+  out.rc2 = bi.rho - a0 * a0;
+  if (out.rc2 <= 0.0) return false;
+  for (int a = 0; a < 3; ++a) out.q[a] = bi.c[a] + a0 * out.nu[a];
+  return true;
+}
+
+// Points of the circle on the plane mu . x = h (0 or 2), appended to pts (3 doubles each).
+int circle_plane(const Circle3 &cc, const double *mu, double h, std::vector<double> &pts) {
+  const double mn = dot3(mu, cc.nu);
+  const double mm = dot3(mu, mu);
+  const double den = mm - mn * mn;
+  if (den <= 1e-24 * mm) return 0;
+  const double lam = (h - dot3(mu, cc.q)) / den;
+  double p0[3];
+  for (int a = 0; a < 3; ++a) p0[a] = cc.q[a] + lam * (mu[a] - mn * cc.nu[a]);
+  const double s2 = cc.rc2 - lam * lam * den;
+  if (s2 < 0.0) return 0;
+  const double ell[3] = {cc.nu[1] * mu[2] - cc.nu[2] * mu[1], cc.nu[2] * mu[0] - cc.nu[0] * mu[2],
+                         cc.nu[0] * mu[1] - cc.nu[1] * mu[0]};
+  const double f = std::sqrt(s2) / std::sqrt(den);
+  for (int a = 0; a < 3; ++a) pts.push_back(p0[a] - f * ell[a]);
+  for (int a = 0; a < 3; ++a) pts.push_back(p0[a] + f * ell[a]);
+  return 2;
+}
+
+int axis_plane_points(const Circle3 &cc, int A, double v, std::vector<double> &pts) {
+  const double mu[3] = {A == 0 ? 1.0 : 0.0, A == 1 ? 1.0 : 0.0, A == 2 ? 1.0 : 0.0};
+  return circle_plane(cc, mu, v, pts);
+}
+
+// Bounding box of the circle overlaps the open box in the listed 3D axes (b.m of them).
+bool circle_overlaps(const Circle3 &cc, const int *axes, const Box &b) {
+  for (int j = 0; j < b.m; ++j) {
+    const int A = axes[j];
+    const double hw = std::sqrt(cc.rc2) * std::sqrt(std::fmax(0.0, 1.0 - cc.nu[A] * cc.nu[A]));
+    if (!(cc.q[A] - hw < b.hi[j] && cc.q[A] + hw > b.lo[j])) return false;
+  }
+  return true;
+}
+
+bool in_open(const double *x, const Box &b) {
+  for (int a = 0; a < b.m; ++a)
+    if (!(b.lo[a] < x[a] && x[a] < b.hi[a])) return false;
+  return true;
+}
+
+// A break curve of the rectangle rule: a circle in the rectangle's coordinates (c3 = false) or
+// an intersection circle in 3D seen along the dropped axis.
+struct Curve {
+  bool c3;
+  double C[2], r2;
+  Circle3 circ;
+};
+
+// Squared distance from the rectangle to the curve's points with tangent along direction a
+// (the nearer one); 0 if one lies inside the open rectangle.
+double tangent_clearance(const Curve &cv, int a, const int *axes, const Box &b) {
+  const int o = 1 - a;
+  double pts[2][2];
+  if (!cv.c3) {
+    const double r = std::sqrt(cv.r2);
+    const double t[2] = {cv.C[o] - r, cv.C[o] + r};
+    for (int i = 0; i < 2; ++i) {
+      pts[i][a] = cv.C[a];
+      pts[i][o] = t[i];
+    }
+  } else {
+    const Circle3 &cc = cv.circ;
+    const int O = axes[o];
+    const double den = 1.0 - cc.nu[O] * cc.nu[O];
+    if (den <= 1e-12) return 0.0;
+    const double rc = std::sqrt(cc.rc2);
+    const double sd = std::sqrt(den);
+    const double sg[2] = {-1.0, 1.0};
+    for (int i = 0; i < 2; ++i) {
+      double p[3];
+      for (int bb = 0; bb < 3; ++bb)
+        p[bb] = cc.q[bb] + sg[i] * rc * (((bb == O ? 1.0 : 0.0) - cc.nu[O] * cc.nu[bb]) / sd);
+      pts[i][0] = p[axes[0]];
+      pts[i][1] = p[axes[1]];
+    }
+  }
+  double best = INFINITY;
+  for (int i = 0; i < 2; ++i) {
+    if (in_open(pts[i], b)) return 0.0;
+    double dmin2, dmax2;
+    box_dist2(pts[i], b, dmin2, dmax2);
+    best = std::fmin(best, dmin2);
+  }
+  return best;
+}
+
+// Coordinates (direction 1 - along of the rectangle) of the curve's points with coordinate
+// `along` equal to v.
+void curve_points_at(const Curve &cv, int along, double v, const int *axes, std::vector<double> &out) {
+  const int other = 1 - along;
+  if (!cv.c3) {
+    const double rr = cv.r2 - (v - cv.C[along]) * (v - cv.C[along]);
+    if (rr <= 0.0) return;
+    const double s = std::sqrt(rr);
+    out.push_back(cv.C[other] - s);
+    out.push_back(cv.C[other] + s);
+    return;
+  }
+  std::vector<double> pts;
+  const int n = axis_plane_points(cv.circ, axes[along], v, pts);
+  for (int i = 0; i < n; ++i) out.push_back(pts[3 * i + axes[other]]);
+}
+
+void curve_rule_2d(const Box &b, const std::vector<Curve> &curves, const std::vector<double> &points,
+                   const int *axes, const Gauss1 &g, int depth, std::vector<QPoint> &out) {
+  std::vector<Curve> keep;
+  for (const Curve &cv : curves) {
+    if (!cv.c3) {
+      double dmin2, dmax2;
+      box_dist2(cv.C, b, dmin2, dmax2);
+      if (dmin2 < cv.r2 && cv.r2 < dmax2) keep.push_back(cv);
+    } else if (circle_overlaps(cv.circ, axes, b)) {
+      keep.push_back(cv);
+    }
+  }
+  if (keep.empty()) {
+    tensor_rule(b, g, out);
+    return;
+  }
+  int a = -1;
+  double best = 0.0;
+  for (int cand = 0; cand < 2; ++cand) {
+    double v = INFINITY;
+    for (const Curve &cv : keep) v = std::fmin(v, tangent_clearance(cv, cand, axes, b));
+    if (v > best) {
+      best = v;
+      a = cand;
+    }
+  }
+  if (a < 0) {
+    if (depth < kMaxDepth) {
+      for (int bits = 0; bits < 4; ++bits) curve_rule_2d(child(b, bits), keep, points, axes, g, depth + 1, out);
+      return;
+    }
+    a = 0;
+  }
+  const int o = 1 - a;
+  std::vector<double> splits, cand;
+  for (const Curve &cv : keep) {
+    const double vs[2] = {b.lo[a], b.hi[a]};
+    for (double v : vs) {
+      cand.clear();
+      curve_points_at(cv, a, v, axes, cand);
+      for (double t : cand)
+        if (b.lo[o] < t && t < b.hi[o]) splits.push_back(t);
+    }
+  }
+  for (size_t i = 0; i < points.size() / 2; ++i) {
+    const double t = points[2 * i + o];
+    if (b.lo[o] < t && t < b.hi[o]) splits.push_back(t);
+  }
+  std::vector<double> roots;
+  for (const auto &po : pieces_of(b.lo[o], b.hi[o], splits))
+    for (int io = 0; io < g.q; ++io) {
+      const double xo = po.first + (po.second - po.first) * g.x[io];
+      const double wo = (po.second - po.first) * g.w[io];
+      roots.clear();
+      for (const Curve &cv : keep) {
+        cand.clear();
+        curve_points_at(cv, o, xo, axes, cand);
+        for (double t : cand)
+          if (b.lo[a] < t && t < b.hi[a]) roots.push_back(t);
+      }
+      for (const auto &pa : pieces_of(b.lo[a], b.hi[a], roots))
+        for (int i = 0; i < g.q; ++i) {
+          QPoint p{};
+          p.x[o] = xo;
+          p.x[a] = pa.first + (pa.second - pa.first) * g.x[i];
+          p.w = wo * ((pa.second - pa.first) * g.w[i]);
+          out.push_back(p);
+        }
+    }
+}
+
+// Height direction of a union box (-1 if none is valid with `check`).
+int union_height(const std::vector<Fn> &act, const Box &b, bool check) {
+  int k = -1;
+  double best = -1.0;
+  for (int kk = 0; kk < b.m; ++kk) {
+    bool ok = true;
+    double v = INFINITY;
+    for (const Fn &f : act) {
+      if (check && b.lo[kk] < f.c[kk] && f.c[kk] < b.hi[kk]) ok = false;
+      v = std::fmin(v, std::fabs(0.5 * (b.lo[kk] + b.hi[kk]) - f.c[kk]));
+    }
+    if (!ok) continue;
+    if (v > best) {
+      best = v;
+      k = kk;
+    }
+  }
+  return k;
+}
+
+void union_outer(const Box &b, const std::vector<Fn> &act, int k, bool valid, const Gauss1 &g,
+                 std::vector<QPoint> &out) {
+  const int na = (int)act.size();
+  if (b.m == 2) {
+    const int a = 1 - k;
+    std::vector<double> splits;
+    for (const Fn &f : act) {
+      const double vs[2] = {b.lo[k], b.hi[k]};
+      for (double v : vs) {
+        const double r2 = f.rho - (v - f.c[k]) * (v - f.c[k]);
+        if (r2 > 0.0) {
+          const double s = std::sqrt(r2);
+          const double t[2] = {f.c[a] - s, f.c[a] + s};
+          for (double tt : t)
+            if (b.lo[a] < tt && tt < b.hi[a]) splits.push_back(tt);
+        }
+      }
+      if (!valid && b.lo[k] < f.c[k] && f.c[k] < b.hi[k]) {
+        const double R = std::sqrt(f.rho);
+        const double t[2] = {f.c[a] - R, f.c[a] + R};
+        for (double tt : t)
+          if (b.lo[a] < tt && tt < b.hi[a]) splits.push_back(tt);
+      }
+    }
+    for (int i = 0; i < na; ++i)
+      for (int j = i + 1; j < na; ++j) {
+        const Fn &ci = act[i], &cj = act[j];
+        const double dv[2] = {cj.c[0] - ci.c[0], cj.c[1] - ci.c[1]};
+        const double D2 = dv[0] * dv[0] + dv[1] * dv[1];
+        if (D2 == 0.0) continue;
+        const double D = std::sqrt(D2);
+        const double nu[2] = {dv[0] / D, dv[1] / D};
+        const double a0 = (D2 + ci.rho - cj.rho) / (2.0 * D);
+        const double rc2 = ci.rho - a0 * a0;
+        if (rc2 <= 0.0) continue;
+        const double rc = std::sqrt(rc2);
+        const double qc[2] = {ci.c[0] + a0 * nu[0], ci.c[1] + a0 * nu[1]};
+        const double sg[2] = {-1.0, 1.0};
+        for (double sgn : sg) {
+          const double p[2] = {qc[0] - sgn * rc * nu[1], qc[1] + sgn * rc * nu[0]};
+          if (b.lo[a] < p[a] && p[a] < b.hi[a]) splits.push_back(p[a]);
+        }
+      }
+    for (const auto &pc : pieces_of(b.lo[a], b.hi[a], splits))
+      for (int i = 0; i < g.q; ++i) {
+        QPoint p{};
+        p.x[0] = pc.first + (pc.second - pc.first) * g.x[i];
+        p.w = (pc.second - pc.first) * g.w[i];
+        out.push_back(p);
+      }
+    return;
+  }
+  int axes[2], j = 0;
+  for (int bb = 0; bb < 3; ++bb)
+    if (bb != k) axes[j++] = bb;
+  std::vector<Curve> curves;
+  for (const Fn &f : act) {
+    const double vs[2] = {b.lo[k], b.hi[k]};
+    for (double v : vs) {
+      const double r2 = f.rho - (v - f.c[k]) * (v - f.c[k]);
+      if (r2 > 0.0) {
+        Curve cv{};
+        cv.C[0] = f.c[axes[0]];
+        cv.C[1] = f.c[axes[1]];
+        cv.r2 = r2;
+        curves.push_back(cv);
+      }
+    }
+    if (!valid && b.lo[k] < f.c[k] && f.c[k] < b.hi[k]) {
+      Curve cv{};
+      cv.C[0] = f.c[axes[0]];
+      cv.C[1] = f.c[axes[1]];
+      cv.r2 = f.rho;
+      curves.push_back(cv);
+    }
+  }
+  const int all3[3] = {0, 1, 2};
+  std::vector<double> pts3;
+  for (int i = 0; i < na; ++i)
+    for (int jj = i + 1; jj < na; ++jj) {
+      Curve cv{};
+      cv.c3 = true;
+      if (!pair_circle(act[i], act[jj], cv.circ) || !circle_overlaps(cv.circ, all3, b)) continue;
+      curves.push_back(cv);
+      axis_plane_points(cv.circ, k, b.lo[k], pts3);
+      axis_plane_points(cv.circ, k, b.hi[k], pts3);
+      for (int l = jj + 1; l < na; ++l) {
+        const Fn &fi = act[i], &fl = act[l];
+        double mu[3];
+        for (int bb = 0; bb < 3; ++bb) mu[bb] = fl.c[bb] - fi.c[bb];
+        const double hpl = 0.5 * ((dot3(fl.c, fl.c) - dot3(fi.c, fi.c)) - fl.rho + fi.rho);
+        circle_plane(cv.circ, mu, hpl, pts3);
+      }
+    }
+  std::vector<double> points;
+  for (size_t i = 0; i < pts3.size() / 3; ++i) {
+    points.push_back(pts3[3 * i + axes[0]]);
+    points.push_back(pts3[3 * i + axes[1]]);
+  }
+  curve_rule_2d(drop_dim(b, k), curves, points, axes, g, 0, out);
+}
+
+void union_box_rules(const Box &b, const std::vector<Fn> &balls, const Gauss1 &g, int depth,
+                     bool surface, std::vector<QPoint> &vol, std::vector<QPoint> &surf,
+                     std::vector<QLine> *lines) {
+  bool contained = false;
+  std::vector<Fn> act;
+  for (const Fn &f : balls) {
+    double dmin2, dmax2;
+    box_dist2(f.c, b, dmin2, dmax2);
+    if (dmax2 <= f.rho)
+      contained = true;
+    else if (dmin2 < f.rho)
+      act.push_back(f);
+  }
+  if (contained) {
+    tensor_rule(b, g, vol, lines);
+    return;
+  }
+  if (act.empty()) return;
+  if (act.size() == 1) {
+    sphere_box_rules(b, act[0].c, act[0].rho, g, depth, surface, vol, surf, lines);
+    return;
+  }
+  if (b.m == 1) {
+    if (surface) throw QuadError{};
+    std::vector<double> roots;
+    for (const Fn &f : act) {
+      const double s = std::sqrt(f.rho);
+      const double t[2] = {f.c[0] - s, f.c[0] + s};
+      for (double tt : t)
+        if (b.lo[0] < tt && tt < b.hi[0]) roots.push_back(tt);
+    }
+    const int64_t vbeg = (int64_t)vol.size();
+    for (const auto &pc : pieces_of(b.lo[0], b.hi[0], roots)) {
+      const double mid = 0.5 * (pc.first + pc.second);
+      bool in = false;
+      for (const Fn &f : act) in = in || ((mid - f.c[0]) * (mid - f.c[0]) - f.rho < 0.0);
+      if (in)
+        for (int i = 0; i < g.q; ++i) {
+          QPoint p{};
+          p.x[0] = pc.first + (pc.second - pc.first) * g.x[i];
+          p.w = (pc.second - pc.first) * g.w[i];
+          vol.push_back(p);
+        }
+    }
+    if (lines && (int64_t)vol.size() > vbeg) lines->push_back(QLine{0, vbeg, (int64_t)vol.size() - vbeg, -1});
+    return;
+  }
+  int k = union_height(act, b, true);
+  const bool valid = k >= 0;
+  if (!valid) {
+    if (depth < kMaxDepth) {
+      for (int bits = 0; bits < (1 << b.m); ++bits)
+        union_box_rules(child(b, bits), act, g, depth + 1, surface, vol, surf, lines);
+      return;
+    }
+    k = union_height(act, b, false);
+  }
+  std::vector<QPoint> outer;
+  union_outer(b, act, k, valid, g, outer);
+  struct Iv {
+    double a, b;
+    int idx;
+  };
+  struct Merged {
+    double a, b;
+    int ia, ib;
+  };
+  std::vector<Iv> ivs;
+  std::vector<Merged> merged;
+  for (const QPoint &op : outer) {
+    ivs.clear();
+    for (int idx = 0; idx < (int)act.size(); ++idx) {
+      const Fn &f = act[idx];
+      double csub[kMaxDim];
+      drop_vec(f.c, b.m, k, csub);
+      const double r2 = f.rho - dist2(op.x, csub, b.m - 1);
+      if (r2 > 0.0) {
+        const double s = std::sqrt(r2);
+        double a = f.c[k] - s, bb = f.c[k] + s;
+        if (a < b.lo[k]) a = b.lo[k];
+        if (bb > b.hi[k]) bb = b.hi[k];
+        if (a < bb) ivs.push_back(Iv{a, bb, idx});
+      }
+    }
+    std::sort(ivs.begin(), ivs.end(), [](const Iv &x, const Iv &y) {
+      return x.a < y.a || (x.a == y.a && x.idx < y.idx);
+    });
+    merged.clear();
+    for (const Iv &iv : ivs) {
+      if (!merged.empty() && iv.a <= merged.back().b) {
+        if (iv.b > merged.back().b) {
+          merged.back().b = iv.b;
+          merged.back().ib = iv.idx;
+        }
+      } else {
+        merged.push_back(Merged{iv.a, iv.b, iv.idx, iv.idx});
+      }
+    }
+    const int64_t vbeg = (int64_t)vol.size();
+    for (const Merged &mg : merged)
+      for (int i = 0; i < g.q; ++i) {
+        QPoint p{};
+        insert_coord(op.x, b.m, k, mg.a + (mg.b - mg.a) * g.x[i], p.x);
+        p.w = op.w * ((mg.b - mg.a) * g.w[i]);
+        vol.push_back(p);
+      }
+    const int64_t vcnt = (int64_t)vol.size() - vbeg;
+    int nsurf = 0;
+    if (surface)
+      for (const Merged &mg : merged) {
+        const double ts[2] = {mg.a, mg.b};
+        const int own[2] = {mg.ia, mg.ib};
+        const bool on[2] = {mg.a > b.lo[k], mg.b < b.hi[k]};
+        for (int e = 0; e < 2; ++e) {
+          if (!on[e]) continue;
+          const Fn &f = act[own[e]];
+          QPoint p{};
+          insert_coord(op.x, b.m, k, ts[e], p.x);
+          const double nrm = std::sqrt(dist2(p.x, f.c, b.m));
+          for (int a = 0; a < b.m; ++a) p.nrm[a] = (p.x[a] - f.c[a]) / nrm;
+          p.w = op.w * (std::sqrt(f.rho) / std::fabs(ts[e] - f.c[k]));
+          if (lines) {
+            if (nsurf == 0)
+              lines->push_back(QLine{k, vbeg, vcnt, (int64_t)surf.size()});
+            else
+              lines->push_back(QLine{k, vbeg + vcnt, 0, (int64_t)surf.size()});
+          }
+          surf.push_back(p);
+          ++nsurf;
+        }
+      }
+    if (lines && nsurf == 0 && vcnt > 0) lines->push_back(QLine{k, vbeg, vcnt, -1});
+  }
+}
+
+// ------------------------------------------------------------------------------------------
 // Dimension-reduction quadrature for a plane psi = n . x - off
 // ------------------------------------------------------------------------------------------
 // psi is monotone along every direction with n_k != 0, so no bisection is needed: the height
@@ -661,47 +1155,36 @@ void build_tables_1d(int p, Tables1D &t) {
 
 namespace {
 
-// Union of separated balls: the spheres of the cut cells among the two cells of a face.
-int union_face_candidates(const HostOperator &op, int64_t e, int64_t nb, int32_t *cand) {
-  int n = 0;
+// Union of balls: the spheres that meet a cut cell or one of the two cells of a face
+// (ascending, without repeats).
+void union_face_candidates(const HostOperator &op, int64_t e, int64_t nb, std::vector<int32_t> &cand) {
+  cand.clear();
   for (int64_t c : {e, nb}) {
     if (c < 0 || op.act_type[c] != 1) continue;
-    const int32_t s = op.cut_sphere[op.cut_of[c]];
-    if (n == 0 || cand[0] != s) cand[n++] = s;
+    const int32_t ci = op.cut_of[c];
+    for (int64_t i = op.cut_sph_off[ci]; i < op.cut_sph_off[ci + 1]; ++i) cand.push_back(op.cut_sph[i]);
   }
-  return n;
+  std::sort(cand.begin(), cand.end());
+  cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
 }
 
-// Type of a face of the union of separated balls: 0 full (in a ball), 1 cut, 2 empty, -1 if it
-// meets two spheres.  A face of an inside cell lies in that cell's ball; otherwise every ball that
-// contains or meets the face meets both (cut) cells, so their spheres are the only candidates.
+// Type of a face of a union of balls: 0 full (in one ball), 1 cut (a sphere meets it), 2 empty.
+// A face of an inside cell lies in that cell's ball; otherwise every ball that contains or meets
+// the face meets both (cut) cells, so their spheres are the only candidates.
 int union_face_type(const HostOperator &op, const Box &fb, int64_t e, int64_t nb) {
   if (op.act_type[e] == 0 || op.act_type[nb] == 0) return 0;
-  int32_t cand[2];
-  const int n = union_face_candidates(op, e, nb, cand);
+  std::vector<int32_t> cand;
+  union_face_candidates(op, e, nb, cand);
   int crossing = 0;
-  for (int i = 0; i < n; ++i) {
-    const double *sp = &op.spheres[4 * (size_t)cand[i]];
+  for (int32_t i : cand) {
+    const double *sp = &op.spheres[4 * (size_t)i];
     double dmin2, dmax2;
     box_dist2(sp, fb, dmin2, dmax2);
     const double r2 = sp[3] * sp[3];
     if (dmax2 <= r2) return 0;
-    if (dmin2 < r2 && dmax2 > r2) ++crossing;
+    if (dmin2 < r2) ++crossing;
   }
-  return crossing == 0 ? 2 : (crossing == 1 ? 1 : -1);
-}
-
-// The one sphere that meets a cut face of the union.
-const double *union_face_sphere(const HostOperator &op, const Box &fb, int64_t e, int64_t nb) {
-  int32_t cand[2];
-  const int n = union_face_candidates(op, e, nb, cand);
-  for (int i = 0; i < n; ++i) {
-    const double *sp = &op.spheres[4 * (size_t)cand[i]];
-    double dmin2, dmax2;
-    box_dist2(sp, fb, dmin2, dmax2);
-    if (dmin2 < sp[3] * sp[3] && dmax2 > sp[3] * sp[3]) return sp;
-  }
-  return &op.spheres[4 * (size_t)cand[0]];  // not reached for a cut face
+  return crossing == 0 ? 2 : 1;
 }
 
 }  // namespace
@@ -830,11 +1313,10 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
   op.n_background = total;
   op.id_map.assign(total, -1);
   std::vector<int8_t> bg_type(total);
-  std::vector<int32_t> bg_sphere;  // union of balls: the one sphere that meets a cut cell
+  std::vector<std::pair<int64_t, int32_t>> bg_cross;  // union of balls: (cell, sphere meeting it)
   if (op.ls_kind == UF_LS_SPHERES) {
     // every ball updates the cells of its bounding box (cells beyond it lie outside the ball)
     std::vector<uint8_t> inside(total, 0), crossings(total, 0);
-    bg_sphere.assign(total, -1);
     const int ns = (int)(op.spheres.size() / 4);
     for (int i = 0; i < ns; ++i) {
       const double *c = &op.spheres[4 * i];
@@ -865,18 +1347,17 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
             if (dmax2 <= r2) {
               inside[flat] = 1;
             } else if (dmin2 < r2 && dmax2 > r2) {
-              if (crossings[flat] < 255) ++crossings[flat];
-              bg_sphere[flat] = i;
+              crossings[flat] = 1;
+              bg_cross.emplace_back(flat, i);
             }
           }
     }
-    for (int64_t flat = 0; flat < total; ++flat) {
-      if (!inside[flat] && crossings[flat] > 1) {
-        msg = "a cell meets two spheres: UF_LS_SPHERES needs separated spheres";
-        return UF_EGEOMETRY;
-      }
-      bg_type[flat] = inside[flat] ? 0 : (crossings[flat] == 1 ? 1 : 2);
-    }
+    for (int64_t flat = 0; flat < total; ++flat)
+      bg_type[flat] = inside[flat] ? 0 : (crossings[flat] ? 1 : 2);
+    std::stable_sort(bg_cross.begin(), bg_cross.end(),
+                     [](const std::pair<int64_t, int32_t> &a, const std::pair<int64_t, int32_t> &b) {
+                       return a.first < b.first;
+                     });
   } else {
     for (int64_t flat = 0; flat < total; ++flat) {
       Box b;
@@ -921,6 +1402,8 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
   op.nbr.assign(op.n_active * nf, -1);
   op.flags.assign(op.n_active, 0u);
   op.cut_of.assign(op.n_active, -1);
+  size_t cross_pos = 0;  // cut cells ascend in background order, as bg_cross does
+  if (op.ls_kind == UF_LS_SPHERES) op.cut_sph_off.assign(1, 0);
   for (int64_t e = 0; e < op.n_active; ++e) {
     if (op.act_type[e] == 1) {
       op.flags[e] |= kCellCut;
@@ -932,7 +1415,10 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
           flat += (int64_t)op.act_index[e * 3 + a] * stride;
           stride *= op.N[a];
         }
-        op.cut_sphere.push_back(bg_sphere[flat]);
+        while (cross_pos < bg_cross.size() && bg_cross[cross_pos].first < flat) ++cross_pos;
+        for (; cross_pos < bg_cross.size() && bg_cross[cross_pos].first == flat; ++cross_pos)
+          op.cut_sph.push_back(bg_cross[cross_pos].second);
+        op.cut_sph_off.push_back((int64_t)op.cut_sph.size());
       }
     } else {
       ++op.n_inside;
@@ -973,10 +1459,6 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
           // a face lies in a closed inside cell, or meets (or lies in) only the spheres of its two
           // cut cells
           ftype = union_face_type(op, face_box(e_minus, axis), e, nb);
-          if (ftype < 0) {
-            msg = "a face meets two spheres: UF_LS_SPHERES needs separated spheres";
-            return UF_EGEOMETRY;
-          }
         } else {
           ftype = classify(face_box(e_minus, axis));
         }
@@ -1010,6 +1492,8 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
   op.fline_off.assign(1, 0);
   std::vector<QPoint> vol, surf, fq;
   std::vector<QLine> lines;
+  std::vector<Fn> balls;
+  std::vector<int32_t> cand;
   try {
     for (int64_t c = 0; c < op.n_cut; ++c) {
       const int64_t e = op.cut_cells[c];
@@ -1026,8 +1510,15 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
       if (op.ls_kind == UF_LS_PLANE) {
         plane_box_rules(b, op.normal, op.offset, g, true, vol, surf, &lines);
       } else if (op.ls_kind == UF_LS_SPHERES) {
-        const double *sp = &op.spheres[4 * (size_t)op.cut_sphere[c]];
-        sphere_box_rules(b, sp, sp[3] * sp[3], g, 0, true, vol, surf, &lines);
+        balls.clear();
+        for (int64_t i = op.cut_sph_off[c]; i < op.cut_sph_off[c + 1]; ++i) {
+          const double *sp = &op.spheres[4 * (size_t)op.cut_sph[i]];
+          Fn f{};
+          for (int a = 0; a < d; ++a) f.c[a] = sp[a];
+          f.rho = sp[3] * sp[3];
+          balls.push_back(f);
+        }
+        union_box_rules(b, balls, g, 0, true, vol, surf, &lines);
       } else {
         sphere_box_rules(b, op.center, op.radius * op.radius, g, 0, true, vol, surf, &lines);
       }
@@ -1062,14 +1553,33 @@ uf_status build_host_operator(const uf_params &prm, HostOperator &op, std::strin
             double nsub[kMaxDim];
             drop_vec(op.normal, d, axis, nsub);
             plane_box_rules(sub, nsub, op.offset - op.normal[axis] * xa, g, false, fq, dummy, &lines);
+          } else if (op.ls_kind == UF_LS_SPHERES) {
+            // the balls whose sphere meets the face, cut by the face's plane
+            union_face_candidates(op, e, op.nbr[e * nf + f], cand);
+            bool contained = false;
+            balls.clear();
+            for (int32_t i : cand) {
+              const double *sp = &op.spheres[4 * (size_t)i];
+              double dmin2, dmax2;
+              box_dist2(sp, fb, dmin2, dmax2);
+              const double r2 = sp[3] * sp[3];
+              if (dmax2 <= r2) {
+                contained = true;
+              } else if (dmin2 < r2) {
+                Fn disc{};
+                drop_vec(sp, d, axis, disc.c);
+                const double da = xa - sp[axis];
+                disc.rho = r2 - da * da;
+                balls.push_back(disc);
+              }
+            }
+            if (contained)
+              tensor_rule(sub, g, fq, &lines);
+            else
+              union_box_rules(sub, balls, g, 0, false, fq, dummy, &lines);
           } else {
             const double *cen = op.center;
             double R = op.radius;
-            if (op.ls_kind == UF_LS_SPHERES) {
-              const double *sp = union_face_sphere(op, fb, e, op.nbr[e * nf + f]);
-              cen = sp;
-              R = sp[3];
-            }
             const double da = xa - cen[axis];
             const double rho = R * R - da * da;
             double csub[kMaxDim];

@@ -18,6 +18,8 @@ CASES = {
     "3d_plane_q3_4": workloads.plane(p=3, N=4, dim=3),
     "3d_q3_5_volume_gp": dict(workloads.small(p=3, N=5), gp_kind="volume", gp_tau=0.7),
     "3d_spheres_q2_8": workloads.spheres(p=2, N=8, m=2, R=0.2),
+    "3d_random_spheres_q2_8": workloads.spheres_random(p=2, N=8, n=8, R=0.22, seed=5,
+                                                       discretization="cg"),
 }
 
 

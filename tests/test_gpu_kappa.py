@@ -21,9 +21,10 @@ def _op(cfg, kappa):
 @pytest.mark.parametrize("cfg", [workloads.cfg_kappa(N=6), workloads.small(p=2, N=8),
                                  workloads.small(p=2, N=10, dim=2),
                                  dict(workloads.small(p=3, N=6), gp_kind="volume", gp_tau=0.7),
-                                 workloads.plane(p=2, N=5, dim=3)],
+                                 workloads.plane(p=2, N=5, dim=3),
+                                 workloads.spheres_random(p=2, N=8, n=8, R=0.22, seed=5)],
                          ids=["3d_q3_6_check_grid", "3d_q2_8", "2d_q2_10", "3d_q3_6_volume_gp",
-                              "3d_plane_q2_5"])
+                              "3d_plane_q2_5", "3d_random_spheres_q2_8"])
 def test_kappa_gradient_matches_oracle(cfg):
     o = forms.Oracle(mesh.problem_from_dict(cfg))
     kappa = workloads.kappa_vector(o.mesh.n_active, seed=4)

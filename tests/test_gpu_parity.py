@@ -61,6 +61,10 @@ SMALL = {
     # unions of separated balls
     "3d_spheres_q2_10": workloads.spheres(p=2, N=10, m=2, R=0.2),
     "2d_spheres_q3_16": workloads.spheres(p=3, N=16, m=3, R=0.12, dim=2),
+    # unions of intersecting balls (cells met by two and three spheres, covered cut cells)
+    "3d_random_spheres_q2_10": workloads.spheres_random(p=2, N=10, n=8, R=0.22, seed=5),
+    "3d_random_spheres_q1_14": workloads.spheres_random(p=1, N=14, n=14, R=(0.08, 0.22), seed=6),
+    "2d_random_spheres_q3_16": workloads.spheres_random(p=3, N=16, n=9, R=0.19, seed=2, dim=2),
     # half-spaces below tilted planes (the plane benchmark's geometry)
     "2d_plane_q2_7": workloads.plane(p=2, N=7, dim=2),
     "3d_plane_q1_6": workloads.plane(p=1, N=6, dim=3),

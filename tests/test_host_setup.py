@@ -20,6 +20,10 @@ CASES = {
     "3d_plane_on_axis_q1": workloads.plane(p=1, N=4, dim=3, normal=(0.0, 0.0, 1.0), offset_cells=2.5),
     "3d_spheres_q2": workloads.spheres(p=2, N=10, m=2, R=0.2),
     "2d_spheres_q3": workloads.spheres(p=3, N=16, m=3, R=0.12, dim=2),
+    # intersecting balls: cells with two and three spheres, triple points, covered cells
+    "3d_random_spheres_q2": workloads.spheres_random(p=2, N=10, n=8, R=0.22, seed=5),
+    "3d_random_spheres_q1_radii": workloads.spheres_random(p=1, N=14, n=14, R=(0.08, 0.22), seed=6),
+    "2d_random_spheres_q3": workloads.spheres_random(p=3, N=16, n=9, R=0.19, seed=2, dim=2),
 }
 
 
@@ -96,14 +100,16 @@ def test_gpu_parity_cases_cover_every_lane_group():
     assert any(all(v > 0 for v in c) for c in classes)
 
 
-def test_union_rejects_touching_spheres():
-    from paper_2404_07911_gb300.binding import UF_EGEOMETRY, UnfittedError
-
-    cfg = workloads.spheres(p=1, N=8, m=2, R=0.2)
-    cfg["spheres"] = [(0.3, 0.5, 0.5, 0.21), (0.72, 0.5, 0.5, 0.2)]
-    with pytest.raises(UnfittedError) as err:
-        UnfittedOperator(cfg, device=-1)
-    assert err.value.status == UF_EGEOMETRY
+def test_random_spheres_cases_hold_multi_sphere_cells():
+    """The intersecting cases exercise cells met by two and by three spheres."""
+    for name in ("3d_random_spheres_q2", "3d_random_spheres_q1_radii", "2d_random_spheres_q3"):
+        o = forms.Oracle(mesh.problem_from_dict(CASES[name]))
+        counts = []
+        for e in np.nonzero(o.mesh.active_type == mesh.CUT)[0]:
+            lo, hi = mesh.cell_box(o.prob, o.mesh.index_of(int(e)))
+            counts.append(len(mesh.crossing_spheres(o.prob, lo, hi)[1]))
+        counts = np.array(counts)
+        assert (counts >= 2).sum() > 10 and (counts >= 3).sum() > 0, name
 
 
 def test_regular_spheres_benchmark_counts():

@@ -165,7 +165,7 @@ def sphere_lattice(m, R, dim=3):
 
 
 def spheres(p=2, N=12, m=2, R=0.2, dim=3, discretization="dg", quad_order=None, seed=11):
-    """Union of m^d separated balls of radius R on a lattice in [0, 1]^d, N cells per direction;
+    """Union of m^d balls of radius R on a lattice in [0, 1]^d, N cells per direction;
     penalties as for the ball workloads."""
     pad = (0.0,) * (3 - dim)
     return dict(name=f"{dim}d_{discretization}_q{p}_{m}^{dim}_spheres_{N}", dim=dim, degree=p,
@@ -173,6 +173,29 @@ def spheres(p=2, N=12, m=2, R=0.2, dim=3, discretization="dg", quad_order=None, 
                 center=(0.0, 0.0, 0.0), radius=1.0, ls_kind="spheres",
                 spheres=sphere_lattice(m, R, dim), quad_order=quad_order if quad_order else p + 1,
                 seed=seed, discretization=discretization, **_penalties(p))
+
+
+def random_spheres(n, R, seed, dim=3):
+    """n balls of radius R (a number, or a (min, max) range drawn uniformly) with centres drawn
+    uniformly in the unit box: numpy default_rng(seed), all centres first (x, y, z per ball),
+    then the radii.  The balls intersect freely."""
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(0.0, 1.0, size=(n, dim))
+    r = np.full(n, float(R)) if np.isscalar(R) else rng.uniform(R[0], R[1], size=n)
+    out = []
+    for i in range(n):
+        xyz = [float(v) for v in c[i]] + [0.0] * (3 - dim)
+        out.append((xyz[0], xyz[1], xyz[2], float(r[i])))
+    return out
+
+
+def spheres_random(p=2, N=12, n=6, R=0.2, seed=5, dim=3, discretization="dg", quad_order=None):
+    """Union of n intersecting balls (random_spheres) in [0, 1]^d, N cells per direction."""
+    c = spheres(p=p, N=N, m=1, R=R if np.isscalar(R) else R[1], dim=dim,
+                discretization=discretization, quad_order=quad_order)
+    c["spheres"] = random_spheres(n, R, seed, dim)
+    c["name"] = f"{dim}d_{discretization}_q{p}_{n}_random_spheres_{N}"
+    return c
 
 
 def cfg_spheres_regular(p=1, discretization="dg"):
