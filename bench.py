@@ -536,9 +536,16 @@ def run_accuracy(args, local):
 
 
 def run_spheres(args, local):
-    """Regular-spheres benchmark: 1000 separated balls, 192^3 background cells, DG Q1 (about
-    1.5e7 DoFs, cut-cell ratio 0.48): MDoF/s of A x in FP64 and FP32, rows of cut and inside
-    cells sampled against the oracle."""
+    """Union-of-spheres benchmarks on 192^3 background cells: 1000 regular balls (DG Q1, about
+    1.5e7 DoFs, cut-cell ratio 0.48) and 100 random intersecting balls (DG Q1, 1.3e7 DoFs, and
+    DG Q3, 1.05e8 DoFs, cut-cell ratio 0.18): MDoF/s of A x in FP64 and FP32, rows of cut and
+    inside cells sampled against the oracle."""
+    for cfg in (workloads.cfg_spheres_regular(), workloads.cfg_spheres_random(1),
+                workloads.cfg_spheres_random(3)):
+        _run_spheres_one(cfg, local)
+
+
+def _run_spheres_one(cfg, local):
     import torch
 
     from oracle import forms, mesh
@@ -547,7 +554,6 @@ def run_spheres(args, local):
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    cfg = workloads.cfg_spheres_regular()
     t0 = time.perf_counter()
     op = UnfittedOperator(cfg, precisions=UF_FP64 | UF_FP32, device=local)
     t_setup = time.perf_counter() - t0
@@ -576,7 +582,7 @@ def run_spheres(args, local):
     ref = o.apply_rows(xh, cells)
     g64 = y64.cpu().numpy().reshape(-1, nd)[cells]
     print(json.dumps({
-        "metric": "regular spheres benchmark: MDoF/s of A x",
+        "metric": "union-of-spheres benchmark: MDoF/s of A x",
         "config": {"workload": cfg["name"], "n_dofs": n, "n_active": info["n_active"],
                    "n_cut": info["n_cut"], "cut_ratio": round(info["n_cut"] / info["n_active"], 4),
                    "lane_classes": list(info["cut_lane_classes"]), "setup_s": round(t_setup, 2)},
@@ -587,6 +593,8 @@ def run_spheres(args, local):
                       for (prec, kern, _), (tot, cnt) in sorted(kt.items())},
         "l2": "flushed before every launch"}), flush=True)
     op.close()
+    del x64, x32, y64, y32
+    torch.cuda.empty_cache()
 
 
 def run_solve(args, local):

@@ -198,6 +198,17 @@ def spheres_random(p=2, N=12, n=6, R=0.2, seed=5, dim=3, discretization="dg", qu
     return c
 
 
+def cfg_spheres_random(p=1, discretization="dg"):
+    """The paper's random-spheres benchmark (Sec. 6): 100 randomly placed, intersecting balls;
+    their placement and radii are not given, so: random_spheres(100, (0.02, 0.131), seed 4),
+    radius range and seed fitted to the printed DoF count and cut-cell ratio of the DG Q1 case,
+    12^3 background cells refined four times (192^3); p = 1 and p = 3 on the same mesh."""
+    c = spheres_random(p=p, N=192, n=100, R=(0.02, 0.131), seed=4, discretization=discretization)
+    c["name"] = f"3d_{discretization}_q{p}_100_random_spheres_192^3"
+    c["seed"] = 13
+    return c
+
+
 def cfg_spheres_regular(p=1, discretization="dg"):
     """The paper's regular-spheres benchmark (Sec. 6): 1000 balls on a regular pattern; their
     radius and placement are not given, so: the 10^3 lattice of the unit cube, radius 0.0362
