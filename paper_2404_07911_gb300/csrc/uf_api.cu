@@ -139,6 +139,37 @@ void uf::structured_matrices(const uf::HostOperator &op, std::vector<double> &ou
 namespace {
 using uf::structured_matrices;
 
+// Inverse of a small SPD matrix (n x n, row-major) by Gauss-Jordan elimination with partial
+// pivoting.
+std::vector<double> invert_small(std::vector<double> a, int n) {
+  std::vector<double> inv(n * n, 0.0);
+  for (int i = 0; i < n; ++i) inv[i * n + i] = 1.0;
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < n; ++r)
+      if (std::fabs(a[r * n + col]) > std::fabs(a[piv * n + col])) piv = r;
+    for (int c2 = 0; c2 < n; ++c2) {
+      std::swap(a[col * n + c2], a[piv * n + c2]);
+      std::swap(inv[col * n + c2], inv[piv * n + c2]);
+    }
+    const double dinv = 1.0 / a[col * n + col];
+    for (int c2 = 0; c2 < n; ++c2) {
+      a[col * n + c2] *= dinv;
+      inv[col * n + c2] *= dinv;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == col) continue;
+      const double f = a[r * n + col];
+      if (f == 0.0) continue;
+      for (int c2 = 0; c2 < n; ++c2) {
+        a[r * n + c2] -= f * a[col * n + c2];
+        inv[r * n + c2] -= f * inv[col * n + c2];
+      }
+    }
+  }
+  return inv;
+}
+
 // kappa = 1 variants of the per-axis self matrix (32, indexed by inside | full_lo << 1 |
 // gp_lo << 2 | full_hi << 3 | gp_hi << 4) and of a ghost-penalty neighbour coupling
 // (4, indexed by 2 * side + full), from the constant matrices of structured_matrices.
@@ -347,27 +378,32 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   const size_t o_fpo = L.take(sizeof(int32_t) * (nfl + 1));
   const size_t o_fpt = L.take(sizeof(T) * std::max<int64_t>(nfp, 1));
   const size_t o_fpw = L.take(sizeof(T) * std::max<int64_t>(nfp, 1));
-  std::vector<double> mats, lself, lnbgp;
+  std::vector<double> mats, lself0, lnbgp0;
   structured_matrices(H, mats);
-  // the device copy of the structured tables: dow, dnb (after the 16 matrices) carry h^{d-1} / 2
-  std::vector<double> smat = mats;
-  {
-    const double half_hf = 0.5 * std::pow(H.h, d - 1);
-    for (int i = 0; i < 4 * n; ++i) smat[16 * n * n + i] = half_hf * mats[16 * n * n + i];
-  }
+  // The structured kernel evaluates sum_a (M .. L_a .. M) u as (M (x) M (x) M) sum_a M_a^{-1} L_a u
+  // (3 mass sweeps in 3D instead of 5), so every per-axis 1D table is premultiplied by M^{-1}.
+  const int nn = n * n;
+  const std::vector<double> minv = invert_small(std::vector<double>(mats.begin() + nn, mats.begin() + 2 * nn), n);
+  auto premul = [&](const std::vector<double> &m, size_t blocks, bool transpose) {
+    std::vector<double> out(blocks * nn);
+    for (size_t b = 0; b < blocks; ++b)
+      for (int r = 0; r < n; ++r)
+        for (int c2 = 0; c2 < n; ++c2) {
+          double acc = 0.0;
+          for (int k = 0; k < n; ++k)
+            acc += minv[r * n + k] * (transpose ? m[b * nn + c2 * n + k] : m[b * nn + k * n + c2]);
+          out[b * nn + r * n + c2] = acc;
+        }
+    return out;
+  };
+  const std::vector<double> smat = premul(mats, 16, false), smatT = premul(mats, 16, true);
   const size_t o_smat = L.take(sizeof(T) * smat.size());
-  variant_tables(H, mats, lself, lnbgp);
+  const size_t o_smatT = L.take(sizeof(T) * smatT.size());
+  variant_tables(H, mats, lself0, lnbgp0);
+  const std::vector<double> lself = premul(lself0, 32, false), lnbgp = premul(lnbgp0, 4, false);
   const size_t o_lself = L.take(sizeof(T) * lself.size());
   const size_t o_lnbgp = L.take(sizeof(T) * lnbgp.size());
-  auto transposed = [&](const std::vector<double> &m) {
-    std::vector<double> t(m.size());
-    const int nn = n * n;
-    for (size_t b = 0; b < m.size() / nn; ++b)
-      for (int r = 0; r < n; ++r)
-        for (int c2 = 0; c2 < n; ++c2) t[b * nn + r * n + c2] = m[b * nn + c2 * n + r];
-    return t;
-  };
-  const std::vector<double> lselfT = transposed(lself), lnbgpT = transposed(lnbgp);
+  const std::vector<double> lselfT = premul(lself0, 32, true), lnbgpT = premul(lnbgp0, 4, true);
   const size_t o_lselfT = L.take(sizeof(T) * lselfT.size());
   const size_t o_lnbgpT = L.take(sizeof(T) * lnbgpT.size());
   // FP64: the 1D basis at every line and point (the FP64 pipe is the bottleneck there, HBM is not)
@@ -451,6 +487,7 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   put_t(o_fpw, fpt_w);
   put_t(o_lself, lself);
   put_t(o_smat, smat);
+  put_t(o_smatT, smatT);
   put_t(o_lnbgp, lnbgp);
   put_t(o_lselfT, lselfT);
   put_t(o_lnbgpT, lnbgpT);
@@ -513,6 +550,7 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   A.fpt_w = TP(o_fpw);
   A.lself = TP(o_lself);
   A.smat = TP(o_smat);
+  A.smatT = TP(o_smatT);
   A.lnbgp = TP(o_lnbgp);
   A.lselfT = TP(o_lselfT);
   A.lnbgpT = TP(o_lnbgpT);
@@ -548,10 +586,24 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   pd.n_vlines = nvl;
   pd.n_flines = nfl;
 
-  // constant tables
-  pd.struct_tables.assign(sizeof(T) * smat.size(), 0);
-  T *st = reinterpret_cast<T *>(pd.struct_tables.data());
-  for (size_t i = 0; i < smat.size(); ++i) st[i] = (T)smat[i];
+  // constant tables (layout of StructTables): the 16 matrices, M^{-1} dow and dnb (both with
+  // h^{d-1} / 2), and the columns of M^{-1} at the two face nodes
+  {
+    const double half_hf = 0.5 * std::pow(H.h, d - 1);
+    std::vector<double> tabs(mats.begin(), mats.begin() + 16 * nn);
+    for (int s2 = 0; s2 < 2; ++s2)
+      for (int r = 0; r < n; ++r) {
+        double acc = 0.0;
+        for (int k = 0; k < n; ++k) acc += minv[r * n + k] * (half_hf * mats[16 * nn + s2 * n + k]);
+        tabs.push_back(acc);
+      }
+    for (int i = 0; i < 2 * n; ++i) tabs.push_back(half_hf * mats[16 * nn + 2 * n + i]);
+    for (int s2 = 0; s2 < 2; ++s2)
+      for (int r = 0; r < n; ++r) tabs.push_back(minv[r * n + (s2 ? n - 1 : 0)]);
+    pd.struct_tables.assign(sizeof(T) * tabs.size(), 0);
+    T *st = reinterpret_cast<T *>(pd.struct_tables.data());
+    for (size_t i = 0; i < tabs.size(); ++i) st[i] = (T)tabs[i];
+  }
   pd.point_tables.assign(sizeof(T) * 6 * n, 0);
   T *ptab = reinterpret_cast<T *>(pd.point_tables.data());
   for (int i = 0; i < n; ++i) {
@@ -774,10 +826,10 @@ uf_status uf_get_info(const uf_operator *op, uf_info *info) {
         if (f % 2 == 1) ++struct_faces;  // count each interior face once (from its lower cell)
       }
     }
-  // structured kernel: per cell and axis one L line sweep (n^{d+1} FMA + n^d scalings),
-  // ghost-penalty neighbour couplings as full line sweeps (n^{d+1} FMA), SIPG-only neighbour
-  // couplings in rank-2 form (4n + 8 flops per line), and the shared in-face mass sweeps
-  // (5 in 3D, 2 in 2D, n^{d+1} FMA each); plus the per-cell matrix build if kappa varies.
+  // structured kernel: per cell and axis one M^{-1} L line sweep (n^{d+1} FMA), ghost-penalty
+  // neighbour couplings as full line sweeps (n^{d+1} FMA), SIPG-only neighbour couplings in
+  // rank-2 form, the sum of the axes ((d - 1) n^d adds) and one mass sweep per direction
+  // (n^{d+1} FMA each); plus the per-cell matrix build if kappa varies.
   int64_t gp_faces_cell = 0, r2_faces_cell = 0;
   for (int64_t e = 0; e < H.n_active; ++e)
     for (int f = 0; f < nf; ++f) {
@@ -790,10 +842,12 @@ uf_status uf_get_info(const uf_operator *op, uf_info *info) {
   const double sweep = nline * n * n;  // FMA per line sweep of a cell
   const bool uni = kappa_is_uniform(H.kappa);
   // uniform kappa: lines for kappa = 1, rows scaled once (not at all for kappa = 1); rank-2
-  // couplings 2n FMA + 2 per line (the face factors are folded into the 1D trace tables)
-  double fl_struct = 2.0 * ((double)H.n_active * (d * sweep + (d == 3 ? 5 : 2) * sweep) +
+  // couplings per line: the neighbour's derivative (n FMA), two rank-1 updates (2n FMA) and the
+  // coefficient (1 FMA; 2 multiplies more when kappa varies)
+  double fl_struct = 2.0 * ((double)H.n_active * (d * sweep + d * sweep) +
                             (double)gp_faces_cell * sweep) +
-                     (double)r2_faces_cell * nline * (uni ? 4 * n + 3 : 4 * n + 6);
+                     (double)H.n_active * (d - 1) * nd +
+                     (double)r2_faces_cell * nline * (uni ? 6 * n + 2 : 6 * n + 5);
   if (uni && H.kappa[0] != 1.0) fl_struct += (double)H.n_active * nd;
   if (!uni) fl_struct += (double)H.n_active * d * n * n * 2.0 * 13.0;
   // cut-cell kernel: 1D basis (values and derivatives) 14n - 8, values only 6n - 4 flops when

@@ -33,7 +33,8 @@ struct StructTables {
   T mass[N * N];
   T a[2][N * N], pen[2][N * N], gp[2][N * N];
   T b[2][N * N], c[2][N * N], qn[2][N * N], hn[2][N * N];
-  T dow[2][N], dnb[2][N];
+  T dow[2][N], dnb[2][N];  // dow premultiplied by M^{-1}; both carry h^{d-1} / 2
+  T me[2][N];              // column of M^{-1} at the face node of side s (0 or N - 1)
 };
 
 // 1D data for point evaluation of the Lagrange basis at arbitrary reference coordinates.
@@ -87,14 +88,17 @@ struct DevArrays {
   const T *fline_o;           // outer in-face reference coordinate (3D)
   const int32_t *fpt_off;     // [n_flines + 1]
   const T *fpt_t, *fpt_w;     // [n_face_points]
-  // Structured 1D matrices for kappa = 1, indexed by the face flags of one axis:
-  // lself[v], v = inside | full_lo << 1 | gp_lo << 2 | full_hi << 3 | gp_hi << 4, and
-  // lnbgp[2 * s + full] for a ghost-penalty face on side s.  When kappa is uniform
-  // (kappa_uniform != 0) every structured term scales with that value.
+  // Structured 1D matrices for kappa = 1, indexed by the face flags of one axis, all
+  // premultiplied by M^{-1} (the structured kernel applies M (x) M (x) M once to the sum of the
+  // axes' line results): lself[v], v = inside | full_lo << 1 | gp_lo << 2 | full_hi << 3 |
+  // gp_hi << 4, and lnbgp[2 * s + full] for a ghost-penalty face on side s.  When kappa is
+  // uniform (kappa_uniform != 0) every structured term scales with that value.
   const T *lself, *lnbgp;
-  const T *lselfT, *lnbgpT;  // the same tables transposed (adjoint)
-  // the StructTables in global memory (flat, same layout), for reads with a per-thread index
-  const T *smat;
+  const T *lselfT, *lnbgpT;  // M^{-1} times the transposed tables (adjoint)
+  // the 16 constant 1D matrices Q_k of StructTables (same order) premultiplied by M^{-1}, for
+  // the per-cell matrices when kappa varies (read with a per-thread index)
+  const T *smat;   // M^{-1} Q_k
+  const T *smatT;  // M^{-1} Q_k^T (adjoint)
   // FP64 only (null otherwise): the 1D basis at every line and point, precomputed at creation
   // (values and derivatives; faces values only): vline_b [line][4n] = phi, phi' of the lower and
   // upper outer coordinate; vpt_b / spt_b [point][2n]; fline_b [face line][n]; fpt_b [point][n].

@@ -138,11 +138,11 @@ __host__ __device__ constexpr int struct_cells_per_block() {
 // Structured terms
 // ------------------------------------------------------------------------------------------
 //
-// y_K = sum_a (M .. L_a .. M) u_K + sum_faces (M .. L_f .. M) u_nb with W_a = L_a u_K +
-// sum_{faces along a} L_f u_nb computed line by line (phase 1), then the in-face mass sweeps
-// shared between axes (phase 2):
-//   3D: y = M_z (M_y W_x + M_x W_y) + M_y M_x W_z     (5 sweeps instead of 6)
-//   2D: y = M_y W_x + M_x W_y
+// y_K = sum_a (M .. L_a .. M) u_K + sum_faces (M .. L_f .. M) u_nb = (M (x) .. (x) M) Z with
+// Z = sum_a Z_a, Z_a = M^{-1} (L_a u_K + sum_{faces along a} L_f u_nb): the 1D tables carry
+// M^{-1}, so phase 1 computes every Z_a line by line and phase 2 sums the axes and applies the
+// mass matrix once per direction (3 sweeps in 3D, 2 in 2D, instead of 5 and 2 for
+// M_z (M_y W_x + M_x W_y) + M_y M_x W_z with W_a = M_a Z_a).
 template <typename T, int N>
 __device__ __forceinline__ void apply_line(const T *__restrict__ Lm, const T *u, T *w, bool accumulate) {
 #pragma unroll
@@ -242,12 +242,10 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
     // per-cell 1D matrices from the constant ones and kappa; the constant matrices are read from
     // their global-memory copy (each thread reads its own entry: coalesced through L1), matrix
     // `which` (kv 0, mass 1, a 2, pen 4, gp 6, b 8, c 10, qn 12, hn 14, + side) at which * NN
-    const T *Q = d.smat;
+    const T *Q = ADJ ? d.smatT : d.smat;  // M^{-1} Q_k (adjoint: M^{-1} Q_k^T)
     for (int a = 0; a < DIM; ++a)
       for (int idx = t; idx < NN; idx += TPC) {
-        const int r = idx / N, m = idx % N;
-        const int tr = ADJ ? (m * N + r) : idx;
-        T self = inside ? kap * __ldg(Q + tr) : T(0);
+        T self = inside ? kap * __ldg(Q + idx) : T(0);
         T ln[2] = {T(0), T(0)};
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
@@ -255,8 +253,8 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
           if (nb[f] < 0) continue;
           const bool full = bit(fl, bit_full(f));
           const bool gp = bit(fl, bit_gp(f));
-          if (full) self += kap * __ldg(Q + (2 + s) * NN + tr) + kavg[f] * __ldg(Q + (4 + s) * NN + tr);
-          if (gp) self += kavg[f] * __ldg(Q + (6 + s) * NN + tr);
+          if (full) self += kap * __ldg(Q + (2 + s) * NN + idx) + kavg[f] * __ldg(Q + (4 + s) * NN + idx);
+          if (gp) self += kavg[f] * __ldg(Q + (6 + s) * NN + idx);
           if (gp) {
             if (!ADJ) {
               if (full)
@@ -267,9 +265,9 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
               // transpose of the neighbour's coupling toward this cell (its face 1 - s)
               const int so = 1 - s;
               if (full)
-                ln[s] += knb[f] * __ldg(Q + (8 + so) * NN + tr) + kap * __ldg(Q + (10 + so) * NN + tr) +
-                         kavg[f] * __ldg(Q + (12 + so) * NN + tr);
-              ln[s] += kavg[f] * __ldg(Q + (14 + so) * NN + tr);
+                ln[s] += knb[f] * __ldg(Q + (8 + so) * NN + idx) + kap * __ldg(Q + (10 + so) * NN + idx) +
+                         kavg[f] * __ldg(Q + (12 + so) * NN + idx);
+              ln[s] += kavg[f] * __ldg(Q + (14 + so) * NN + idx);
             }
           }
         }
@@ -322,20 +320,22 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
             apply_line<T, N>(s_l[c][a][1 + s], un, w, true);
           }
         } else {
-          // rank-2 SIPG coupling (the transposed coupling of a symmetric flux is the same form);
-          // the device copies of dow and dnb carry the factor h^{d-1} / 2
+          // rank-2 SIPG coupling (the transposed coupling of a symmetric flux is the same form):
+          // M^{-1} (ca dow - g e_own) with the device tables M^{-1} dow and me = M^{-1} e_own;
+          // dow and dnb carry the factor h^{d-1} / 2
           const T alpha = un[s ? 0 : N - 1];
           T beta = T(0);
 #pragma unroll
           for (int m = 0; m < N; ++m) beta = fma(tab.dnb[s][m], un[m], beta);
           const T ca = uniform ? alpha : kap * alpha;
-#pragma unroll
-          for (int r = 0; r < N; ++r) w[r] = fma(ca, tab.dow[s][r], w[r]);
+          T g;
           if constexpr (uniform) {
-            w[s ? N - 1 : 0] -= fma(sc.hf_sigma, alpha, beta);
+            g = fma(sc.hf_sigma, alpha, beta);
           } else {
-            w[s ? N - 1 : 0] -= fma(knb[f], beta, (sc.hf_sigma * kavg[f]) * alpha);
+            g = fma(knb[f], beta, (sc.hf_sigma * kavg[f]) * alpha);
           }
+#pragma unroll
+          for (int r = 0; r < N; ++r) w[r] = fma(-g, tab.me[s][r], fma(ca, tab.dow[s][r], w[r]));
         }
       }
 #pragma unroll
@@ -344,54 +344,65 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
   }
   __syncthreads();
 
-  // ---- phase 2: in-face mass sweeps (M symmetric: the adjoint uses the same sweeps)
+  // ---- phase 2: y = (M (x) .. (x) M) sum_a Z_a (M symmetric: the adjoint uses the same sweeps)
   const T *M = tab.mass;
   if constexpr (DIM == 2) {
     if (has_cell) {
-      mass_line<T, N>(M, s_w[0][c], sline_base<DIM, N>(1, t), P);  // M_y W_x
-      mass_line<T, N>(M, s_w[1][c], sline_base<DIM, N>(0, t), 1);  // M_x W_y
-    }
-    __syncthreads();
-    if (has_cell) {
-      // y = W_x + W_y; thread t writes the x-line t
-      const int base = line_base<DIM, N>(0, t), sb = sline_base<DIM, N>(0, t);
-#pragma unroll
-      for (int r = 0; r < N; ++r) {
-        const T v = s_w[0][c][sb + r] + s_w[1][c][sb + r];
-        y[(size_t)e * ND + base + r] = scale_rows ? yscale * v : v;
-      }
-    }
-  } else {
-    if (has_cell) {
-      mass_line<T, N>(M, s_w[0][c], sline_base<DIM, N>(1, t), P);  // W_x <- M_y W_x
-      mass_line<T, N>(M, s_w[2][c], sline_base<DIM, N>(0, t), 1);  // W_z <- M_x W_z
-    }
-    __syncthreads();
-    if (has_cell) {
-      // W_x += M_x W_y (x-lines)
+      // Z_x <- M_x (Z_x + Z_y) along x-lines
       const int bx = sline_base<DIM, N>(0, t);
       T a[N];
 #pragma unroll
-      for (int m = 0; m < N; ++m) a[m] = s_w[1][c][bx + m];
+      for (int m = 0; m < N; ++m) a[m] = s_w[0][c][bx + m] + s_w[1][c][bx + m];
 #pragma unroll
       for (int r = 0; r < N; ++r) {
-        T acc = s_w[0][c][bx + r];
+        T acc = T(0);
 #pragma unroll
         for (int m = 0; m < N; ++m) acc = fma(M[r * N + m], a[m], acc);
         s_w[0][c][bx + r] = acc;
       }
-      mass_line<T, N>(M, s_w[2][c], sline_base<DIM, N>(1, t), P);  // W_z <- M_y W_z
     }
     __syncthreads();
     if (has_cell) {
-      // y = M_z W_x + W_z along z-lines
+      // y = M_y Z_x along y-lines
+      const int by = line_base<DIM, N>(1, t), sby = sline_base<DIM, N>(1, t);
+      T a[N];
+#pragma unroll
+      for (int m = 0; m < N; ++m) a[m] = s_w[0][c][sby + m * P];
+#pragma unroll
+      for (int r = 0; r < N; ++r) {
+        T acc = T(0);
+#pragma unroll
+        for (int m = 0; m < N; ++m) acc = fma(M[r * N + m], a[m], acc);
+        y[(size_t)e * ND + by + r * N] = scale_rows ? yscale * acc : acc;
+      }
+    }
+  } else {
+    if (has_cell) {
+      // Z_x <- M_x (Z_x + Z_y + Z_z) along x-lines
+      const int bx = sline_base<DIM, N>(0, t);
+      T a[N];
+#pragma unroll
+      for (int m = 0; m < N; ++m) a[m] = (s_w[0][c][bx + m] + s_w[1][c][bx + m]) + s_w[2][c][bx + m];
+#pragma unroll
+      for (int r = 0; r < N; ++r) {
+        T acc = T(0);
+#pragma unroll
+        for (int m = 0; m < N; ++m) acc = fma(M[r * N + m], a[m], acc);
+        s_w[0][c][bx + r] = acc;
+      }
+    }
+    __syncthreads();
+    if (has_cell) mass_line<T, N>(M, s_w[0][c], sline_base<DIM, N>(1, t), P);  // Z_x <- M_y Z_x
+    __syncthreads();
+    if (has_cell) {
+      // y = M_z Z_x along z-lines
       const int bz = line_base<DIM, N>(2, t), sbz = sline_base<DIM, N>(2, t);
       T a[N];
 #pragma unroll
       for (int m = 0; m < N; ++m) a[m] = s_w[0][c][sbz + m * P * N];
 #pragma unroll
       for (int r = 0; r < N; ++r) {
-        T acc = s_w[2][c][sbz + r * P * N];
+        T acc = T(0);
 #pragma unroll
         for (int m = 0; m < N; ++m) acc = fma(M[r * N + m], a[m], acc);
         y[(size_t)e * ND + bz + r * N * N] = scale_rows ? yscale * acc : acc;
