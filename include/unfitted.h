@@ -157,8 +157,14 @@ uf_status uf_vmult(uf_operator *op, int precision, void *y, const void *x, void 
 uf_status uf_vmult_adjoint(uf_operator *op, int precision, void *y, const void *g, void *stream);
 
 /* End-to-end y = A x with HOST buffers: copies x (host, pinned or pageable) to a library-owned
- * device buffer allocated at creation, applies A, copies y back, and synchronises `stream`
- * before returning.  Errors as uf_vmult. */
+ * device buffer allocated at creation, applies A, copies y back, and synchronises before
+ * returning.  Discontinuous operators with at least 8192 cells run it as a pipeline over 16
+ * parts of consecutive cells: x is copied in part by part on a library-owned stream, each part's
+ * kernels start on a library-owned stream of its own (earlier parts at higher priority) once x has
+ * reached its face neighbours, and its rows of y are copied out on a second library-owned stream
+ * while later parts compute (the copies overlap the kernels when the host buffers are pinned);
+ * the result equals uf_vmult's bit for bit, and later work on `stream` is ordered after it.  The
+ * first call creates the streams (non-blocking) and their events.  Errors as uf_vmult. */
 uf_status uf_vmult_host(uf_operator *op, int precision, void *y_host, const void *x_host,
                         void *stream);
 

@@ -3,7 +3,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <numeric>
@@ -292,6 +294,35 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
     cut_idx[i] = order[i];
     cut_list[i] = H.cut_cells[order[i]];
   }
+  // parts of the host-buffer pipeline: kPipeParts runs of consecutive cells (discontinuous
+  // operators with enough cells); the cut cells of each part keep the order above, so each part
+  // has the same three lane classes; all parts' lists are stored one after the other
+  const int n_parts = (!H.cg && na >= 8 * 1024) ? uf::kPipeParts : 1;
+  std::vector<int32_t> part_list, part_idx;
+  std::vector<std::array<int32_t, 6>> part_meta;  // cell_begin, cell_end, 4 slot bounds
+  {
+    std::vector<std::vector<int32_t>> bucket(n_parts);
+    auto part_of = [&](int64_t e) { return (int)((e * n_parts) / na); };
+    for (int64_t i = 0; i < nc; ++i) bucket[part_of(H.cut_cells[order[i]])].push_back(order[i]);
+    for (int pi = 0; pi < n_parts; ++pi) {
+      std::array<int32_t, 6> m{};
+      // the cells with part_of(e) == pi: ceil(pi na / n_parts) <= e < ceil((pi + 1) na / n_parts)
+      const int64_t cb = (na * pi + n_parts - 1) / n_parts, ce = (na * (pi + 1) + n_parts - 1) / n_parts;
+      m[0] = (int32_t)cb;
+      m[1] = (int32_t)ce;
+      m[2] = (int32_t)part_list.size();
+      int cls[3] = {0, 0, 0};
+      for (int32_t c : bucket[pi]) {
+        part_list.push_back(H.cut_cells[c]);
+        part_idx.push_back(c);
+        ++cls[lanes[c] == 32 ? 0 : (lanes[c] == 16 ? 1 : 2)];
+      }
+      m[3] = m[2] + cls[0];
+      m[4] = m[3] + cls[1];
+      m[5] = m[4] + cls[2];
+      part_meta.push_back(m);
+    }
+  }
 
   // ---- line-structured point data (lines of a cell sorted by axis)
   std::vector<int32_t> vline_koff(nc * 4), vpt_off, lsurf, fline_koff(nc * nf * 3), fpt_off, vline_grp;
@@ -361,6 +392,8 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   const size_t o_kappa = L.take(sizeof(T) * na);
   const size_t o_clist = L.take(sizeof(int32_t) * std::max<int64_t>(nc, 1));
   const size_t o_cidx = L.take(sizeof(int32_t) * std::max<int64_t>(nc, 1));
+  const size_t o_plist = L.take(sizeof(int32_t) * std::max<int64_t>(nc, 1));
+  const size_t o_pidx = L.take(sizeof(int32_t) * std::max<int64_t>(nc, 1));
   const size_t o_vlk = L.take(sizeof(int32_t) * std::max<int64_t>(nc * 4, 1));
   const size_t o_vo0 = L.take(sizeof(T) * std::max<int64_t>(nvl, 1));
   const size_t o_vo1 = L.take(sizeof(T) * std::max<int64_t>(nvl, 1));
@@ -469,6 +502,8 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   put_t(o_kappa, H.kappa);
   put(o_clist, cut_list.data(), sizeof(int32_t) * nc);
   put(o_cidx, cut_idx.data(), sizeof(int32_t) * nc);
+  put(o_plist, part_list.data(), sizeof(int32_t) * nc);
+  put(o_pidx, part_idx.data(), sizeof(int32_t) * nc);
   put_i(o_vlk, vline_koff);
   put_t(o_vo0, vline_o0);
   put_t(o_vo1, vline_o1);
@@ -532,6 +567,33 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   A.kappa = pd.kappa_dev;
   A.cut_list = I32(o_clist);
   A.cut_idx = I32(o_cidx);
+  {
+    // parts: face neighbours lie within `halo` cells of a cell
+    int64_t halo = 0;
+    for (int64_t e = 0; e < na; ++e)
+      for (int f = 0; f < nf; ++f) {
+        const int32_t nb = H.nbr[e * nf + f];
+        if (nb >= 0) halo = std::max<int64_t>(halo, std::llabs((long long)(nb - e)));
+      }
+    pd.parts.clear();
+    pd.part_needs.clear();
+    for (size_t pi = 0; pi < part_meta.size(); ++pi) {
+      const auto &m = part_meta[pi];
+      uf::LaunchRange r{};
+      r.cell_begin = m[0];
+      r.cell_end = m[1];
+      r.cut_list = I32(o_plist);
+      r.cut_idx = I32(o_pidx);
+      for (int i = 0; i < 4; ++i) r.split[i] = m[2 + i];
+      pd.parts.push_back(r);
+    }
+    for (size_t pi = 0; pi < part_meta.size(); ++pi) {
+      const int64_t last = std::min<int64_t>(part_meta[pi][1] + halo, na) - 1;
+      int need = (int)pi;
+      while (need + 1 < (int)part_meta.size() && part_meta[need + 1][0] <= last) ++need;
+      pd.part_needs.push_back(need);
+    }
+  }
   A.vline_koff = I32(o_vlk);
   A.vline_o0 = TP(o_vo0);
   A.vline_o1 = TP(o_vo1);
@@ -642,7 +704,7 @@ void release(PrecisionData<T> &pd) {
 
 template <typename T>
 uf_status vmult_t(uf_operator *op, PrecisionData<T> &pd, void *y, const void *x, void *stream,
-                  bool adjoint) {
+                  bool adjoint, const uf::LaunchRange *rg = nullptr) {
   if (!pd.present) return fail(UF_EINVAL, "operator was not created with this precision");
   const bool cg = op->host.cg;
   const int64_t nvec = cg ? op->host.n_cg : op->host.n_active * op->host.ndof;
@@ -652,7 +714,7 @@ uf_status vmult_t(uf_operator *op, PrecisionData<T> &pd, void *y, const void *x,
   if (xb < yb + bytes && yb < xb + bytes) return fail(UF_EINVAL, "x and y overlap");
   DeviceGuard guard(op->device);
   void *const *ev = nullptr;
-  if (op->prof_next < op->prof.size()) {
+  if (!rg && op->prof_next < op->prof.size()) {
     ProfSlot &slot = op->prof[op->prof_next++];
     slot.prec = sizeof(T) == 8 ? 0 : 1;
     slot.adjoint = adjoint ? 1 : 0;
@@ -666,7 +728,7 @@ uf_status vmult_t(uf_operator *op, PrecisionData<T> &pd, void *y, const void *x,
   if (err == 0)
     err = uf::launch_vmult<T>(op->host.dim, op->host.n, pd.arrays, pd.struct_tables.data(),
                               pd.point_tables.data(), pd.scalars, cg ? pd.y_loc : static_cast<T *>(y),
-                              cg ? pd.x_loc : static_cast<const T *>(x), adjoint, stream, ev);
+                              cg ? pd.x_loc : static_cast<const T *>(x), adjoint, stream, ev, rg);
   if (err == 0 && cg)
     err = uf::cg_node_sum<T>(static_cast<T *>(y), pd.y_loc, pd.cg_own_off, pd.cg_own_idx, op->host.n_cg, cs);
   if (err != 0)
@@ -697,6 +759,79 @@ uf_status vmult_dispatch(uf_operator *op, int precision, void *y, const void *x,
   if (st != UF_OK) return st;
   if (precision == UF_FP64) return vmult_t<double>(op, op->f64, y, x, stream, adjoint);
   return vmult_t<float>(op, op->f32, y, x, stream, adjoint);
+}
+
+}  // namespace
+
+namespace {
+
+// Host-buffer y = A x of a discontinuous operator as a pipeline over consecutive-cell parts: all
+// parts of x are copied in on one stream, part i's kernels start on a stream of their own once x
+// reaches its face neighbours (the parts write disjoint rows of y, so their kernels may overlap
+// one another), and its rows of y are copied out on a third stream, so the copies overlap the
+// kernels.  The results equal the single-launch path bit for bit (every cell is evaluated by the
+// same code from the same data).
+template <typename T>
+uf_status host_pipeline(uf_operator *op, PrecisionData<T> &pd, T *y_host, const T *x_host,
+                        cudaStream_t s, bool adjoint) {
+  const int np = (int)pd.parts.size();
+  cudaError_t err = cudaSuccess;
+  if (!op->pipe_in) err = cudaStreamCreateWithFlags(&op->pipe_in, cudaStreamNonBlocking);
+  if (err == cudaSuccess && !op->pipe_out) err = cudaStreamCreateWithFlags(&op->pipe_out, cudaStreamNonBlocking);
+  // earlier parts run at higher priority: the parts overlap where one alone would leave SMs idle,
+  // but finish roughly in order, so the copies out start early
+  int prio_low = 0, prio_high = 0;
+  if (err == cudaSuccess) err = cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+  while (err == cudaSuccess && op->pipe_run.size() < (size_t)uf::kPipeParts) {
+    const int i = (int)op->pipe_run.size();
+    const int levels = prio_low - prio_high + 1;  // priorities run from prio_high (most urgent) up
+    const int prio = prio_high + (levels > 1 ? (i * levels) / uf::kPipeParts : 0);
+    cudaStream_t r;
+    err = cudaStreamCreateWithPriority(&r, cudaStreamNonBlocking, prio);
+    if (err == cudaSuccess) op->pipe_run.push_back(r);
+  }
+  while (err == cudaSuccess && op->pipe_ev.size() < (size_t)(1 + 2 * uf::kPipeParts)) {
+    cudaEvent_t e;
+    err = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    if (err == cudaSuccess) op->pipe_ev.push_back(e);
+  }
+  if (err != cudaSuccess) return fail(UF_ECUDA, std::string("pipeline setup: ") + cudaGetErrorString(err));
+  const size_t nd = (size_t)op->host.ndof;
+  T *xb = static_cast<T *>(pd.xbuf);
+  T *yb = static_cast<T *>(pd.ybuf);
+  cudaEvent_t *ev = op->pipe_ev.data();
+  // the copies start after the work already queued on the caller's stream
+  err = cudaEventRecord(ev[0], s);
+  if (err == cudaSuccess) err = cudaStreamWaitEvent(op->pipe_in, ev[0], 0);
+  if (err == cudaSuccess) err = cudaStreamWaitEvent(op->pipe_out, ev[0], 0);
+  for (int j = 0; j < np && err == cudaSuccess; ++j) {
+    const size_t off = nd * (size_t)pd.parts[j].cell_begin;
+    const size_t cnt = nd * (size_t)(pd.parts[j].cell_end - pd.parts[j].cell_begin);
+    err = cudaMemcpyAsync(xb + off, x_host + off, sizeof(T) * cnt, cudaMemcpyHostToDevice, op->pipe_in);
+    if (err == cudaSuccess) err = cudaEventRecord(ev[1 + j], op->pipe_in);
+  }
+  if (err != cudaSuccess) return fail(UF_ECUDA, std::string("H2D copy: ") + cudaGetErrorString(err));
+  for (int i = 0; i < np; ++i) {
+    cudaStream_t run = op->pipe_run[i];
+    err = cudaStreamWaitEvent(run, ev[0], 0);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(run, ev[1 + pd.part_needs[i]], 0);
+    if (err != cudaSuccess) return fail(UF_ECUDA, std::string("pipeline wait: ") + cudaGetErrorString(err));
+    const uf_status st = vmult_t<T>(op, pd, yb, xb, run, adjoint, &pd.parts[i]);
+    if (st != UF_OK) return st;
+    const size_t off = nd * (size_t)pd.parts[i].cell_begin;
+    const size_t cnt = nd * (size_t)(pd.parts[i].cell_end - pd.parts[i].cell_begin);
+    err = cudaEventRecord(ev[1 + uf::kPipeParts + i], run);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(op->pipe_out, ev[1 + uf::kPipeParts + i], 0);
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(y_host + off, yb + off, sizeof(T) * cnt, cudaMemcpyDeviceToHost, op->pipe_out);
+    if (err != cudaSuccess) return fail(UF_ECUDA, std::string("D2H copy: ") + cudaGetErrorString(err));
+  }
+  // every part's kernels precede its copy out on pipe_out; later work on the caller's stream
+  // follows all of them
+  err = cudaStreamSynchronize(op->pipe_out);
+  for (int i = 0; i < np && err == cudaSuccess; ++i) err = cudaStreamWaitEvent(s, ev[1 + uf::kPipeParts + i], 0);
+  if (err != cudaSuccess) return fail(UF_ECUDA, std::string("D2H copy: ") + cudaGetErrorString(err));
+  return UF_OK;
 }
 
 }  // namespace
@@ -924,6 +1059,14 @@ static uf_status vmult_host_impl(uf_operator *op, int precision, void *y_host,
   uf_status st = check_vmult_args(op, precision, y_host, x_host);
   if (st != UF_OK) return st;
   DeviceGuard guard(op->device);
+  if (!op->host.cg) {
+    if (precision == UF_FP64 && op->f64.present && op->f64.parts.size() > 1)
+      return host_pipeline<double>(op, op->f64, static_cast<double *>(y_host),
+                                   static_cast<const double *>(x_host), reinterpret_cast<cudaStream_t>(stream), adjoint);
+    if (precision == UF_FP32 && op->f32.present && op->f32.parts.size() > 1)
+      return host_pipeline<float>(op, op->f32, static_cast<float *>(y_host),
+                                  static_cast<const float *>(x_host), reinterpret_cast<cudaStream_t>(stream), adjoint);
+  }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const size_t elem = precision == UF_FP64 ? sizeof(double) : sizeof(float);
   const size_t bytes = elem * (size_t)(op->host.cg ? op->host.n_cg : op->host.n_active * op->host.ndof);
@@ -1094,6 +1237,10 @@ uf_status uf_destroy(uf_operator *op) {
     if (op->kg_scratch) cudaFree(op->kg_scratch);
     for (ProfSlot &slot : op->prof)
       for (int k = 0; k < 4; ++k) cudaEventDestroy(slot.ev[k]);
+    for (cudaEvent_t e : op->pipe_ev) cudaEventDestroy(e);
+    for (cudaStream_t r : op->pipe_run) cudaStreamDestroy(r);
+    if (op->pipe_in) cudaStreamDestroy(op->pipe_in);
+    if (op->pipe_out) cudaStreamDestroy(op->pipe_out);
     release(op->f64);
     release(op->f32);
   }

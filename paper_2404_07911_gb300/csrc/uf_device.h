@@ -117,12 +117,21 @@ inline int cut_lanes_for(int n, int64_t lines) {
   return (n > 5 || lines > 16) ? 32 : (lines > 8 ? 16 : 8);
 }
 
+// A part of y = A x: the active cells [cell_begin, cell_end) and, of the cut cells among them,
+// the slots [split[0], split[3]) of cut_list / cut_idx (32-lane class up to split[1], 16-lane
+// class up to split[2], then 8 lanes).  The parts of the host-buffer pipeline.
+struct LaunchRange {
+  int32_t cell_begin, cell_end;
+  const int32_t *cut_list, *cut_idx;
+  int32_t split[4];
+};
+
 // Launchers (uf_kernels_*.cu).  Return cudaError_t as int.
 // ev: optional events recorded around the structured kernel (ev[0], ev[1]) and the cut-cell
-// kernel (ev[2], ev[3]); nullptr when not profiling.
+// kernel (ev[2], ev[3]); nullptr when not profiling.  rg: nullptr for the whole operator.
 template <typename T>
 int launch_vmult(int dim, int n, const DevArrays<T> &d, const void *tables_struct,
                  const void *tables_point, const Scalars<T> &s, T *y, const T *x, bool adjoint,
-                 void *stream, void *const *ev);
+                 void *stream, void *const *ev, const LaunchRange *rg = nullptr);
 
 }  // namespace uf

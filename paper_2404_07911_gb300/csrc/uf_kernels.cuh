@@ -175,7 +175,8 @@ __device__ __forceinline__ void mass_line(const T *__restrict__ M, T *v, int bas
 template <typename T, int DIM, int N, bool ADJ, bool UNI>
 __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ StructTables<T, N> tab,
                                                      const DevArrays<T> d, const Scalars<T> sc,
-                                                     T *__restrict__ y, const T *__restrict__ x) {
+                                                     T *__restrict__ y, const T *__restrict__ x,
+                                                     int cell_begin, int cell_end) {
   using G = Geo<DIM, N>;
   constexpr int ND = G::ND, NL = G::NL, NF = G::NF, NN = N * N;
   constexpr int CPB = struct_cells_per_block<T, DIM, N>();
@@ -187,16 +188,16 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
   __shared__ __align__(16) T s_l[CPB][DIM][3][NN];  // per-cell matrices when kappa is not uniform
 
   const int tid = threadIdx.x;
-  const int first = blockIdx.x * CPB;
+  const int first = cell_begin + blockIdx.x * CPB;
   const int c = tid / TPC;
   const int t = tid % TPC;
   const bool active_thread = (c < CPB);
   const int e = first + c;
-  const bool has_cell = active_thread && (e < d.n_active);
+  const bool has_cell = active_thread && (e < cell_end);
   constexpr bool uniform = UNI;  // kappa uniform (d.kappa_uniform != 0)
 
   {
-    const int ncell = min(CPB, d.n_active - first);
+    const int ncell = min(CPB, cell_end - first);
     const T *src = x + (size_t)first * ND;
     for (int i = tid; i < ncell * ND; i += blockDim.x) {
       const int l = i % ND;
@@ -1143,37 +1144,48 @@ int launch_cut(const PointTables<T, N> &ptab, const DevArrays<T> &d, const Scala
 }
 
 template <typename T, int DIM, int N>
-int launch_vmult_t(const DevArrays<T> &d, const void *tables_struct, const void *tables_point,
+int launch_vmult_t(const DevArrays<T> &d0, const void *tables_struct, const void *tables_point,
                    const Scalars<T> &s, T *y, const T *x, bool adjoint, cudaStream_t stream,
-                   void *const *ev) {
+                   void *const *ev, const LaunchRange *rg) {
   using G = Geo<DIM, N>;
   constexpr int CPB = struct_cells_per_block<T, DIM, N>();
+  // whole operator, or one part of it (its cells and its cut-cell slots in the part's own list)
+  DevArrays<T> d = d0;
+  int cb = 0, ce = d.n_active;
+  int sp[4] = {0, d.cut_split[0], d.cut_split[1], d.n_cut};
+  if (rg) {
+    cb = rg->cell_begin;
+    ce = rg->cell_end;
+    d.cut_list = rg->cut_list;
+    d.cut_idx = rg->cut_idx;
+    for (int i = 0; i < 4; ++i) sp[i] = rg->split[i];
+  }
   const int threads = ((CPB * G::NL + 31) / 32) * 32;
-  const int blocks = (d.n_active + CPB - 1) / CPB;
+  const int blocks = (ce - cb + CPB - 1) / CPB;
   const auto &tab = *reinterpret_cast<const StructTables<T, N> *>(tables_struct);
   if (ev) cudaEventRecord(static_cast<cudaEvent_t>(ev[0]), stream);
   if (blocks > 0) {
     const bool uni = d.kappa_uniform != 0;
     if (adjoint && uni)
-      struct_kernel<T, DIM, N, true, true><<<blocks, threads, 0, stream>>>(tab, d, s, y, x);
+      struct_kernel<T, DIM, N, true, true><<<blocks, threads, 0, stream>>>(tab, d, s, y, x, cb, ce);
     else if (adjoint)
-      struct_kernel<T, DIM, N, true, false><<<blocks, threads, 0, stream>>>(tab, d, s, y, x);
+      struct_kernel<T, DIM, N, true, false><<<blocks, threads, 0, stream>>>(tab, d, s, y, x, cb, ce);
     else if (uni)
-      struct_kernel<T, DIM, N, false, true><<<blocks, threads, 0, stream>>>(tab, d, s, y, x);
+      struct_kernel<T, DIM, N, false, true><<<blocks, threads, 0, stream>>>(tab, d, s, y, x, cb, ce);
     else
-      struct_kernel<T, DIM, N, false, false><<<blocks, threads, 0, stream>>>(tab, d, s, y, x);
+      struct_kernel<T, DIM, N, false, false><<<blocks, threads, 0, stream>>>(tab, d, s, y, x, cb, ce);
   }
   if (ev) cudaEventRecord(static_cast<cudaEvent_t>(ev[1]), stream);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return (int)err;
   if (ev) cudaEventRecord(static_cast<cudaEvent_t>(ev[2]), stream);
-  if (d.n_cut > 0) {
+  if (sp[3] > sp[0]) {
     const auto &ptab = *reinterpret_cast<const PointTables<T, N> *>(tables_point);
     // the three lane classes are contiguous in cut_list (32, 16, 8 lanes per cell)
-    int e2 = launch_cut<T, DIM, N, 32>(ptab, d, s, y, x, stream, 0, d.cut_split[0]);
+    int e2 = launch_cut<T, DIM, N, 32>(ptab, d, s, y, x, stream, sp[0], sp[1]);
     if constexpr (N <= 5) {
-      if (e2 == 0) e2 = launch_cut<T, DIM, N, 16>(ptab, d, s, y, x, stream, d.cut_split[0], d.cut_split[1]);
-      if (e2 == 0) e2 = launch_cut<T, DIM, N, 8>(ptab, d, s, y, x, stream, d.cut_split[1], d.n_cut);
+      if (e2 == 0) e2 = launch_cut<T, DIM, N, 16>(ptab, d, s, y, x, stream, sp[1], sp[2]);
+      if (e2 == 0) e2 = launch_cut<T, DIM, N, 8>(ptab, d, s, y, x, stream, sp[2], sp[3]);
     }
     if (e2 != 0) return e2;
   }
@@ -1184,9 +1196,9 @@ int launch_vmult_t(const DevArrays<T> &d, const void *tables_struct, const void 
 template <typename T>
 int launch_vmult_impl(int dim, int n, const DevArrays<T> &d, const void *ts, const void *tp,
                       const Scalars<T> &s, T *y, const T *x, bool adjoint, cudaStream_t st,
-                      void *const *ev) {
+                      void *const *ev, const LaunchRange *rg) {
 #define UF_CASE(D, NN)                                                         \
-  if (dim == D && n == NN) return launch_vmult_t<T, D, NN>(d, ts, tp, s, y, x, adjoint, st, ev);
+  if (dim == D && n == NN) return launch_vmult_t<T, D, NN>(d, ts, tp, s, y, x, adjoint, st, ev, rg);
   UF_CASE(2, 2) UF_CASE(2, 3) UF_CASE(2, 4) UF_CASE(2, 5) UF_CASE(2, 6) UF_CASE(2, 7)
   UF_CASE(2, 8) UF_CASE(2, 9) UF_CASE(3, 2) UF_CASE(3, 3) UF_CASE(3, 4) UF_CASE(3, 5)
   UF_CASE(3, 6) UF_CASE(3, 7) UF_CASE(3, 8) UF_CASE(3, 9)

@@ -12,6 +12,8 @@
 
 namespace uf {
 
+constexpr int kPipeParts = 16;  // parts of the host-buffer pipeline (large discontinuous operators)
+
 // Sets the thread-local message returned by uf_last_error and returns st.
 uf_status fail(uf_status st, const std::string &msg);
 
@@ -28,6 +30,10 @@ struct PrecisionData {
   Scalars<T> scalars{};
   size_t device_bytes = 0;
   int64_t n_vlines = 0, n_flines = 0;
+  // host-buffer pipeline (discontinuous operators): consecutive-cell parts of y = A x, and for
+  // part i the last part whose x must be on the device before it runs (face neighbours)
+  std::vector<LaunchRange> parts;
+  std::vector<int> part_needs;
   // continuous operators: global node of every cell-local DoF, owners of every node, and the
   // cell-local work vectors of the gather / kernels / node-sum sequence
   int32_t *cg_l2g = nullptr, *cg_own_off = nullptr, *cg_own_idx = nullptr;
@@ -96,6 +102,9 @@ struct uf_operator {
   size_t prof_next = 0;
   uf::CsrData csr64, csr32;
   uf::CgSolveData cgs;           // continuous operators: solver work vectors
+  cudaStream_t pipe_in = nullptr, pipe_out = nullptr;  // copy streams of the host-buffer path
+  std::vector<cudaStream_t> pipe_run;                 // one kernel stream per part
+  std::vector<cudaEvent_t> pipe_ev;                   // [start, per part: in, done]
   double *kg_tables = nullptr;   // kappa-derivative 1D matrices (FP64)
   double *kg_scratch = nullptr;  // [n_active][1 + 2d] per-cell partials of the kappa gradient
 };

@@ -217,6 +217,30 @@ def test_host_buffer_path_matches_device(full):
     assert np.array_equal(y_host32.astype(np.float64), y_dev32)
 
 
+@pytest.mark.parametrize("cfg", [workloads.small(p=2, N=128, dim=2), workloads.small(p=1, N=32)],
+                         ids=["2d_q2_128", "3d_q1_32"])
+def test_host_pipeline_matches_device(cfg):
+    """Operators with at least 8192 cells take the pipelined host path (parts of consecutive
+    cells, copies overlapping the kernels): bit for bit the device path, vmult and adjoint, FP64
+    and FP32, with a log-normal coefficient."""
+    from paper_2404_07911_gb300 import UnfittedOperator
+    from paper_2404_07911_gb300.binding import UF_FP32, UF_FP64
+
+    n_active = mesh.Mesh(mesh.problem_from_dict(cfg)).n_active
+    assert n_active >= 8192
+    op = UnfittedOperator(cfg, device=0, kappa=workloads.kappa_vector(n_active, seed=4))
+    x = workloads.uniform_vector(op.n_dofs, 3)
+    for dt, prec in ((np.float64, UF_FP64), (np.float32, UF_FP32)):
+        xh = x.astype(dt)
+        for adjoint in (False, True):
+            yh = np.empty_like(xh)
+            op.vmult_host_ptr(prec, yh.ctypes.data, xh.ctypes.data, 0, adjoint=adjoint)
+            xt = torch.from_numpy(xh).cuda()
+            yd = (op.vmult_adjoint(xt) if adjoint else op.vmult(xt)).cpu().numpy()
+            assert np.array_equal(yh, yd), (dt, adjoint)
+    op.close()
+
+
 def test_parity_volume_gp_with_kappa():
     """Volume ghost penalty with a log-normal coefficient: {kappa} on the patches, the general
     per-cell path of the structured kernel, vmult and adjoint."""
