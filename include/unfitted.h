@@ -172,6 +172,22 @@ uf_status uf_vmult_host(uf_operator *op, int precision, void *y_host, const void
 uf_status uf_vmult_adjoint_host(uf_operator *op, int precision, void *y_host, const void *g_host,
                                 void *stream);
 
+/* Asynchronous uf_vmult_host / uf_vmult_adjoint_host: the same copies and kernels, queued after
+ * the work already on `stream`, without waiting; y_host holds the result, and x_host / g_host
+ * may be changed, after uf_host_wait(op, stream).  Pipelined operators keep two device staging
+ * sets per precision and alternate them, so consecutive calls overlap (the copies of one with
+ * the kernels of the previous one); a call on a set still in use waits on the device for it.
+ * Host buffers must be pinned for the copies to be asynchronous (pageable buffers make the calls
+ * block).  Errors as uf_vmult. */
+uf_status uf_vmult_host_async(uf_operator *op, int precision, void *y_host, const void *x_host,
+                              void *stream);
+uf_status uf_vmult_adjoint_host_async(uf_operator *op, int precision, void *y_host,
+                                      const void *g_host, void *stream);
+
+/* Waits until every host-buffer product queued on `stream` (and the library's own pipeline
+ * streams) has finished, its results on the host.  Errors: UF_EINVAL, UF_ENODEVICE, UF_ECUDA. */
+uf_status uf_host_wait(uf_operator *op, void *stream);
+
 /* Kernel timing: uf_profile_begin creates `capacity` pairs of CUDA events (not stream-ordered;
  * call it outside any timed region); every kernel that vmult / vmult_adjoint launches afterwards
  * is bracketed by an event pair recorded on its stream, until the pairs run out.

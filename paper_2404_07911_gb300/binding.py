@@ -88,7 +88,8 @@ class uf_solve_stats(ctypes.Structure):
 UF_SOLVE_FP64, UF_SOLVE_IR = 0, 1
 
 EXPORTED = ["uf_create_unfitted_operator", "uf_get_info", "uf_vmult", "uf_vmult_adjoint",
-            "uf_vmult_host", "uf_vmult_adjoint_host", "uf_profile_begin", "uf_profile_end",
+            "uf_vmult_host", "uf_vmult_adjoint_host", "uf_vmult_host_async",
+            "uf_vmult_adjoint_host_async", "uf_host_wait", "uf_profile_begin", "uf_profile_end",
             "uf_set_kappa", "uf_export_cells", "uf_export_cut_cell_rule",
             "uf_export_cut_face_rule", "uf_assemble_csr", "uf_csr_info", "uf_csr_spmv",
             "uf_export_csr", "uf_release_csr", "uf_kappa_gradient", "uf_kappa_gradient_noalloc",
@@ -116,6 +117,9 @@ def load_library(path=None):
     lib.uf_vmult_adjoint.argtypes = [P, ctypes.c_int, P, P, P]
     lib.uf_vmult_host.argtypes = [P, ctypes.c_int, P, P, P]
     lib.uf_vmult_adjoint_host.argtypes = [P, ctypes.c_int, P, P, P]
+    lib.uf_vmult_host_async.argtypes = [P, ctypes.c_int, P, P, P]
+    lib.uf_vmult_adjoint_host_async.argtypes = [P, ctypes.c_int, P, P, P]
+    lib.uf_host_wait.argtypes = [P, P]
     lib.uf_profile_begin.argtypes = [P, ctypes.c_int]
     lib.uf_profile_end.argtypes = [P, ctypes.POINTER(uf_kernel_times)]
     lib.uf_set_kappa.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
@@ -280,11 +284,19 @@ class UnfittedOperator:
         _check(_lib.uf_vmult_host(self._h, prec, _ptr(y), _ptr(x), st))
         return y
 
-    def vmult_host_ptr(self, precision, y_ptr, x_ptr, stream_ptr, adjoint=False):
-        """uf_vmult_host / uf_vmult_adjoint_host on raw host pointers (pinned torch tensors)."""
-        fn = _lib.uf_vmult_adjoint_host if adjoint else _lib.uf_vmult_host
+    def vmult_host_ptr(self, precision, y_ptr, x_ptr, stream_ptr, adjoint=False, wait=True):
+        """uf_vmult_host / uf_vmult_adjoint_host on raw host pointers (pinned torch tensors);
+        wait=False: the _async entry points (the result is ready once the stream completes)."""
+        if wait:
+            fn = _lib.uf_vmult_adjoint_host if adjoint else _lib.uf_vmult_host
+        else:
+            fn = _lib.uf_vmult_adjoint_host_async if adjoint else _lib.uf_vmult_host_async
         _check(fn(self._h, precision, ctypes.c_void_p(y_ptr), ctypes.c_void_p(x_ptr),
                   ctypes.c_void_p(stream_ptr)))
+
+    def host_wait(self, stream_ptr):
+        """uf_host_wait: the queued asynchronous host-buffer products are complete."""
+        _check(_lib.uf_host_wait(self._h, ctypes.c_void_p(stream_ptr)))
 
     def profile_begin(self, capacity):
         """Bracket the next `capacity` operator applications' kernels with CUDA events."""

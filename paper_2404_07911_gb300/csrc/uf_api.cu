@@ -539,6 +539,12 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   const size_t vec_bytes = sizeof(T) * (size_t)H.n_active * H.ndof;
   err = cudaMalloc(&pd.xbuf, vec_bytes);
   if (err == cudaSuccess) err = cudaMalloc(&pd.ybuf, vec_bytes);
+  // the second staging set and the set events exist for pipelined operators (several parts)
+  const bool piped = part_meta.size() > 1;
+  if (err == cudaSuccess && piped) err = cudaMalloc(&pd.xbuf2, vec_bytes);
+  if (err == cudaSuccess && piped) err = cudaMalloc(&pd.ybuf2, vec_bytes);
+  for (int b = 0; b < 2 && err == cudaSuccess && piped; ++b)
+    err = cudaEventCreateWithFlags(&pd.set_free[b], cudaEventDisableTiming);
   if (err != cudaSuccess) return fail(UF_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(err));
   err = cudaMemcpy(pd.base, img.data(), L.bytes, cudaMemcpyHostToDevice);
   if (err != cudaSuccess) return fail(UF_ECUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(err));
@@ -697,7 +703,12 @@ void release(PrecisionData<T> &pd) {
   if (pd.base) cudaFree(pd.base);
   if (pd.xbuf) cudaFree(pd.xbuf);
   if (pd.ybuf) cudaFree(pd.ybuf);
-  pd.base = pd.xbuf = pd.ybuf = nullptr;
+  if (pd.xbuf2) cudaFree(pd.xbuf2);
+  if (pd.ybuf2) cudaFree(pd.ybuf2);
+  for (cudaEvent_t &e : pd.set_free)
+    if (e) cudaEventDestroy(e);
+  pd.set_free[0] = pd.set_free[1] = nullptr;
+  pd.base = pd.xbuf = pd.ybuf = pd.xbuf2 = pd.ybuf2 = nullptr;
   pd.present = false;
 }
 
@@ -773,7 +784,7 @@ namespace {
 // same code from the same data).
 template <typename T>
 uf_status host_pipeline(uf_operator *op, PrecisionData<T> &pd, T *y_host, const T *x_host,
-                        cudaStream_t s, bool adjoint) {
+                        cudaStream_t s, bool adjoint, bool wait) {
   const int np = (int)pd.parts.size();
   cudaError_t err = cudaSuccess;
   if (!op->pipe_in) err = cudaStreamCreateWithFlags(&op->pipe_in, cudaStreamNonBlocking);
@@ -797,12 +808,17 @@ uf_status host_pipeline(uf_operator *op, PrecisionData<T> &pd, T *y_host, const 
   }
   if (err != cudaSuccess) return fail(UF_ECUDA, std::string("pipeline setup: ") + cudaGetErrorString(err));
   const size_t nd = (size_t)op->host.ndof;
-  T *xb = static_cast<T *>(pd.xbuf);
-  T *yb = static_cast<T *>(pd.ybuf);
+  // staging set of this call; it is reused once the latest call on it has copied y out
+  const int set = pd.next_set;
+  pd.next_set ^= 1;
+  T *xb = static_cast<T *>(set ? pd.xbuf2 : pd.xbuf);
+  T *yb = static_cast<T *>(set ? pd.ybuf2 : pd.ybuf);
+  const bool reuse = pd.set_used[set];
   cudaEvent_t *ev = op->pipe_ev.data();
   // the copies start after the work already queued on the caller's stream
   err = cudaEventRecord(ev[0], s);
   if (err == cudaSuccess) err = cudaStreamWaitEvent(op->pipe_in, ev[0], 0);
+  if (err == cudaSuccess && reuse) err = cudaStreamWaitEvent(op->pipe_in, pd.set_free[set], 0);
   if (err == cudaSuccess) err = cudaStreamWaitEvent(op->pipe_out, ev[0], 0);
   for (int j = 0; j < np && err == cudaSuccess; ++j) {
     const size_t off = nd * (size_t)pd.parts[j].cell_begin;
@@ -814,6 +830,7 @@ uf_status host_pipeline(uf_operator *op, PrecisionData<T> &pd, T *y_host, const 
   for (int i = 0; i < np; ++i) {
     cudaStream_t run = op->pipe_run[i];
     err = cudaStreamWaitEvent(run, ev[0], 0);
+    if (err == cudaSuccess && reuse) err = cudaStreamWaitEvent(run, pd.set_free[set], 0);
     if (err == cudaSuccess) err = cudaStreamWaitEvent(run, ev[1 + pd.part_needs[i]], 0);
     if (err != cudaSuccess) return fail(UF_ECUDA, std::string("pipeline wait: ") + cudaGetErrorString(err));
     const uf_status st = vmult_t<T>(op, pd, yb, xb, run, adjoint, &pd.parts[i]);
@@ -826,10 +843,13 @@ uf_status host_pipeline(uf_operator *op, PrecisionData<T> &pd, T *y_host, const 
       err = cudaMemcpyAsync(y_host + off, yb + off, sizeof(T) * cnt, cudaMemcpyDeviceToHost, op->pipe_out);
     if (err != cudaSuccess) return fail(UF_ECUDA, std::string("D2H copy: ") + cudaGetErrorString(err));
   }
-  // every part's kernels precede its copy out on pipe_out; later work on the caller's stream
-  // follows all of them
-  err = cudaStreamSynchronize(op->pipe_out);
-  for (int i = 0; i < np && err == cudaSuccess; ++i) err = cudaStreamWaitEvent(s, ev[1 + uf::kPipeParts + i], 0);
+  // every part's kernels precede its copy out on pipe_out, so set_free marks the end of the
+  // call; a synchronous call also orders later work on the caller's stream after it (an
+  // asynchronous one does not, so that the next call's copies can start: uf_host_wait joins)
+  err = cudaEventRecord(pd.set_free[set], op->pipe_out);
+  pd.set_used[set] = true;
+  if (err == cudaSuccess && wait) err = cudaStreamWaitEvent(s, pd.set_free[set], 0);
+  if (err == cudaSuccess && wait) err = cudaEventSynchronize(pd.set_free[set]);
   if (err != cudaSuccess) return fail(UF_ECUDA, std::string("D2H copy: ") + cudaGetErrorString(err));
   return UF_OK;
 }
@@ -1055,17 +1075,19 @@ uf_status uf_vmult_adjoint(uf_operator *op, int precision, void *y, const void *
 }
 
 static uf_status vmult_host_impl(uf_operator *op, int precision, void *y_host,
-                                 const void *x_host, void *stream, bool adjoint) {
+                                 const void *x_host, void *stream, bool adjoint, bool wait) {
   uf_status st = check_vmult_args(op, precision, y_host, x_host);
   if (st != UF_OK) return st;
   DeviceGuard guard(op->device);
   if (!op->host.cg) {
     if (precision == UF_FP64 && op->f64.present && op->f64.parts.size() > 1)
       return host_pipeline<double>(op, op->f64, static_cast<double *>(y_host),
-                                   static_cast<const double *>(x_host), reinterpret_cast<cudaStream_t>(stream), adjoint);
+                                   static_cast<const double *>(x_host), reinterpret_cast<cudaStream_t>(stream),
+                                   adjoint, wait);
     if (precision == UF_FP32 && op->f32.present && op->f32.parts.size() > 1)
       return host_pipeline<float>(op, op->f32, static_cast<float *>(y_host),
-                                  static_cast<const float *>(x_host), reinterpret_cast<cudaStream_t>(stream), adjoint);
+                                  static_cast<const float *>(x_host), reinterpret_cast<cudaStream_t>(stream),
+                                  adjoint, wait);
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const size_t elem = precision == UF_FP64 ? sizeof(double) : sizeof(float);
@@ -1078,19 +1100,39 @@ static uf_status vmult_host_impl(uf_operator *op, int precision, void *y_host,
   st = vmult_dispatch(op, precision, yb, xb, stream, adjoint);
   if (st != UF_OK) return st;
   err = cudaMemcpyAsync(y_host, yb, bytes, cudaMemcpyDeviceToHost, s);
-  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  if (err == cudaSuccess && wait) err = cudaStreamSynchronize(s);
   if (err != cudaSuccess) return fail(UF_ECUDA, std::string("D2H copy: ") + cudaGetErrorString(err));
   return UF_OK;
 }
 
 uf_status uf_vmult_host(uf_operator *op, int precision, void *y_host, const void *x_host,
                         void *stream) {
-  return vmult_host_impl(op, precision, y_host, x_host, stream, false);
+  return vmult_host_impl(op, precision, y_host, x_host, stream, false, true);
 }
 
 uf_status uf_vmult_adjoint_host(uf_operator *op, int precision, void *y_host, const void *g_host,
                                 void *stream) {
-  return vmult_host_impl(op, precision, y_host, g_host, stream, true);
+  return vmult_host_impl(op, precision, y_host, g_host, stream, true, true);
+}
+
+uf_status uf_host_wait(uf_operator *op, void *stream) {
+  if (!op) return fail(UF_EINVAL, "NULL operator");
+  if (op->device < 0) return fail(UF_ENODEVICE, "operator was created host-only");
+  DeviceGuard guard(op->device);
+  cudaError_t err = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+  if (err == cudaSuccess && op->pipe_out) err = cudaStreamSynchronize(op->pipe_out);
+  if (err != cudaSuccess) return fail(UF_ECUDA, std::string("uf_host_wait: ") + cudaGetErrorString(err));
+  return UF_OK;
+}
+
+uf_status uf_vmult_host_async(uf_operator *op, int precision, void *y_host, const void *x_host,
+                              void *stream) {
+  return vmult_host_impl(op, precision, y_host, x_host, stream, false, false);
+}
+
+uf_status uf_vmult_adjoint_host_async(uf_operator *op, int precision, void *y_host,
+                                      const void *g_host, void *stream) {
+  return vmult_host_impl(op, precision, y_host, g_host, stream, true, false);
 }
 
 uf_status uf_profile_begin(uf_operator *op, int capacity) {

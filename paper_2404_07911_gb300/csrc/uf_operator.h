@@ -23,6 +23,13 @@ struct PrecisionData {
   void *base = nullptr;        // one device allocation for all arrays of this precision
   void *xbuf = nullptr;        // device staging buffers of uf_vmult_host
   void *ybuf = nullptr;
+  // second staging set (pipelined operators): consecutive host-buffer calls alternate sets, so
+  // an asynchronous call's copies overlap the previous call's kernels; set_free[b] is recorded
+  // after the last copy out of the latest call on set b
+  void *xbuf2 = nullptr, *ybuf2 = nullptr;
+  int next_set = 0;
+  bool set_used[2] = {false, false};
+  cudaEvent_t set_free[2] = {nullptr, nullptr};
   T *kappa_dev = nullptr;
   DevArrays<T> arrays{};
   std::vector<unsigned char> struct_tables;  // StructTables<T, n>

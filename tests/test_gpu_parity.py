@@ -238,6 +238,19 @@ def test_host_pipeline_matches_device(cfg):
             xt = torch.from_numpy(xh).cuda()
             yd = (op.vmult_adjoint(xt) if adjoint else op.vmult(xt)).cpu().numpy()
             assert np.array_equal(yh, yd), (dt, adjoint)
+    # asynchronous calls on pinned buffers: four chained products (both staging sets twice)
+    # before one synchronisation, each equal to its device result
+    s = torch.cuda.Stream()
+    xs = [torch.from_numpy(workloads.uniform_vector(op.n_dofs, 10 + i)).pin_memory() for i in range(4)]
+    ys = [torch.empty_like(v).pin_memory() for v in xs]
+    for i in range(4):
+        op.vmult_host_ptr(UF_FP64, ys[i].data_ptr(), xs[i].data_ptr(), s.cuda_stream,
+                          adjoint=(i % 2 == 1), wait=False)
+    op.host_wait(s.cuda_stream)
+    for i in range(4):
+        xt = xs[i].cuda()
+        yd = (op.vmult_adjoint(xt) if i % 2 == 1 else op.vmult(xt)).cpu()
+        assert torch.equal(ys[i], yd), i
     op.close()
 
 
