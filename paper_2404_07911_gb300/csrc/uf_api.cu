@@ -437,6 +437,18 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   const size_t o_lself = L.take(sizeof(T) * lself.size());
   const size_t o_lnbgp = L.take(sizeof(T) * lnbgp.size());
   const std::vector<double> lselfT = premul(lself0, 32, true), lnbgpT = premul(lnbgp0, 4, true);
+  auto transposed = [&](const std::vector<double> &m) {
+    std::vector<double> t(m.size());
+    for (size_t b = 0; b < m.size() / nn; ++b)
+      for (int r = 0; r < n; ++r)
+        for (int c2 = 0; c2 < n; ++c2) t[b * nn + r * n + c2] = m[b * nn + c2 * n + r];
+    return t;
+  };
+  const std::vector<double> lselfxT = transposed(lself0), lnbgpxT = transposed(lnbgp0);
+  const size_t o_lselfx = L.take(sizeof(T) * lself0.size());
+  const size_t o_lnbgpx = L.take(sizeof(T) * lnbgp0.size());
+  const size_t o_lselfxT = L.take(sizeof(T) * lselfxT.size());
+  const size_t o_lnbgpxT = L.take(sizeof(T) * lnbgpxT.size());
   const size_t o_lselfT = L.take(sizeof(T) * lselfT.size());
   const size_t o_lnbgpT = L.take(sizeof(T) * lnbgpT.size());
   // FP64: the 1D basis at every line and point (the FP64 pipe is the bottleneck there, HBM is not)
@@ -526,6 +538,10 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   put_t(o_lnbgp, lnbgp);
   put_t(o_lselfT, lselfT);
   put_t(o_lnbgpT, lnbgpT);
+  put_t(o_lselfx, lself0);
+  put_t(o_lnbgpx, lnbgp0);
+  put_t(o_lselfxT, lselfxT);
+  put_t(o_lnbgpxT, lnbgpxT);
   if (pre) {
     put_t(o_vlb, vline_b);
     put_t(o_vpb, vpt_b);
@@ -622,6 +638,10 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   A.lnbgp = TP(o_lnbgp);
   A.lselfT = TP(o_lselfT);
   A.lnbgpT = TP(o_lnbgpT);
+  A.lselfx = TP(o_lselfx);
+  A.lnbgpx = TP(o_lnbgpx);
+  A.lselfxT = TP(o_lselfxT);
+  A.lnbgpxT = TP(o_lnbgpxT);
   A.vline_b = pre ? TP(o_vlb) : nullptr;
   A.vpt_b = pre ? TP(o_vpb) : nullptr;
   A.spt_b = pre ? TP(o_spb) : nullptr;
@@ -668,6 +688,7 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
     for (int i = 0; i < 2 * n; ++i) tabs.push_back(half_hf * mats[16 * nn + 2 * n + i]);
     for (int s2 = 0; s2 < 2; ++s2)
       for (int r = 0; r < n; ++r) tabs.push_back(minv[r * n + (s2 ? n - 1 : 0)]);
+    for (int i = 0; i < 2 * n; ++i) tabs.push_back(half_hf * mats[16 * nn + i]);  // dowx
     pd.struct_tables.assign(sizeof(T) * tabs.size(), 0);
     T *st = reinterpret_cast<T *>(pd.struct_tables.data());
     for (size_t i = 0; i < tabs.size(); ++i) st[i] = (T)tabs[i];
@@ -985,24 +1006,32 @@ uf_status uf_get_info(const uf_operator *op, uf_info *info) {
   // neighbour couplings as full line sweeps (n^{d+1} FMA), SIPG-only neighbour couplings in
   // rank-2 form, the sum of the axes ((d - 1) n^d adds) and one mass sweep per direction
   // (n^{d+1} FMA each); plus the per-cell matrix build if kappa varies.
-  int64_t gp_faces_cell = 0, r2_faces_cell = 0;
+  int64_t gp_faces_cell = 0, r2_faces_cell = 0, r2_faces_axis0 = 0;
   for (int64_t e = 0; e < H.n_active; ++e)
     for (int f = 0; f < nf; ++f) {
       const uint32_t fl = H.flags[e];
-      if (fl & uf::face_bit_gp(f))
+      if (fl & uf::face_bit_gp(f)) {
         ++gp_faces_cell;
-      else if (fl & uf::face_bit_sipg_full(f))
+      } else if (fl & uf::face_bit_sipg_full(f)) {
         ++r2_faces_cell;
+        if (f < 2) ++r2_faces_axis0;
+      }
     }
   const double sweep = nline * n * n;  // FMA per line sweep of a cell
   const bool uni = kappa_is_uniform(H.kappa);
   // uniform kappa: lines for kappa = 1, rows scaled once (not at all for kappa = 1); rank-2
   // couplings per line: the neighbour's derivative (n FMA), two rank-1 updates (2n FMA) and the
-  // coefficient (1 FMA; 2 multiplies more when kappa varies)
+  // coefficient (1 FMA; 2 multiplies more when kappa varies); with uniform kappa axis 0 is
+  // applied after its mass sweep in W space: one rank-1 update and a single-entry correction
+  // (4n + 2 flops per line) and one axis fewer in the sum
   double fl_struct = 2.0 * ((double)H.n_active * (d * sweep + d * sweep) +
                             (double)gp_faces_cell * sweep) +
-                     (double)H.n_active * (d - 1) * nd +
-                     (double)r2_faces_cell * nline * (uni ? 6 * n + 2 : 6 * n + 5);
+                     (double)H.n_active * (uni ? d - 2 : d - 1) * nd;
+  if (uni)
+    fl_struct += (double)(r2_faces_cell - r2_faces_axis0) * nline * (6 * n + 2) +
+                 (double)r2_faces_axis0 * nline * (4 * n + 2);
+  else
+    fl_struct += (double)r2_faces_cell * nline * (6 * n + 5);
   if (uni && H.kappa[0] != 1.0) fl_struct += (double)H.n_active * nd;
   if (!uni) fl_struct += (double)H.n_active * d * n * n * 2.0 * 13.0;
   // cut-cell kernel: 1D basis (values and derivatives) 14n - 8, values only 6n - 4 flops when

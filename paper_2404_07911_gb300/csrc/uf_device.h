@@ -35,6 +35,7 @@ struct StructTables {
   T b[2][N * N], c[2][N * N], qn[2][N * N], hn[2][N * N];
   T dow[2][N], dnb[2][N];  // dow premultiplied by M^{-1}; both carry h^{d-1} / 2
   T me[2][N];              // column of M^{-1} at the face node of side s (0 or N - 1)
+  T dowx[2][N];            // dow without M^{-1} (axis 0 of the uniform-kappa path), h^{d-1} / 2
 };
 
 // 1D data for point evaluation of the Lagrange basis at arbitrary reference coordinates.
@@ -95,6 +96,9 @@ struct DevArrays {
   // uniform (kappa_uniform != 0) every structured term scales with that value.
   const T *lself, *lnbgp;
   const T *lselfT, *lnbgpT;  // M^{-1} times the transposed tables (adjoint)
+  // the same tables without M^{-1}, for axis 0 of the uniform-kappa path (its lines are applied
+  // in the first mass sweep, where M_0 M_0^{-1} cancels)
+  const T *lselfx, *lnbgpx, *lselfxT, *lnbgpxT;
   // the 16 constant 1D matrices Q_k of StructTables (same order) premultiplied by M^{-1}, for
   // the per-cell matrices when kappa varies (read with a per-thread index)
   const T *smat;   // M^{-1} Q_k

@@ -172,6 +172,51 @@ __device__ __forceinline__ void mass_line(const T *__restrict__ M, T *v, int bas
   for (int r = 0; r < N; ++r) v[base + r * st] = b[r];
 }
 
+// Axis 0 of the uniform-kappa path in W space (tables without M^{-1}), for the x-line whose
+// DoFs are u: w += L_0 u + the couplings of the two axis-0 neighbours (ghost penalty: full 1D
+// matrix; SIPG only: rank 2).  Added after the mass sweep along axis 0, which is then the only
+// sweep that sees these terms' M_0 M_0^{-1} = I.
+template <typename T, int DIM, int N, bool ADJ>
+__device__ __forceinline__ void axis0_lines(const StructTables<T, N> &tab, const DevArrays<T> &d,
+                                            const Scalars<T> &sc, const T *__restrict__ x,
+                                            const int *nb, uint32_t fl, bool inside, int t,
+                                            const T *u, T *w) {
+  constexpr int ND = Geo<DIM, N>::ND, NN = N * N;
+  int v = inside ? 1 : 0;
+  v |= bit(fl, bit_full(0)) ? 2 : 0;
+  v |= bit(fl, bit_gp(0)) ? 4 : 0;
+  v |= bit(fl, bit_full(1)) ? 8 : 0;
+  v |= bit(fl, bit_gp(1)) ? 16 : 0;
+  apply_line<T, N>((ADJ ? d.lselfxT : d.lselfx) + v * NN, u, w, true);
+  const int base = line_base<DIM, N>(0, t);
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    if (nb[s] < 0) continue;
+    const bool full = bit(fl, bit_full(s));
+    const bool gp = bit(fl, bit_gp(s));
+    if (!full && !gp) continue;
+    T un[N];
+    const T *xn = x + (size_t)nb[s] * ND + base;
+#pragma unroll
+    for (int m = 0; m < N; ++m) un[m] = __ldg(xn + m);
+    if (gp) {
+      const T *Lg = ADJ ? d.lnbgpxT + (2 * (1 - s) + (full ? 1 : 0)) * NN
+                        : d.lnbgpx + (2 * s + (full ? 1 : 0)) * NN;
+      apply_line<T, N>(Lg, un, w, true);
+    } else {
+      // rank-2 SIPG coupling: dow times the neighbour's face value, minus the neighbour's normal
+      // derivative and penalty at the own face node
+      const T alpha = un[s ? 0 : N - 1];
+      T beta = T(0);
+#pragma unroll
+      for (int m = 0; m < N; ++m) beta = fma(tab.dnb[s][m], un[m], beta);
+#pragma unroll
+      for (int r = 0; r < N; ++r) w[r] = fma(alpha, tab.dowx[s][r], w[r]);
+      w[s ? N - 1 : 0] -= fma(sc.hf_sigma, alpha, beta);
+    }
+  }
+}
+
 template <typename T, int DIM, int N, bool ADJ, bool UNI>
 __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ StructTables<T, N> tab,
                                                      const DevArrays<T> d, const Scalars<T> sc,
@@ -279,10 +324,11 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
   }
   __syncthreads();
 
-  // ---- phase 1: W_a = L_a u + neighbour couplings, one line per thread and axis
+  // ---- phase 1: Z_a = M^{-1} (L_a u + neighbour couplings), one line per thread and axis (the
+  // uniform-kappa path leaves axis 0 to the first mass sweep)
   if (has_cell) {
 #pragma unroll 1
-    for (int a = 0; a < DIM; ++a) {
+    for (int a = uniform ? 1 : 0; a < DIM; ++a) {
       const int base = line_base<DIM, N>(a, t);  // global layout (neighbour lines)
       const int st = stride_of<N>(a);
       const int sb = sline_base<DIM, N>(a, t);   // shared-memory layout
@@ -349,18 +395,26 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
   const T *M = tab.mass;
   if constexpr (DIM == 2) {
     if (has_cell) {
-      // Z_x <- M_x (Z_x + Z_y) along x-lines
+      // Z_x <- M_x (Z_x + Z_y) along x-lines (uniform kappa: M_x Z_y + L_x u + x-neighbours)
       const int bx = sline_base<DIM, N>(0, t);
-      T a[N];
+      T a[N], o[N];
 #pragma unroll
-      for (int m = 0; m < N; ++m) a[m] = s_w[0][c][bx + m] + s_w[1][c][bx + m];
+      for (int m = 0; m < N; ++m) a[m] = uniform ? s_w[1][c][bx + m] : s_w[0][c][bx + m] + s_w[1][c][bx + m];
 #pragma unroll
       for (int r = 0; r < N; ++r) {
         T acc = T(0);
 #pragma unroll
         for (int m = 0; m < N; ++m) acc = fma(M[r * N + m], a[m], acc);
-        s_w[0][c][bx + r] = acc;
+        o[r] = acc;
       }
+      if constexpr (uniform) {
+        T u[N];
+#pragma unroll
+        for (int m = 0; m < N; ++m) u[m] = s_u[c][bx + m];
+        axis0_lines<T, DIM, N, ADJ>(tab, d, sc, x, nb, fl, inside, t, u, o);
+      }
+#pragma unroll
+      for (int r = 0; r < N; ++r) s_w[0][c][bx + r] = o[r];
     }
     __syncthreads();
     if (has_cell) {
@@ -379,18 +433,29 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
     }
   } else {
     if (has_cell) {
-      // Z_x <- M_x (Z_x + Z_y + Z_z) along x-lines
+      // Z_x <- M_x (Z_x + Z_y + Z_z) along x-lines (uniform kappa: M_x (Z_y + Z_z) + L_x u +
+      // x-neighbours)
       const int bx = sline_base<DIM, N>(0, t);
-      T a[N];
+      T a[N], o[N];
 #pragma unroll
-      for (int m = 0; m < N; ++m) a[m] = (s_w[0][c][bx + m] + s_w[1][c][bx + m]) + s_w[2][c][bx + m];
+      for (int m = 0; m < N; ++m)
+        a[m] = uniform ? s_w[1][c][bx + m] + s_w[2][c][bx + m]
+                       : (s_w[0][c][bx + m] + s_w[1][c][bx + m]) + s_w[2][c][bx + m];
 #pragma unroll
       for (int r = 0; r < N; ++r) {
         T acc = T(0);
 #pragma unroll
         for (int m = 0; m < N; ++m) acc = fma(M[r * N + m], a[m], acc);
-        s_w[0][c][bx + r] = acc;
+        o[r] = acc;
       }
+      if constexpr (uniform) {
+        T u[N];
+#pragma unroll
+        for (int m = 0; m < N; ++m) u[m] = s_u[c][bx + m];
+        axis0_lines<T, DIM, N, ADJ>(tab, d, sc, x, nb, fl, inside, t, u, o);
+      }
+#pragma unroll
+      for (int r = 0; r < N; ++r) s_w[0][c][bx + r] = o[r];
     }
     __syncthreads();
     if (has_cell) mass_line<T, N>(M, s_w[0][c], sline_base<DIM, N>(1, t), P);  // Z_x <- M_y Z_x
