@@ -432,6 +432,7 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   const std::vector<double> smat = premul(mats, 16, false), smatT = premul(mats, 16, true);
   const size_t o_smat = L.take(sizeof(T) * smat.size());
   const size_t o_smatT = L.take(sizeof(T) * smatT.size());
+  const size_t o_smat0 = L.take(sizeof(T) * 16 * nn);
   variant_tables(H, mats, lself0, lnbgp0);
   const std::vector<double> lself = premul(lself0, 32, false), lnbgp = premul(lnbgp0, 4, false);
   const size_t o_lself = L.take(sizeof(T) * lself.size());
@@ -535,6 +536,7 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   put_t(o_lself, lself);
   put_t(o_smat, smat);
   put_t(o_smatT, smatT);
+  put_t(o_smat0, std::vector<double>(mats.begin(), mats.begin() + 16 * nn));
   put_t(o_lnbgp, lnbgp);
   put_t(o_lselfT, lselfT);
   put_t(o_lnbgpT, lnbgpT);
@@ -635,6 +637,7 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   A.lself = TP(o_lself);
   A.smat = TP(o_smat);
   A.smatT = TP(o_smatT);
+  A.smat0 = TP(o_smat0);
   A.lnbgp = TP(o_lnbgp);
   A.lselfT = TP(o_lselfT);
   A.lnbgpT = TP(o_lnbgpT);
@@ -1032,8 +1035,19 @@ uf_status uf_get_info(const uf_operator *op, uf_info *info) {
                  (double)r2_faces_axis0 * nline * (4 * n + 2);
   else
     fl_struct += (double)r2_faces_cell * nline * (6 * n + 5);
-  if (uni && H.kappa[0] != 1.0) fl_struct += (double)H.n_active * nd;
-  if (!uni) fl_struct += (double)H.n_active * d * n * n * 2.0 * 13.0;
+  // FP32 keeps the form without M^{-1}: every axis in phase 1, rank-2 couplings in W space
+  // (2n FMA + 2 flops per line; 3 more when kappa varies), 5 in-face mass sweeps in 3D (2 in 2D)
+  double fl_struct32 = 2.0 * ((double)H.n_active * (d * sweep + (d == 3 ? 5 : 2) * sweep) +
+                              (double)gp_faces_cell * sweep) +
+                       (double)r2_faces_cell * nline * (uni ? 4 * n + 3 : 4 * n + 6);
+  if (uni && H.kappa[0] != 1.0) {
+    fl_struct += (double)H.n_active * nd;
+    fl_struct32 += (double)H.n_active * nd;
+  }
+  if (!uni) {
+    fl_struct += (double)H.n_active * d * n * n * 2.0 * 13.0;
+    fl_struct32 += (double)H.n_active * d * n * n * 2.0 * 13.0;
+  }
   // cut-cell kernel: 1D basis (values and derivatives) 14n - 8, values only 6n - 4 flops when
   // evaluated (FP32); the FP64 kernels read them from tables (fb = fbv = 0)
   const double vlines = (double)H.vol_lines.size(), flines = (double)H.face_lines.size();
@@ -1061,7 +1075,7 @@ uf_status uf_get_info(const uf_operator *op, uf_info *info) {
   };
   info->kernel_flops_built[0] = fl_struct;
   info->kernel_flops_built[1] = cut_flops(true);
-  info->kernel_flops_built_fp32[0] = fl_struct;
+  info->kernel_flops_built_fp32[0] = fl_struct32;
   info->kernel_flops_built_fp32[1] = cut_flops(false);
 
   // Algorithmic FMAs from the paper's complexity model (evaluation + integration = x2).

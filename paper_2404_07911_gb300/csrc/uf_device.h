@@ -96,13 +96,14 @@ struct DevArrays {
   // uniform (kappa_uniform != 0) every structured term scales with that value.
   const T *lself, *lnbgp;
   const T *lselfT, *lnbgpT;  // M^{-1} times the transposed tables (adjoint)
-  // the same tables without M^{-1}, for axis 0 of the uniform-kappa path (its lines are applied
-  // in the first mass sweep, where M_0 M_0^{-1} cancels)
+  // the same tables without M^{-1}: axis 0 of the FP64 uniform-kappa path (its lines are applied
+  // in the first mass sweep, where M_0 M_0^{-1} cancels) and every axis of FP32
   const T *lselfx, *lnbgpx, *lselfxT, *lnbgpxT;
   // the 16 constant 1D matrices Q_k of StructTables (same order) premultiplied by M^{-1}, for
   // the per-cell matrices when kappa varies (read with a per-thread index)
   const T *smat;   // M^{-1} Q_k
   const T *smatT;  // M^{-1} Q_k^T (adjoint)
+  const T *smat0;  // Q_k themselves (FP32, which keeps the form without M^{-1})
   // FP64 only (null otherwise): the 1D basis at every line and point, precomputed at creation
   // (values and derivatives; faces values only): vline_b [line][4n] = phi, phi' of the lower and
   // upper outer coordinate; vpt_b / spt_b [point][2n]; fline_b [face line][n]; fpt_b [point][n].

@@ -231,6 +231,10 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
   __shared__ __align__(16) T s_u[CPB][SND];
   __shared__ __align__(16) T s_w[DIM][CPB][SND];
   __shared__ __align__(16) T s_l[CPB][DIM][3][NN];  // per-cell matrices when kappa is not uniform
+  // FP32 keeps the form without M^{-1} (W_a = L_a u + couplings, then the shared in-face mass
+  // sweeps y = M_z (M_y W_x + M_x W_y) + M_y M_x W_z): its rounding errors are not amplified by
+  // M^{-1}, which the FP32 solves inside iterative refinement depend on
+  constexpr bool WS = sizeof(T) == 4;
 
   const int tid = threadIdx.x;
   const int first = cell_begin + blockIdx.x * CPB;
@@ -288,10 +292,12 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
     // per-cell 1D matrices from the constant ones and kappa; the constant matrices are read from
     // their global-memory copy (each thread reads its own entry: coalesced through L1), matrix
     // `which` (kv 0, mass 1, a 2, pen 4, gp 6, b 8, c 10, qn 12, hn 14, + side) at which * NN
-    const T *Q = ADJ ? d.smatT : d.smat;  // M^{-1} Q_k (adjoint: M^{-1} Q_k^T)
+    // FP64: M^{-1} Q_k (adjoint: M^{-1} Q_k^T); FP32: Q_k, transposed by the index (adjoint)
+    const T *Q = WS ? d.smat0 : (ADJ ? d.smatT : d.smat);
     for (int a = 0; a < DIM; ++a)
       for (int idx = t; idx < NN; idx += TPC) {
-        T self = inside ? kap * __ldg(Q + idx) : T(0);
+        const int tr = (WS && ADJ) ? ((idx % N) * N + idx / N) : idx;
+        T self = inside ? kap * __ldg(Q + tr) : T(0);
         T ln[2] = {T(0), T(0)};
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
@@ -299,8 +305,8 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
           if (nb[f] < 0) continue;
           const bool full = bit(fl, bit_full(f));
           const bool gp = bit(fl, bit_gp(f));
-          if (full) self += kap * __ldg(Q + (2 + s) * NN + idx) + kavg[f] * __ldg(Q + (4 + s) * NN + idx);
-          if (gp) self += kavg[f] * __ldg(Q + (6 + s) * NN + idx);
+          if (full) self += kap * __ldg(Q + (2 + s) * NN + tr) + kavg[f] * __ldg(Q + (4 + s) * NN + tr);
+          if (gp) self += kavg[f] * __ldg(Q + (6 + s) * NN + tr);
           if (gp) {
             if (!ADJ) {
               if (full)
@@ -311,9 +317,9 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
               // transpose of the neighbour's coupling toward this cell (its face 1 - s)
               const int so = 1 - s;
               if (full)
-                ln[s] += knb[f] * __ldg(Q + (8 + so) * NN + idx) + kap * __ldg(Q + (10 + so) * NN + idx) +
-                         kavg[f] * __ldg(Q + (12 + so) * NN + idx);
-              ln[s] += kavg[f] * __ldg(Q + (14 + so) * NN + idx);
+                ln[s] += knb[f] * __ldg(Q + (8 + so) * NN + tr) + kap * __ldg(Q + (10 + so) * NN + tr) +
+                         kavg[f] * __ldg(Q + (12 + so) * NN + tr);
+              ln[s] += kavg[f] * __ldg(Q + (14 + so) * NN + tr);
             }
           }
         }
@@ -328,7 +334,7 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
   // uniform-kappa path leaves axis 0 to the first mass sweep)
   if (has_cell) {
 #pragma unroll 1
-    for (int a = uniform ? 1 : 0; a < DIM; ++a) {
+    for (int a = (uniform && !WS) ? 1 : 0; a < DIM; ++a) {
       const int base = line_base<DIM, N>(a, t);  // global layout (neighbour lines)
       const int st = stride_of<N>(a);
       const int sb = sline_base<DIM, N>(a, t);   // shared-memory layout
@@ -342,7 +348,7 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
         v |= bit(fl, bit_gp(2 * a)) ? 4 : 0;
         v |= bit(fl, bit_full(2 * a + 1)) ? 8 : 0;
         v |= bit(fl, bit_gp(2 * a + 1)) ? 16 : 0;
-        apply_line<T, N>((ADJ ? d.lselfT : d.lself) + v * NN, u, w, false);
+        apply_line<T, N>((WS ? (ADJ ? d.lselfxT : d.lselfx) : (ADJ ? d.lselfT : d.lself)) + v * NN, u, w, false);
       } else {
         apply_line<T, N>(s_l[c][a][0], u, w, false);
       }
@@ -360,8 +366,8 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
         if (gp) {
           if (uniform) {
             // transpose of the neighbour's table entry (its face 1 - s) for the adjoint
-            const T *Lg = ADJ ? d.lnbgpT + (2 * (1 - s) + (full ? 1 : 0)) * NN
-                              : d.lnbgp + (2 * s + (full ? 1 : 0)) * NN;
+            const T *Lg = ADJ ? (WS ? d.lnbgpxT : d.lnbgpT) + (2 * (1 - s) + (full ? 1 : 0)) * NN
+                              : (WS ? d.lnbgpx : d.lnbgp) + (2 * s + (full ? 1 : 0)) * NN;
             apply_line<T, N>(Lg, un, w, true);
           } else {
             apply_line<T, N>(s_l[c][a][1 + s], un, w, true);
@@ -381,8 +387,15 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
           } else {
             g = fma(knb[f], beta, (sc.hf_sigma * kavg[f]) * alpha);
           }
+          if constexpr (WS) {
+            // W space: ca dow - g e_own
 #pragma unroll
-          for (int r = 0; r < N; ++r) w[r] = fma(-g, tab.me[s][r], fma(ca, tab.dow[s][r], w[r]));
+            for (int r = 0; r < N; ++r) w[r] = fma(ca, tab.dowx[s][r], w[r]);
+            w[s ? N - 1 : 0] -= g;
+          } else {
+#pragma unroll
+            for (int r = 0; r < N; ++r) w[r] = fma(-g, tab.me[s][r], fma(ca, tab.dow[s][r], w[r]));
+          }
         }
       }
 #pragma unroll
@@ -393,7 +406,60 @@ __global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ Str
 
   // ---- phase 2: y = (M (x) .. (x) M) sum_a Z_a (M symmetric: the adjoint uses the same sweeps)
   const T *M = tab.mass;
-  if constexpr (DIM == 2) {
+  if constexpr (WS && DIM == 2) {
+    // FP32: y = M_y W_x + M_x W_y
+    if (has_cell) {
+      mass_line<T, N>(M, s_w[0][c], sline_base<DIM, N>(1, t), P);  // M_y W_x
+      mass_line<T, N>(M, s_w[1][c], sline_base<DIM, N>(0, t), 1);  // M_x W_y
+    }
+    __syncthreads();
+    if (has_cell) {
+      // y = W_x + W_y; thread t writes the x-line t
+      const int base = line_base<DIM, N>(0, t), sb = sline_base<DIM, N>(0, t);
+#pragma unroll
+      for (int r = 0; r < N; ++r) {
+        const T v = s_w[0][c][sb + r] + s_w[1][c][sb + r];
+        y[(size_t)e * ND + base + r] = scale_rows ? yscale * v : v;
+      }
+    }
+  } else if constexpr (WS) {
+    // FP32: y = M_z (M_y W_x + M_x W_y) + M_y M_x W_z
+    if (has_cell) {
+      mass_line<T, N>(M, s_w[0][c], sline_base<DIM, N>(1, t), P);  // W_x <- M_y W_x
+      mass_line<T, N>(M, s_w[2][c], sline_base<DIM, N>(0, t), 1);  // W_z <- M_x W_z
+    }
+    __syncthreads();
+    if (has_cell) {
+      // W_x += M_x W_y (x-lines)
+      const int bx = sline_base<DIM, N>(0, t);
+      T a[N];
+#pragma unroll
+      for (int m = 0; m < N; ++m) a[m] = s_w[1][c][bx + m];
+#pragma unroll
+      for (int r = 0; r < N; ++r) {
+        T acc = s_w[0][c][bx + r];
+#pragma unroll
+        for (int m = 0; m < N; ++m) acc = fma(M[r * N + m], a[m], acc);
+        s_w[0][c][bx + r] = acc;
+      }
+      mass_line<T, N>(M, s_w[2][c], sline_base<DIM, N>(1, t), P);  // W_z <- M_y W_z
+    }
+    __syncthreads();
+    if (has_cell) {
+      // y = M_z W_x + W_z along z-lines
+      const int bz = line_base<DIM, N>(2, t), sbz = sline_base<DIM, N>(2, t);
+      T a[N];
+#pragma unroll
+      for (int m = 0; m < N; ++m) a[m] = s_w[0][c][sbz + m * P * N];
+#pragma unroll
+      for (int r = 0; r < N; ++r) {
+        T acc = s_w[2][c][sbz + r * P * N];
+#pragma unroll
+        for (int m = 0; m < N; ++m) acc = fma(M[r * N + m], a[m], acc);
+        y[(size_t)e * ND + bz + r * N * N] = scale_rows ? yscale * acc : acc;
+      }
+    }
+  } else if constexpr (DIM == 2) {
     if (has_cell) {
       // Z_x <- M_x (Z_x + Z_y) along x-lines (uniform kappa: M_x Z_y + L_x u + x-neighbours)
       const int bx = sline_base<DIM, N>(0, t);
