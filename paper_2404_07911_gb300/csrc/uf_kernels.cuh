@@ -130,8 +130,26 @@ __host__ __device__ constexpr int struct_cells_per_block() {
   constexpr int SND = (DIM == 2) ? (N | 1) * N : (N | 1) * N * N;
   constexpr int cell_bytes = (int)sizeof(T) * (SND * (1 + DIM) + DIM * 3 * N * N);
   constexpr int by_smem = 40960 / cell_bytes;
-  constexpr int cpb = by_threads < by_smem ? by_threads : by_smem;
-  return cpb < 1 ? 1 : cpb;
+  int cpb = by_threads < by_smem ? by_threads : by_smem;
+  if (cpb < 1) cpb = 1;
+  // The warps of a CTA issue for all their lanes: when the cells leave more than 10 % of the
+  // lanes idle (n = 6, 7 in 3D: 36 and 49 lines per cell), take the cell count up to 256 threads
+  // and the 48 KB of static shared memory with the fewest idle lanes.
+  auto idle = [](int c) { return ((c * NL + 31) / 32) * 32 - c * NL; };
+  if (idle(cpb) * 10 > ((cpb * NL + 31) / 32) * 32) {
+    int best = cpb;
+    for (int c = 1; c * NL <= 256 && c * cell_bytes <= 48 * 1024; ++c)
+      if (idle(c) * ((best * NL + 31) / 32) * 32 < idle(best) * ((c * NL + 31) / 32) * 32) best = c;
+    cpb = best;
+  }
+  return cpb;
+}
+
+// Threads of a structured-kernel CTA (whole warps).
+template <typename T, int DIM, int N>
+__host__ __device__ constexpr int struct_threads() {
+  constexpr int NL = (DIM == 2) ? N : N * N;
+  return ((struct_cells_per_block<T, DIM, N>() * NL + 31) / 32) * 32;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -218,7 +236,7 @@ __device__ __forceinline__ void axis0_lines(const StructTables<T, N> &tab, const
 }
 
 template <typename T, int DIM, int N, bool ADJ, bool UNI>
-__global__ void __launch_bounds__(128) struct_kernel(const __grid_constant__ StructTables<T, N> tab,
+__global__ void __launch_bounds__(struct_threads<T, DIM, N>()) struct_kernel(const __grid_constant__ StructTables<T, N> tab,
                                                      const DevArrays<T> d, const Scalars<T> sc,
                                                      T *__restrict__ y, const T *__restrict__ x,
                                                      int cell_begin, int cell_end) {

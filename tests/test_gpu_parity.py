@@ -55,6 +55,12 @@ SMALL = {
     "3d_q4_6": workloads.small(p=4, N=6),
     "3d_q3_center_on_grid": workloads.small(p=3, N=6, center=(0.0, 0.0, 0.0)),
     "3d_q6_4": workloads.small(p=6, N=4),
+    # every structured-kernel block shape: n = 6, 7 take 4 and 3 cells per CTA (160 threads),
+    # n = 9 one cell (FP32: 3 cells, 256 threads); 2D n = 6, 7 take 16 and 9 cells
+    "3d_q5_4": workloads.small(p=5, N=4),
+    "3d_q7_3": workloads.small(p=7, N=3),
+    "3d_q8_3": workloads.small(p=8, N=3),
+    "2d_q6_8": workloads.small(p=6, N=8, dim=2),
     # volume-based ghost penalty on stable-neighbour patches
     "3d_q3_6_volume_gp": dict(workloads.small(p=3, N=6), gp_kind="volume", gp_tau=0.7),
     "2d_q2_10_volume_gp": dict(workloads.small(p=2, N=10, dim=2), gp_kind="volume"),
