@@ -127,10 +127,14 @@ typedef struct {
 } uf_info;
 
 /* Per-kernel device times collected between uf_profile_begin and uf_profile_end, indexed
- * [precision: 0 = FP64, 1 = FP32][kernel: 0 = structured, 1 = cut cells][0 = vmult, 1 = adjoint]. */
+ * [precision: 0 = FP64, 1 = FP32][kernel: 0 = structured, 1 = cut cells][0 = vmult, 1 = adjoint]:
+ * ms_total sums the bracketed times, launches counts the bracketed evaluations (one per vmult)
+ * and kernel_launches the kernel launches inside them (the cut-cell kernel launches once per
+ * non-empty lane class). */
 typedef struct {
   double ms_total[2][2][2];
   int64_t launches[2][2][2];
+  int64_t kernel_launches[2][2][2];
 } uf_kernel_times;
 
 /* Build the operator: classify the background cells against the level set, number the active

@@ -72,7 +72,8 @@ class uf_info(ctypes.Structure):
 
 
 class uf_kernel_times(ctypes.Structure):
-    _fields_ = [("ms_total", ctypes.c_double * 8), ("launches", ctypes.c_int64 * 8)]
+    _fields_ = [("ms_total", ctypes.c_double * 8), ("launches", ctypes.c_int64 * 8),
+                ("kernel_launches", ctypes.c_int64 * 8)]
 
 
 class uf_solve_params(ctypes.Structure):
@@ -303,9 +304,11 @@ class UnfittedOperator:
         _check(_lib.uf_profile_begin(self._h, int(capacity)))
 
     def profile_end(self):
-        """{(precision, kernel, direction): (total ms, launches)} of the profiled kernels."""
+        """{(precision, kernel, direction): (total ms, evaluations)} of the profiled kernels; the
+        number of kernel launches they made is left in self.profiled_kernel_launches."""
         t = uf_kernel_times()
         _check(_lib.uf_profile_end(self._h, ctypes.byref(t)))
+        self.profiled_kernel_launches = int(sum(t.kernel_launches))
         out = {}
         for pi, prec in enumerate(("fp64", "fp32")):
             for ki, kern in enumerate(("struct", "cut")):

@@ -1213,6 +1213,16 @@ uf_status uf_profile_end(uf_operator *op, uf_kernel_times *out) {
         if (err != cudaSuccess && first_err == cudaSuccess) first_err = err;
         out->ms_total[slot.prec][kern][slot.adjoint] += ms;
         out->launches[slot.prec][kern][slot.adjoint] += 1;
+        int64_t nk = 1;
+        if (kern == 1) {
+          // one launch per non-empty lane class: [0, split0), [split0, split1), [split1, n_cut)
+          const int32_t *sp = slot.prec == 0 ? op->f64.arrays.cut_split : op->f32.arrays.cut_split;
+          const int64_t nc = op->host.n_cut;
+          nk = (sp[0] > 0 ? 1 : 0) + (sp[1] > sp[0] ? 1 : 0) + (nc > sp[1] ? 1 : 0);
+        } else if (op->host.n_active == 0) {
+          nk = 0;
+        }
+        out->kernel_launches[slot.prec][kern][slot.adjoint] += nk;
       }
     }
     for (int k = 0; k < 4; ++k) cudaEventDestroy(slot.ev[k]);

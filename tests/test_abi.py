@@ -77,6 +77,19 @@ def test_vmult_on_host_only_operator_is_refused():
     assert st == binding.UF_EINVAL
 
 
+def test_host_buffer_calls_on_host_only_operator_are_refused():
+    op = UnfittedOperator(workloads.cfg_2d_q1(), device=-1)
+    lib = binding.load_library()
+    buf = np.zeros(op.n_dofs)
+    p = buf.ctypes.data_as(ctypes.c_void_p)
+    for fn in (lib.uf_vmult_host, lib.uf_vmult_adjoint_host, lib.uf_vmult_host_async,
+               lib.uf_vmult_adjoint_host_async):
+        assert fn(op._h, binding.UF_FP64, p, p, None) == binding.UF_ENODEVICE
+    assert lib.uf_host_wait(op._h, None) == binding.UF_ENODEVICE
+    assert lib.uf_host_wait(None, None) == binding.UF_EINVAL
+    op.close()
+
+
 def test_kappa_validation():
     cfg = workloads.cfg_2d_q1()
     with pytest.raises(UnfittedError):
