@@ -112,6 +112,23 @@ def test_random_spheres_cases_hold_multi_sphere_cells():
         assert (counts >= 2).sum() > 10 and (counts >= 3).sum() > 0, name
 
 
+@pytest.mark.parametrize("balls", [
+    [(0.45, 0.52, 0.48, 0.3), (0.45, 0.52, 0.48, 0.3)],   # the same ball twice
+    [(0.45, 0.52, 0.48, 0.3), (0.5, 0.5, 0.5, 0.12)],     # a ball inside another
+    [(0.3, 0.5, 0.5, 0.2), (0.7, 0.5, 0.5, 0.2)],         # touching balls
+    [(0.5, 0.5, 0.5, 0.3), (0.5, 0.5, 0.5, 0.2)],         # concentric
+    [(0.35, 0.5, 0.5, 0.2), (0.6, 0.5, 0.5, 0.2)],        # intersection circle in a grid-axis plane
+], ids=["duplicate", "nested", "touching", "concentric", "axis_aligned_pair"])
+def test_degenerate_unions_match_oracle(balls):
+    cfg = workloads.spheres(p=2, N=10, m=1, R=0.2)
+    cfg["spheres"] = balls
+    CASES["_degenerate"] = cfg
+    try:
+        test_setup_matches_oracle("_degenerate")
+    finally:
+        del CASES["_degenerate"]
+
+
 def test_regular_spheres_benchmark_counts():
     """1000 balls of radius 0.0362 on the 10^3 lattice of the unit cube, 192^3 cells, DG Q1:
     15,224,320 DoFs at a cut-cell ratio of 0.479 (the paper prints 15,264,256 and 0.478)."""

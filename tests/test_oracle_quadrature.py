@@ -348,6 +348,19 @@ def test_union_of_two_intersecting_balls_converges():
     assert errs[0][0] / errs[2][0] > 16 ** 2 and errs[0][1] / errs[2][1] > 16 ** 2
 
 
+def test_union_with_intersection_circle_in_a_grid_plane_converges():
+    """Centres on one grid axis: the intersection circle lies in a plane x = const, seen along
+    y or z as a segment; the rule still converges at high order."""
+    balls = [(0.35, 0.5, 0.5, 0.2), (0.6, 0.5, 0.5, 0.2)]
+    vol, area = _union_two_closed_forms(balls)
+    errs = []
+    for N in (8, 16, 32):
+        _, vw, sx, sw, sn = _all_rules(_spheres_prob(N, 4, balls))
+        errs.append((abs(vw.sum() - vol) / vol, abs(sw.sum() - area) / area))
+    assert errs[-1][0] < 1e-9 and errs[-1][1] < 1e-8
+    assert errs[0][0] / errs[2][0] > 16 ** 2 and errs[0][1] / errs[2][1] > 16 ** 2
+
+
 def test_union_of_two_intersecting_discs():
     (x1, y1, _, R1), (x2, y2, _, R2) = _TWO
     D = math.hypot(x2 - x1, y2 - y1)
