@@ -332,8 +332,9 @@ uf_status uf_manufactured_rhs(const uf_operator *op, double omega, double *b);
 uf_status uf_l2_error(const uf_operator *op, double omega, const double *x, double *err,
                       double *norm);
 
-/* Release every host and device resource of op.  NULL is accepted (no-op).  The caller must
- * make sure no stream still runs work of op. */
+/* Release every host and device resource of op.  NULL is accepted (no-op).  The library's own
+ * pipeline streams (asynchronous host-buffer products) are waited for; the caller must make sure
+ * none of its streams still runs other work of op. */
 uf_status uf_destroy(uf_operator *op);
 
 /* Thread-local message of the last failing call of this thread ("" if none). */

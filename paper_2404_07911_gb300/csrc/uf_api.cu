@@ -1325,6 +1325,10 @@ uf_status uf_destroy(uf_operator *op) {
   if (!op) return UF_OK;
   if (op->device >= 0) {
     DeviceGuard guard(op->device);
+    // queued asynchronous host-buffer products finish before their buffers go
+    for (cudaStream_t r : op->pipe_run) cudaStreamSynchronize(r);
+    if (op->pipe_in) cudaStreamSynchronize(op->pipe_in);
+    if (op->pipe_out) cudaStreamSynchronize(op->pipe_out);
     uf::release_csr(op->csr64);
     uf::release_csr(op->csr32);
     uf::cg_free(op);
