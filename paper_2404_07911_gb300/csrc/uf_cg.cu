@@ -293,6 +293,37 @@ __global__ void k_jacobi(T *__restrict__ z, const T *__restrict__ r, const T *__
   if (i < n) z[i] = invd[i] * r[i];
 }
 
+// 16-byte packs of a vector (the solver's work vectors are separate cudaMalloc allocations, so
+// their packs are aligned): V entries per pack.
+template <typename T>
+struct Pack;
+template <>
+struct Pack<float> {
+  static constexpr int V = 4;
+  __device__ __forceinline__ static void load(const float *a, int64_t j, float *o) {
+    const float4 v = reinterpret_cast<const float4 *>(a)[j];
+    o[0] = v.x;
+    o[1] = v.y;
+    o[2] = v.z;
+    o[3] = v.w;
+  }
+  __device__ __forceinline__ static void store(float *a, int64_t j, const float *o) {
+    reinterpret_cast<float4 *>(a)[j] = make_float4(o[0], o[1], o[2], o[3]);
+  }
+};
+template <>
+struct Pack<double> {
+  static constexpr int V = 2;
+  __device__ __forceinline__ static void load(const double *a, int64_t j, double *o) {
+    const double2 v = reinterpret_cast<const double2 *>(a)[j];
+    o[0] = v.x;
+    o[1] = v.y;
+  }
+  __device__ __forceinline__ static void store(double *a, int64_t j, const double *o) {
+    reinterpret_cast<double2 *>(a)[j] = make_double2(o[0], o[1]);
+  }
+};
+
 // Block sums of (s0, s1) over kDotThreads threads, written to part[blockIdx.x] and
 // part[kDotBlocks + blockIdx.x] (fixed order).
 __device__ __forceinline__ void block_sums(double a0, double a1, double *__restrict__ part) {
@@ -371,9 +402,18 @@ __global__ void __launch_bounds__(kDotThreads) k_pcg_pq(const T *__restrict__ p,
                                                         int64_t n, double *__restrict__ part,
                                                         const PcgScalars *__restrict__ sc) {
   if (sc->status != 0) return;
+  constexpr int V = Pack<T>::V;
+  const int64_t nv = n / V;
   double acc = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    acc = fma((double)p[i], (double)q[i], acc);
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += (int64_t)gridDim.x * blockDim.x) {
+    T pv[V], qv[V];
+    Pack<T>::load(p, j, pv);
+    Pack<T>::load(q, j, qv);
+#pragma unroll
+    for (int e = 0; e < V; ++e) acc = fma((double)pv[e], (double)qv[e], acc);
+  }
+  if (blockIdx.x == 0)  // the last n mod V entries
+    for (int64_t i = nv * V + threadIdx.x; i < n; i += blockDim.x) acc = fma((double)p[i], (double)q[i], acc);
   block_sums(acc, 0.0, part);
 }
 
@@ -385,16 +425,38 @@ __global__ void __launch_bounds__(kDotThreads)
                  const PcgScalars *__restrict__ sc) {
   if (sc->status != 0) return;
   const T alpha = (T)sc->alpha;
+  constexpr int V = Pack<T>::V;
+  const int64_t nv = n / V;
   double a0 = 0.0, a1 = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    x[i] = fma(alpha, p[i], x[i]);
-    const T ri = fma(-alpha, q[i], r[i]);
-    const T zi = invd[i] * ri;
-    r[i] = ri;
-    z[i] = zi;
-    a0 = fma((double)ri, (double)zi, a0);
-    a1 = fma((double)ri, (double)ri, a1);
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += (int64_t)gridDim.x * blockDim.x) {
+    T xv[V], rv[V], pv[V], qv[V], dv[V], zv[V];
+    Pack<T>::load(x, j, xv);
+    Pack<T>::load(r, j, rv);
+    Pack<T>::load(p, j, pv);
+    Pack<T>::load(q, j, qv);
+    Pack<T>::load(invd, j, dv);
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      xv[e] = fma(alpha, pv[e], xv[e]);
+      rv[e] = fma(-alpha, qv[e], rv[e]);
+      zv[e] = dv[e] * rv[e];
+      a0 = fma((double)rv[e], (double)zv[e], a0);
+      a1 = fma((double)rv[e], (double)rv[e], a1);
+    }
+    Pack<T>::store(x, j, xv);
+    Pack<T>::store(r, j, rv);
+    Pack<T>::store(z, j, zv);
   }
+  if (blockIdx.x == 0)  // the last n mod V entries
+    for (int64_t i = nv * V + threadIdx.x; i < n; i += blockDim.x) {
+      x[i] = fma(alpha, p[i], x[i]);
+      const T ri = fma(-alpha, q[i], r[i]);
+      const T zi = invd[i] * ri;
+      r[i] = ri;
+      z[i] = zi;
+      a0 = fma((double)ri, (double)zi, a0);
+      a1 = fma((double)ri, (double)ri, a1);
+    }
   block_sums(a0, a1, part);
 }
 
@@ -429,14 +491,27 @@ __global__ void k_pcg_beta(const double *__restrict__ part, PcgScalars *__restri
   }
 }
 
-// p = z + beta p
+// p = z + beta p (one 16-byte pack per thread; block 0 also takes the last n mod V entries)
 template <typename T>
 __global__ void k_pcg_direction(T *__restrict__ p, const T *__restrict__ z, int64_t n,
                                 const PcgScalars *__restrict__ sc) {
   if (sc->status != 0) return;
   const T beta = (T)sc->beta;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) p[i] = fma(beta, p[i], z[i]);
+  constexpr int V = Pack<T>::V;
+  const int64_t nv = n / V;
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < nv) {
+    T pv[V], zv[V];
+    Pack<T>::load(p, j, pv);
+    Pack<T>::load(z, j, zv);
+#pragma unroll
+    for (int e = 0; e < V; ++e) pv[e] = fma(beta, pv[e], zv[e]);
+    Pack<T>::store(p, j, pv);
+  }
+  if (blockIdx.x == 0 && nv * V + threadIdx.x < n) {
+    const int64_t i = nv * V + threadIdx.x;
+    p[i] = fma(beta, p[i], z[i]);
+  }
 }
 
 // r = b - q
@@ -549,7 +624,7 @@ uf_status pcg(SolveCtx &c, int precision, const T *invd, T *x, T *r, T *z, T *p,
       k_pcg_alpha<<<1, kDotThreads, 0, c.s>>>(c.dot_part, c.sc);
       k_pcg_update<T><<<kDotBlocks, kDotThreads, 0, c.s>>>(x, r, z, p, q, invd, n, c.dot_part, c.sc);
       k_pcg_beta<<<1, kDotThreads, 0, c.s>>>(c.dot_part, c.sc);
-      k_pcg_direction<T><<<nblk(n), 256, 0, c.s>>>(p, z, n, c.sc);
+      k_pcg_direction<T><<<nblk(std::max<int64_t>(n / Pack<T>::V, 1)), 256, 0, c.s>>>(p, z, n, c.sc);
     }
     launched += chunk;
     cudaError_t err = cudaMemcpyAsync(c.sc_host, c.sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, c.s);
