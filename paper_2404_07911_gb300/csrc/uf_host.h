@@ -67,7 +67,7 @@ struct HostOperator {
   int ls_kind = 0;                      // UF_LS_SPHERE or UF_LS_PLANE
   double normal[kMaxDim] = {0, 0, 0};   // plane: phi = normal . x - offset
   double offset = 0;
-  std::vector<double> spheres;          // union of separated balls: [n][4] = (cx, cy, cz, R)
+  std::vector<double> spheres;          // union of balls: [n][4] = (cx, cy, cz, R)
   std::vector<int64_t> cut_sph_off;     // [n_cut + 1] union of balls: spheres meeting each cut
   std::vector<int32_t> cut_sph;         //   cell, cut_sph[cut_sph_off[c] .. cut_sph_off[c + 1])
 
