@@ -402,7 +402,7 @@ def run_ours(args, rank, world, local):
                 "alu_frac": round(alu_frac, 4)}
     roof["algorithmic_bytes_per_launch"] = byts
     roof["algorithmic_flops_per_launch"] = flops
-    roof["algorithmic_flops_source"] = ("paper arithmetic-complexity model (Sec. 4.1) applied to "
+    roof["algorithmic_flops_source"] = ("paper arithmetic-complexity model (Sec. 5.1) applied to "
                                         "the launch's cells, faces and points")
     roof["avg_launch_ms"] = round(avg_s * 1e3, 5)
     roof["as_built_tflops"] = round(tfl_built, 4)

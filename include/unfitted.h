@@ -79,7 +79,7 @@ typedef struct {
                              face of a cut cell; UF_GP_VOLUME: gp_tau / h^2 {kappa} int_P [u]_P [v]_P on
                              stable-neighbour patches P (paper Sec. 2.2, Eq. volume_based_gp): every
                              cut cell with its active face neighbour of largest volume fraction, [u]_P
-                             the own polynomial minus the neighbour's extended one (Sec. 3.4).  Either
+                             the own polynomial minus the neighbour's extended one (Sec. 3.3).  Either
                              is off when gp_max_order = 0. */
   double gp_tau;          /* tau_v of UF_GP_VOLUME */
   const double *ls_spheres;  /* UF_LS_SPHERES: host array [ls_n_spheres][4] = (cx, cy, cz, R), copied
@@ -104,7 +104,7 @@ typedef struct {
    * surface normal; per line: two outer coordinates and offsets), FP64 and FP32 data. */
   double bytes_fp64, bytes_fp32;
   /* Algorithmic floating-point operations of one vmult (FMA = 2) from the paper's arithmetic
-   * complexity model (Sec. 4.1: structured cell 6 k^4, structured face 7 k^3, unstructured cell
+   * complexity model (Sec. 5.1: structured cell 6 k^4, structured face 7 k^3, unstructured cell
    * point 2 k^3 + 3 k^2 + 4 k, unstructured face point 3 k^2 + 4 k plus k^3 per face side, each
    * for evaluation and again for integration, k = p + 1) applied to this operator's inside cells,
    * structured faces, ghost-penalty orders, and unstructured points. */
@@ -140,7 +140,7 @@ typedef struct {
 /* Build the operator: classify the background cells against the level set, number the active
  * cells, type the interior faces, generate the dimension-reduction quadrature of every cut cell
  * and cut face, and (device >= 0) upload everything to the device in the precisions requested.
- * Untimed setup (the paper excludes it, Sec. 5.2).  On success *out owns all library memory.
+ * Untimed setup (the paper excludes it, Sec. 6.2).  On success *out owns all library memory.
  * Errors: UF_EINVAL (NULL, dim/degree/q/sizes out of range), UF_EUNSUPPORTED (anisotropic cells,
  * unknown level set), UF_EGEOMETRY, UF_ENOMEM, UF_ECUDA. */
 uf_status uf_create_unfitted_operator(const uf_params *params, uf_operator **out);
@@ -201,7 +201,7 @@ uf_status uf_host_wait(uf_operator *op, void *stream);
 uf_status uf_profile_begin(uf_operator *op, int capacity);
 uf_status uf_profile_end(uf_operator *op, uf_kernel_times *out);
 
-/* Assembled-matrix baseline (paper Sec. 3.1 / Sec. 4.1, matrix-based evaluation).
+/* Assembled-matrix baseline (paper Sec. 3.1 / Sec. 5.1, matrix-based evaluation).
  * uf_assemble_csr builds the operator's matrix on the device in CSR form (int64 row offsets
  * [n_dofs + 1], int32 column indices, values in `precision`; columns ascending per row) by
  * applying the FP64 matrix-free operator to distance-2-coloured unit vectors (n^d applications
@@ -283,7 +283,7 @@ uf_status uf_export_cut_face_rule(const uf_operator *op, int64_t e, int axis, in
  * FP64.  Any pointer may be NULL.  Errors: UF_EINVAL (NULL op, not a UF_CG operator). */
 uf_status uf_export_cg(const uf_operator *op, int32_t *l2g, double *rhs, double *diag);
 
-/* Solve A x = b with Jacobi-preconditioned CG (the solver of the paper's Sec. 3.5 is a PCG; its
+/* Solve A x = b with Jacobi-preconditioned CG (the solver of the paper's Sec. 3.6 is a PCG; its
  * multigrid preconditioner is out of scope), for a continuous (UF_CG) or a discontinuous (UF_DG)
  * operator.  The Jacobi diagonal is computed on the host in FP64 (for UF_DG, and the work
  * vectors with it, on the first call: that call allocates device memory) and follows

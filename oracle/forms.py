@@ -192,7 +192,7 @@ class Oracle:
     def volume_gp_blocks(self, e_minus, axis):
         """Blocks of the volume ghost penalty tau_v / h^2 {kappa} int_P [v]_P [u]_P on the patch
         P = K- cup K+ (Sec. 2.2, Eq. volume_based_gp): on each cell of the patch [u]_P is the own
-        polynomial minus the other cell's polynomial extended to it (Sec. 3.4), integrated with the
+        polynomial minus the other cell's polynomial extended to it (Sec. 3.3), integrated with the
         tensor Gauss rule of the full cell."""
         prob = self.prob
         cells, kap, kavg = self._face_setup(e_minus, axis)

@@ -3,7 +3,7 @@ infrastructure only).
 
 The paper generates the cut-cell (volume, surface) and cut-face rules with the dimension
 reduction method of Saye (2015) (Sec. 1, Sec. 2.3) and adds uniform subdivision when needed
-(Sec. 4.1, arithmetic-complexity paragraph on refined cut cells).  The paper states no details, so
+(Sec. 5.1, arithmetic-complexity paragraph on refined cut cells).  The paper states no details, so
 this module restates the method for level sets of the form psi(x) = |x - c|^2 - rho, for which
 every root along a coordinate line has a closed form.  This fixes one deterministic rule (the
 CUDA library's host setup implements the same reading independently):

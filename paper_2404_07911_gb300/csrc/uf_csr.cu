@@ -1,5 +1,5 @@
 // Assembled-matrix baseline: the operator as a CSR matrix and its SpMV (arXiv 2404.07911,
-// Sec. 3.1: the same element operators give the sparse matrix; Sec. 4.1 models the matrix-based
+// Sec. 3.1: the same element operators give the sparse matrix; Sec. 5.1 models the matrix-based
 // evaluation at 12 bytes and 2 FLOPs per nonzero with 32-bit column indices).
 //
 // Assembly takes the matrix column by column from the matrix-free operator (Sec. 3.1: "local

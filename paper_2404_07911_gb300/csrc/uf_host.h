@@ -3,7 +3,7 @@
 // The setup follows arXiv 2404.07911, Sec. 2.3 (quadrature classification): background cells
 // are classified as inside / cut / outside against the level set, interior faces as full / cut /
 // empty, and the cut cells and cut faces receive dimension-reduction quadrature (Saye's method,
-// cited in Sec. 1) generated once; Sec. 5.2 excludes this setup from the timed operator.
+// cited in Sec. 1) generated once; Sec. 6.2 excludes this setup from the timed operator.
 #pragma once
 
 #include <cstdint>

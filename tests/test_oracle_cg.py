@@ -1,6 +1,6 @@
 """Pins of the oracle's continuous Q_p operator (CPU).
 
-* numbering: the CG DoF count the paper prints in Sec. 5.2 (CG, p = 3, 48^3: 1,597,645);
+* numbering: the CG DoF count the paper prints in Sec. 6.2 (CG, p = 3, 48^3: 1,597,645);
 * the exact solution of -Lap u = 1 in the ball with u = 0 on the sphere is the quadratic
   u = (R^2 - |x - c|^2) / (2 d); it lies in Q_p for p >= 2, and the Nitsche / ghost-penalty form
   is consistent, so the discrete solution reproduces it up to the quadrature error (this pins the

@@ -23,7 +23,7 @@ benchmark configurations:
                        Nitsche u = 0, ghost penalty orders 1..4, f = 1 (the solve workload).
   * ``small(...)``     reduced grids of the same geometry for tests the oracle finishes in seconds.
   * ``plane(...)``     half-space below a slightly tilted plane in a box of cubes (the paper's plane
-                       benchmark, Sec. 5.3, positions the plane to set the ratio of cut cells);
+                       benchmark, Sec. 5.2, positions the plane to set the ratio of cut cells);
                        ``cfg_plane(kind, ratio)`` sizes the box so that the cut layer is a fraction
                        ``ratio`` of the active cells.
 
