@@ -55,7 +55,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--cpu-sample-cells", type=int, default=120,
-                    help="cells of the oracle's bounded sample (cpu_baseline / reference arm)")
+                    help="cells per host core of the oracle's bounded sample (cpu_baseline, "
+                         "reference arm, --config oracle)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--gp", choices=("face", "volume"), default="face",
                     help="ghost penalty of the headline and accuracy workloads: face-based "
@@ -64,14 +65,15 @@ def parse_args():
     ap.add_argument("--no-csr", action="store_true",
                     help="skip the assembled-matrix (CSR SpMV) comparison")
     ap.add_argument("--config", choices=("q3", "solve", "sweep", "kappa", "plane", "accuracy",
-                                         "spheres"),
+                                         "spheres", "oracle"),
                     default="q3",
                     help="q3: the headline step (default); solve: CG Q4 time to solution, IR vs "
                          "FP64; sweep: degree sweep p = 1..8 at ~2e7 DoFs; kappa: forward vs "
                          "forward + backward of the differentiable operator; plane: throughput "
                          "against the ratio of cut cells (DG Q1, CG Q3); accuracy: convergence of "
                          "the sphere accuracy benchmark (CG, DG, p = 1..4); spheres: the "
-                         "regular 1000-spheres benchmark (DG Q1)")
+                         "regular 1000-spheres benchmark (DG Q1); oracle: the CPU oracle on all host "
+                         "cores and on one (2D Q1 disc, 3D Q3 ball, kappa workload)")
     return ap.parse_args()
 
 
@@ -133,25 +135,90 @@ def _blas_single_thread():
         return None
 
 
-def cpu_baseline(cfg, n_cells, budget_s=20.0):
-    cores = _blas_single_thread() or 1
-    cells, n_dofs = oracle_sample(cfg, n_cells)
+# The oracle's rows are timed in worker processes, one per host core (started with `spawn`, so
+# that a CUDA context of the parent is never forked); each worker builds the workload's input once
+# and, per step, a fresh oracle applied to its share of the sampled cells.
+_POOL_CFG = None
+_POOL_X = None
+
+
+def _oracle_pool_init(cfg, n_dofs):
+    global _POOL_CFG, _POOL_X
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    _blas_single_thread()
+    _POOL_CFG = cfg
     x64 = workloads.uniform_vector(n_dofs, cfg["seed"])
-    x32r = x64.astype(np.float32).astype(np.float64)
+    _POOL_X = (x64, x64.astype(np.float32).astype(np.float64))
+
+
+def _oracle_pool_task(cells):
+    t0 = time.perf_counter()
+    oracle_step(_POOL_CFG, _POOL_X[0], _POOL_X[1], cells)
+    return time.perf_counter() - t0
+
+
+def host_cpu():
+    """(logical cores, CPU model string) of this host."""
+    model = ""
+    try:
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":")[0].strip().lower()
+            if key in ("model name", "cpu part", "hardware") and not model:
+                model = line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+
+    return os.cpu_count() or 1, f"{platform.machine()} {model}".strip()
+
+
+def time_oracle(cfg, cells_per_core, cores, steps, budget_s, seed=3):
+    """Wall time of oracle steps (A x FP64, A x FP32-rounded, A^T x FP64 on the rows of a sampled
+    cell set) with `cores` worker processes, cells_per_core cells each.  Returns (GDoF/s, cells,
+    step seconds list)."""
+    import multiprocessing as mp
+
+    cells, n_dofs = oracle_sample(cfg, cells_per_core * cores, seed)
+    chunks = [cells[i::cores] for i in range(cores)]
     nd = (cfg["degree"] + 1) ** cfg["dim"]
-    times = []
-    t_start = time.perf_counter()
-    while True:
-        t0 = time.perf_counter()
-        oracle_step(cfg, x64, x32r, cells)
-        times.append(time.perf_counter() - t0)
-        if time.perf_counter() - t_start > budget_s or len(times) >= 5:
-            break
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores, initializer=_oracle_pool_init, initargs=(cfg, n_dofs)) as pool:
+        pool.map(_oracle_pool_task, chunks[:cores])  # warm-up: imports and first oracle per worker
+        times = []
+        t_start = time.perf_counter()
+        while len(times) < steps:
+            t0 = time.perf_counter()
+            pool.map(_oracle_pool_task, chunks)
+            times.append(time.perf_counter() - t0)
+            if time.perf_counter() - t_start > budget_s:
+                break
     t = statistics.median(times)
-    return {"value": 3 * len(cells) * nd / t / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{len(cells)} active cells of the workload (inside/cut mix of the full grid, "
-                      f"seed 3), rows of A x FP64 + A x FP32-rounded + A^T x per step, "
-                      f"median of {len(times)} steps of {t:.2f} s each, BLAS 1 thread"}
+    return 3 * len(cells) * nd / t / 1e9, len(cells), times
+
+
+def oracle_sample_cells(cfg, n_cells):
+    """A bounded sample that the oracle finishes in seconds: at most every active cell."""
+    from oracle import mesh
+
+    return min(n_cells, mesh.Mesh(mesh.problem_from_dict(cfg)).n_active)
+
+
+def cpu_baseline(cfg, cells_per_core, budget_s=20.0):
+    host_cores, model = host_cpu()
+    cells_per_core = oracle_sample_cells(cfg, cells_per_core * host_cores) // host_cores or 1
+    v_all, n_all, t_all = time_oracle(cfg, cells_per_core, host_cores, 5, budget_s)
+    v_one, n_one, t_one = time_oracle(cfg, cells_per_core, 1, 3, budget_s / 2)
+    return {"value": v_all, "unit": UNIT, "cores": host_cores, "kind": "oracle",
+            "sample": f"{n_all} active cells of the workload (inside/cut mix of the full grid, "
+                      f"seed 3), rows of A x FP64 + A x FP32-rounded + A^T x FP64 per step, "
+                      f"{host_cores} worker processes ({cells_per_core} cells each, fresh oracle "
+                      f"per step, BLAS 1 thread each), median of {len(t_all)} steps of "
+                      f"{statistics.median(t_all):.2f} s wall",
+            "host": model,
+            "single_core": {"value": v_one, "unit": UNIT, "cores": 1,
+                            "sample": f"{n_one} cells, median of {len(t_one)} steps of "
+                                      f"{statistics.median(t_one):.2f} s"}}
 
 
 # ------------------------------------------------------------------------------ clocks
@@ -227,6 +294,77 @@ def kernel_traffic(name):
         return float(rec[name])
     except Exception:
         return None
+
+
+def binding_roof(byts, flops, seconds, hbm_gbs, alu_tflops):
+    """Fraction of the binding roof: t_roof / t with t_roof = max(bytes / BW, FLOPs / peak) for
+    the work as executed (algorithmic bytes, floating-point operations of the kernels as built)."""
+    t_hbm = byts / (hbm_gbs * 1e9)
+    t_alu = flops / (alu_tflops * 1e12)
+    bound = "hbm" if t_hbm >= t_alu else "alu"
+    return bound, max(t_hbm, t_alu) / seconds, t_hbm / seconds, t_alu / seconds
+
+
+def roofline_figures(info, ktimes, hbm, n):
+    """Per kernel and per product (FP64 A x, FP32 A x, FP64 A^T x): average launch time, HBM
+    fraction (algorithmic bytes), FP-pipe fraction (FLOPs as built), binding-roof fraction; the
+    paper-model FLOP rate is kept beside them.  Returns (kernel table, products, roofline object of
+    the kernel with the largest total time)."""
+    kernels = []
+    parts = {}
+    for (prec, kern, dirn), (ms, cnt) in ktimes.items():
+        ki = 0 if kern == "struct" else 1
+        byts = info["kernel_bytes_fp64" if prec == "fp64" else "kernel_bytes_fp32"][ki]
+        flops_model = info["kernel_flops"][ki]
+        flops = info["kernel_flops_built" if prec == "fp64" else "kernel_flops_built_fp32"][ki]
+        avg_s = ms / cnt / 1e3
+        peak = FP64_PEAK_TFLOPS if prec == "fp64" else FP32_PEAK_TFLOPS
+        bound, frac, hbm_frac, alu_frac = binding_roof(byts, flops, avg_s, hbm, peak)
+        name = f"{kern}_kernel_{prec}{'_adjoint' if dirn == 'adjoint' else ''}"
+        kernels.append({"name": name, "prec": prec, "total_ms": ms, "avg_s": avg_s, "bytes": byts,
+                        "flops": flops, "flops_model": flops_model, "peak": peak, "bound": bound,
+                        "frac": frac, "hbm_frac": hbm_frac, "alu_frac": alu_frac})
+        p = parts.setdefault(f"{prec}_{dirn}", {"s": 0.0, "bytes": 0.0, "flops": 0.0, "peak": peak})
+        p["s"] += avg_s
+        p["bytes"] += byts
+        p["flops"] += flops
+    products = {}
+    for key, p in parts.items():
+        bound, frac, hbm_frac, alu_frac = binding_roof(p["bytes"], p["flops"], p["s"], hbm, p["peak"])
+        products[key] = {"ms": round(p["s"] * 1e3, 4), "gdofs": round(n / p["s"] / 1e9, 3),
+                         "bound": bound, "roof_frac": round(frac, 4), "hbm_frac": round(hbm_frac, 4),
+                         "pipe_frac": round(alu_frac, 4)}
+    kernels.sort(key=lambda k: -k["total_ms"])
+    table = {k["name"]: {"avg_ms": round(k["avg_s"] * 1e3, 5),
+                         "gb_s": round(k["bytes"] / k["avg_s"] / 1e9, 1),
+                         "tflops_as_built": round(k["flops"] / k["avg_s"] / 1e12, 4),
+                         "bound": k["bound"], "roof_frac": round(k["frac"], 4),
+                         "hbm_frac": round(k["hbm_frac"], 4), "pipe_frac": round(k["alu_frac"], 4),
+                         "model_flops_equiv_frac": round(k["flops_model"] / k["avg_s"] / 1e12 / k["peak"], 4)}
+             for k in kernels}
+    k = kernels[0]
+    if k["bound"] == "alu":
+        roof = {"bound": "alu", "achieved": round(k["flops"] / k["avg_s"] / 1e12, 4),
+                "peak": round(k["peak"], 4), "unit": "TFLOP/s",
+                "peak_source": f"derived: {SM_COUNT} SMs x "
+                               f"{'2 FP64' if k['prec'] == 'fp64' else '128 FP32'} FMA/clk x 2 x "
+                               f"{SM_MAX_GHZ} GHz"}
+    else:
+        roof = {"bound": "hbm", "achieved": round(k["bytes"] / k["avg_s"] / 1e9, 2), "peak": hbm,
+                "unit": "GB/s", "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+    roof.update({"frac": round(k["frac"], 4), "traffic": kernel_traffic(k["name"]),
+                 "kernel": k["name"], "hbm_frac_of_measured": round(k["hbm_frac"], 4),
+                 "pipe_frac": round(k["alu_frac"], 4),
+                 "algorithmic_bytes_per_launch": k["bytes"],
+                 "flops_per_launch_as_built": k["flops"],
+                 "flops_source": "floating-point operations of the kernel as built, counted from the "
+                                 "launch's cells, faces, lines and points (FMA = 2)",
+                 "model_flops_per_launch": k["flops_model"],
+                 "model_flops_equiv_frac": round(k["flops_model"] / k["avg_s"] / 1e12 / k["peak"], 4),
+                 "model_flops_source": "paper arithmetic-complexity model (Sec. 5.1) applied to the "
+                                       "launch's cells, faces and points",
+                 "avg_launch_ms": round(k["avg_s"] * 1e3, 5)})
+    return table, products, roof
 
 
 def run_ours(args, rank, world, local):
@@ -363,54 +501,8 @@ def run_ours(args, rank, world, local):
     # ---- per-kernel figures from the events of the timed region
     peaks = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    parts = {}
-    kernels = []
-    for (prec, kern, dirn), (ms, cnt) in ktimes.items():
-        ki = 0 if kern == "struct" else 1
-        byts = info["kernel_bytes_fp64" if prec == "fp64" else "kernel_bytes_fp32"][ki]
-        flops = info["kernel_flops"][ki]
-        flops_built = info["kernel_flops_built" if prec == "fp64" else "kernel_flops_built_fp32"][ki]
-        avg_s = ms / cnt / 1e3
-        alu_peak = FP64_PEAK_TFLOPS if prec == "fp64" else FP32_PEAK_TFLOPS
-        gbs = byts / avg_s / 1e9
-        tfl = flops / avg_s / 1e12
-        name = f"{kern}_kernel_{prec}{'_adjoint' if dirn == 'adjoint' else ''}"
-        kernels.append((ms, name, prec, gbs, tfl, alu_peak, byts, flops, avg_s,
-                        flops_built / avg_s / 1e12))
-        key = f"{prec}_{dirn}"
-        parts.setdefault(key, {"ms": 0.0})
-        parts[key]["ms"] += ms / cnt
-    for key in parts:
-        parts[key]["gdofs"] = n / (parts[key]["ms"] / 1e3) / 1e9
-        parts[key]["ms"] = round(parts[key]["ms"], 4)
-        parts[key]["gdofs"] = round(parts[key]["gdofs"], 3)
-    kernels.sort(reverse=True)
-    ms, name, prec, gbs, tfl, alu_peak, byts, flops, avg_s, tfl_built = kernels[0]
-    hbm_frac = gbs / hbm
-    alu_frac = tfl / alu_peak
-    traffic = kernel_traffic(name)
-    if alu_frac >= hbm_frac:
-        roof = {"bound": "alu", "achieved": round(tfl, 4), "peak": round(alu_peak, 4),
-                "unit": "TFLOP/s", "frac": round(alu_frac, 4), "traffic": traffic,
-                "kernel": name, "peak_source": f"derived: {SM_COUNT} SMs x "
-                f"{'2 FP64' if prec == 'fp64' else '128 FP32'} FMA/clk x 2 x {SM_MAX_GHZ} GHz",
-                "hbm_frac_of_measured": round(hbm_frac, 4)}
-    else:
-        roof = {"bound": "hbm", "achieved": round(gbs, 2), "peak": hbm, "unit": "GB/s",
-                "frac": round(hbm_frac, 4), "traffic": traffic, "kernel": name,
-                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
-                "alu_frac": round(alu_frac, 4)}
-    roof["algorithmic_bytes_per_launch"] = byts
-    roof["algorithmic_flops_per_launch"] = flops
-    roof["algorithmic_flops_source"] = ("paper arithmetic-complexity model (Sec. 5.1) applied to "
-                                        "the launch's cells, faces and points")
-    roof["avg_launch_ms"] = round(avg_s * 1e3, 5)
-    roof["as_built_tflops"] = round(tfl_built, 4)
-    roof["as_built_pipe_frac"] = round(tfl_built / alu_peak, 4)
-    kernel_table = {k[1]: {"avg_ms": round(k[8] * 1e3, 5), "gb_s": round(k[3], 1),
-                           "hbm_frac": round(k[3] / hbm, 4), "tflops_model": round(k[4], 3),
-                           "alu_frac_model": round(k[4] / k[5], 4),
-                           "alu_frac_as_built": round(k[9] / k[5], 4)} for k in kernels}
+    kernel_table, parts, dominant = roofline_figures(info, ktimes, hbm, n)
+    roof = dominant
     launches = op.profiled_kernel_launches  # kernel launches inside the timed region
 
     result = {
@@ -687,7 +779,8 @@ def run_solve(args, local):
 
 
 def run_sweep(args, local):
-    """Degree sweep p = 1..8 at about 2e7 DoFs: FP64 / FP32 GDoF/s and errors vs the oracle."""
+    """Degree sweep p = 1..8 at about 2e7 DoFs: FP64 / FP32 GDoF/s, HBM / FP-pipe / binding-roof
+    fractions per product and kernel, and errors vs the oracle."""
     import torch
 
     from oracle import forms, mesh
@@ -696,6 +789,7 @@ def run_sweep(args, local):
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    hbm = float(measured_peaks().get("hbm_gbs", 6800.0))
     for p in range(1, 9):
         cfg = workloads.cfg_sweep(p)
         op = UnfittedOperator(cfg, precisions=UF_FP64 | UF_FP32, device=local)
@@ -713,8 +807,7 @@ def run_sweep(args, local):
         ms64 = _event_ms(lambda: op.vmult(x64, y64, stream), K, stream, flush)
         ms32 = _event_ms(lambda: op.vmult(x32, y32, stream), K, stream, flush)
         kt = op.profile_end()
-        kernels = {f"{kern}_{prec}": round(tot / cnt, 4)
-                   for (prec, kern, _), (tot, cnt) in sorted(kt.items())}
+        ktab, prods, _ = roofline_figures(op.info, kt, hbm, n)
         o = forms.Oracle(mesh.problem_from_dict(cfg))
         cut = np.nonzero(o.mesh.active_type == mesh.CUT)[0]
         ins = np.nonzero(o.mesh.active_type == mesh.INSIDE)[0]
@@ -735,7 +828,8 @@ def run_sweep(args, local):
             "fp32": {"ms": round(ms32, 4), "gdofs": round(n / ms32 / 1e6, 3),
                      "rel_err_vs_rounded_input": float(np.max(np.abs(g32 - ref32)) / sc),
                      "rel_err_vs_fp64_oracle": float(np.max(np.abs(g32 - ref)) / sc)},
-            "kernel_ms": kernels, "l2": "flushed before every launch"}), flush=True)
+            "products": prods, "kernels": ktab, "hbm_peak_gbs": hbm,
+            "l2": "flushed before every launch"}), flush=True)
         op.close()
         del x64, x32, y64, y32
         torch.cuda.empty_cache()
@@ -784,33 +878,55 @@ def run_kappa(args, local):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    cores = _blas_single_thread() or 1
     cfg = workloads.cfg_3d_q3()
-    cells, n_dofs = oracle_sample(cfg, args.cpu_sample_cells)
-    x64 = workloads.uniform_vector(n_dofs, cfg["seed"])
-    x32r = x64.astype(np.float32).astype(np.float64)
-    nd = (cfg["degree"] + 1) ** cfg["dim"]
-    for _ in range(args.warmup):
-        oracle_step(cfg, x64, x32r, cells)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle_step(cfg, x64, x32r, cells)
-    t = time.perf_counter() - t0
-    value = args.steps * 3 * len(cells) * nd / t / 1e9
-    sample = (f"{len(cells)} active cells of the workload (inside/cut mix of the full grid, seed 3), "
-              f"rows of A x FP64 + A x FP32-rounded + A^T x per step, fresh oracle per step")
+    cores, model = host_cpu()
+    cpc = oracle_sample_cells(cfg, args.cpu_sample_cells * cores) // cores or 1
+    value, n_cells, times = time_oracle(cfg, cpc, cores, args.warmup + args.steps, 1e9)
+    times = times[args.warmup:]
+    t = sum(times)
+    value = args.steps * 3 * n_cells * (cfg["degree"] + 1) ** cfg["dim"] / t / 1e9
+    sample = (f"{n_cells} active cells of the workload (inside/cut mix of the full grid, seed 3), "
+              f"rows of A x FP64 + A x FP32-rounded + A^T x FP64 per step, {cores} worker "
+              f"processes ({cpc} cells each, fresh oracle per step, BLAS 1 thread each)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": cfg["name"], "n_dofs": n_dofs, "degree": cfg["degree"],
+        "config": {"workload": cfg["name"], "n_dofs": workloads_n_dofs(cfg), "degree": cfg["degree"],
                    "step": "A x FP64 + A x FP32 + A^T x FP64 (rows of the sampled cells)",
                    "parallelism": "rank 0 only"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "host": model},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
+
+
+def workloads_n_dofs(cfg):
+    from oracle import mesh
+
+    return int(mesh.Mesh(mesh.problem_from_dict(cfg)).n_dofs)
+
+
+def run_oracle_timing(args):
+    """The oracle on the host cores (all, and one) for the 2D Q1 disc, the 3D Q3 ball and the
+    log-normal-kappa 48^3 workloads: GDoF/s of sampled rows (every active cell of the 2D case)."""
+    from oracle import mesh
+
+    cores, model = host_cpu()
+    out = {"host": model, "host_cores": cores, "unit": UNIT, "workloads": []}
+    for cfg in (workloads.cfg_2d_q1(), workloads.cfg_3d_q3(), workloads.cfg_kappa()):
+        n_active = mesh.Mesh(mesh.problem_from_dict(cfg)).n_active
+        cpc = max(1, min(args.cpu_sample_cells, n_active // cores))
+        v_all, n_all, t_all = time_oracle(cfg, cpc, cores, 5, 30.0)
+        v_one, n_one, t_one = time_oracle(cfg, cpc, 1, 3, 15.0)
+        out["workloads"].append({"workload": cfg["name"], "n_active": n_active,
+                                 "all_cores": {"cores": cores, "cells": n_all, "value": v_all,
+                                               "step_s": statistics.median(t_all)},
+                                 "one_core": {"cores": 1, "cells": n_one, "value": v_one,
+                                              "step_s": statistics.median(t_one)}})
+        print(json.dumps(out["workloads"][-1]), flush=True)
+    print(json.dumps(out), flush=True)
 
 
 def main():
@@ -835,6 +951,8 @@ def main():
         run_accuracy(args, local)
     elif args.config == "spheres":
         run_spheres(args, local)
+    elif args.config == "oracle":
+        run_oracle_timing(args)
     else:
         run_ours(args, rank, world, local)
 

@@ -247,7 +247,12 @@ uf_status uf_kappa_gradient(uf_operator *op, double *dk, const double *r, const 
  *    capture;
  *  - every call on a device shares the one array and leaves its contents behind: calls whose
  *    kernels overlap on the GPU (different streams, or different operators on one device) race
- *    and must be serialised by the caller.
+ *    and must be serialised by the caller;
+ *  - for a UF_CG operator the call also gathers r and x into the operator's own cell-local work
+ *    vectors, which uf_vmult, uf_vmult_adjoint, uf_kappa_gradient and uf_solve use too: on one
+ *    CG operator it must not overlap any of those calls;
+ *  - the cached address belongs to the device's current context: after cudaDeviceReset (or a
+ *    reset of the primary context) the entry point must not be called again in that process.
  * The call itself performs no cudaMalloc / cudaFree; the operator was allocated at creation. */
 uf_status uf_kappa_gradient_noalloc(uf_operator *op, double *dk, const double *r,
                                     const double *x, void *stream);
@@ -272,6 +277,20 @@ uf_status uf_set_kappa(uf_operator *op, const double *kappa_host);
  *   increasing order) and physical weights; *count = 0 unless the face is a cut face.
  * Errors: UF_EINVAL (index out of range, NULL count). */
 uf_status uf_export_cells(const uf_operator *op, int32_t *type, int32_t *index);
+/* Per cut cell c (active order), host arrays [n_cut], any may be NULL: volume points, volume
+ * lines (points of the dimension-reduction rule that share all but one coordinate), cut-face
+ * lines, and the lanes of the cell's class in the FP64 cut-cell kernel (32, 16 or 8; the FP32
+ * kernel runs the 16-lane class with 32 lanes).  Errors: UF_EINVAL (NULL op).  (Not in the
+ * paper: lets tests pick cells by the kernel's work decomposition.) */
+uf_status uf_export_cut_cell_counts(const uf_operator *op, int32_t *vol_points, int32_t *vol_lines,
+                                    int32_t *face_lines, int32_t *lanes);
+/* The volume lines of cut cell c in the order the cut-cell kernel walks them: by line axis, and
+ * within an axis in contiguous groups of lines that share one outer coordinate.  axis[count],
+ * group_start[count] (1 for the first line of a group), points[count] (volume points on the
+ * line); group_start and points may be NULL.  Call with axis == NULL to get *count first.
+ * Errors: UF_EINVAL (index out of range, NULL count). */
+uf_status uf_export_cut_cell_lines(const uf_operator *op, int64_t c, int32_t *axis,
+                                   int32_t *group_start, int32_t *points, int64_t *count);
 uf_status uf_export_cut_cell_rule(const uf_operator *op, int64_t c, int kind, double *xi,
                                   double *w, double *normal, int64_t *count);
 uf_status uf_export_cut_face_rule(const uf_operator *op, int64_t e, int axis, int side,

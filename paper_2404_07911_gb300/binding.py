@@ -92,6 +92,7 @@ EXPORTED = ["uf_create_unfitted_operator", "uf_get_info", "uf_vmult", "uf_vmult_
             "uf_vmult_host", "uf_vmult_adjoint_host", "uf_vmult_host_async",
             "uf_vmult_adjoint_host_async", "uf_host_wait", "uf_profile_begin", "uf_profile_end",
             "uf_set_kappa", "uf_export_cells", "uf_export_cut_cell_rule",
+            "uf_export_cut_cell_counts", "uf_export_cut_cell_lines",
             "uf_export_cut_face_rule", "uf_assemble_csr", "uf_csr_info", "uf_csr_spmv",
             "uf_export_csr", "uf_release_csr", "uf_kappa_gradient", "uf_kappa_gradient_noalloc",
             "uf_set_kappa_device", "uf_export_cg", "uf_solve", "uf_manufactured_rhs", "uf_l2_error",
@@ -129,6 +130,8 @@ def load_library(path=None):
                                             ctypes.POINTER(ctypes.c_int64)]
     lib.uf_export_cut_face_rule.argtypes = [P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, P, P,
                                             ctypes.POINTER(ctypes.c_int64)]
+    lib.uf_export_cut_cell_counts.argtypes = [P, P, P, P, P]
+    lib.uf_export_cut_cell_lines.argtypes = [P, ctypes.c_int64, P, P, P, ctypes.POINTER(ctypes.c_int64)]
     lib.uf_assemble_csr.argtypes = [P, ctypes.c_int]
     lib.uf_csr_info.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
                                 ctypes.POINTER(ctypes.c_double)]
@@ -393,6 +396,22 @@ class UnfittedOperator:
         _check(_lib.uf_export_cut_cell_rule(self._h, c, kind, _ptr(xi), _ptr(w), _ptr(nrm),
                                             ctypes.byref(cnt)))
         return (xi, w, nrm) if kind == 1 else (xi, w)
+
+    def export_cut_cell_counts(self):
+        """Per cut cell (active order): volume points, volume lines, cut-face lines and the lanes
+        of its class in the FP64 cut-cell kernel, as int32 arrays [n_cut]."""
+        nc = self.info["n_cut"]
+        out = [np.zeros(nc, dtype=np.int32) for _ in range(4)]
+        _check(_lib.uf_export_cut_cell_counts(self._h, *[_ptr(a) for a in out]))
+        return tuple(out)
+
+    def export_cut_cell_lines(self, c):
+        """(axis, group_start, points) of cut cell c's volume lines in kernel order."""
+        cnt = ctypes.c_int64()
+        _check(_lib.uf_export_cut_cell_lines(self._h, c, None, None, None, ctypes.byref(cnt)))
+        out = [np.zeros(cnt.value, dtype=np.int32) for _ in range(3)]
+        _check(_lib.uf_export_cut_cell_lines(self._h, c, *[_ptr(a) for a in out], ctypes.byref(cnt)))
+        return tuple(out)
 
     def solve(self, b, x=None, mode="ir", tol=1e-10, inner_tol=1e-4, max_iter=100000,
               max_outer=50, stream=None):

@@ -1311,6 +1311,46 @@ uf_status uf_export_cut_face_rule(const uf_operator *op, int64_t e, int axis, in
   return UF_OK;
 }
 
+uf_status uf_export_cut_cell_counts(const uf_operator *op, int32_t *vol_points, int32_t *vol_lines,
+                                    int32_t *face_lines, int32_t *lanes) {
+  if (!op) return fail(UF_EINVAL, "NULL argument");
+  const uf::HostOperator &H = op->host;
+  const int nf = 2 * H.dim;
+  for (int64_t c = 0; c < H.n_cut; ++c) {
+    if (vol_points) vol_points[c] = (int32_t)(H.vol_off[c + 1] - H.vol_off[c]);
+    if (vol_lines) vol_lines[c] = (int32_t)(H.vline_off[c + 1] - H.vline_off[c]);
+    if (face_lines) face_lines[c] = (int32_t)(H.fline_off[(c + 1) * nf] - H.fline_off[c * nf]);
+    if (lanes) lanes[c] = uf::cut_lanes_of_cell(H, c);
+  }
+  return UF_OK;
+}
+
+uf_status uf_export_cut_cell_lines(const uf_operator *op, int64_t c, int32_t *axis,
+                                   int32_t *group_start, int32_t *points, int64_t *count) {
+  if (!op || !count) return fail(UF_EINVAL, "NULL argument");
+  const uf::HostOperator &H = op->host;
+  if (c < 0 || c >= H.n_cut) return fail(UF_EINVAL, "index out of range");
+  *count = H.vline_off[c + 1] - H.vline_off[c];
+  if (!axis) return UF_OK;
+  // the order of the device arrays: lines sorted by axis, then contiguous groups per axis
+  std::vector<uf::QLine> ls(H.vol_lines.begin() + H.vline_off[c], H.vol_lines.begin() + H.vline_off[c + 1]);
+  std::stable_sort(ls.begin(), ls.end(), [](const uf::QLine &a, const uf::QLine &b) { return a.k < b.k; });
+  int64_t i = 0;
+  for (int k = 0; k < H.dim; ++k) {
+    std::vector<const uf::QLine *> lk;
+    for (const uf::QLine &ln : ls)
+      if (ln.k == k) lk.push_back(&ln);
+    std::vector<int> gstart;
+    group_lines(H, lk, gstart);
+    for (size_t j = 0; j < lk.size(); ++j, ++i) {
+      axis[i] = k;
+      if (group_start) group_start[i] = gstart[j] == (int)j ? 1 : 0;
+      if (points) points[i] = (int32_t)lk[j]->vcnt;
+    }
+  }
+  return UF_OK;
+}
+
 uf_status uf_export_cg(const uf_operator *op, int32_t *l2g, double *rhs, double *diag) {
   if (!op) return fail(UF_EINVAL, "NULL argument");
   const uf::HostOperator &H = op->host;
