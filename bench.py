@@ -162,9 +162,16 @@ def host_cpu():
     """(logical cores, CPU model string) of this host."""
     model = ""
     try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip().lower() == "model name":
+                model = line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
         for line in open("/proc/cpuinfo"):
             key = line.split(":")[0].strip().lower()
-            if key in ("model name", "cpu part", "hardware") and not model:
+            if key in ("model name", "cpu part") and not model:
                 model = line.split(":", 1)[1].strip()
     except OSError:
         pass

@@ -26,6 +26,7 @@
 #include <type_traits>
 
 #include "uf_device.h"
+#include "uf_struct_planes.cuh"
 
 namespace uf {
 
@@ -1313,7 +1314,12 @@ int launch_vmult_t(const DevArrays<T> &d0, const void *tables_struct, const void
   const int blocks = (ce - cb + CPB - 1) / CPB;
   const auto &tab = *reinterpret_cast<const StructTables<T, N> *>(tables_struct);
   if (ev) cudaEventRecord(static_cast<cudaEvent_t>(ev[0]), stream);
-  if (blocks > 0) {
+  bool planes = false;  // FP32, 3D, n <= 5, uniform kappa: one thread per z-plane of a cell
+  if constexpr (std::is_same<T, float>::value && DIM == 3 && N <= 5) planes = d.kappa_uniform != 0;
+  if (planes) {
+    if constexpr (std::is_same<T, float>::value && DIM == 3 && N <= 5)
+      launch_struct_planes<N>(tab, d, s, y, x, adjoint, stream, cb, ce);
+  } else if (blocks > 0) {
     const bool uni = d.kappa_uniform != 0;
     if (adjoint && uni)
       struct_kernel<T, DIM, N, true, true><<<blocks, threads, 0, stream>>>(tab, d, s, y, x, cb, ce);
