@@ -1315,7 +1315,9 @@ int launch_vmult_t(const DevArrays<T> &d0, const void *tables_struct, const void
   const auto &tab = *reinterpret_cast<const StructTables<T, N> *>(tables_struct);
   if (ev) cudaEventRecord(static_cast<cudaEvent_t>(ev[0]), stream);
   bool planes = false;  // FP32, 3D, n <= 5, uniform kappa: one thread per z-plane of a cell
-  if constexpr (std::is_same<T, float>::value && DIM == 3 && N <= 5) planes = d.kappa_uniform != 0;
+  if constexpr (std::is_same<T, float>::value && DIM == 3 && N <= 5)
+    planes = d.kappa_uniform != 0 &&
+             (N != 4 || ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) % 16 == 0));
   if (planes) {
     if constexpr (std::is_same<T, float>::value && DIM == 3 && N <= 5)
       launch_struct_planes<N>(tab, d, s, y, x, adjoint, stream, cb, ce);

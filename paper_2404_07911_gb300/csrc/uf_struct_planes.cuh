@@ -34,7 +34,9 @@ struct PlaneCfg {
   static constexpr int SC = (N == 4) ? ND + 4 : ND + 1;  // padded cell stride in shared memory
 };
 
-// n consecutive floats from p (16-byte or 8-byte vectors where n and the alignment allow).
+// n consecutive floats at p: one 16-byte access for n = 4 (every such p in the kernel is a multiple
+// of 4 floats past a 16-byte aligned base: shared arrays, and x / y, which the host checks), scalar
+// accesses otherwise.
 template <int N>
 __device__ __forceinline__ void ld_run(const float *p, float *o) {
   if constexpr (N == 4) {
@@ -43,10 +45,6 @@ __device__ __forceinline__ void ld_run(const float *p, float *o) {
     o[1] = v.y;
     o[2] = v.z;
     o[3] = v.w;
-  } else if constexpr (N == 2) {
-    const float2 v = *reinterpret_cast<const float2 *>(p);
-    o[0] = v.x;
-    o[1] = v.y;
   } else {
 #pragma unroll
     for (int m = 0; m < N; ++m) o[m] = p[m];
@@ -60,10 +58,6 @@ __device__ __forceinline__ void ldg_run(const float *p, float *o) {
     o[1] = v.y;
     o[2] = v.z;
     o[3] = v.w;
-  } else if constexpr (N == 2) {
-    const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
-    o[0] = v.x;
-    o[1] = v.y;
   } else {
 #pragma unroll
     for (int m = 0; m < N; ++m) o[m] = __ldg(p + m);
@@ -73,8 +67,6 @@ template <int N>
 __device__ __forceinline__ void st_run(float *p, const float *v) {
   if constexpr (N == 4) {
     *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
-  } else if constexpr (N == 2) {
-    *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
   } else {
 #pragma unroll
     for (int m = 0; m < N; ++m) p[m] = v[m];
@@ -371,7 +363,8 @@ __global__ void __launch_bounds__(PlaneCfg<N>::THREADS) struct_plane_kernel(
   for (int j = 0; j < N; ++j) st_run<N>(yp + j * N, S + j * N);
 }
 
-// Launch of the plane kernel on cells [cb, ce) (uniform kappa, 3D, FP32, n <= 5).
+// Launch of the plane kernel on cells [cb, ce) (uniform kappa, 3D, FP32, n <= 5; for n = 4, x and
+// y 16-byte aligned).
 template <int N>
 void launch_struct_planes(const StructTables<float, N> &tab, const DevArrays<float> &d,
                           const Scalars<float> &s, float *y, const float *x, bool adjoint,
