@@ -32,6 +32,11 @@ struct PlaneCfg {
   static constexpr int CPB = 4 * CPW;     // cells per CTA (4 warps)
   static constexpr int THREADS = 128;
   static constexpr int SC = (N == 4) ? ND + 4 : ND + 1;  // padded cell stride in shared memory
+  // registers capped for 6 CTAs (24 warps) per SM: the kernel waits on neighbour reads from L2,
+  // and 24 warps hide them better than 20 with the uncapped 96 registers (n = 4: 36 us against
+  // 39 us on the 64^3 Q3 workload; an asynchronous prefetch of the neighbour data into shared
+  // memory, which cuts residency to 4 CTAs, took 54 us)
+  static constexpr int MINB = 6;
 };
 
 // n consecutive floats at p: one 16-byte access for n = 4 (every such p in the kernel is a multiple
@@ -109,7 +114,7 @@ __device__ __forceinline__ void plane_couple(const StructTables<float, N> &tab, 
 }
 
 template <int N, bool ADJ>
-__global__ void __launch_bounds__(PlaneCfg<N>::THREADS) struct_plane_kernel(
+__global__ void __launch_bounds__(PlaneCfg<N>::THREADS, PlaneCfg<N>::MINB) struct_plane_kernel(
     const __grid_constant__ StructTables<float, N> tab, const DevArrays<float> d,
     const Scalars<float> sc, float *__restrict__ y, const float *__restrict__ x, int cell_begin,
     int cell_end) {
