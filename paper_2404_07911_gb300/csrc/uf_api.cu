@@ -493,6 +493,25 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
         for (int i = 0; i < n; ++i) fline_b[l * n + i] = v[i];
       }
   }
+  // FP64, per volume line: stiffness and mass integrals of the 1D basis over the line's points
+  std::vector<double> vline_km(pre ? (size_t)std::max<int64_t>(nvl, 1) * 2 * nn : 0, 0.0);
+  if (pre) {
+    double v[uf::kMaxN], dv[uf::kMaxN];
+    const double ih2 = 1.0 / (H.h * H.h);
+    for (int64_t l = 0; l < nvl; ++l) {
+      double *K = vline_km.data() + (size_t)l * 2 * nn, *M = K + nn;
+      for (int32_t p = vpt_off[l]; p < vpt_off[l + 1]; ++p) {
+        uf::lagrange_values(H.t, vpt_t[p], v, dv);
+        const double w = vpt_w[p] * ih2;
+        for (int i = 0; i < n; ++i)
+          for (int j = 0; j < n; ++j) {
+            K[i * n + j] += w * dv[i] * dv[j];
+            M[i * n + j] += w * v[i] * v[j];
+          }
+      }
+    }
+  }
+  const size_t o_vkm = pre ? L.take(sizeof(T) * vline_km.size()) : 0;
   const size_t o_vlb = pre ? L.take(sizeof(T) * vline_b.size()) : 0;
   const size_t o_vpb = pre ? L.take(sizeof(T) * vpt_b.size()) : 0;
   const size_t o_spb = pre ? L.take(sizeof(T) * spt_b.size()) : 0;
@@ -545,6 +564,7 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   put_t(o_lselfxT, lselfxT);
   put_t(o_lnbgpxT, lnbgpxT);
   if (pre) {
+    put_t(o_vkm, vline_km);
     put_t(o_vlb, vline_b);
     put_t(o_vpb, vpt_b);
     put_t(o_spb, spt_b);
@@ -645,6 +665,7 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   A.lnbgpx = TP(o_lnbgpx);
   A.lselfxT = TP(o_lselfxT);
   A.lnbgpxT = TP(o_lnbgpxT);
+  A.vline_km = pre ? TP(o_vkm) : nullptr;
   A.vline_b = pre ? TP(o_vlb) : nullptr;
   A.vpt_b = pre ? TP(o_vpb) : nullptr;
   A.spt_b = pre ? TP(o_spb) : nullptr;
@@ -989,7 +1010,8 @@ uf_status uf_get_info(const uf_operator *op, uf_info *info) {
     kb[0] = 2.0 * S * (double)info->n_dofs + (double)H.n_active * (4.0 * nf + 4.0 + S);
     kb[1] = 3.0 * S * (double)H.n_cut * H.ndof +
             (double)H.n_cut * (4.0 * 2 + 4.0 * 4 + 4.0 * 3 * nf + S) +
-            S * (2.0 * info->n_vol_points + (2.0 + d) * info->n_surf_points +
+            S * ((S == 8.0 ? 2.0 * H.n * H.n * info->n_vol_lines : 2.0 * info->n_vol_points) +
+                 (2.0 + d) * info->n_surf_points +
                  2.0 * info->n_face_points) +
             vl * (2.0 * S + 8.0) + flh * (S + 4.0);
     (s == 0 ? info->bytes_fp64 : info->bytes_fp32) = kb[0] + kb[1];
@@ -1058,13 +1080,21 @@ uf_status uf_get_info(const uf_operator *op, uf_info *info) {
     if (d == 3) {
       // per group: contraction along the shared axis and expansion back (2 n^3 FMA each);
       // per line: its own outer axis, evaluation and integration (3 n^2 FMA each)
+      // per line: its own outer axis and the integration back (3 n^2 FMA each), and the
+      // line integrals of its volume points (3 n^2 FMA)
       fl += vgroups * (fb + 8 * n * n * n) + vlines * (fb + 12 * n * n);
-      fl += (double)info->n_vol_points * (fb + 2 * 3 * n + 4 + 2 * 3 * n);
+      if (tables)
+        fl += vlines * 6 * n * n;
+      else
+        fl += (double)info->n_vol_points * (fb + 2 * 3 * n + 4 + 2 * 3 * n);
       fl += (double)info->n_surf_points * (fb + 2 * 4 * n + 16 + 2 * 3 * n + 6);
       fl += flines * (fbv + 2 * 2 * n * n + 2 * 2 * n * n);
     } else {
       fl += vlines * (fb + 2 * 2 * n * n + 2 * 2 * n * n);
-      fl += (double)info->n_vol_points * (fb + 2 * 2 * n + 3 + 2 * 2 * n);
+      if (tables)
+        fl += vlines * 2 * 2 * n * n;
+      else
+        fl += (double)info->n_vol_points * (fb + 2 * 2 * n + 3 + 2 * 2 * n);
       fl += (double)info->n_surf_points * (fb + 2 * 3 * n + 12 + 2 * 2 * n + 4);
       fl += flines * (2 * 2 * n);
     }

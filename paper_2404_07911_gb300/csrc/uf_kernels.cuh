@@ -628,6 +628,81 @@ __device__ __forceinline__ void point_basis(const PointTables<T, N> &pt, const T
   }
 }
 
+// The volume points of a line enter only through the line integrals K, M (FP64: read from the
+// precomputed vline_km, which takes 3 n^2 FMA per line instead of 6 n per point on the FP64 pipe),
+// or point by point with the 1D basis evaluated in registers (FP32: the latency-bound FP32 kernel
+// measured faster without the extra table reads).
+template <typename T>
+constexpr bool kLineIntegrals = sizeof(T) == sizeof(double);
+
+// z += cf w_p (phi'(t_p) phi'(t_p)^T w0, phi phi^T w1, phi phi^T w2) over the line's points.
+template <typename T, int N>
+__device__ __forceinline__ void point_integrals(const PointTables<T, N> &pt, const DevArrays<T> &d,
+                                                T cfv, int line, const T *w0, const T *w1,
+                                                const T *w2, T *z0, T *z1, T *z2, bool third) {
+#pragma unroll
+  for (int m = 0; m < N; ++m) {
+    z0[m] = T(0);
+    z1[m] = T(0);
+    z2[m] = T(0);
+  }
+  const int pb = __ldg(d.vpt_off + line), pe = __ldg(d.vpt_off + line + 1);
+#pragma unroll 1
+  for (int p = pb; p < pe; ++p) {
+    T cv[N], cd[N];
+    point_basis<T, N>(pt, d.vpt_b, d.vpt_t, p, cv, cd);
+    T gk = T(0), gb = T(0), gc = T(0);
+#pragma unroll
+    for (int m = 0; m < N; ++m) {
+      gk = fma(cd[m], w0[m], gk);
+      gb = fma(cv[m], w1[m], gb);
+      if (third) gc = fma(cv[m], w2[m], gc);
+    }
+    // kappa int grad v . grad u: reference gradients carry 1/h each
+    const T cf = cfv * __ldg(d.vpt_w + p);
+    gk *= cf;
+    gb *= cf;
+    gc *= cf;
+#pragma unroll
+    for (int m = 0; m < N; ++m) {
+      z0[m] = fma(gk, cd[m], z0[m]);
+      z1[m] = fma(gb, cv[m], z1[m]);
+      if (third) z2[m] = fma(gc, cv[m], z2[m]);
+    }
+  }
+}
+
+// z0 = kappa K w0, z1 = kappa M w1 (and z2 = kappa M w2 when `third`) with the n x n line
+// integrals K, M stored one after the other at km (rows start on multiples of n elements).
+template <typename T, int N>
+__device__ __forceinline__ void line_products(const T *km, T kap, const T *w0, const T *w1,
+                                              const T *w2, T *z0, T *z1, T *z2, bool third) {
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+    T kr[N], mr[N];
+    load_row<T, N>(km + r * N, kr);
+    load_row<T, N>(km + N * N + r * N, mr);
+    T a0 = T(0), a1 = T(0), a2 = T(0);
+#pragma unroll
+    for (int m = 0; m < N; ++m) {
+      a0 = fma(kr[m], w0[m], a0);
+      a1 = fma(mr[m], w1[m], a1);
+      if (third) a2 = fma(mr[m], w2[m], a2);
+    }
+    z0[r] = a0;
+    z1[r] = a1;
+    z2[r] = a2;
+  }
+  if (kap != T(1)) {
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+      z0[r] *= kap;
+      z1[r] *= kap;
+      z2[r] *= kap;
+    }
+  }
+}
+
 // The cut-cell kernel runs one warp per CTA; each cut cell is handled by a group of S lanes
 // (S = 32, 16 or 8: the CTA then holds 32 / S cells), and S lines form a chunk.  A chunk of the
 // 3D volume part holds at most cut_gmax line groups (it ends early at the next group start once
@@ -807,36 +882,43 @@ __device__ __forceinline__ void cut_volume_3d(const PointTables<T, N> &pt, const
           w1[m] = a1;
           w2[m] = a2;
         }
+        // kappa int grad v . grad u over the line's volume points: with the line's integrals
+        // K_l (derivatives along the line) and M_l (values), z0 = kappa K_l w0, z1 = kappa M_l w1,
+        // z2 = kappa M_l w2 (both carry h^{-2}: a reference gradient has 1/h per factor)
         T z0[N], z1[N], z2[N];
-#pragma unroll
-        for (int m = 0; m < N; ++m) {
-          z0[m] = T(0);
-          z1[m] = T(0);
-          z2[m] = T(0);
-        }
-        const int pb = __ldg(d.vpt_off + line), pe = __ldg(d.vpt_off + line + 1);
-        const T cfv = kap * sc.inv_h2;
-#pragma unroll 1
-        for (int p = pb; p < pe; ++p) {
-          T cv[N], cd[N];
-          point_basis<T, N>(pt, d.vpt_b, d.vpt_t, p, cv, cd);
-          T gk = T(0), gb = T(0), gc = T(0);
+        if constexpr (kLineIntegrals<T>) {
+          line_products<T, N>(d.vline_km + (size_t)line * 2 * N * N, kap, w0, w1, w2, z0, z1, z2, true);
+        } else {
 #pragma unroll
           for (int m = 0; m < N; ++m) {
-            gk = fma(cd[m], w0[m], gk);
-            gb = fma(cv[m], w1[m], gb);
-            gc = fma(cv[m], w2[m], gc);
+            z0[m] = T(0);
+            z1[m] = T(0);
+            z2[m] = T(0);
           }
-          // kappa int grad v . grad u: reference gradients carry 1/h each
-          const T cf = cfv * __ldg(d.vpt_w + p);
-          gk *= cf;
-          gb *= cf;
-          gc *= cf;
+          const int pb = __ldg(d.vpt_off + line), pe = __ldg(d.vpt_off + line + 1);
+          const T cfv = kap * sc.inv_h2;
+#pragma unroll 1
+          for (int p = pb; p < pe; ++p) {
+            T cv[N], cd[N];
+            point_basis<T, N>(pt, d.vpt_b, d.vpt_t, p, cv, cd);
+            T gk = T(0), gb = T(0), gc = T(0);
 #pragma unroll
-          for (int m = 0; m < N; ++m) {
-            z0[m] = fma(gk, cd[m], z0[m]);
-            z1[m] = fma(gb, cv[m], z1[m]);
-            z2[m] = fma(gc, cv[m], z2[m]);
+            for (int m = 0; m < N; ++m) {
+              gk = fma(cd[m], w0[m], gk);
+              gb = fma(cv[m], w1[m], gb);
+              gc = fma(cv[m], w2[m], gc);
+            }
+            // kappa int grad v . grad u: reference gradients carry 1/h each
+            const T cf = cfv * __ldg(d.vpt_w + p);
+            gk *= cf;
+            gb *= cf;
+            gc *= cf;
+#pragma unroll
+            for (int m = 0; m < N; ++m) {
+              z0[m] = fma(gk, cd[m], z0[m]);
+              z1[m] = fma(gb, cv[m], z1[m]);
+              z2[m] = fma(gc, cv[m], z2[m]);
+            }
           }
         }
         const int sp = __ldg(d.lsurf + line);
@@ -1011,37 +1093,13 @@ __global__ void __launch_bounds__(32) cut_kernel(const __grid_constant__ PointTa
               }
             }
           }
+          // volume points of the line through its integrals K_l, M_l (see cut_volume_3d)
           T z0[N], z1[N], z2[N];
-  #pragma unroll
-          for (int m = 0; m < N; ++m) {
-            z0[m] = T(0);
-            z1[m] = T(0);
-            z2[m] = T(0);
-          }
-          const int pb = __ldg(d.vpt_off + line), pe = __ldg(d.vpt_off + line + 1);
-          const T cfv = kap * sc.inv_h2;
-  #pragma unroll 1
-          for (int p = pb; p < pe; ++p) {
-            T cv[N], cd[N];
-            point_basis<T, N>(pt, d.vpt_b, d.vpt_t, p, cv, cd);
-            T gk = T(0), gb = T(0), gc = T(0);
-  #pragma unroll
-            for (int m = 0; m < N; ++m) {
-              gk = fma(cd[m], w0[m], gk);
-              gb = fma(cv[m], w1[m], gb);
-              if constexpr (DIM == 3) gc = fma(cv[m], w2[m], gc);
-            }
-            // kappa int grad v . grad u: reference gradients carry 1/h each
-            const T cf = cfv * __ldg(d.vpt_w + p);
-            gk *= cf;
-            gb *= cf;
-            gc *= cf;
-  #pragma unroll
-            for (int m = 0; m < N; ++m) {
-              z0[m] = fma(gk, cd[m], z0[m]);
-              z1[m] = fma(gb, cv[m], z1[m]);
-              if constexpr (DIM == 3) z2[m] = fma(gc, cv[m], z2[m]);
-            }
+          if constexpr (kLineIntegrals<T>) {
+            line_products<T, N>(d.vline_km + (size_t)line * 2 * N * N, kap, w0, w1, w2, z0, z1, z2,
+                                DIM == 3);
+          } else {
+            point_integrals<T, N>(pt, d, kap * sc.inv_h2, line, w0, w1, w2, z0, z1, z2, DIM == 3);
           }
           const int sp = __ldg(d.lsurf + line);
           if (sp >= 0) {
