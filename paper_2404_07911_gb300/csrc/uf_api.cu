@@ -283,8 +283,11 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
     cost[c] = (H.vol_off[c + 1] - H.vol_off[c]) + (H.surf_off[c + 1] - H.surf_off[c]) +
               (H.cface_off[(c + 1) * nf] - H.cface_off[c * nf]);
     lanes[c] = uf::cut_lanes_of_cell(H, c);
+#ifndef UF_F32_LANES16
+#define UF_F32_LANES16 0
+#endif
     // FP32: the 16-lane groups measured slower than full warps (the 8-lane ones faster)
-    if (sizeof(T) == sizeof(float) && lanes[c] == 16) lanes[c] = 32;
+    if (!UF_F32_LANES16 && sizeof(T) == sizeof(float) && lanes[c] == 16) lanes[c] = 32;
   }
   std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
     return lanes[a] != lanes[b] ? lanes[a] > lanes[b] : cost[a] > cost[b];
@@ -1245,10 +1248,11 @@ uf_status uf_profile_end(uf_operator *op, uf_kernel_times *out) {
         out->launches[slot.prec][kern][slot.adjoint] += 1;
         int64_t nk = 1;
         if (kern == 1) {
-          // one launch per non-empty lane class: [0, split0), [split0, split1), [split1, n_cut)
+          // FP64: one launch for all lane classes; FP32: one per non-empty class
           const int32_t *sp = slot.prec == 0 ? op->f64.arrays.cut_split : op->f32.arrays.cut_split;
           const int64_t nc = op->host.n_cut;
-          nk = (sp[0] > 0 ? 1 : 0) + (sp[1] > sp[0] ? 1 : 0) + (nc > sp[1] ? 1 : 0);
+          nk = slot.prec == 0 ? (nc > 0 ? 1 : 0)
+                              : (sp[0] > 0 ? 1 : 0) + (sp[1] > sp[0] ? 1 : 0) + (nc > sp[1] ? 1 : 0);
         } else if (op->host.n_active == 0) {
           nk = 0;
         }

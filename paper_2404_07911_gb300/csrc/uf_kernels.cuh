@@ -984,11 +984,12 @@ __device__ __forceinline__ void cut_volume_3d(const PointTables<T, N> &pt, const
   }
 }
 
+// The cut cells of one lane class handled by CTA `block` of that class (one warp; 32 / S cells).
 template <typename T, int DIM, int N, int S>
-__global__ void __launch_bounds__(32) cut_kernel(const __grid_constant__ PointTables<T, N> pt,
-                                                 const DevArrays<T> d, const Scalars<T> sc,
-                                                 T *__restrict__ y, const T *__restrict__ x,
-                                                 int slot_begin, int slot_end) {
+__device__ __forceinline__ void cut_cells(const PointTables<T, N> &pt, const DevArrays<T> &d,
+                                          const Scalars<T> &sc, T *__restrict__ y,
+                                          const T *__restrict__ x, int slot_begin, int slot_end,
+                                          int block) {
   using G = Geo<DIM, N>;
   using SM = CutSmem<T, DIM, N, S>;
   constexpr int ND = G::ND, NL = G::NL, NF = G::NF;
@@ -1014,7 +1015,7 @@ __global__ void __launch_bounds__(32) cut_kernel(const __grid_constant__ PointTa
   int *s_tag = reinterpret_cast<int *>(sm + SM::total) + SM::itag;
 
   const int tid = threadIdx.x - gshift;
-  const int slot = slot_begin + blockIdx.x * CPW + grp;  // cut_list range of this lane class
+  const int slot = slot_begin + block * CPW + grp;  // cut_list range of this lane class
   if (slot >= slot_end) return;  // a whole lane group leaves together
   const int e = __ldg(d.cut_list + slot);
   const int ci = __ldg(d.cut_idx + slot);
@@ -1332,23 +1333,83 @@ __global__ void __launch_bounds__(32) cut_kernel(const __grid_constant__ PointTa
   for (int i = tid; i < ND; i += CH) y[(size_t)e * ND + i] += s_acc[i];
 }
 
+// Cut cells of the lane classes in CLS (bit 0: 32 lanes, bit 1: 16, bit 2: 8) in one launch: the
+// first CTAs take the 32-lane class (one cell each, most expensive first), then the 16-lane class
+// (two cells per CTA), then the 8-lane class (four).  FP64 launches all classes together, so
+// that they fill each other's tails instead of ending in partial waves (the 64^3 Q3 ball: 0.377
+// -> 0.356 ms); FP32, whose kernel is latency-bound, keeps one launch per class (a kernel holding
+// every class's code measured 17 % slower there).
+template <typename T, int DIM, int N, int CLS>
+__global__ void __launch_bounds__(32) cut_kernel(const __grid_constant__ PointTables<T, N> pt,
+                                                 const DevArrays<T> d, const Scalars<T> sc,
+                                                 T *__restrict__ y, const T *__restrict__ x,
+                                                 int s0, int s1, int s2, int s3) {
+  int b = blockIdx.x;
+  if constexpr ((CLS & 1) != 0) {
+    const int b32 = s1 - s0;
+    if (b < b32) {
+      cut_cells<T, DIM, N, 32>(pt, d, sc, y, x, s0, s1, b);
+      return;
+    }
+    b -= b32;
+  }
+  if constexpr (N <= 5 && (CLS & 2) != 0) {
+    const int b16 = (s2 - s1 + 1) / 2;
+    if (b < b16) {
+      cut_cells<T, DIM, N, 16>(pt, d, sc, y, x, s1, s2, b);
+      return;
+    }
+    b -= b16;
+  }
+  if constexpr (N <= 5 && (CLS & 4) != 0) cut_cells<T, DIM, N, 8>(pt, d, sc, y, x, s2, s3, b);
+}
+
+// Dynamic shared memory of a launch of the classes in CLS: the largest need among its non-empty
+// classes (sp: the slot bounds of the 32-, 16- and 8-lane classes).
+template <typename T, int DIM, int N, int CLS>
+size_t cut_smem_bytes(const int *sp) {
+  size_t m = ((CLS & 1) && sp[1] > sp[0]) ? CutSmem<T, DIM, N, 32>::stride : 0;
+  if constexpr (N <= 5) {
+    const size_t m16 = ((CLS & 2) && sp[2] > sp[1]) ? 2 * CutSmem<T, DIM, N, 16>::stride : 0;
+    const size_t m8 = ((CLS & 4) && sp[3] > sp[2]) ? 4 * CutSmem<T, DIM, N, 8>::stride : 0;
+    m = m16 > m ? m16 : m;
+    m = m8 > m ? m8 : m;
+  }
+  return m;
+}
+
 // ------------------------------------------------------------------------------------------
 // Launch
 // ------------------------------------------------------------------------------------------
-template <typename T, int DIM, int N, int S>
-int launch_cut(const PointTables<T, N> &ptab, const DevArrays<T> &d, const Scalars<T> &s, T *y,
-               const T *x, cudaStream_t stream, int begin, int end) {
-  if (end <= begin) return 0;
-  using SM = CutSmem<T, DIM, N, S>;
-  constexpr int CPW = 32 / S;
-  constexpr size_t smem = CPW * SM::stride;
+template <typename T, int DIM, int N, int CLS>
+int launch_cut_classes(const PointTables<T, N> &ptab, const DevArrays<T> &d, const Scalars<T> &s,
+                       T *y, const T *x, cudaStream_t stream, const int *sp) {
+  int blocks = 0;
+  if (CLS & 1) blocks += sp[1] - sp[0];
+  if (N <= 5 && (CLS & 2)) blocks += (sp[2] - sp[1] + 1) / 2;
+  if (N <= 5 && (CLS & 4)) blocks += (sp[3] - sp[2] + 3) / 4;
+  if (blocks <= 0) return 0;
+  const size_t smem = cut_smem_bytes<T, DIM, N, CLS>(sp);
   if (smem > 48 * 1024) {
-    const cudaError_t err = cudaFuncSetAttribute(cut_kernel<T, DIM, N, S>,
+    const cudaError_t err = cudaFuncSetAttribute(cut_kernel<T, DIM, N, CLS>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return (int)err;
   }
-  cut_kernel<T, DIM, N, S><<<(end - begin + CPW - 1) / CPW, 32, smem, stream>>>(ptab, d, s, y, x, begin, end);
+  cut_kernel<T, DIM, N, CLS><<<blocks, 32, smem, stream>>>(ptab, d, s, y, x, sp[0], sp[1], sp[2], sp[3]);
   return (int)cudaGetLastError();
+}
+
+template <typename T, int DIM, int N>
+int launch_cut(const PointTables<T, N> &ptab, const DevArrays<T> &d, const Scalars<T> &s, T *y,
+               const T *x, cudaStream_t stream, const int *sp) {
+  if constexpr (sizeof(T) == sizeof(double)) {
+    return launch_cut_classes<T, DIM, N, 7>(ptab, d, s, y, x, stream, sp);
+  } else {
+    int e = launch_cut_classes<T, DIM, N, 1>(ptab, d, s, y, x, stream, sp);
+    if (e == 0) e = launch_cut_classes<T, DIM, N, 2>(ptab, d, s, y, x, stream, sp);
+    if (e == 0) e = launch_cut_classes<T, DIM, N, 4>(ptab, d, s, y, x, stream, sp);
+    return e;
+  }
 }
 
 template <typename T, int DIM, int N>
@@ -1397,11 +1458,7 @@ int launch_vmult_t(const DevArrays<T> &d0, const void *tables_struct, const void
   if (sp[3] > sp[0]) {
     const auto &ptab = *reinterpret_cast<const PointTables<T, N> *>(tables_point);
     // the three lane classes are contiguous in cut_list (32, 16, 8 lanes per cell)
-    int e2 = launch_cut<T, DIM, N, 32>(ptab, d, s, y, x, stream, sp[0], sp[1]);
-    if constexpr (N <= 5) {
-      if (e2 == 0) e2 = launch_cut<T, DIM, N, 16>(ptab, d, s, y, x, stream, sp[1], sp[2]);
-      if (e2 == 0) e2 = launch_cut<T, DIM, N, 8>(ptab, d, s, y, x, stream, sp[2], sp[3]);
-    }
+    const int e2 = launch_cut<T, DIM, N>(ptab, d, s, y, x, stream, sp);
     if (e2 != 0) return e2;
   }
   if (ev) cudaEventRecord(static_cast<cudaEvent_t>(ev[3]), stream);
