@@ -201,6 +201,19 @@ uf_status uf_host_wait(uf_operator *op, void *stream);
 uf_status uf_profile_begin(uf_operator *op, int capacity);
 uf_status uf_profile_end(uf_operator *op, uf_kernel_times *out);
 
+/* The split FP32 operator, y = A x with FP32 device vectors x, y [n_dofs]: the rows of the cells
+ * that carry Nitsche or ghost-penalty terms (cut cells and cells with a ghost-penalty face; for
+ * UF_CG the cell-local rows before the sum over shared nodes) are evaluated with the FP64
+ * kernels on the FP32 input and rounded once to FP32, every other row with the FP32 kernels.
+ * It is the inner operator of UF_SOLVE_IR_SPLIT (paper Sec. 3.6 iterative solution; the split
+ * reads the task's precision pattern: FP64 only where the penalty terms of small cut fractions
+ * live).  This implementation runs the FP64 kernels on every cell and keeps the split rows, so
+ * it costs an FP32 plus an FP64 application.  The first call builds the cell list (a device
+ * allocation); the call uses the FP64 staging buffers of uf_vmult_host (UF_DG) or the FP64
+ * cell-local vectors (UF_CG), so no other call on the operator may overlap it.
+ * Errors: UF_EINVAL (missing precision, overlap), UF_ENODEVICE, UF_ENOMEM, UF_ECUDA. */
+uf_status uf_vmult_split(uf_operator *op, float *y, const float *x, void *stream);
+
 /* Assembled-matrix baseline (paper Sec. 3.1 / Sec. 5.1, matrix-based evaluation).
  * uf_assemble_csr builds the operator's matrix on the device in CSR form (int64 row offsets
  * [n_dofs + 1], int32 column indices, values in `precision`; columns ascending per row) by
@@ -313,7 +326,16 @@ uf_status uf_export_cg(const uf_operator *op, int32_t *l2g, double *rhs, double 
  *   UF_SOLVE_IR    iterative refinement: FP64 residual r = b - A x, FP32 PCG on A d = r / ||r||
  *                  to a relative reduction inner_tol, FP64 update x += ||r|| d, repeated until
  *                  the FP64 relative residual is <= tol (FP64 only for the outer residual and the
- *                  update; the FP32 operator carries the Nitsche and ghost-penalty terms).
+ *                  update; the FP32 operator carries the Nitsche and ghost-penalty terms);
+ *   UF_SOLVE_IR_SPLIT the same refinement with the split inner operator: the rows of the cells
+ *                  that carry Nitsche or ghost-penalty terms (cut cells and cells with a
+ *                  ghost-penalty face) are evaluated in FP64 from the FP32 input and rounded
+ *                  once to FP32, the other rows in FP32 (this implementation runs the FP64
+ *                  kernels on every cell and keeps those rows, so it costs more than an FP64
+ *                  operator application; it measures the effect of the split on the
+ *                  refinement).  It uses the FP64 staging buffers of uf_vmult_host (UF_DG) or
+ *                  the FP64 cell-local vectors (UF_CG), so no other call on the operator may
+ *                  overlap it.
  * x (in: initial guess, out: solution) and b are FP64 device vectors [n_dofs].  Synchronous on
  * return.  The dot products (deterministic two-pass FP64 reductions), alpha and beta stay in
  * device memory; the host reads the stopping state once per 32 iterations, so up to 31 operator
@@ -321,7 +343,7 @@ uf_status uf_export_cg(const uf_operator *op, int32_t *l2g, double *rhs, double 
  * (all inner iterations in IR mode), max_outer the refinement steps / restarts.
  * UF_CG: work vectors are allocated at creation; UF_DG: on the first call.  Errors: UF_EINVAL
  * (missing precision, bad parameters, breakdown), UF_ENOMEM, UF_ENODEVICE, UF_ECUDA. */
-enum { UF_SOLVE_FP64 = 0, UF_SOLVE_IR = 1 };
+enum { UF_SOLVE_FP64 = 0, UF_SOLVE_IR = 1, UF_SOLVE_IR_SPLIT = 2 };
 typedef struct {
   int mode;
   double tol;

@@ -86,7 +86,7 @@ class uf_solve_stats(ctypes.Structure):
                 ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
 
 
-UF_SOLVE_FP64, UF_SOLVE_IR = 0, 1
+UF_SOLVE_FP64, UF_SOLVE_IR, UF_SOLVE_IR_SPLIT = 0, 1, 2
 
 EXPORTED = ["uf_create_unfitted_operator", "uf_get_info", "uf_vmult", "uf_vmult_adjoint",
             "uf_vmult_host", "uf_vmult_adjoint_host", "uf_vmult_host_async",
@@ -95,7 +95,7 @@ EXPORTED = ["uf_create_unfitted_operator", "uf_get_info", "uf_vmult", "uf_vmult_
             "uf_export_cut_cell_counts", "uf_export_cut_cell_lines",
             "uf_export_cut_face_rule", "uf_assemble_csr", "uf_csr_info", "uf_csr_spmv",
             "uf_export_csr", "uf_release_csr", "uf_kappa_gradient", "uf_kappa_gradient_noalloc",
-            "uf_set_kappa_device", "uf_export_cg", "uf_solve", "uf_manufactured_rhs", "uf_l2_error",
+            "uf_set_kappa_device", "uf_vmult_split", "uf_export_cg", "uf_solve", "uf_manufactured_rhs", "uf_l2_error",
             "uf_destroy", "uf_last_error"]
 
 _lib = None
@@ -141,6 +141,7 @@ def load_library(path=None):
     lib.uf_kappa_gradient.argtypes = [P, P, P, P, P]
     lib.uf_kappa_gradient_noalloc.argtypes = [P, P, P, P, P]
     lib.uf_set_kappa_device.argtypes = [P, P, P]
+    lib.uf_vmult_split.argtypes = [P, P, P, P]
     lib.uf_export_cg.argtypes = [P, P, P, P]
     lib.uf_solve.argtypes = [P, ctypes.POINTER(uf_solve_params), P, P, ctypes.POINTER(uf_solve_stats), P]
     lib.uf_manufactured_rhs.argtypes = [P, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
@@ -273,6 +274,15 @@ class UnfittedOperator:
     def vmult(self, x, y=None, stream=None):
         """y = A x on the device (stream-ordered)."""
         return self._apply(_lib.uf_vmult, x, y, stream)
+
+    def vmult_split(self, x, y=None, stream=None):
+        """The split FP32 operator (rows of cut and ghost-penalty cells from the FP64 kernels,
+        rounded once); x float32 CUDA tensor."""
+        import torch
+
+        if x.dtype != torch.float32:
+            raise ValueError("x must be float32")
+        return self._apply(lambda h, prec, yp, xp, sp: _lib.uf_vmult_split(h, yp, xp, sp), x, y, stream)
 
     def vmult_adjoint(self, g, y=None, stream=None):
         """y = A^T g on the device (stream-ordered)."""
@@ -421,7 +431,10 @@ class UnfittedOperator:
 
         if x is None:
             x = torch.zeros_like(b)
-        prm = uf_solve_params(UF_SOLVE_IR if mode == "ir" else UF_SOLVE_FP64, tol, inner_tol,
+        modes = {"ir": UF_SOLVE_IR, "fp64": UF_SOLVE_FP64, "ir_split": UF_SOLVE_IR_SPLIT}
+        if mode not in modes:
+            raise ValueError("mode must be 'fp64', 'ir' or 'ir_split'")
+        prm = uf_solve_params(modes[mode], tol, inner_tol,
                               max_iter, max_outer)
         st = uf_solve_stats()
         _check(_lib.uf_solve(self._h, ctypes.byref(prm), ctypes.c_void_p(x.data_ptr()),

@@ -804,6 +804,59 @@ uf_status check_vmult_args(uf_operator *op, int precision, void *y, const void *
 
 }  // namespace
 
+namespace uf {
+__global__ void k_f32_to_f64(double *__restrict__ out, const float *__restrict__ in, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (double)in[i];
+}
+// y32 rows of the listed cells = the FP64 rows rounded once (one thread per DoF).
+__global__ void k_rows_to_f32(float *__restrict__ y32, const double *__restrict__ y64,
+                              const int32_t *__restrict__ cells, int64_t n_cells, int nd) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_cells * nd) return;
+  const int64_t r = (int64_t)cells[i / nd] * nd + i % nd;
+  y32[r] = (float)y64[r];
+}
+}  // namespace uf
+
+uf_status uf::vmult_split(uf_operator *op, float *y, const float *x, cudaStream_t s) {
+  PrecisionData<float> &p32 = op->f32;
+  PrecisionData<double> &p64 = op->f64;
+  if (!p32.present || !p64.present) return fail(UF_EINVAL, "the split operator needs FP32 and FP64");
+  const CgSolveData &w = op->cgs;
+  const bool cg = op->host.cg;
+  const int64_t n_loc = op->host.n_active * op->host.ndof;
+  DeviceGuard guard(op->device);
+  // cell-local input in both precisions (the FP64 copy is the FP32 input widened, exactly)
+  int err = 0;
+  if (cg) err = cg_gather<float>(p32.x_loc, x, p32.cg_l2g, n_loc, s);
+  const float *xl32 = cg ? p32.x_loc : x;
+  float *yl32 = cg ? p32.y_loc : y;
+  double *xl64 = cg ? p64.x_loc : static_cast<double *>(p64.xbuf);
+  double *yl64 = cg ? p64.y_loc : static_cast<double *>(p64.ybuf);
+  const unsigned blocks = (unsigned)((n_loc + 255) / 256);
+  if (err == 0 && n_loc > 0) {
+    k_f32_to_f64<<<blocks, 256, 0, s>>>(xl64, xl32, n_loc);
+    err = (int)cudaGetLastError();
+  }
+  if (err == 0)
+    err = launch_vmult<float>(op->host.dim, op->host.n, p32.arrays, p32.struct_tables.data(),
+                              p32.point_tables.data(), p32.scalars, yl32, xl32, false, s, nullptr);
+  if (err == 0 && w.n_split > 0) {
+    err = launch_vmult<double>(op->host.dim, op->host.n, p64.arrays, p64.struct_tables.data(),
+                               p64.point_tables.data(), p64.scalars, yl64, xl64, false, s, nullptr);
+    if (err == 0) {
+      const int64_t m = w.n_split * op->host.ndof;
+      k_rows_to_f32<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(yl32, yl64, w.split_cells, w.n_split,
+                                                                op->host.ndof);
+      err = (int)cudaGetLastError();
+    }
+  }
+  if (err == 0 && cg) err = cg_node_sum<float>(y, p32.y_loc, p32.cg_own_off, p32.cg_own_idx, op->host.n_cg, s);
+  if (err != 0) return fail(UF_ECUDA, std::string("kernel launch: ") + cudaGetErrorString((cudaError_t)err));
+  return UF_OK;
+}
+
 uf_status uf::vmult_launch(uf_operator *op, int precision, void *y, const void *x, void *stream,
                            bool adjoint) {
   if (precision == UF_FP64) return vmult_t<double>(op, op->f64, y, x, stream, adjoint);
@@ -1144,6 +1197,21 @@ uf_status uf_get_info(const uf_operator *op, uf_info *info) {
 
 uf_status uf_vmult(uf_operator *op, int precision, void *y, const void *x, void *stream) {
   return vmult_dispatch(op, precision, y, x, stream, false);
+}
+
+uf_status uf_vmult_split(uf_operator *op, float *y, const float *x, void *stream) {
+  uf_status st = check_vmult_args(op, UF_FP32, y, x);
+  if (st != UF_OK) return st;
+  if (!op->f32.present || !op->f64.present)
+    return fail(UF_EINVAL, "the split operator needs the FP32 and the FP64 operator");
+  const int64_t nvec = op->host.cg ? op->host.n_cg : op->host.n_active * op->host.ndof;
+  const char *xb = reinterpret_cast<const char *>(x), *yb = reinterpret_cast<const char *>(y);
+  const size_t bytes = sizeof(float) * (size_t)nvec;
+  if (xb < yb + bytes && yb < xb + bytes) return fail(UF_EINVAL, "x and y overlap");
+  DeviceGuard guard(op->device);
+  st = uf::split_cells_alloc(op);
+  if (st != UF_OK) return st;
+  return uf::vmult_split(op, y, x, reinterpret_cast<cudaStream_t>(stream));
 }
 
 uf_status uf_vmult_adjoint(uf_operator *op, int precision, void *y, const void *g, void *stream) {

@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "uf_operator.h"
@@ -582,6 +583,9 @@ struct SolveCtx {
   PcgScalars *sc_host;     // pinned host
 };
 
+// pcg's operator code for the split FP32 operator (rows of cut and ghost-penalty cells in FP64).
+constexpr int kSplitPrecision = 3;
+
 // Iterations enqueued between two reads of the stopping state.  The kernels of iterations
 // after the stop are no-ops except the operator's own, so at most kChunk - 1 vmults are spent
 // past convergence while the host never waits inside a chunk.
@@ -618,7 +622,13 @@ uf_status pcg(SolveCtx &c, int precision, const T *invd, T *x, T *r, T *z, T *p,
   for (int launched = 0;;) {
     const int chunk = started ? std::min(kChunk, maxit - launched) : 0;
     for (int i = 0; i < chunk; ++i) {
-      uf_status st = vmult_launch(c.op, precision, q, p, c.s, false);
+      uf_status st;
+      if constexpr (std::is_same<T, float>::value) {
+        st = precision == kSplitPrecision ? vmult_split(c.op, q, p, c.s)
+                                          : vmult_launch(c.op, precision, q, p, c.s, false);
+      } else {
+        st = vmult_launch(c.op, precision, q, p, c.s, false);
+      }
       if (st != UF_OK) return st;
       k_pcg_pq<T><<<kDotBlocks, kDotThreads, 0, c.s>>>(p, q, n, c.dot_part, c.sc);
       k_pcg_alpha<<<1, kDotThreads, 0, c.s>>>(c.dot_part, c.sc);
@@ -661,8 +671,9 @@ extern "C" uf_status uf_solve(uf_operator *op, const uf_solve_params *prm, doubl
     }
   }
   if (!op->cgs.ready) return fail(UF_EINVAL, "the solver's work vectors are missing");
-  if (prm->mode != UF_SOLVE_FP64 && prm->mode != UF_SOLVE_IR) return fail(UF_EINVAL, "bad solve mode");
-  if (prm->mode == UF_SOLVE_IR && !op->f32.present) return fail(UF_EINVAL, "IR needs the FP32 operator");
+  if (prm->mode != UF_SOLVE_FP64 && prm->mode != UF_SOLVE_IR && prm->mode != UF_SOLVE_IR_SPLIT)
+    return fail(UF_EINVAL, "bad solve mode");
+  if (prm->mode != UF_SOLVE_FP64 && !op->f32.present) return fail(UF_EINVAL, "IR needs the FP32 operator");
   if (!op->f64.present) return fail(UF_EINVAL, "uf_solve needs the FP64 operator");
   if (!(prm->tol > 0.0) || prm->max_iter < 1) return fail(UF_EINVAL, "bad tolerance or iteration cap");
   uf::DeviceGuard guard(op->device);
@@ -685,7 +696,12 @@ extern "C" uf_status uf_solve(uf_operator *op, const uf_solve_params *prm, doubl
     uf::k_residual<<<uf::nblk(n), 256, 0, s>>>(w.r64, b, w.q64, n);
     return UF_OK;
   };
-  const bool ir = prm->mode == UF_SOLVE_IR;
+  if (prm->mode == UF_SOLVE_IR_SPLIT) {
+    const uf_status s0 = uf::split_cells_alloc(op);
+    if (s0 != UF_OK) return s0;
+  }
+  const bool ir = prm->mode == UF_SOLVE_IR || prm->mode == UF_SOLVE_IR_SPLIT;
+  const int inner_op = prm->mode == UF_SOLVE_IR_SPLIT ? uf::kSplitPrecision : UF_FP32;
   int total_it = 0, outer = 0;
   double rel = 1.0;
   if (st == UF_OK && bnorm == 0.0) {
@@ -709,7 +725,7 @@ extern "C" uf_status uf_solve(uf_operator *op, const uf_solve_params *prm, doubl
       double rel_in = 1.0;
       if (ir) {
         uf::k_scale_to_f32<<<uf::nblk(n), 256, 0, s>>>(w.r32, w.r64, 1.0 / rn, n);
-        st = uf::pcg<float>(c, UF_FP32, w.invd32, w.d32, w.r32, w.z32, w.p32, w.q32,
+        st = uf::pcg<float>(c, inner_op, w.invd32, w.d32, w.r32, w.z32, w.p32, w.q32,
                             prm->inner_tol > 0.0 ? prm->inner_tol : 1e-4, prm->max_iter - total_it,
                             &its, &rel_in);
         if (st != UF_OK) break;
@@ -774,6 +790,28 @@ uf_status cg_alloc(uf_operator *op) {
   return cg_upload_diag(op);
 }
 
+uf_status split_cells_alloc(uf_operator *op) {
+  CgSolveData &w = op->cgs;
+  if (w.split_built) return UF_OK;
+  // the cells that carry Nitsche or ghost-penalty terms: cut, or with a ghost-penalty face
+  std::vector<int32_t> cells;
+  const int nf = 2 * op->host.dim;
+  for (int64_t e = 0; e < op->host.n_active; ++e) {
+    uint32_t gp = 0;
+    for (int f = 0; f < nf; ++f) gp |= op->host.flags[e] & face_bit_gp(f);
+    if ((op->host.flags[e] & 1u) || gp) cells.push_back((int32_t)e);
+  }
+  if (!cells.empty()) {
+    cudaError_t err = cudaMalloc((void **)&w.split_cells, cells.size() * sizeof(int32_t));
+    if (err == cudaSuccess)
+      err = cudaMemcpy(w.split_cells, cells.data(), cells.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (err != cudaSuccess) return fail(UF_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(err));
+  }
+  w.n_split = (int64_t)cells.size();
+  w.split_built = true;
+  return UF_OK;
+}
+
 uf_status cg_upload_diag(uf_operator *op) {
   CgSolveData &w = op->cgs;
   const int64_t n = solve_size(op->host);
@@ -794,7 +832,7 @@ uf_status cg_upload_diag(uf_operator *op) {
 void cg_free(uf_operator *op) {
   CgSolveData &w = op->cgs;
   void *ptrs[] = {w.r64, w.q64, w.d64, w.z64, w.p64, w.invd64, w.r32, w.q32, w.d32,
-                  w.z32, w.p32, w.invd32, w.dot_part, w.dot_out, w.sc};
+                  w.z32, w.p32, w.invd32, w.dot_part, w.dot_out, w.sc, w.split_cells};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (w.dot_host) cudaFreeHost(w.dot_host);

@@ -67,6 +67,11 @@ struct CgSolveData {
   float *invd32 = nullptr;
   double *dot_part = nullptr, *dot_out = nullptr, *dot_host = nullptr;
   PcgScalars *sc = nullptr, *sc_host = nullptr;  // device / pinned host copy
+  // cells whose rows the split FP32 operator evaluates in FP64 (cut cells and cells with a
+  // ghost-penalty face): the Nitsche and ghost-penalty terms live there
+  int32_t *split_cells = nullptr;
+  int64_t n_split = 0;
+  bool split_built = false;
 };
 
 struct ProfSlot {
@@ -124,6 +129,10 @@ inline int cut_lanes_of_cell(const HostOperator &H, int64_t c) {
   const int64_t fl = H.fline_off[(c + 1) * nf] - H.fline_off[c * nf];
   return cut_lanes_for(H.n, vl > fl ? vl : fl);
 }
+// FP32 y = A x with the rows of the split cells (CgSolveData::split_cells) evaluated in FP64 from
+// the FP32 input and rounded once: the inner operator of the split iterative refinement.
+uf_status vmult_split(uf_operator *op, float *y, const float *x, cudaStream_t stream);
+uf_status split_cells_alloc(uf_operator *op);  // builds CgSolveData::split_cells once
 // Launch y = A x (or A^T x) of the operator's kernels on `stream` (no argument checks).
 uf_status vmult_launch(uf_operator *op, int precision, void *y, const void *x, void *stream,
                        bool adjoint);

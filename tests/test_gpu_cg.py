@@ -84,7 +84,7 @@ def _node_coords(o):
     return X
 
 
-@pytest.mark.parametrize("mode", ["ir", "fp64"])
+@pytest.mark.parametrize("mode", ["ir", "fp64", "ir_split"])
 @pytest.mark.parametrize("key,q,tol_exact", [("2d_q3_10", 10, 1e-9), ("3d_q2_6", 8, 1e-6)])
 def test_cg_solvers(mode, key, q, tol_exact):
     cfg = _cg(dict(CASES[key], quad_order=q))
@@ -108,5 +108,44 @@ def test_cg_solvers(mode, key, q, tol_exact):
     dim = cfg["dim"]
     u_ex = (1.0 - np.sum((X - np.asarray(cfg["center"][:dim])) ** 2, axis=1)) / (2 * dim)
     assert np.max(np.abs(u - u_ex)) <= tol_exact * np.max(np.abs(u_ex))
-    if mode == "ir":
+    if mode != "fp64":
         assert stats["outer"] >= 2  # the FP32 inner solves alone cannot reach 1e-10
+
+
+def test_split_operator_rows():
+    """The split FP32 operator (inner operator of mode ir_split): on a discontinuous problem the
+    rows of cut cells and of cells with a ghost-penalty face (the active face neighbours of cut
+    cells) equal the FP64 operator applied to the FP32 input, rounded once, bit for bit, and every
+    other row equals the FP32 operator; on a continuous problem (node sums in FP32) the result
+    stays within FP32 accuracy of the FP64 operator."""
+    from paper_2404_07911_gb300 import UnfittedOperator
+
+    cfg = workloads.small(p=2, N=6)
+    op = UnfittedOperator(cfg, device=0)
+    nd = op.info["dofs_per_cell"]
+    m = mesh.Mesh(mesh.problem_from_dict(cfg))
+    o = forms.Oracle(mesh.problem_from_dict(cfg))
+    cut = set(int(e) for e in np.nonzero(m.active_type == mesh.CUT)[0])
+    split = set(cut)
+    for e in cut:
+        split.update(nb for _, _, nb in o.faces_of(e))
+    split = np.array(sorted(split))
+    other = np.setdiff1d(np.arange(m.n_active), split)
+    assert len(split) > 0 and len(other) > 0
+    x32 = torch.from_numpy(workloads.uniform_vector(op.n_dofs, 3).astype(np.float32)).cuda()
+    ys = op.vmult_split(x32).cpu().numpy().reshape(-1, nd)
+    y32 = op.vmult(x32).cpu().numpy().reshape(-1, nd)
+    y64 = op.vmult(x32.double()).cpu().numpy().reshape(-1, nd)
+    assert np.array_equal(ys[split], y64[split].astype(np.float32))
+    assert np.array_equal(ys[other], y32[other])
+    op.close()
+
+    cfg = _cg(workloads.small(p=2, N=6))
+    op = UnfittedOperator(cfg, device=0)
+    x32 = torch.from_numpy(workloads.uniform_vector(op.n_dofs, 4).astype(np.float32)).cuda()
+    ys = op.vmult_split(x32).double().cpu().numpy()
+    y32 = op.vmult(x32).double().cpu().numpy()
+    y64 = op.vmult(x32.double()).cpu().numpy()
+    assert np.max(np.abs(ys - y64)) <= 1e-5 * np.max(np.abs(y64))
+    assert not np.array_equal(ys, y32)
+    op.close()
