@@ -205,14 +205,22 @@ uf_status uf_profile_end(uf_operator *op, uf_kernel_times *out);
  * that carry Nitsche or ghost-penalty terms (cut cells and cells with a ghost-penalty face; for
  * UF_CG the cell-local rows before the sum over shared nodes) are evaluated with the FP64
  * kernels on the FP32 input and rounded once to FP32, every other row with the FP32 kernels.
- * It is the inner operator of UF_SOLVE_IR_SPLIT (paper Sec. 3.6 iterative solution; the split
- * reads the task's precision pattern: FP64 only where the penalty terms of small cut fractions
- * live).  This implementation runs the FP64 kernels on every cell and keeps the split rows, so
- * it costs an FP32 plus an FP64 application.  The first call builds the cell list (a device
- * allocation); the call uses the FP64 staging buffers of uf_vmult_host (UF_DG) or the FP64
- * cell-local vectors (UF_CG), so no other call on the operator may overlap it.
+ * With uf_set_split_fraction only the cut cells below a volume fraction (and their face
+ * neighbours) are split.  It is the inner operator of UF_SOLVE_IR_SPLIT (paper Sec. 3.6
+ * iterative solution; FP64 only where the penalty terms of small cut fractions live).  The FP64 structured kernel runs on the list of split cells, the FP64 cut-cell kernel
+ * on every cut cell, and only the split cells and their face neighbours are widened to FP64.
+ * The first call builds the cell lists (a device allocation); the call uses the FP64 staging
+ * buffers of uf_vmult_host (UF_DG) or the FP64 cell-local vectors (UF_CG), so no other call on
+ * the operator may overlap it.
  * Errors: UF_EINVAL (missing precision, overlap), UF_ENODEVICE, UF_ENOMEM, UF_ECUDA. */
 uf_status uf_vmult_split(uf_operator *op, float *y, const float *x, void *stream);
+
+/* Which cut cells get FP64 rows in the split operator: those whose volume fraction
+ * |K cap Omega| / h^d is below `fraction`, with their active face neighbours (whose rows hold the
+ * ghost-penalty couplings to them); fraction >= 1 (the default) takes every cut cell.  The cell
+ * lists are rebuilt on the next split call.  Errors: UF_EINVAL (NULL op, fraction <= 0).  (Not
+ * in the paper: selects the "tiny cut fractions" of the split precision pattern.) */
+uf_status uf_set_split_fraction(uf_operator *op, double fraction);
 
 /* Assembled-matrix baseline (paper Sec. 3.1 / Sec. 5.1, matrix-based evaluation).
  * uf_assemble_csr builds the operator's matrix on the device in CSR form (int64 row offsets
@@ -330,12 +338,9 @@ uf_status uf_export_cg(const uf_operator *op, int32_t *l2g, double *rhs, double 
  *   UF_SOLVE_IR_SPLIT the same refinement with the split inner operator: the rows of the cells
  *                  that carry Nitsche or ghost-penalty terms (cut cells and cells with a
  *                  ghost-penalty face) are evaluated in FP64 from the FP32 input and rounded
- *                  once to FP32, the other rows in FP32 (this implementation runs the FP64
- *                  kernels on every cell and keeps those rows, so it costs more than an FP64
- *                  operator application; it measures the effect of the split on the
- *                  refinement).  It uses the FP64 staging buffers of uf_vmult_host (UF_DG) or
- *                  the FP64 cell-local vectors (UF_CG), so no other call on the operator may
- *                  overlap it.
+ *                  once to FP32, the other rows in FP32 (uf_vmult_split).  It uses the FP64
+ *                  staging buffers of uf_vmult_host (UF_DG) or the FP64 cell-local vectors
+ *                  (UF_CG), so no other call on the operator may overlap it.
  * x (in: initial guess, out: solution) and b are FP64 device vectors [n_dofs].  Synchronous on
  * return.  The dot products (deterministic two-pass FP64 reductions), alpha and beta stay in
  * device memory; the host reads the stopping state once per 32 iterations, so up to 31 operator

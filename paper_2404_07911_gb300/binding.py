@@ -95,7 +95,7 @@ EXPORTED = ["uf_create_unfitted_operator", "uf_get_info", "uf_vmult", "uf_vmult_
             "uf_export_cut_cell_counts", "uf_export_cut_cell_lines",
             "uf_export_cut_face_rule", "uf_assemble_csr", "uf_csr_info", "uf_csr_spmv",
             "uf_export_csr", "uf_release_csr", "uf_kappa_gradient", "uf_kappa_gradient_noalloc",
-            "uf_set_kappa_device", "uf_vmult_split", "uf_export_cg", "uf_solve", "uf_manufactured_rhs", "uf_l2_error",
+            "uf_set_kappa_device", "uf_vmult_split", "uf_set_split_fraction", "uf_export_cg", "uf_solve", "uf_manufactured_rhs", "uf_l2_error",
             "uf_destroy", "uf_last_error"]
 
 _lib = None
@@ -142,6 +142,7 @@ def load_library(path=None):
     lib.uf_kappa_gradient_noalloc.argtypes = [P, P, P, P, P]
     lib.uf_set_kappa_device.argtypes = [P, P, P]
     lib.uf_vmult_split.argtypes = [P, P, P, P]
+    lib.uf_set_split_fraction.argtypes = [P, ctypes.c_double]
     lib.uf_export_cg.argtypes = [P, P, P, P]
     lib.uf_solve.argtypes = [P, ctypes.POINTER(uf_solve_params), P, P, ctypes.POINTER(uf_solve_stats), P]
     lib.uf_manufactured_rhs.argtypes = [P, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
@@ -283,6 +284,11 @@ class UnfittedOperator:
         if x.dtype != torch.float32:
             raise ValueError("x must be float32")
         return self._apply(lambda h, prec, yp, xp, sp: _lib.uf_vmult_split(h, yp, xp, sp), x, y, stream)
+
+    def set_split_fraction(self, fraction):
+        """Cut cells below this volume fraction (and their face neighbours) get FP64 rows in the
+        split operator (>= 1: every cut cell)."""
+        _check(_lib.uf_set_split_fraction(self._h, float(fraction)))
 
     def vmult_adjoint(self, g, y=None, stream=None):
         """y = A^T g on the device (stream-ordered)."""

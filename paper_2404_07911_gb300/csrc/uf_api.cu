@@ -805,9 +805,13 @@ uf_status check_vmult_args(uf_operator *op, int precision, void *y, const void *
 }  // namespace
 
 namespace uf {
-__global__ void k_f32_to_f64(double *__restrict__ out, const float *__restrict__ in, int64_t n) {
+// out rows of the listed cells = in rows widened to FP64 (one thread per DoF).
+__global__ void k_rows_to_f64(double *__restrict__ out, const float *__restrict__ in,
+                              const int32_t *__restrict__ cells, int64_t n_cells, int nd) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = (double)in[i];
+  if (i >= n_cells * nd) return;
+  const int64_t r = (int64_t)cells[i / nd] * nd + i % nd;
+  out[r] = (double)in[r];
 }
 // y32 rows of the listed cells = the FP64 rows rounded once (one thread per DoF).
 __global__ void k_rows_to_f32(float *__restrict__ y32, const double *__restrict__ y64,
@@ -834,21 +838,34 @@ uf_status uf::vmult_split(uf_operator *op, float *y, const float *x, cudaStream_
   float *yl32 = cg ? p32.y_loc : y;
   double *xl64 = cg ? p64.x_loc : static_cast<double *>(p64.xbuf);
   double *yl64 = cg ? p64.y_loc : static_cast<double *>(p64.ybuf);
-  const unsigned blocks = (unsigned)((n_loc + 255) / 256);
-  if (err == 0 && n_loc > 0) {
-    k_f32_to_f64<<<blocks, 256, 0, s>>>(xl64, xl32, n_loc);
+  const int nd = op->host.ndof;
+  if (err == 0 && w.n_halo > 0) {
+    const int64_t m = w.n_halo * nd;
+    k_rows_to_f64<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(xl64, xl32, w.halo_cells, w.n_halo, nd);
     err = (int)cudaGetLastError();
   }
   if (err == 0)
     err = launch_vmult<float>(op->host.dim, op->host.n, p32.arrays, p32.struct_tables.data(),
                               p32.point_tables.data(), p32.scalars, yl32, xl32, false, s, nullptr);
   if (err == 0 && w.n_split > 0) {
-    err = launch_vmult<double>(op->host.dim, op->host.n, p64.arrays, p64.struct_tables.data(),
-                               p64.point_tables.data(), p64.scalars, yl64, xl64, false, s, nullptr);
+    // FP64 rows of the split cells only: the structured kernel on their list, the cut-cell
+    // kernel on the cut cells among them
+    const DevArrays<double> &a = p64.arrays;
+    LaunchRange rg{};
+    rg.cell_begin = 0;
+    rg.cell_end = (int32_t)w.n_split;
+    rg.cut_list = w.split_cut_list;
+    rg.cut_idx = w.split_cut_idx;
+    rg.split[0] = 0;
+    rg.split[1] = w.split_cut_class[0];
+    rg.split[2] = w.split_cut_class[1];
+    rg.split[3] = w.split_cut_class[2];
+    rg.cells = w.split_cells;
+    err = launch_vmult<double>(op->host.dim, op->host.n, a, p64.struct_tables.data(),
+                               p64.point_tables.data(), p64.scalars, yl64, xl64, false, s, nullptr, &rg);
     if (err == 0) {
-      const int64_t m = w.n_split * op->host.ndof;
-      k_rows_to_f32<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(yl32, yl64, w.split_cells, w.n_split,
-                                                                op->host.ndof);
+      const int64_t m = w.n_split * nd;
+      k_rows_to_f32<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(yl32, yl64, w.split_cells, w.n_split, nd);
       err = (int)cudaGetLastError();
     }
   }
@@ -1212,6 +1229,19 @@ uf_status uf_vmult_split(uf_operator *op, float *y, const float *x, void *stream
   st = uf::split_cells_alloc(op);
   if (st != UF_OK) return st;
   return uf::vmult_split(op, y, x, reinterpret_cast<cudaStream_t>(stream));
+}
+
+uf_status uf_set_split_fraction(uf_operator *op, double fraction) {
+  if (!op) return fail(UF_EINVAL, "NULL argument");
+  if (!(fraction > 0.0)) return fail(UF_EINVAL, "the split fraction must be positive");
+  if (fraction != op->split_fraction) {
+    if (op->device >= 0) {
+      DeviceGuard guard(op->device);
+      uf::split_cells_free(op);
+    }
+    op->split_fraction = fraction;
+  }
+  return UF_OK;
 }
 
 uf_status uf_vmult_adjoint(uf_operator *op, int precision, void *y, const void *g, void *stream) {

@@ -793,23 +793,74 @@ uf_status cg_alloc(uf_operator *op) {
 uf_status split_cells_alloc(uf_operator *op) {
   CgSolveData &w = op->cgs;
   if (w.split_built) return UF_OK;
-  // the cells that carry Nitsche or ghost-penalty terms: cut, or with a ghost-penalty face
-  std::vector<int32_t> cells;
-  const int nf = 2 * op->host.dim;
-  for (int64_t e = 0; e < op->host.n_active; ++e) {
-    uint32_t gp = 0;
-    for (int f = 0; f < nf; ++f) gp |= op->host.flags[e] & face_bit_gp(f);
-    if ((op->host.flags[e] & 1u) || gp) cells.push_back((int32_t)e);
+  const HostOperator &H = op->host;
+  const int nf = 2 * H.dim;
+  // T: the cut cells whose volume fraction |K cap Omega| / h^d is below the split fraction (all
+  // cut cells for a fraction >= 1); the split cells are T and their active face neighbours,
+  // whose rows hold the ghost-penalty couplings to T
+  const double theta = op->split_fraction, hd = std::pow(H.h, H.dim);
+  std::vector<char> in_split(H.n_active, 0), in_halo(H.n_active, 0);
+  for (int64_t c = 0; c < H.n_cut; ++c) {
+    double vol = 0.0;
+    for (int64_t p = H.vol_off[c]; p < H.vol_off[c + 1]; ++p) vol += H.vol_w[p];
+    if (theta < 1.0 && !(vol < theta * hd)) continue;
+    const int32_t e = H.cut_cells[c];
+    in_split[e] = 1;
+    for (int f = 0; f < nf; ++f) {
+      const int32_t nb = H.nbr[(size_t)e * nf + f];
+      if (nb >= 0) in_split[nb] = 1;
+    }
   }
-  if (!cells.empty()) {
-    cudaError_t err = cudaMalloc((void **)&w.split_cells, cells.size() * sizeof(int32_t));
+  std::vector<int32_t> cells, halo, scut[3], sidx[3];
+  for (int64_t e = 0; e < H.n_active; ++e)
+    if (in_split[e]) {
+      cells.push_back((int32_t)e);
+      in_halo[e] = 1;
+      for (int f = 0; f < nf; ++f) {
+        const int32_t nb = H.nbr[(size_t)e * nf + f];
+        if (nb >= 0) in_halo[nb] = 1;
+      }
+      const int32_t c = H.cut_of[e];
+      if (c >= 0) {
+        // the cut cells among the split cells, by lane class as in the full cut-cell list
+        const int l = cut_lanes_of_cell(H, c), k = l == 32 ? 0 : (l == 16 ? 1 : 2);
+        scut[k].push_back((int32_t)e);
+        sidx[k].push_back(c);
+      }
+    }
+  for (int64_t e = 0; e < H.n_active; ++e)
+    if (in_halo[e]) halo.push_back((int32_t)e);
+  std::vector<int32_t> all(cells);
+  all.insert(all.end(), halo.begin(), halo.end());
+  const size_t o_cut = all.size();
+  for (int k = 0; k < 3; ++k) all.insert(all.end(), scut[k].begin(), scut[k].end());
+  const size_t o_idx = all.size();
+  for (int k = 0; k < 3; ++k) all.insert(all.end(), sidx[k].begin(), sidx[k].end());
+  if (!all.empty()) {
+    cudaError_t err = cudaMalloc((void **)&w.split_cells, all.size() * sizeof(int32_t));
     if (err == cudaSuccess)
-      err = cudaMemcpy(w.split_cells, cells.data(), cells.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+      err = cudaMemcpy(w.split_cells, all.data(), all.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (err != cudaSuccess) return fail(UF_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(err));
   }
   w.n_split = (int64_t)cells.size();
+  w.halo_cells = w.split_cells + cells.size();
+  w.n_halo = (int64_t)halo.size();
+  w.split_cut_list = w.split_cells + o_cut;
+  w.split_cut_idx = w.split_cells + o_idx;
+  w.split_cut_class[0] = (int32_t)scut[0].size();
+  w.split_cut_class[1] = w.split_cut_class[0] + (int32_t)scut[1].size();
+  w.split_cut_class[2] = w.split_cut_class[1] + (int32_t)scut[2].size();
   w.split_built = true;
   return UF_OK;
+}
+
+void split_cells_free(uf_operator *op) {
+  CgSolveData &w = op->cgs;
+  if (w.split_cells) cudaFree(w.split_cells);
+  w.split_cells = w.halo_cells = w.split_cut_list = w.split_cut_idx = nullptr;
+  w.n_split = w.n_halo = 0;
+  w.split_cut_class[0] = w.split_cut_class[1] = w.split_cut_class[2] = 0;
+  w.split_built = false;
 }
 
 uf_status cg_upload_diag(uf_operator *op) {

@@ -137,6 +137,8 @@ struct LaunchRange {
   int32_t cell_begin, cell_end;
   const int32_t *cut_list, *cut_idx;
   int32_t split[4];
+  // when set (FP64 only): the structured kernel takes the cells cells[cell_begin .. cell_end)
+  const int32_t *cells;
 };
 
 // Launchers (uf_kernels_*.cu).  Return cudaError_t as int.

@@ -236,11 +236,13 @@ __device__ __forceinline__ void axis0_lines(const StructTables<T, N> &tab, const
   }
 }
 
-template <typename T, int DIM, int N, bool ADJ, bool UNI>
+// LIST: the cells are cell_list[cell_begin .. cell_end) instead of cell_begin .. cell_end.
+template <typename T, int DIM, int N, bool ADJ, bool UNI, bool LIST = false>
 __global__ void __launch_bounds__(struct_threads<T, DIM, N>()) struct_kernel(const __grid_constant__ StructTables<T, N> tab,
                                                      const DevArrays<T> d, const Scalars<T> sc,
                                                      T *__restrict__ y, const T *__restrict__ x,
-                                                     int cell_begin, int cell_end) {
+                                                     int cell_begin, int cell_end,
+                                                     const int32_t *__restrict__ cell_list = nullptr) {
   using G = Geo<DIM, N>;
   constexpr int ND = G::ND, NL = G::NL, NF = G::NF, NN = N * N;
   constexpr int CPB = struct_cells_per_block<T, DIM, N>();
@@ -260,16 +262,23 @@ __global__ void __launch_bounds__(struct_threads<T, DIM, N>()) struct_kernel(con
   const int c = tid / TPC;
   const int t = tid % TPC;
   const bool active_thread = (c < CPB);
-  const int e = first + c;
-  const bool has_cell = active_thread && (e < cell_end);
+  const bool has_cell = active_thread && (first + c < cell_end);
+  const int e = LIST ? (has_cell ? __ldg(cell_list + first + c) : 0) : first + c;
   constexpr bool uniform = UNI;  // kappa uniform (d.kappa_uniform != 0)
 
   {
     const int ncell = min(CPB, cell_end - first);
-    const T *src = x + (size_t)first * ND;
-    for (int i = tid; i < ncell * ND; i += blockDim.x) {
-      const int l = i % ND;
-      s_u[i / ND][l + (P - N) * (l / N)] = src[i];
+    if constexpr (LIST) {
+      for (int i = tid; i < ncell * ND; i += blockDim.x) {
+        const int l = i % ND;
+        s_u[i / ND][l + (P - N) * (l / N)] = x[(size_t)__ldg(cell_list + first + i / ND) * ND + l];
+      }
+    } else {
+      const T *src = x + (size_t)first * ND;
+      for (int i = tid; i < ncell * ND; i += blockDim.x) {
+        const int l = i % ND;
+        s_u[i / ND][l + (P - N) * (l / N)] = src[i];
+      }
     }
   }
 
@@ -1435,9 +1444,21 @@ int launch_vmult_t(const DevArrays<T> &d0, const void *tables_struct, const void
   if (ev) cudaEventRecord(static_cast<cudaEvent_t>(ev[0]), stream);
   bool planes = false;  // FP32, 3D, n <= 5, uniform kappa: one thread per z-plane of a cell
   if constexpr (std::is_same<T, float>::value && DIM == 3 && N <= 5)
-    planes = d.kappa_uniform != 0 &&
+    planes = d.kappa_uniform != 0 && !(rg && rg->cells) &&
              (N != 4 || ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) % 16 == 0));
-  if (planes) {
+  if (rg && rg->cells) {
+    // a list of cells (FP64, y = A x rows of those cells)
+    if constexpr (sizeof(T) == sizeof(double)) {
+      if (blocks > 0) {
+        if (d.kappa_uniform != 0)
+          struct_kernel<T, DIM, N, false, true, true><<<blocks, threads, 0, stream>>>(tab, d, s, y, x, cb, ce, rg->cells);
+        else
+          struct_kernel<T, DIM, N, false, false, true><<<blocks, threads, 0, stream>>>(tab, d, s, y, x, cb, ce, rg->cells);
+      }
+    } else {
+      return (int)cudaErrorInvalidValue;
+    }
+  } else if (planes) {
     if constexpr (std::is_same<T, float>::value && DIM == 3 && N <= 5)
       launch_struct_planes<N>(tab, d, s, y, x, adjoint, stream, cb, ce);
   } else if (blocks > 0) {

@@ -71,6 +71,13 @@ struct CgSolveData {
   // ghost-penalty face): the Nitsche and ghost-penalty terms live there
   int32_t *split_cells = nullptr;
   int64_t n_split = 0;
+  // the split cells and their active face neighbours (the FP64 kernels read those cells' input)
+  int32_t *halo_cells = nullptr;
+  int64_t n_halo = 0;
+  // the cut cells among the split cells (active ids, cut indices), sorted by lane class; class
+  // ends [32 lanes, 16 lanes, 8 lanes]
+  int32_t *split_cut_list = nullptr, *split_cut_idx = nullptr;
+  int32_t split_cut_class[3] = {0, 0, 0};
   bool split_built = false;
 };
 
@@ -114,6 +121,7 @@ struct uf_operator {
   size_t prof_next = 0;
   uf::CsrData csr64, csr32;
   uf::CgSolveData cgs;           // continuous operators: solver work vectors
+  double split_fraction = 1.0;   // cut cells below this volume fraction get FP64 split rows
   cudaStream_t pipe_in = nullptr, pipe_out = nullptr;  // copy streams of the host-buffer path
   std::vector<cudaStream_t> pipe_run;                 // one kernel stream per part
   std::vector<cudaEvent_t> pipe_ev;                   // [start, per part: in, done]
@@ -133,6 +141,7 @@ inline int cut_lanes_of_cell(const HostOperator &H, int64_t c) {
 // the FP32 input and rounded once: the inner operator of the split iterative refinement.
 uf_status vmult_split(uf_operator *op, float *y, const float *x, cudaStream_t stream);
 uf_status split_cells_alloc(uf_operator *op);  // builds CgSolveData::split_cells once
+void split_cells_free(uf_operator *op);        // drops them (rebuilt on the next use)
 // Launch y = A x (or A^T x) of the operator's kernels on `stream` (no argument checks).
 uf_status vmult_launch(uf_operator *op, int precision, void *y, const void *x, void *stream,
                        bool adjoint);

@@ -138,6 +138,21 @@ def test_split_operator_rows():
     y64 = op.vmult(x32.double()).cpu().numpy().reshape(-1, nd)
     assert np.array_equal(ys[split], y64[split].astype(np.float32))
     assert np.array_equal(ys[other], y32[other])
+    # only the cut cells below a volume fraction of 0.25, with their face neighbours
+    h3 = op.info["h"] ** 3
+    cut_sorted = sorted(cut)
+    frac = np.array([op.export_cut_cell_rule(c, 0)[1].sum() / h3 for c in range(len(cut_sorted))])
+    tiny = [cut_sorted[c] for c in np.nonzero(frac < 0.25)[0]]
+    sub = set(tiny)
+    for e in tiny:
+        sub.update(nb for _, _, nb in o.faces_of(e))
+    sub = np.array(sorted(sub))
+    assert 0 < len(sub) < len(split)
+    op.set_split_fraction(0.25)
+    ys = op.vmult_split(x32).cpu().numpy().reshape(-1, nd)
+    rest = np.setdiff1d(np.arange(m.n_active), sub)
+    assert np.array_equal(ys[sub], y64[sub].astype(np.float32))
+    assert np.array_equal(ys[rest], y32[rest])
     op.close()
 
     cfg = _cg(workloads.small(p=2, N=6))
