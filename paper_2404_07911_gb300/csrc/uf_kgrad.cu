@@ -81,7 +81,9 @@ __device__ __forceinline__ void mass_sweep(const double *M, const double *src, d
 
 template <int DIM, int N>
 __global__ void __launch_bounds__(128) kgrad_struct_kernel(const double *__restrict__ kg,
+                                                           const __grid_constant__ StructTables<double, N> tab,
                                                            const DevArrays<double> d,
+                                                           const Scalars<double> sc,
                                                            double *__restrict__ S,
                                                            const double *__restrict__ r,
                                                            const double *__restrict__ x) {
@@ -163,10 +165,29 @@ __global__ void __launch_bounds__(128) kgrad_struct_kernel(const double *__restr
         const double *xn = x + (size_t)nb * ND + base;
 #pragma unroll
         for (int m = 0; m < N; ++m) un[m] = __ldg(xn + m * st);
-        const int fi = face_index(full, gp, s);
-        p[0] += dot_apply<N>(kg + (kKnb + fi) * NN, un, rt);
-        p[1 + f] += dot_apply<N>(kg + (kNself + fi) * NN, u, rt) +
-                    dot_apply<N>(kg + (kNnb + fi) * NN, un, rt);
+        if (gp) {
+          const int fi = face_index(full, gp, s);
+          p[0] += dot_apply<N>(kg + (kKnb + fi) * NN, un, rt);
+          p[1 + f] += dot_apply<N>(kg + (kNself + fi) * NN, u, rt) +
+                      dot_apply<N>(kg + (kNnb + fi) * NN, un, rt);
+        } else {
+          // SIPG only: the couplings are rank 2 (Lobatto delta property, as in the operator).
+          // The neighbour's line enters through its face value alpha and the derivative
+          // beta = dnb . un; d/dkappa_e of the coupling is alpha dow - (1/2) hf_sigma alpha e_own,
+          // d/dkappa_nb of it is -(beta + (1/2) hf_sigma alpha) e_own, and the neighbour's share
+          // of the own-own penalty adds (1/2) hf_sigma u_own e_own
+          const double alpha = un[s ? 0 : N - 1];
+          const double rto = rt[s ? N - 1 : 0], uo = u[s ? N - 1 : 0];
+          double beta = 0.0, rdow = 0.0;
+#pragma unroll
+          for (int m = 0; m < N; ++m) {
+            beta = fma(tab.dnb[s][m], un[m], beta);
+            rdow = fma(tab.dowx[s][m], rt[m], rdow);
+          }
+          const double hs = 0.5 * sc.hf_sigma;
+          p[0] += alpha * (rdow - hs * rto);
+          p[1 + f] += rto * (hs * (uo - alpha) - beta);
+        }
       }
     }
 #pragma unroll
@@ -277,22 +298,28 @@ __device__ __forceinline__ void kgrad_volume_grouped(const PointTables<double, N
           wr[1][m] = b1;
           wr[2][m] = b2;
         }
-        const int pb = __ldg(d.vpt_off + line), pe = __ldg(d.vpt_off + line + 1);
-#pragma unroll 1
-        for (int p = pb; p < pe; ++p) {
-          double cv[N], cd[N];
-          point_basis<double, N>(pt, d.vpt_b, d.vpt_t, p, cv, cd);
-          double gx[3] = {0, 0, 0}, gr[3] = {0, 0, 0};
+        // the line's volume points through its integrals K_l, M_l (h^{-2} folded in):
+        // sum_p w_p grad r . grad x / h^2 = wr0 . K_l wx0 + wr1 . M_l wx1 + wr2 . M_l wx2
+        {
+          const double *km = d.vline_km + (size_t)line * 2 * N * N;
+          double acc = 0.0;
 #pragma unroll
-          for (int m = 0; m < N; ++m) {
-            gx[0] = fma(cd[m], wx[0][m], gx[0]);
-            gx[1] = fma(cv[m], wx[1][m], gx[1]);
-            gx[2] = fma(cv[m], wx[2][m], gx[2]);
-            gr[0] = fma(cd[m], wr[0][m], gr[0]);
-            gr[1] = fma(cv[m], wr[1][m], gr[1]);
-            gr[2] = fma(cv[m], wr[2][m], gr[2]);
+          for (int q = 0; q < N; ++q) {
+            double kr[N], mr[N];
+            load_row<double, N>(km + q * N, kr);
+            load_row<double, N>(km + N * N + q * N, mr);
+            double t0 = 0.0, t1 = 0.0;
+#pragma unroll
+            for (int m = 0; m < N; ++m) {
+              t0 = fma(kr[m], wx[0][m], t0);
+              t1 = fma(mr[m], wx[1][m], t1);
+            }
+            double t2 = 0.0;
+#pragma unroll
+            for (int m = 0; m < N; ++m) t2 = fma(mr[m], wx[2][m], t2);
+            acc = fma(wr[0][q], t0, fma(wr[1][q], t1, fma(wr[2][q], t2, acc)));
           }
-          p_self += __ldg(d.vpt_w + p) * sc.inv_h2 * (gx[0] * gr[0] + gx[1] * gr[1] + gx[2] * gr[2]);
+          p_self += acc;
         }
         const int sp = __ldg(d.lsurf + line);
         if (sp >= 0) {
@@ -586,9 +613,10 @@ __global__ void kgrad_gather_kernel(const DevArrays<double> d, const double *__r
 }
 
 template <int DIM, int N>
-int launch_kgrad_t(const double *kg, const DevArrays<double> &d, const void *tables_point,
-                   const Scalars<double> &s, double *S, double *dk, const double *r,
-                   const double *x, cudaStream_t stream) {
+int launch_kgrad_t(const double *kg, const DevArrays<double> &d, const void *tables_struct,
+                   const void *tables_point, const Scalars<double> &s, double *S, double *dk,
+                   const double *r, const double *x, cudaStream_t stream) {
+  const auto &tab = *reinterpret_cast<const StructTables<double, N> *>(tables_struct);
   using SM = KgSmem<DIM, N>;
   constexpr int CPB = SM::CPB;
   const int threads = ((CPB * Geo<DIM, N>::NL + 31) / 32) * 32;
@@ -599,7 +627,7 @@ int launch_kgrad_t(const double *kg, const DevArrays<double> &d, const void *tab
                                (int)SM::bytes);
     if (err != cudaSuccess) return (int)err;
   }
-  kgrad_struct_kernel<DIM, N><<<blocks, threads, SM::bytes, stream>>>(kg, d, S, r, x);
+  kgrad_struct_kernel<DIM, N><<<blocks, threads, SM::bytes, stream>>>(kg, tab, d, s, S, r, x);
   if (d.n_cut > 0) {
     const auto &ptab = *reinterpret_cast<const PointTables<double, N> *>(tables_point);
     kgrad_cut_kernel<DIM, N><<<d.n_cut, 32, 0, stream>>>(ptab, d, s, S, r, x);
@@ -608,11 +636,11 @@ int launch_kgrad_t(const double *kg, const DevArrays<double> &d, const void *tab
   return (int)cudaGetLastError();
 }
 
-int launch_kgrad(int dim, int n, const double *kg, const DevArrays<double> &d, const void *tp,
-                 const Scalars<double> &s, double *S, double *dk, const double *r, const double *x,
-                 cudaStream_t st) {
+int launch_kgrad(int dim, int n, const double *kg, const DevArrays<double> &d, const void *ts,
+                 const void *tp, const Scalars<double> &s, double *S, double *dk, const double *r,
+                 const double *x, cudaStream_t st) {
 #define UF_KCASE(D, NN) \
-  if (dim == D && n == NN) return launch_kgrad_t<D, NN>(kg, d, tp, s, S, dk, r, x, st);
+  if (dim == D && n == NN) return launch_kgrad_t<D, NN>(kg, d, ts, tp, s, S, dk, r, x, st);
   UF_KCASE(2, 2) UF_KCASE(2, 3) UF_KCASE(2, 4) UF_KCASE(2, 5) UF_KCASE(2, 6) UF_KCASE(2, 7)
   UF_KCASE(2, 8) UF_KCASE(2, 9) UF_KCASE(3, 2) UF_KCASE(3, 3) UF_KCASE(3, 4) UF_KCASE(3, 5)
   UF_KCASE(3, 6) UF_KCASE(3, 7) UF_KCASE(3, 8) UF_KCASE(3, 9)
@@ -719,7 +747,7 @@ uf_status uf_kappa_gradient_noalloc(uf_operator *op, double *dk, const double *r
   // Every slot the gather reads is written by the structured kernel of this call before any
   // other kernel reads or accumulates into it, so the buffer needs no clearing.
   int err = uf::launch_kgrad(op->host.dim, op->host.n, op->kg_tables, op->f64.arrays,
-                             op->f64.point_tables.data(), op->f64.scalars, partials, dk, rl, xl, cs);
+                             op->f64.struct_tables.data(), op->f64.point_tables.data(), op->f64.scalars, partials, dk, rl, xl, cs);
   if (err != 0)
     return fail(UF_ECUDA, std::string("kernel launch: ") + cudaGetErrorString((cudaError_t)err));
   return UF_OK;
@@ -743,7 +771,7 @@ uf_status uf_kappa_gradient(uf_operator *op, double *dk, const double *r, const 
     rl = op->f64.y_loc;
   }
   int err = uf::launch_kgrad(op->host.dim, op->host.n, op->kg_tables, op->f64.arrays,
-                             op->f64.point_tables.data(), op->f64.scalars, op->kg_scratch, dk, rl,
+                             op->f64.struct_tables.data(), op->f64.point_tables.data(), op->f64.scalars, op->kg_scratch, dk, rl,
                              xl, cs);
   if (err != 0)
     return fail(UF_ECUDA, std::string("kernel launch: ") + cudaGetErrorString((cudaError_t)err));
