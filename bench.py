@@ -37,7 +37,8 @@ METRIC = "GDoF/s of unfitted DG A·x (3D, k=3) FP64/FP32 + adjoint, % of HBM roo
 UNIT = "GDoF/s"
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC = os.path.join(ROOT, "profiles", "dram_traffic.txt")
-KERNEL_SOURCE = os.path.join(ROOT, "paper_2404_07911_gb300", "csrc", "uf_kernels.cuh")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2404_07911_gb300", "csrc", f)
+                  for f in ("uf_kernels.cuh", "uf_struct_planes.cuh")]
 # Device arithmetic peaks from unit counts and the maximum SM clock (2070 MHz), 152 SMs:
 # FP64 2 FMA / clk / SM (GB300 ships a reduced FP64 pipe), FP32 128 FMA / clk / SM.
 SM_COUNT, SM_MAX_GHZ = 152, 2.070
@@ -295,7 +296,7 @@ def kernel_traffic(name):
             parts = line.split()
             if len(parts) == 2 and not line.startswith("#"):
                 rec[parts[0]] = parts[1]
-        digest = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()[:16]
+        digest = hashlib.sha256(b"".join(open(f, "rb").read() for f in KERNEL_SOURCES)).hexdigest()[:16]
         if rec.get("source_sha256_16") != digest or name not in rec:
             return None
         return float(rec[name])
