@@ -66,7 +66,7 @@ def parse_args():
     ap.add_argument("--no-csr", action="store_true",
                     help="skip the assembled-matrix (CSR SpMV) comparison")
     ap.add_argument("--config", choices=("q3", "solve", "sweep", "kappa", "plane", "accuracy",
-                                         "spheres", "oracle"),
+                                         "spheres", "oracle", "vmult"),
                     default="q3",
                     help="q3: the headline step (default); solve: CG Q4 time to solution, IR vs "
                          "FP64; sweep: degree sweep p = 1..8 at ~2e7 DoFs; kappa: forward vs "
@@ -74,7 +74,10 @@ def parse_args():
                          "against the ratio of cut cells (DG Q1, CG Q3); accuracy: convergence of "
                          "the sphere accuracy benchmark (CG, DG, p = 1..4); spheres: the "
                          "regular 1000-spheres benchmark (DG Q1); oracle: the CPU oracle on all host "
-                         "cores and on one (2D Q1 disc, 3D Q3 ball, kappa workload)")
+                         "cores and on one (2D Q1 disc, 3D Q3 ball, kappa workload); vmult: --steps "
+                         "products of the 3D Q3 ball in one precision, untimed (for profilers)")
+    ap.add_argument("--precision", choices=("fp64", "fp32"), default="fp64",
+                    help="precision of --config vmult")
     return ap.parse_args()
 
 
@@ -801,6 +804,28 @@ def run_solve(args, local):
         "data": "synthetic (f = 1)"}), flush=True)
 
 
+def run_vmult(args, local):
+    """--steps products y = A x of the 3D Q3 64^3 ball workload in one precision, untimed: the
+    launch sequence a profiler captures (struct, then cut-cell kernel(s), per product)."""
+    import torch
+
+    from paper_2404_07911_gb300 import UF_FP32, UF_FP64, UnfittedOperator
+
+    torch.cuda.set_device(local)
+    cfg = workloads.cfg_3d_q3()
+    op = UnfittedOperator(cfg, precisions=UF_FP64 | UF_FP32, device=local)
+    x = torch.from_numpy(workloads.uniform_vector(op.n_dofs, cfg["seed"])).cuda()
+    if args.precision == "fp32":
+        x = x.float()
+    y = torch.empty_like(x)
+    for _ in range(args.steps):
+        op.vmult(x, y)
+    torch.cuda.synchronize()
+    print(json.dumps({"config": "vmult", "precision": args.precision, "products": args.steps,
+                      "max_abs_y": float(y.abs().max())}), flush=True)
+    op.close()
+
+
 def run_sweep(args, local):
     """Degree sweep p = 1..8 at about 2e7 DoFs: FP64 / FP32 GDoF/s, HBM / FP-pipe / binding-roof
     fractions per product and kernel, and errors vs the oracle."""
@@ -976,6 +1001,8 @@ def main():
         run_spheres(args, local)
     elif args.config == "oracle":
         run_oracle_timing(args)
+    elif args.config == "vmult":
+        run_vmult(args, local)
     else:
         run_ours(args, rank, world, local)
 
