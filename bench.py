@@ -76,7 +76,7 @@ def parse_args():
                          "regular 1000-spheres benchmark (DG Q1); oracle: the CPU oracle on all host "
                          "cores and on one (2D Q1 disc, 3D Q3 ball, kappa workload); vmult: --steps "
                          "products of the 3D Q3 ball in one precision, untimed (for profilers)")
-    ap.add_argument("--precision", choices=("fp64", "fp32"), default="fp64",
+    ap.add_argument("--precision", choices=("fp64", "fp32", "fp64dw"), default="fp64",
                     help="precision of --config vmult")
     return ap.parse_args()
 
@@ -840,7 +840,10 @@ def run_vmult(args, local):
         x = x.float()
     y = torch.empty_like(x)
     for _ in range(args.steps):
-        op.vmult(x, y)
+        if args.precision == "fp64dw":
+            op.vmult_dw(x, y)
+        else:
+            op.vmult(x, y)
     torch.cuda.synchronize()
     print(json.dumps({"config": "vmult", "precision": args.precision, "products": args.steps,
                       "max_abs_y": float(y.abs().max())}), flush=True)

@@ -48,7 +48,9 @@ typedef enum {
 enum { UF_FP64 = 1, UF_FP32 = 2 };     /* precision flags (bit mask in uf_params.precisions) */
 /* uf_vmult / uf_vmult_adjoint only: FP64 vectors with the structured terms evaluated in double-word
  * arithmetic on the FP32 pipe (3D, n <= 4, uniform kappa; elsewhere the FP64 structured kernel)
- * and the cut-cell terms in FP64.  Needs the FP64 operator.  (Not in the paper.) */
+ * and the cut-cell terms in FP64.  Needs the FP64 operator; the input is converted to double
+ * words in the FP64 staging buffer of uf_vmult_host, so such a call must not overlap a
+ * host-buffer call on the same operator.  (Not in the paper.) */
 enum { UF_FP64_DW = 4 };
 enum { UF_LS_SPHERE = 0, UF_LS_PLANE = 1, UF_LS_SPHERES = 2 };  /* level set kinds */
 enum { UF_DG = 0, UF_CG = 1 };         /* discretizations (uf_params.discretization) */

@@ -686,6 +686,7 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   }
   A.kappa_uniform = kappa_is_uniform(H.kappa) ? 1 : 0;
   A.struct_dw = 0;
+  A.dw_scratch = nullptr;
   A.n_active = (int32_t)na;
   A.n_cut = (int32_t)nc;
   {
@@ -787,6 +788,7 @@ uf_status vmult_t(uf_operator *op, PrecisionData<T> &pd, void *y, const void *x,
   if (cg) err = uf::cg_gather<T>(pd.x_loc, static_cast<const T *>(x), pd.cg_l2g, n_loc, cs);
   uf::DevArrays<T> arrays = pd.arrays;
   arrays.struct_dw = dw ? 1 : 0;
+  arrays.dw_scratch = dw ? pd.xbuf : nullptr;  // the FP64 staging buffer (n_active * n^d doubles)
   if (err == 0)
     err = uf::launch_vmult<T>(op->host.dim, op->host.n, arrays, pd.struct_tables.data(),
                               pd.point_tables.data(), pd.scalars, cg ? pd.y_loc : static_cast<T *>(y),
