@@ -76,7 +76,7 @@ def parse_args():
                          "regular 1000-spheres benchmark (DG Q1); oracle: the CPU oracle on all host "
                          "cores and on one (2D Q1 disc, 3D Q3 ball, kappa workload); vmult: --steps "
                          "products of the 3D Q3 ball in one precision, untimed (for profilers)")
-    ap.add_argument("--precision", choices=("fp64", "fp32", "fp64dw"), default="fp64",
+    ap.add_argument("--precision", choices=("fp64", "fp32"), default="fp64",
                     help="precision of --config vmult")
     return ap.parse_args()
 
@@ -433,7 +433,6 @@ def run_ours(args, rank, world, local):
     barrier()
     step_ms = [ev_s[k].elapsed_time(ev_e[k]) for k in range(K)]
     ktimes = op.profile_end()
-    launches = op.profiled_kernel_launches  # kernel launches inside the timed region
     value, total_s = replica_throughput(sum(step_ms) / 1e3, K * 3 * n, world, device="cuda")
     value /= 1e9
     total_ms = total_s * 1e3
@@ -481,26 +480,6 @@ def run_ours(args, rank, world, local):
     barrier()
     conc_ms = sum(a.elapsed_time(b) for a, b in evc) / Kw
 
-    # ---- FP64 with the structured terms in double-word arithmetic on the FP32 pipe (reported
-    # beside the FP64 products; same L2 flush before every application)
-    ydw = torch.empty_like(x64)
-    for _ in range(3):
-        op.vmult_dw(x64, ydw, stream)
-        op.vmult_dw(x64, ydw, stream, adjoint=True)
-    Kd = max(3, min(K, 50))
-    op.profile_begin(2 * Kd)
-    ms_dw = _event_ms(lambda: op.vmult_dw(x64, ydw, stream), Kd, stream, flush)
-    ms_dwa = _event_ms(lambda: op.vmult_dw(x64, ydw, stream, adjoint=True), Kd, stream, flush)
-    kt_dw = op.profile_end()
-    op.vmult(x64, y64, stream)
-    op.vmult_dw(x64, ydw, stream)
-    torch.cuda.synchronize()
-    dw_part = {"vmult_ms": round(ms_dw, 4), "adjoint_ms": round(ms_dwa, 4),
-               "vmult_gdofs": round(n / ms_dw / 1e6, 3),
-               "kernel_ms": {f"{k}_{dr}": round(t / c, 4) for (p, k, dr), (t, c) in kt_dw.items()},
-               "rel_diff_vs_fp64": float((ydw - y64).abs().max() / y64.abs().max()),
-               "note": "FP64 vectors; structured terms in double-word FP32 arithmetic, cut cells in FP64"}
-
     # ---- end to end through the C ABI with pinned host buffers (copies inside the region)
     xh64 = torch.from_numpy(x_host).pin_memory()
     xh32 = xh64.float().pin_memory()
@@ -535,6 +514,7 @@ def run_ours(args, rank, world, local):
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     kernel_table, parts, dominant = roofline_figures(info, ktimes, hbm, n)
     roof = dominant
+    launches = op.profiled_kernel_launches  # kernel launches inside the timed region
 
     result = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": K,
@@ -553,7 +533,6 @@ def run_ours(args, rank, world, local):
                     "unit": UNIT},
         "three_streams": {"ms_per_step": round(conc_ms, 5), "value": round(3 * n / conc_ms / 1e6, 4),
                           "unit": UNIT, "l2": "flushed before every step"},
-        "fp64_double_word": dw_part,
         "gpu_launches": int(launches),
         "clocks": clk,
     }
@@ -840,10 +819,7 @@ def run_vmult(args, local):
         x = x.float()
     y = torch.empty_like(x)
     for _ in range(args.steps):
-        if args.precision == "fp64dw":
-            op.vmult_dw(x, y)
-        else:
-            op.vmult(x, y)
+        op.vmult(x, y)
     torch.cuda.synchronize()
     print(json.dumps({"config": "vmult", "precision": args.precision, "products": args.steps,
                       "max_abs_y": float(y.abs().max())}), flush=True)

@@ -46,12 +46,6 @@ typedef enum {
 } uf_status;
 
 enum { UF_FP64 = 1, UF_FP32 = 2 };     /* precision flags (bit mask in uf_params.precisions) */
-/* uf_vmult / uf_vmult_adjoint only: FP64 vectors with the structured terms evaluated in double-word
- * arithmetic on the FP32 pipe (3D, n <= 4, uniform kappa; elsewhere the FP64 structured kernel)
- * and the cut-cell terms in FP64.  Needs the FP64 operator; the input is converted to double
- * words in the FP64 staging buffer of uf_vmult_host, so such a call must not overlap a
- * host-buffer call on the same operator.  (Not in the paper.) */
-enum { UF_FP64_DW = 4 };
 enum { UF_LS_SPHERE = 0, UF_LS_PLANE = 1, UF_LS_SPHERES = 2 };  /* level set kinds */
 enum { UF_DG = 0, UF_CG = 1 };         /* discretizations (uf_params.discretization) */
 enum { UF_GP_FACE = 0, UF_GP_VOLUME = 1 }; /* ghost penalties (uf_params.gp_kind) */
@@ -156,8 +150,7 @@ uf_status uf_get_info(const uf_operator *op, uf_info *info);
 
 /* y = A x (paper Eq. operatorevaluation / Eq. matrixfreeopcompact, Sec. 3.1), matrix-free.
  * precision: UF_FP64 (x, y are double[n_dofs]) or UF_FP32 (float[n_dofs]); the operator must
- * have been created with that precision; UF_FP64_DW: double vectors, structured terms in
- * double-word arithmetic (see UF_FP64_DW).  x and y are device pointers that must not overlap.
+ * have been created with that precision.  x and y are device pointers that must not overlap.
  * Stream-ordered; no allocation, no synchronisation.  Errors: UF_EINVAL, UF_ENODEVICE,
  * UF_ECUDA (launch failure). */
 uf_status uf_vmult(uf_operator *op, int precision, void *y, const void *x, void *stream);

@@ -13,7 +13,6 @@ from . import build as _build
 
 UF_OK, UF_EINVAL, UF_ENOMEM, UF_ECUDA, UF_EUNSUPPORTED, UF_EGEOMETRY, UF_ENODEVICE = range(7)
 UF_FP64, UF_FP32 = 1, 2
-UF_FP64_DW = 4
 UF_LS_SPHERE = 0
 UF_LS_PLANE = 1
 UF_LS_SPHERES = 2
@@ -290,16 +289,6 @@ class UnfittedOperator:
         """Cut cells below this volume fraction (and their face neighbours) get FP64 rows in the
         split operator (>= 1: every cut cell)."""
         _check(_lib.uf_set_split_fraction(self._h, float(fraction)))
-
-    def vmult_dw(self, x, y=None, stream=None, adjoint=False):
-        """y = A x (or A^T x) on FP64 vectors with the structured terms in double-word arithmetic
-        on the FP32 pipe (UF_FP64_DW)."""
-        import torch
-
-        if x.dtype != torch.float64:
-            raise ValueError("x must be float64")
-        fn = _lib.uf_vmult_adjoint if adjoint else _lib.uf_vmult
-        return self._apply(lambda h, prec, yp, xp, sp: fn(h, UF_FP64_DW, yp, xp, sp), x, y, stream)
 
     def vmult_adjoint(self, g, y=None, stream=None):
         """y = A^T g on the device (stream-ordered)."""

@@ -685,8 +685,6 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
     if (err != cudaSuccess) return fail(UF_ECUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(err));
   }
   A.kappa_uniform = kappa_is_uniform(H.kappa) ? 1 : 0;
-  A.struct_dw = 0;
-  A.dw_scratch = nullptr;
   A.n_active = (int32_t)na;
   A.n_cut = (int32_t)nc;
   {
@@ -765,7 +763,7 @@ void release(PrecisionData<T> &pd) {
 
 template <typename T>
 uf_status vmult_t(uf_operator *op, PrecisionData<T> &pd, void *y, const void *x, void *stream,
-                  bool adjoint, const uf::LaunchRange *rg = nullptr, bool dw = false) {
+                  bool adjoint, const uf::LaunchRange *rg = nullptr) {
   if (!pd.present) return fail(UF_EINVAL, "operator was not created with this precision");
   const bool cg = op->host.cg;
   const int64_t nvec = cg ? op->host.n_cg : op->host.n_active * op->host.ndof;
@@ -786,11 +784,8 @@ uf_status vmult_t(uf_operator *op, PrecisionData<T> &pd, void *y, const void *x,
   const int64_t n_loc = op->host.n_active * op->host.ndof;
   int err = 0;
   if (cg) err = uf::cg_gather<T>(pd.x_loc, static_cast<const T *>(x), pd.cg_l2g, n_loc, cs);
-  uf::DevArrays<T> arrays = pd.arrays;
-  arrays.struct_dw = dw ? 1 : 0;
-  arrays.dw_scratch = dw ? pd.xbuf : nullptr;  // the FP64 staging buffer (n_active * n^d doubles)
   if (err == 0)
-    err = uf::launch_vmult<T>(op->host.dim, op->host.n, arrays, pd.struct_tables.data(),
+    err = uf::launch_vmult<T>(op->host.dim, op->host.n, pd.arrays, pd.struct_tables.data(),
                               pd.point_tables.data(), pd.scalars, cg ? pd.y_loc : static_cast<T *>(y),
                               cg ? pd.x_loc : static_cast<const T *>(x), adjoint, stream, ev, rg);
   if (err == 0 && cg)
@@ -889,10 +884,9 @@ namespace {
 
 uf_status vmult_dispatch(uf_operator *op, int precision, void *y, const void *x, void *stream,
                          bool adjoint) {
-  const bool dw = precision == UF_FP64_DW;
-  uf_status st = check_vmult_args(op, dw ? UF_FP64 : precision, y, x);
+  uf_status st = check_vmult_args(op, precision, y, x);
   if (st != UF_OK) return st;
-  if (precision == UF_FP64 || dw) return vmult_t<double>(op, op->f64, y, x, stream, adjoint, nullptr, dw);
+  if (precision == UF_FP64) return vmult_t<double>(op, op->f64, y, x, stream, adjoint);
   return vmult_t<float>(op, op->f32, y, x, stream, adjoint);
 }
 

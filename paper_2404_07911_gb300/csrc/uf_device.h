@@ -117,8 +117,6 @@ struct DevArrays {
   // 6 n FMA per point).
   const T *vline_km;
   int32_t kappa_uniform;
-  int32_t struct_dw;  // FP64: structured terms in double-word arithmetic where available
-  void *dw_scratch;   // with struct_dw: n_active * n^d double words for the converted input
   int32_t n_active, n_cut;
   // the cut-cell kernel gives cut_list[0 .. cut_split[0]) 32 lanes per cell, [cut_split[0] ..
   // cut_split[1]) 16 lanes (2 cells per warp) and the rest 8 lanes (4 cells per warp)

@@ -27,7 +27,6 @@
 
 #include "uf_device.h"
 #include "uf_struct_planes.cuh"
-#include "uf_struct_dw.cuh"
 
 namespace uf {
 
@@ -1447,13 +1446,7 @@ int launch_vmult_t(const DevArrays<T> &d0, const void *tables_struct, const void
   if constexpr (std::is_same<T, float>::value && DIM == 3 && N <= 5)
     planes = d.kappa_uniform != 0 && !(rg && rg->cells) &&
              (N != 4 || ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) % 16 == 0));
-  bool dwk = false;  // FP64 in double-word arithmetic (3D, n <= 4, uniform kappa)
-  if constexpr (sizeof(T) == sizeof(double) && DIM == 3 && N <= 4)
-    dwk = d.struct_dw != 0 && d.dw_scratch != nullptr && d.kappa_uniform != 0 && !(rg && rg->cells);
-  if (dwk) {
-    if constexpr (sizeof(T) == sizeof(double) && DIM == 3 && N <= 4)
-      launch_struct_dw<N>(tab, d, s, y, x, static_cast<dw *>(d.dw_scratch), adjoint, stream, cb, ce);
-  } else if (rg && rg->cells) {
+  if (rg && rg->cells) {
     // a list of cells (FP64, y = A x rows of those cells)
     if constexpr (sizeof(T) == sizeof(double)) {
       if (blocks > 0) {

@@ -99,23 +99,6 @@ def test_parity_fp64_fp32_adjoint(key):
     assert _rel(y32, A @ x32) <= TOL32
 
 
-@pytest.mark.parametrize("key", list(SMALL))
-def test_parity_fp64_double_word(key):
-    """UF_FP64_DW: FP64 vectors, structured terms in double-word arithmetic on the FP32 pipe
-    (3D, n <= 4, uniform kappa; the FP64 structured kernel elsewhere): the same 1e-12 bound
-    against the oracle, vmult and adjoint, on every parity configuration (p = 1..8)."""
-    cfg = SMALL[key]
-    o, A = _oracle(key)
-    op = _gpu_op(cfg)
-    x = workloads.uniform_vector(op.n_dofs, cfg["seed"])
-    xt = torch.from_numpy(x).cuda()
-    y = op.vmult_dw(xt).cpu().numpy()
-    torch.cuda.synchronize()
-    assert _rel(y, A @ x) <= TOL64
-    ya = op.vmult_dw(xt, adjoint=True).cpu().numpy()
-    assert _rel(ya, A.T @ x) <= TOL64
-
-
 def test_parity_kappa_lognormal():
     cfg = workloads.small(p=3, N=6)
     o0 = forms.Oracle(mesh.problem_from_dict(cfg))
@@ -214,20 +197,6 @@ def test_full_size_sampled_rows_fp64_fp32(full):
     x32 = x.astype(np.float32).astype(np.float64)
     y32 = _apply(op, x32, dtype=torch.float32).reshape(-1, nd)[cells]
     assert _rel(y32, o.apply_rows(x32, cells)) <= TOL32
-
-
-def test_full_size_double_word_rows(full):
-    """The 64^3 Q3 workload in UF_FP64_DW (its structured kernel runs in double words): sampled
-    rows against the oracle at 1e-12, and the whole vector against the FP64 product."""
-    cfg, op, o, x = full
-    nd = op.info["dofs_per_cell"]
-    cells = _sample_cells(o)
-    xt = torch.from_numpy(x).cuda()
-    y = op.vmult_dw(xt)
-    y64 = op.vmult(xt)
-    torch.cuda.synchronize()
-    assert _rel(y.cpu().numpy().reshape(-1, nd)[cells], o.apply_rows(x, cells)) <= TOL64
-    assert ((y - y64).abs().max() / y64.abs().max()).item() <= TOL64
 
 
 def test_full_size_symmetry_and_determinism(full):
