@@ -735,7 +735,9 @@ template <typename T, int DIM, int N, int S>
 struct CutSmem {
   static constexpr int ND = Geo<DIM, N>::ND, NL = Geo<DIM, N>::NL, NF = Geo<DIM, N>::NF;
   static constexpr int CH = S;
-  static constexpr int GMAX = cut_gmax<N>() < S ? cut_gmax<N>() : S;
+  // at most GMAX groups per chunk: cut_gmax, and half the lanes for the 16- and 8-lane classes
+  // (their cells have few groups; the smaller partial arrays raise residency)
+  static constexpr int GMAX = cut_gmax<N>() < (S >= 32 ? S : S / 2) ? cut_gmax<N>() : (S >= 32 ? S : S / 2);
   static constexpr int cmax(int a, int b) { return a > b ? a : b; }
   static constexpr int u = 0;                    // [ND] the cell's DoFs
   static constexpr int acc = u + ND;             // [ND] accumulated output rows

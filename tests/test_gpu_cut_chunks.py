@@ -3,9 +3,9 @@
 The cut-cell kernel hands each cut cell to a group of S lanes (S = 32, 16 or 8; the FP32 kernel
 runs the 16-lane class with 32 lanes) and walks the cell's volume lines axis by axis in chunks of
 at most S lines, one line per lane.  The lines of an axis come in groups that share one outer
-coordinate; a chunk holds at most GMAX groups (16 for n <= 5, 8 above, never more than S) and
-ends before the start of group GMAX + 1, and a group that does not fit restarts in the next
-chunk.  `chunks_of_cell` restates that rule from the exported line structure, so that the tests
+coordinate; a chunk holds at most GMAX groups (16 for n <= 5, 8 above, and never more than S / 2
+in the 16- and 8-lane classes) and ends before the start of group GMAX + 1, and a group that does
+not fit restarts in the next chunk.  `chunks_of_cell` restates that rule from the exported line structure, so that the tests
 can assert which paths their cells take:
   * an axis whose lines need more than one chunk;
   * a chunk ended early because it reached GMAX groups;
@@ -35,7 +35,7 @@ def cut_gmax(n):
 def chunks_of_cell(axis, group_start, lanes, n):
     """Chunks of the 3D volume phase of one cut cell: (axis, first line within the axis, lines,
     ended because it reached GMAX groups, a group continues in the next chunk)."""
-    gmax = min(cut_gmax(n), lanes)
+    gmax = min(cut_gmax(n), lanes if lanes >= 32 else lanes // 2)
     out = []
     for k in range(3):
         idx = np.nonzero(axis == k)[0]
