@@ -194,13 +194,13 @@ __global__ void __launch_bounds__(128) kgrad_struct_kernel(const double *__restr
     for (int k = 0; k <= NF; ++k) s_part[t * (1 + NF) + k] = p[k];
   }
   __syncthreads();
-  if (has_cell && t == 0) {
-    for (int k = 0; k <= NF; ++k) {
+  // thread k of the cell sums slot k over the cell's lines (the same order as one thread would)
+  if (has_cell)
+    for (int k = t; k <= NF; k += TPC) {
       double acc = 0.0;
       for (int q = 0; q < TPC; ++q) acc += s_part[q * (1 + NF) + k];
       S[(size_t)e * (1 + NF) + k] = acc;
     }
-  }
 }
 
 // Volume and surface integrands of r^T (dA/dkappa_K) x on a 3D cut cell, with the two-level line
