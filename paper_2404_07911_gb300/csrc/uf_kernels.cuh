@@ -1349,7 +1349,8 @@ __device__ __forceinline__ void cut_cells(const PointTables<T, N> &pt, const Dev
 // (two cells per CTA), then the 8-lane class (four).  FP64 launches all classes together, so
 // that they fill each other's tails instead of ending in partial waves (the 64^3 Q3 ball: 0.377
 // -> 0.356 ms); FP32, whose kernel is latency-bound, keeps one launch per class (a kernel holding
-// every class's code measured 17 % slower there).
+// every class's code measured 17 % slower there), and so do the parts of the host-buffer
+// pipeline, whose launches overlap on several streams (merged: end-to-end 8.92 -> 8.62 GDoF/s).
 template <typename T, int DIM, int N, int CLS>
 __global__ void __launch_bounds__(32) cut_kernel(const __grid_constant__ PointTables<T, N> pt,
                                                  const DevArrays<T> d, const Scalars<T> sc,
@@ -1410,10 +1411,12 @@ int launch_cut_classes(const PointTables<T, N> &ptab, const DevArrays<T> &d, con
   return (int)cudaGetLastError();
 }
 
+// merged: all lane classes in one launch (FP64 products of the whole operator; the parts of the
+// host-buffer pipeline, which run on several streams at once, keep one launch per class)
 template <typename T, int DIM, int N>
 int launch_cut(const PointTables<T, N> &ptab, const DevArrays<T> &d, const Scalars<T> &s, T *y,
-               const T *x, cudaStream_t stream, const int *sp) {
-  if constexpr (sizeof(T) == sizeof(double)) {
+               const T *x, cudaStream_t stream, const int *sp, bool merged) {
+  if (merged) {
     return launch_cut_classes<T, DIM, N, 7>(ptab, d, s, y, x, stream, sp);
   } else {
     int e = launch_cut_classes<T, DIM, N, 1>(ptab, d, s, y, x, stream, sp);
@@ -1481,7 +1484,8 @@ int launch_vmult_t(const DevArrays<T> &d0, const void *tables_struct, const void
   if (sp[3] > sp[0]) {
     const auto &ptab = *reinterpret_cast<const PointTables<T, N> *>(tables_point);
     // the three lane classes are contiguous in cut_list (32, 16, 8 lanes per cell)
-    const int e2 = launch_cut<T, DIM, N>(ptab, d, s, y, x, stream, sp);
+    const bool merged = sizeof(T) == sizeof(double) && (!rg || rg->cells);
+    const int e2 = launch_cut<T, DIM, N>(ptab, d, s, y, x, stream, sp, merged);
     if (e2 != 0) return e2;
   }
   if (ev) cudaEventRecord(static_cast<cudaEvent_t>(ev[3]), stream);
