@@ -122,6 +122,14 @@ __device__ __forceinline__ uint32_t bit_full(int f) { return 1u << (1 + 3 * f); 
 __device__ __forceinline__ uint32_t bit_cut(int f) { return 1u << (2 + 3 * f); }
 __device__ __forceinline__ uint32_t bit_gp(int f) { return 1u << (3 + 3 * f); }
 
+// FP64 at n = 9 in 3D: the structured kernel's cells live in dynamic shared memory, so that a
+// CTA can hold three of them (243 of 256 lanes busy; one cell in 48 KB of static arrays leaves
+// 15 of 96 lanes idle).
+template <typename T, int DIM, int N>
+__host__ __device__ constexpr bool struct_dynamic_smem() {
+  return DIM == 3 && N == 9 && sizeof(T) == 8;
+}
+
 // Cells per CTA of the structured kernel: one thread per line (n^{d-1} per cell), at most 128
 // threads, and the shared memory of the cells (u, W per axis, per-cell matrices) under 40 KB.
 template <typename T, int DIM, int N>
@@ -139,7 +147,8 @@ __host__ __device__ constexpr int struct_cells_per_block() {
   auto idle = [](int c) { return ((c * NL + 31) / 32) * 32 - c * NL; };
   if (idle(cpb) * 10 > ((cpb * NL + 31) / 32) * 32) {
     int best = cpb;
-    for (int c = 1; c * NL <= 256 && c * cell_bytes <= 48 * 1024; ++c)
+    constexpr int smem_cap = struct_dynamic_smem<T, DIM, N>() ? 96 * 1024 : 48 * 1024;
+    for (int c = 1; c * NL <= 256 && c * cell_bytes <= smem_cap; ++c)
       if (idle(c) * ((best * NL + 31) / 32) * 32 < idle(best) * ((c * NL + 31) / 32) * 32) best = c;
     cpb = best;
   }
@@ -249,9 +258,19 @@ __global__ void __launch_bounds__(struct_threads<T, DIM, N>()) struct_kernel(con
   constexpr int TPC = NL;
   constexpr int P = spad<N>(), SND = snd<DIM, N>();
 
-  __shared__ __align__(16) T s_u[CPB][SND];
-  __shared__ __align__(16) T s_w[DIM][CPB][SND];
-  __shared__ __align__(16) T s_l[CPB][DIM][3][NN];  // per-cell matrices when kappa is not uniform
+  // u, W per axis and the per-cell matrices (non-uniform kappa): static arrays, or the dynamic
+  // shared memory in the same order (struct_smem_bytes)
+  constexpr bool DYN = struct_dynamic_smem<T, DIM, N>();
+  __shared__ __align__(16) T s_u_st[DYN ? 1 : CPB][SND];
+  __shared__ __align__(16) T s_w_st[DIM][DYN ? 1 : CPB][SND];
+  __shared__ __align__(16) T s_l_st[DYN ? 1 : CPB][DIM][3][NN];
+  extern __shared__ __align__(16) unsigned char struct_dyn[];
+  auto &s_u = *reinterpret_cast<T (*)[CPB][SND]>(DYN ? static_cast<void *>(struct_dyn)
+                                                     : static_cast<void *>(s_u_st));
+  auto &s_w = *reinterpret_cast<T (*)[DIM][CPB][SND]>(
+      DYN ? static_cast<void *>(struct_dyn + sizeof(T) * CPB * SND) : static_cast<void *>(s_w_st));
+  auto &s_l = *reinterpret_cast<T (*)[CPB][DIM][3][NN]>(
+      DYN ? static_cast<void *>(struct_dyn + sizeof(T) * (1 + DIM) * CPB * SND) : static_cast<void *>(s_l_st));
   // FP32 keeps the form without M^{-1} (W_a = L_a u + couplings, then the shared in-face mass
   // sweeps y = M_z (M_y W_x + M_x W_y) + M_y M_x W_z): its rounding errors are not amplified by
   // M^{-1}, which the FP32 solves inside iterative refinement depend on
@@ -718,7 +737,7 @@ __device__ __forceinline__ void line_products(const T *km, T kap, const T *w0, c
 // it has that many; the per-group partial contractions take GMAX n^2 values each).
 template <int N>
 __host__ __device__ constexpr int cut_gmax() {
-  return (N <= 5) ? 16 : 8;
+  return (N <= 5) ? 16 : (N <= 8) ? 8 : 6;
 }
 
 
@@ -744,11 +763,15 @@ struct CutSmem {
   static constexpr int shared = acc + ND;        // region of size `region`:
   //   3D volume: P0, P1 = [GMAX][NL] per group (then Q0, Q1)
   //   2D volume: lt0, lt1 = [CH][NL] per line partial integrals
-  //   faces:     tr = [NF][2][NL] trace jump and flux, ft = [NF][2][NL] face accumulators
-  static constexpr int region = cmax(cmax(2 * GMAX * NL, 2 * CH * NL * (DIM == 2 ? 1 : 0)), 4 * NF * NL);
+  //   faces:     tr = [FB][2][NL] trace jump and flux, ft = [FB][2][NL] face accumulators
+  // cut faces per batch of the face phase: all of them, except at n = 9 in 3D, where batches of
+  // three keep the face arrays as small as the volume phase's with GMAX 6 (FP64: 32.1 KB per
+  // one-warp CTA, 7 CTAs per SM instead of 5 with all faces and GMAX 8)
+  static constexpr int FB = (DIM == 3 && N >= 9) ? 3 : NF;
+  static constexpr int region = cmax(cmax(2 * GMAX * NL, 2 * CH * NL * (DIM == 2 ? 1 : 0)), 4 * FB * NL);
   static constexpr int p0 = shared, p1 = shared + GMAX * NL;
   static constexpr int lt0 = shared, lt1 = shared + CH * NL;
-  static constexpr int tr = shared, ft = shared + 2 * NF * NL;
+  static constexpr int tr = shared, ft = shared + 2 * FB * NL;
   static constexpr int lvb = shared + region;    // [CH][N] per line basis (values)
   static constexpr int ldb = lvb + CH * N;       // [CH][N] (derivatives)
   static constexpr int zz = ldb + CH * N;        // [3][CH][N] per line point integrals
@@ -1173,21 +1196,24 @@ __device__ __forceinline__ void cut_cells(const PointTables<T, N> &pt, const Dev
     }
   }
 
-  // ---- SIPG on cut faces: F cap Omega, in-face lines (Eq. unstructured_face).  All cut faces
-  // of the cell are processed together so that the warp's lanes stay busy.
+  // ---- SIPG on cut faces: F cap Omega, in-face lines (Eq. unstructured_face).  The cut faces
+  // of the cell are processed together (in batches of SM::FB faces, the size of the face
+  // arrays) so that the warp's lanes stay busy.
   int cfl[NF];
   int ncf = 0;
 #pragma unroll
   for (int f = 0; f < NF; ++f)
     if (bit(fl, bit_cut(f))) cfl[ncf++] = f;
-  if (ncf > 0) {
+  const int *koff_cell = d.fline_koff + (size_t)ci * NF * 3;
+  // the cut faces cfl[b0 .. b0 + nbf) (ascending face index: their lines are contiguous)
+  auto face_batch = [&](const int b0, const int nbf) {
     // per cut face, indexed by the in-face DoF tl = i_b' + n i_c' (b' < c' in-face axes): the
     // jump of the traces [u] = u_K - u_nb (the trace of a Lobatto basis is its face-node value)
     // and the average normal flux {kappa d_n u} along the own outward normal; the neighbour's
     // lines are read from global memory (L2)
-    for (int item = tid; item < ncf * NL; item += CH) {
+    for (int item = tid; item < nbf * NL; item += CH) {
       const int fi = item / NL, tl = item % NL;
-      const int f = cfl[fi], axis = f / 2, side = f % 2;
+      const int f = cfl[b0 + fi], axis = f / 2, side = f % 2;
       const int nbe = __ldg(d.nbr + (size_t)e * NF + f);
       const T knb = __ldg(d.kappa + nbe);
       const int base = line_base<DIM, N>(axis, tl);
@@ -1207,24 +1233,24 @@ __device__ __forceinline__ void cut_cells(const PointTables<T, N> &pt, const Dev
       s_ft[fi][1][tl] = T(0);
     }
     __syncwarp(gmask);
-    const int *koff_cell = d.fline_koff + (size_t)ci * NF * 3;
-    const int fl_beg = __ldg(koff_cell);
-    const int fl_end = __ldg(koff_cell + (NF - 1) * 3 + 2);
+    const int fl_beg = (SM::FB >= NF) ? __ldg(koff_cell) : __ldg(koff_cell + cfl[b0] * 3);
+    const int fl_end = (SM::FB >= NF) ? __ldg(koff_cell + (NF - 1) * 3 + 2)
+                                      : __ldg(koff_cell + cfl[b0 + nbf - 1] * 3 + 2);
 #pragma unroll 1
     for (int l0 = fl_beg; l0 < fl_end; l0 += CH) {
       const int line = l0 + tid;
       int tag = -1;
       if (line < fl_end) {
         int fi = 0, kk = 0;
-        for (int j = 0; j < ncf; ++j) {
-          const int *ko = koff_cell + cfl[j] * 3;
+        for (int j = 0; j < nbf; ++j) {
+          const int *ko = koff_cell + cfl[b0 + j] * 3;
           if (line >= __ldg(ko) && line < __ldg(ko + 2)) {
             fi = j;
             kk = (line < __ldg(ko + 1)) ? 0 : 1;
           }
         }
         tag = 2 * fi + kk;
-        const int f = cfl[fi];
+        const int f = cfl[b0 + fi];
         const int nbe = __ldg(d.nbr + (size_t)e * NF + f);
         const T knb = __ldg(d.kappa + nbe);
         const T kavg = T(0.5) * (kap + knb);
@@ -1297,7 +1323,7 @@ __device__ __forceinline__ void cut_cells(const PointTables<T, N> &pt, const Dev
       s_tag[tid] = tag;
       __syncwarp(gmask);
       const int nlines = min(CH, fl_end - l0);
-      for (int item = tid; item < ncf * NL; item += CH) {
+      for (int item = tid; item < nbf * NL; item += CH) {
         const int fi = item / NL, tl = item % NL;
         T av = T(0), ad = T(0);
         for (int q = 0; q < nlines; ++q) {
@@ -1323,8 +1349,8 @@ __device__ __forceinline__ void cut_cells(const PointTables<T, N> &pt, const Dev
     // expand the face accumulators into the cell: phi_l = phi_{i_a}(side) x in-face product
     for (int l = tid; l < ND; l += CH) {
       T add = T(0);
-      for (int fi = 0; fi < ncf; ++fi) {
-        const int f = cfl[fi], axis = f / 2, side = f % 2;
+      for (int fi = 0; fi < nbf; ++fi) {
+        const int f = cfl[b0 + fi], axis = f / 2, side = f % 2;
         const T sgn = side ? T(1) : T(-1);
         const int ia = (l / stride_of<N>(axis)) % N;
         int tl;
@@ -1338,6 +1364,15 @@ __device__ __forceinline__ void cut_cells(const PointTables<T, N> &pt, const Dev
         if (ia == (side ? N - 1 : 0)) add += s_ft[fi][0][tl];
       }
       s_acc[l] += add;
+    }
+  };
+  if constexpr (SM::FB >= NF) {
+    if (ncf > 0) face_batch(0, ncf);
+  } else {
+#pragma unroll 1
+    for (int b0 = 0; b0 < ncf; b0 += SM::FB) {
+      face_batch(b0, min(SM::FB, ncf - b0));
+      __syncwarp(gmask);  // the next batch overwrites the face arrays that this one read
     }
   }
 
@@ -1426,6 +1461,22 @@ int launch_cut(const PointTables<T, N> &ptab, const DevArrays<T> &d, const Scala
   }
 }
 
+// Dynamic shared memory of a structured-kernel launch (struct_dynamic_smem: u, W per axis and,
+// for non-uniform kappa, the per-cell matrices of CPB cells), with the kernel's limit raised to
+// it; 0 for the instances with static arrays.
+template <typename T, int DIM, int N, bool UNI, typename K>
+size_t struct_smem_setup(K kernel) {
+  if constexpr (!struct_dynamic_smem<T, DIM, N>()) {
+    (void)kernel;
+    return 0;
+  } else {
+    constexpr int CPB = struct_cells_per_block<T, DIM, N>(), SND = snd<DIM, N>();
+    constexpr size_t bytes = sizeof(T) * CPB * (SND * (1 + DIM) + (UNI ? 0 : DIM * 3 * N * N));
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return bytes;
+  }
+}
+
 template <typename T, int DIM, int N>
 int launch_vmult_t(const DevArrays<T> &d0, const void *tables_struct, const void *tables_point,
                    const Scalars<T> &s, T *y, const T *x, bool adjoint, cudaStream_t stream,
@@ -1456,9 +1507,13 @@ int launch_vmult_t(const DevArrays<T> &d0, const void *tables_struct, const void
     if constexpr (sizeof(T) == sizeof(double)) {
       if (blocks > 0) {
         if (d.kappa_uniform != 0)
-          struct_kernel<T, DIM, N, false, true, true><<<blocks, threads, 0, stream>>>(tab, d, s, y, x, cb, ce, rg->cells);
+          struct_kernel<T, DIM, N, false, true, true>
+              <<<blocks, threads, struct_smem_setup<T, DIM, N, true>(struct_kernel<T, DIM, N, false, true, true>),
+                 stream>>>(tab, d, s, y, x, cb, ce, rg->cells);
         else
-          struct_kernel<T, DIM, N, false, false, true><<<blocks, threads, 0, stream>>>(tab, d, s, y, x, cb, ce, rg->cells);
+          struct_kernel<T, DIM, N, false, false, true>
+              <<<blocks, threads, struct_smem_setup<T, DIM, N, false>(struct_kernel<T, DIM, N, false, false, true>),
+                 stream>>>(tab, d, s, y, x, cb, ce, rg->cells);
       }
     } else {
       return (int)cudaErrorInvalidValue;
@@ -1469,13 +1524,21 @@ int launch_vmult_t(const DevArrays<T> &d0, const void *tables_struct, const void
   } else if (blocks > 0) {
     const bool uni = d.kappa_uniform != 0;
     if (adjoint && uni)
-      struct_kernel<T, DIM, N, true, true><<<blocks, threads, 0, stream>>>(tab, d, s, y, x, cb, ce);
+      struct_kernel<T, DIM, N, true, true>
+          <<<blocks, threads, struct_smem_setup<T, DIM, N, true>(struct_kernel<T, DIM, N, true, true>), stream>>>(
+              tab, d, s, y, x, cb, ce, nullptr);
     else if (adjoint)
-      struct_kernel<T, DIM, N, true, false><<<blocks, threads, 0, stream>>>(tab, d, s, y, x, cb, ce);
+      struct_kernel<T, DIM, N, true, false>
+          <<<blocks, threads, struct_smem_setup<T, DIM, N, false>(struct_kernel<T, DIM, N, true, false>), stream>>>(
+              tab, d, s, y, x, cb, ce, nullptr);
     else if (uni)
-      struct_kernel<T, DIM, N, false, true><<<blocks, threads, 0, stream>>>(tab, d, s, y, x, cb, ce);
+      struct_kernel<T, DIM, N, false, true>
+          <<<blocks, threads, struct_smem_setup<T, DIM, N, true>(struct_kernel<T, DIM, N, false, true>), stream>>>(
+              tab, d, s, y, x, cb, ce, nullptr);
     else
-      struct_kernel<T, DIM, N, false, false><<<blocks, threads, 0, stream>>>(tab, d, s, y, x, cb, ce);
+      struct_kernel<T, DIM, N, false, false>
+          <<<blocks, threads, struct_smem_setup<T, DIM, N, false>(struct_kernel<T, DIM, N, false, false>), stream>>>(
+              tab, d, s, y, x, cb, ce, nullptr);
   }
   if (ev) cudaEventRecord(static_cast<cudaEvent_t>(ev[1]), stream);
   cudaError_t err = cudaGetLastError();

@@ -3,7 +3,7 @@
 The cut-cell kernel hands each cut cell to a group of S lanes (S = 32, 16 or 8; the FP32 kernel
 runs the 16-lane class with 32 lanes) and walks the cell's volume lines axis by axis in chunks of
 at most S lines, one line per lane.  The lines of an axis come in groups that share one outer
-coordinate; a chunk holds at most GMAX groups (16 for n <= 5, 8 above, and never more than S / 2
+coordinate; a chunk holds at most GMAX groups (16 for n <= 5, 8 for n = 6..8, 6 for n = 9, and never more than S / 2
 in the 16- and 8-lane classes) and ends before the start of group GMAX + 1, and a group that does
 not fit restarts in the next chunk.  `chunks_of_cell` restates that rule from the exported line structure, so that the tests
 can assert which paths their cells take:
@@ -29,7 +29,7 @@ TOL32 = 1e-5
 
 
 def cut_gmax(n):
-    return 16 if n <= 5 else 8
+    return 16 if n <= 5 else 8 if n <= 8 else 6
 
 
 def chunks_of_cell(axis, group_start, lanes, n):
