@@ -386,6 +386,17 @@ uf_status uf_destroy(uf_operator *op);
 /* Thread-local message of the last failing call of this thread ("" if none). */
 const char *uf_last_error(void);
 
+/* Host-side fault injection for tests (the paper has no failure handling of its own).  Every
+ * device allocation, pinned host allocation and operator object of the library counts as one
+ * allocation.  After uf_debug_fail_allocation(k), the next k allocations succeed and the one after
+ * them fails as if memory were exhausted, without calling the allocator.  The call that made it
+ * then returns UF_ENOMEM after releasing what it had allocated, and the hook disarms itself; a
+ * negative k disarms it.  uf_debug_live_allocations reports the library's allocations not yet
+ * released.  Both act on process-wide state; calls on several threads may interleave.
+ * Errors: UF_EINVAL (NULL live). */
+uf_status uf_debug_fail_allocation(int64_t after);
+uf_status uf_debug_live_allocations(int64_t *live);
+
 #ifdef __cplusplus
 }
 #endif

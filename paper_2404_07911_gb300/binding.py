@@ -96,7 +96,7 @@ EXPORTED = ["uf_create_unfitted_operator", "uf_get_info", "uf_vmult", "uf_vmult_
             "uf_export_cut_face_rule", "uf_assemble_csr", "uf_csr_info", "uf_csr_spmv",
             "uf_export_csr", "uf_release_csr", "uf_kappa_gradient", "uf_kappa_gradient_noalloc",
             "uf_set_kappa_device", "uf_vmult_split", "uf_set_split_fraction", "uf_export_cg", "uf_solve", "uf_manufactured_rhs", "uf_l2_error",
-            "uf_destroy", "uf_last_error"]
+            "uf_destroy", "uf_debug_fail_allocation", "uf_debug_live_allocations", "uf_last_error"]
 
 _lib = None
 
@@ -149,6 +149,8 @@ def load_library(path=None):
     lib.uf_l2_error.argtypes = [P, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     lib.uf_destroy.argtypes = [P]
+    lib.uf_debug_fail_allocation.argtypes = [ctypes.c_int64]
+    lib.uf_debug_live_allocations.argtypes = [ctypes.POINTER(ctypes.c_int64)]
     lib.uf_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
         if name != "uf_last_error":
@@ -160,6 +162,19 @@ def load_library(path=None):
 def _check(st):
     if st != UF_OK:
         raise UnfittedError(st, _lib.uf_last_error().decode())
+
+
+def debug_fail_allocation(after):
+    """Fault injection: the library's next `after` allocations succeed, the one after them fails
+    with UF_ENOMEM (negative: disarm)."""
+    _check(load_library().uf_debug_fail_allocation(int(after)))
+
+
+def debug_live_allocations():
+    """The library's device, pinned-host and operator allocations not yet released."""
+    live = ctypes.c_int64()
+    _check(load_library().uf_debug_live_allocations(ctypes.byref(live)))
+    return live.value
 
 
 def _ptr(a):

@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -35,6 +36,61 @@ namespace uf {
 uf_status fail(uf_status st, const std::string &msg) {
   g_last_error = msg;
   return st;
+}
+
+namespace {
+// allocations that succeed before the injected failure (-1: none armed), and the live count
+std::atomic<int64_t> g_fail_after{-1};
+std::atomic<int64_t> g_live_allocations{0};
+
+// True once, for the allocation that the armed hook makes fail; the hook then disarms.
+bool injected_failure() {
+  int64_t v = g_fail_after.load();
+  while (v >= 0)
+    if (g_fail_after.compare_exchange_weak(v, v - 1)) return v == 0;
+  return false;
+}
+}  // namespace
+
+cudaError_t dev_malloc_raw(void **p, size_t bytes) {
+  *p = nullptr;
+  if (injected_failure()) return cudaErrorMemoryAllocation;
+  const cudaError_t err = cudaMalloc(p, bytes);
+  if (err == cudaSuccess && *p) ++g_live_allocations;
+  return err;
+}
+
+cudaError_t pinned_malloc_raw(void **p, size_t bytes) {
+  *p = nullptr;
+  if (injected_failure()) return cudaErrorMemoryAllocation;
+  const cudaError_t err = cudaMallocHost(p, bytes);
+  if (err == cudaSuccess && *p) ++g_live_allocations;
+  return err;
+}
+
+void dev_free(void *p) {
+  if (!p) return;
+  cudaFree(p);
+  --g_live_allocations;
+}
+
+void pinned_free(void *p) {
+  if (!p) return;
+  cudaFreeHost(p);
+  --g_live_allocations;
+}
+
+uf_operator *new_operator() {
+  if (injected_failure()) return nullptr;
+  uf_operator *op = new (std::nothrow) uf_operator();
+  if (op) ++g_live_allocations;
+  return op;
+}
+
+void delete_operator(uf_operator *op) {
+  if (!op) return;
+  delete op;
+  --g_live_allocations;
 }
 }  // namespace uf
 
@@ -575,15 +631,15 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
     put_t(o_fpb, fpt_b);
   }
 
-  cudaError_t err = cudaMalloc(&pd.base, L.bytes);
+  cudaError_t err = uf::dev_malloc(&pd.base, L.bytes);
   if (err != cudaSuccess) return fail(UF_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(err));
   const size_t vec_bytes = sizeof(T) * (size_t)H.n_active * H.ndof;
-  err = cudaMalloc(&pd.xbuf, vec_bytes);
-  if (err == cudaSuccess) err = cudaMalloc(&pd.ybuf, vec_bytes);
+  err = uf::dev_malloc(&pd.xbuf, vec_bytes);
+  if (err == cudaSuccess) err = uf::dev_malloc(&pd.ybuf, vec_bytes);
   // the second staging set and the set events exist for pipelined operators (several parts)
   const bool piped = part_meta.size() > 1;
-  if (err == cudaSuccess && piped) err = cudaMalloc(&pd.xbuf2, vec_bytes);
-  if (err == cudaSuccess && piped) err = cudaMalloc(&pd.ybuf2, vec_bytes);
+  if (err == cudaSuccess && piped) err = uf::dev_malloc(&pd.xbuf2, vec_bytes);
+  if (err == cudaSuccess && piped) err = uf::dev_malloc(&pd.ybuf2, vec_bytes);
   for (int b = 0; b < 2 && err == cudaSuccess && piped; ++b)
     err = cudaEventCreateWithFlags(&pd.set_free[b], cudaEventDisableTiming);
   if (err != cudaSuccess) return fail(UF_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(err));
@@ -592,11 +648,11 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   pd.device_bytes = L.bytes;
   if (H.cg) {
     const int64_t n_loc = H.n_active * H.ndof;
-    err = cudaMalloc(&pd.cg_l2g, n_loc * sizeof(int32_t));
-    if (err == cudaSuccess) err = cudaMalloc(&pd.cg_own_off, (H.n_cg + 1) * sizeof(int32_t));
-    if (err == cudaSuccess) err = cudaMalloc(&pd.cg_own_idx, n_loc * sizeof(int32_t));
-    if (err == cudaSuccess) err = cudaMalloc(&pd.x_loc, n_loc * sizeof(T));
-    if (err == cudaSuccess) err = cudaMalloc(&pd.y_loc, n_loc * sizeof(T));
+    err = uf::dev_malloc(&pd.cg_l2g, n_loc * sizeof(int32_t));
+    if (err == cudaSuccess) err = uf::dev_malloc(&pd.cg_own_off, (H.n_cg + 1) * sizeof(int32_t));
+    if (err == cudaSuccess) err = uf::dev_malloc(&pd.cg_own_idx, n_loc * sizeof(int32_t));
+    if (err == cudaSuccess) err = uf::dev_malloc(&pd.x_loc, n_loc * sizeof(T));
+    if (err == cudaSuccess) err = uf::dev_malloc(&pd.y_loc, n_loc * sizeof(T));
     if (err != cudaSuccess) return fail(UF_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(err));
     cudaMemcpy(pd.cg_l2g, H.cg_l2g.data(), n_loc * sizeof(int32_t), cudaMemcpyHostToDevice);
     cudaMemcpy(pd.cg_own_off, H.cg_own_off.data(), (H.n_cg + 1) * sizeof(int32_t), cudaMemcpyHostToDevice);
@@ -678,8 +734,8 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
     // kappa gradient (FP64): derivative tables and the per-cell partial buffer
     std::vector<double> kg;
     uf::kgrad_tables(H.n, mats, kg);
-    err = cudaMalloc(&op->kg_tables, kg.size() * sizeof(double));
-    if (err == cudaSuccess) err = cudaMalloc(&op->kg_scratch, (size_t)na * (1 + nf) * sizeof(double));
+    err = uf::dev_malloc(&op->kg_tables, kg.size() * sizeof(double));
+    if (err == cudaSuccess) err = uf::dev_malloc(&op->kg_scratch, (size_t)na * (1 + nf) * sizeof(double));
     if (err != cudaSuccess) return fail(UF_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(err));
     err = cudaMemcpy(op->kg_tables, kg.data(), kg.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (err != cudaSuccess) return fail(UF_ECUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(err));
@@ -745,14 +801,14 @@ template <typename T>
 void release(PrecisionData<T> &pd) {
   void *cg[] = {pd.cg_l2g, pd.cg_own_off, pd.cg_own_idx, pd.x_loc, pd.y_loc};
   for (void *p : cg)
-    if (p) cudaFree(p);
+    if (p) uf::dev_free(p);
   pd.cg_l2g = pd.cg_own_off = pd.cg_own_idx = nullptr;
   pd.x_loc = pd.y_loc = nullptr;
-  if (pd.base) cudaFree(pd.base);
-  if (pd.xbuf) cudaFree(pd.xbuf);
-  if (pd.ybuf) cudaFree(pd.ybuf);
-  if (pd.xbuf2) cudaFree(pd.xbuf2);
-  if (pd.ybuf2) cudaFree(pd.ybuf2);
+  if (pd.base) uf::dev_free(pd.base);
+  if (pd.xbuf) uf::dev_free(pd.xbuf);
+  if (pd.ybuf) uf::dev_free(pd.ybuf);
+  if (pd.xbuf2) uf::dev_free(pd.xbuf2);
+  if (pd.ybuf2) uf::dev_free(pd.ybuf2);
   for (cudaEvent_t &e : pd.set_free)
     if (e) cudaEventDestroy(e);
   pd.set_free[0] = pd.set_free[1] = nullptr;
@@ -981,7 +1037,7 @@ uf_status uf_create_unfitted_operator(const uf_params *params, uf_operator **out
   *out = nullptr;
   if ((params->precisions & ~(UF_FP64 | UF_FP32)) != 0)
     return fail(UF_EINVAL, "precisions must be a mask of UF_FP64 | UF_FP32");
-  uf_operator *op = new (std::nothrow) uf_operator();
+  uf_operator *op = uf::new_operator();
   if (!op) return fail(UF_ENOMEM, "host allocation failed");
   std::string msg;
   uf_status st;
@@ -992,13 +1048,13 @@ uf_status uf_create_unfitted_operator(const uf_params *params, uf_operator **out
     msg = "host allocation failed during setup";
   }
   if (st != UF_OK) {
-    delete op;
+    uf::delete_operator(op);
     return fail(st, msg);
   }
   if (params->kappa) {
     for (int64_t e = 0; e < op->host.n_active; ++e) {
       if (!(params->kappa[e] > 0.0) || !std::isfinite(params->kappa[e])) {
-        delete op;
+        uf::delete_operator(op);
         return fail(UF_EINVAL, "kappa must be positive and finite");
       }
       op->host.kappa[e] = params->kappa[e];
@@ -1008,7 +1064,7 @@ uf_status uf_create_unfitted_operator(const uf_params *params, uf_operator **out
     try {
       uf::cg_host_vectors(op->host);
     } catch (const std::bad_alloc &) {
-      delete op;
+      uf::delete_operator(op);
       return fail(UF_ENOMEM, "host allocation failed during setup");
     }
   }
@@ -1016,7 +1072,7 @@ uf_status uf_create_unfitted_operator(const uf_params *params, uf_operator **out
   if (op->device >= 0) {
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || op->device >= ndev) {
-      delete op;
+      uf::delete_operator(op);
       return fail(UF_EINVAL, "CUDA device not available");
     }
     DeviceGuard guard(op->device);
@@ -1032,9 +1088,9 @@ uf_status uf_create_unfitted_operator(const uf_params *params, uf_operator **out
       release(op->f64);
       release(op->f32);
       uf::cg_free(op);
-      if (op->kg_tables) cudaFree(op->kg_tables);
-      if (op->kg_scratch) cudaFree(op->kg_scratch);
-      delete op;
+      if (op->kg_tables) uf::dev_free(op->kg_tables);
+      if (op->kg_scratch) uf::dev_free(op->kg_scratch);
+      uf::delete_operator(op);
       return st;
     }
   }
@@ -1504,8 +1560,8 @@ uf_status uf_destroy(uf_operator *op) {
     uf::release_csr(op->csr64);
     uf::release_csr(op->csr32);
     uf::cg_free(op);
-    if (op->kg_tables) cudaFree(op->kg_tables);
-    if (op->kg_scratch) cudaFree(op->kg_scratch);
+    if (op->kg_tables) uf::dev_free(op->kg_tables);
+    if (op->kg_scratch) uf::dev_free(op->kg_scratch);
     for (ProfSlot &slot : op->prof)
       for (int k = 0; k < 4; ++k) cudaEventDestroy(slot.ev[k]);
     for (cudaEvent_t e : op->pipe_ev) cudaEventDestroy(e);
@@ -1515,10 +1571,21 @@ uf_status uf_destroy(uf_operator *op) {
     release(op->f64);
     release(op->f32);
   }
-  delete op;
+  uf::delete_operator(op);
   return UF_OK;
 }
 
 const char *uf_last_error(void) { return g_last_error.c_str(); }
+
+uf_status uf_debug_fail_allocation(int64_t after) {
+  uf::g_fail_after.store(after < 0 ? -1 : after);
+  return UF_OK;
+}
+
+uf_status uf_debug_live_allocations(int64_t *live) {
+  if (!live) return fail(UF_EINVAL, "NULL argument");
+  *live = uf::g_live_allocations.load();
+  return UF_OK;
+}
 
 }  // extern "C"

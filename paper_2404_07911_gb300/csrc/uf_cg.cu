@@ -682,6 +682,10 @@ extern "C" uf_status uf_solve(uf_operator *op, const uf_solve_params *prm, doubl
   uf::CgSolveData &w = op->cgs;
   uf::SolveCtx c{op, s, n, w.dot_part, w.dot_out, w.dot_host, w.sc, w.sc_host};
   std::memset(stats, 0, sizeof(*stats));
+  if (prm->mode == UF_SOLVE_IR_SPLIT) {
+    const uf_status s0 = uf::split_cells_alloc(op);
+    if (s0 != UF_OK) return s0;
+  }
   cudaEvent_t t0, t1;
   cudaEventCreate(&t0);
   cudaEventCreate(&t1);
@@ -696,10 +700,6 @@ extern "C" uf_status uf_solve(uf_operator *op, const uf_solve_params *prm, doubl
     uf::k_residual<<<uf::nblk(n), 256, 0, s>>>(w.r64, b, w.q64, n);
     return UF_OK;
   };
-  if (prm->mode == UF_SOLVE_IR_SPLIT) {
-    const uf_status s0 = uf::split_cells_alloc(op);
-    if (s0 != UF_OK) return s0;
-  }
   const bool ir = prm->mode == UF_SOLVE_IR || prm->mode == UF_SOLVE_IR_SPLIT;
   const int inner_op = prm->mode == UF_SOLVE_IR_SPLIT ? uf::kSplitPrecision : UF_FP32;
   int total_it = 0, outer = 0;
@@ -763,7 +763,7 @@ uf_status cg_alloc(uf_operator *op) {
   const int64_t n = solve_size(op->host);
   cudaError_t err = cudaSuccess;
   auto A = [&](void **p, size_t bytes) {
-    if (err == cudaSuccess) err = cudaMalloc(p, bytes);
+    if (err == cudaSuccess) err = uf::dev_malloc(p, bytes);
   };
   if (op->f64.present) {
     A((void **)&w.r64, n * 8);
@@ -784,8 +784,8 @@ uf_status cg_alloc(uf_operator *op) {
   A((void **)&w.dot_part, 2 * kDotBlocks * sizeof(double));
   A((void **)&w.dot_out, 2 * sizeof(double));
   A((void **)&w.sc, sizeof(PcgScalars));
-  if (err == cudaSuccess) err = cudaMallocHost((void **)&w.dot_host, 2 * sizeof(double));
-  if (err == cudaSuccess) err = cudaMallocHost((void **)&w.sc_host, sizeof(PcgScalars));
+  if (err == cudaSuccess) err = uf::pinned_malloc((void **)&w.dot_host, 2 * sizeof(double));
+  if (err == cudaSuccess) err = uf::pinned_malloc((void **)&w.sc_host, sizeof(PcgScalars));
   if (err != cudaSuccess) return fail(UF_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(err));
   return cg_upload_diag(op);
 }
@@ -837,7 +837,7 @@ uf_status split_cells_alloc(uf_operator *op) {
   const size_t o_idx = all.size();
   for (int k = 0; k < 3; ++k) all.insert(all.end(), sidx[k].begin(), sidx[k].end());
   if (!all.empty()) {
-    cudaError_t err = cudaMalloc((void **)&w.split_cells, all.size() * sizeof(int32_t));
+    cudaError_t err = uf::dev_malloc((void **)&w.split_cells, all.size() * sizeof(int32_t));
     if (err == cudaSuccess)
       err = cudaMemcpy(w.split_cells, all.data(), all.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (err != cudaSuccess) return fail(UF_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(err));
@@ -856,7 +856,7 @@ uf_status split_cells_alloc(uf_operator *op) {
 
 void split_cells_free(uf_operator *op) {
   CgSolveData &w = op->cgs;
-  if (w.split_cells) cudaFree(w.split_cells);
+  if (w.split_cells) uf::dev_free(w.split_cells);
   w.split_cells = w.halo_cells = w.split_cut_list = w.split_cut_idx = nullptr;
   w.n_split = w.n_halo = 0;
   w.split_cut_class[0] = w.split_cut_class[1] = w.split_cut_class[2] = 0;
@@ -885,9 +885,9 @@ void cg_free(uf_operator *op) {
   void *ptrs[] = {w.r64, w.q64, w.d64, w.z64, w.p64, w.invd64, w.r32, w.q32, w.d32,
                   w.z32, w.p32, w.invd32, w.dot_part, w.dot_out, w.sc, w.split_cells};
   for (void *p : ptrs)
-    if (p) cudaFree(p);
-  if (w.dot_host) cudaFreeHost(w.dot_host);
-  if (w.sc_host) cudaFreeHost(w.sc_host);
+    if (p) uf::dev_free(p);
+  if (w.dot_host) uf::pinned_free(w.dot_host);
+  if (w.sc_host) uf::pinned_free(w.sc_host);
   w = CgSolveData{};
 }
 

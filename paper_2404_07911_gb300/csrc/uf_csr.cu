@@ -89,9 +89,9 @@ __global__ void __launch_bounds__(256) k_spmv(T *__restrict__ y, const T *__rest
 namespace uf {
 
 void release_csr(CsrData &c) {
-  if (c.row_ptr) cudaFree(c.row_ptr);
-  if (c.col) cudaFree(c.col);
-  if (c.val) cudaFree(c.val);
+  if (c.row_ptr) uf::dev_free(c.row_ptr);
+  if (c.col) uf::dev_free(c.col);
+  if (c.val) uf::dev_free(c.val);
   c = CsrData{};
 }
 
@@ -152,20 +152,20 @@ uf_status uf_assemble_csr(uf_operator *op, int precision) {
   int32_t *d_coupled = nullptr;
   int8_t *d_ncoupled = nullptr, *d_color = nullptr;
   auto cleanup = [&]() {
-    if (ystage) cudaFree(ystage);
-    if (xind) cudaFree(xind);
-    if (d_coupled) cudaFree(d_coupled);
-    if (d_ncoupled) cudaFree(d_ncoupled);
-    if (d_color) cudaFree(d_color);
+    if (ystage) uf::dev_free(ystage);
+    if (xind) uf::dev_free(xind);
+    if (d_coupled) uf::dev_free(d_coupled);
+    if (d_ncoupled) uf::dev_free(d_ncoupled);
+    if (d_color) uf::dev_free(d_color);
   };
-  err = cudaMalloc(&csr.row_ptr, (n + 1) * sizeof(int64_t));
-  if (err == cudaSuccess) err = cudaMalloc(&csr.col, nnz * sizeof(int32_t));
-  if (err == cudaSuccess) err = cudaMalloc(&csr.val, nnz * vsize);
-  if (err == cudaSuccess) err = cudaMalloc(&ystage, (size_t)nd * n * sizeof(double));
-  if (err == cudaSuccess) err = cudaMalloc(&xind, n * sizeof(double));
-  if (err == cudaSuccess) err = cudaMalloc(&d_coupled, na * kMaxCoupled * sizeof(int32_t));
-  if (err == cudaSuccess) err = cudaMalloc(&d_ncoupled, na);
-  if (err == cudaSuccess) err = cudaMalloc(&d_color, na);
+  err = uf::dev_malloc(&csr.row_ptr, (n + 1) * sizeof(int64_t));
+  if (err == cudaSuccess) err = uf::dev_malloc(&csr.col, nnz * sizeof(int32_t));
+  if (err == cudaSuccess) err = uf::dev_malloc(&csr.val, nnz * vsize);
+  if (err == cudaSuccess) err = uf::dev_malloc(&ystage, (size_t)nd * n * sizeof(double));
+  if (err == cudaSuccess) err = uf::dev_malloc(&xind, n * sizeof(double));
+  if (err == cudaSuccess) err = uf::dev_malloc(&d_coupled, na * kMaxCoupled * sizeof(int32_t));
+  if (err == cudaSuccess) err = uf::dev_malloc(&d_ncoupled, na);
+  if (err == cudaSuccess) err = uf::dev_malloc(&d_color, na);
   if (err != cudaSuccess) {
     cleanup();
     uf::release_csr(csr);

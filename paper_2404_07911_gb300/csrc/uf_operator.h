@@ -162,4 +162,22 @@ template <typename T>
 int cg_gather(T *x_loc, const T *x, const int32_t *l2g, int64_t n_loc, cudaStream_t s);
 template <typename T>
 int cg_node_sum(T *y, const T *y_loc, const int32_t *off, const int32_t *idx, int64_t n, cudaStream_t s);
+
+// Every device and pinned-host allocation of the library, and every operator object, goes
+// through these: a test can make one of them fail (uf_debug_fail_allocation) and count the live
+// ones (uf_debug_live_allocations).
+cudaError_t dev_malloc_raw(void **p, size_t bytes);
+cudaError_t pinned_malloc_raw(void **p, size_t bytes);
+void dev_free(void *p);     // NULL is ignored
+void pinned_free(void *p);  // NULL is ignored
+template <typename P>
+inline cudaError_t dev_malloc(P **p, size_t bytes) {
+  return dev_malloc_raw(reinterpret_cast<void **>(p), bytes);
+}
+template <typename P>
+inline cudaError_t pinned_malloc(P **p, size_t bytes) {
+  return pinned_malloc_raw(reinterpret_cast<void **>(p), bytes);
+}
+uf_operator *new_operator();           // NULL when the allocation fails
+void delete_operator(uf_operator *op);  // NULL is ignored
 }  // namespace uf
