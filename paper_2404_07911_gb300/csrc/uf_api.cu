@@ -570,6 +570,40 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
       }
     }
   }
+  // FP64, 3D, n <= kFaceMatrixMaxN: per cut cell and cut face, the face's mass matrix over its
+  // points in the in-face tensor basis, tl = i_b' + n i_c' (the index of the cut-cell kernel's
+  // trace arrays: along the line m, along the outer coordinate io, tl = m + n io for lines along
+  // b', io + n m for lines along c'); w (phi_a phi_b) keeps it symmetric bit for bit
+  const bool fmats = pre && d == 3 && n <= uf::kFaceMatrixMaxN;
+  std::vector<int32_t> fmat_idx;
+  std::vector<double> fmat;
+  if (fmats) {
+    const int nl2 = n * n;
+    fmat_idx.assign((size_t)std::max<int64_t>(nc * nf, 1), -1);
+    double v[uf::kMaxN], dv[uf::kMaxN], vo[uf::kMaxN], phi[uf::kMaxN * uf::kMaxN];
+    int32_t cnt = 0;
+    for (int64_t c = 0; c < nc; ++c)
+      for (int f = 0; f < nf; ++f) {
+        const int32_t *ko = &fline_koff[(size_t)(c * nf + f) * 3];
+        if (ko[2] == ko[0]) continue;
+        fmat_idx[c * nf + f] = cnt++;
+        fmat.resize((size_t)cnt * nl2 * nl2, 0.0);
+        double *Mf = fmat.data() + (size_t)(cnt - 1) * nl2 * nl2;
+        for (int32_t l = ko[0]; l < ko[2]; ++l) {
+          const bool along_b = l < ko[1];
+          uf::lagrange_values(H.t, fline_o[l], vo, dv);
+          for (int32_t q = fpt_off[l]; q < fpt_off[l + 1]; ++q) {
+            uf::lagrange_values(H.t, fpt_t[q], v, dv);
+            for (int io = 0; io < n; ++io)
+              for (int m = 0; m < n; ++m) phi[along_b ? m + n * io : io + n * m] = v[m] * vo[io];
+            for (int a = 0; a < nl2; ++a)
+              for (int b = 0; b < nl2; ++b) Mf[a * nl2 + b] += fpt_w[q] * (phi[a] * phi[b]);
+          }
+        }
+      }
+  }
+  const size_t o_fm = fmats ? L.take(sizeof(T) * fmat.size()) : 0;
+  const size_t o_fmi = fmats ? L.take(sizeof(int32_t) * fmat_idx.size()) : 0;
   const size_t o_vkm = pre ? L.take(sizeof(T) * vline_km.size()) : 0;
   const size_t o_vlb = pre ? L.take(sizeof(T) * vline_b.size()) : 0;
   const size_t o_vpb = pre ? L.take(sizeof(T) * vpt_b.size()) : 0;
@@ -622,6 +656,10 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   put_t(o_lnbgpx, lnbgp0);
   put_t(o_lselfxT, lselfxT);
   put_t(o_lnbgpxT, lnbgpxT);
+  if (fmats) {
+    put_t(o_fm, fmat);
+    put_i(o_fmi, fmat_idx);
+  }
   if (pre) {
     put_t(o_vkm, vline_km);
     put_t(o_vlb, vline_b);
@@ -725,6 +763,8 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
   A.lselfxT = TP(o_lselfxT);
   A.lnbgpxT = TP(o_lnbgpxT);
   A.vline_km = pre ? TP(o_vkm) : nullptr;
+  A.fmat = fmats ? TP(o_fm) : nullptr;
+  A.fmat_idx = fmats ? I32(o_fmi) : nullptr;
   A.vline_b = pre ? TP(o_vlb) : nullptr;
   A.vpt_b = pre ? TP(o_vpb) : nullptr;
   A.spt_b = pre ? TP(o_spb) : nullptr;
@@ -1132,17 +1172,23 @@ uf_status uf_get_info(const uf_operator *op, uf_info *info) {
   // lines are L2 hits) and writes y once, plus neighbours / flags / kappa; the cut-cell kernel
   // reads x of the cut cells (own and cut-face neighbours are L2 hits), reads and writes their y
   // rows, and reads the line-structured point data and offsets once.
+  // FP64 in 3D up to kFaceMatrixMaxN reads one n^2 x n^2 mass matrix per cut cell and cut face
+  // (and its index) instead of the face lines and points.
   const double vl = (double)info->n_vol_lines, flh = 0.5 * (double)info->n_face_lines;
+  const bool fmats = d == 3 && H.n <= uf::kFaceMatrixMaxN;
+  const double nl2 = (double)H.n * H.n;
   for (int s = 0; s < 2; ++s) {
     const double S = s == 0 ? 8.0 : 4.0;
     double *kb = s == 0 ? info->kernel_bytes_fp64 : info->kernel_bytes_fp32;
     kb[0] = 2.0 * S * (double)info->n_dofs + (double)H.n_active * (4.0 * nf + 4.0 + S);
+    const double face_bytes = (s == 0 && fmats)
+                                  ? 2.0 * H.n_faces_cut * nl2 * nl2 * S + (double)H.n_cut * nf * 4.0
+                                  : S * 2.0 * info->n_face_points + flh * (S + 4.0);
     kb[1] = 3.0 * S * (double)H.n_cut * H.ndof +
             (double)H.n_cut * (4.0 * 2 + 4.0 * 4 + 4.0 * 3 * nf + S) +
             S * ((S == 8.0 ? 2.0 * H.n * H.n * info->n_vol_lines : 2.0 * info->n_vol_points) +
-                 (2.0 + d) * info->n_surf_points +
-                 2.0 * info->n_face_points) +
-            vl * (2.0 * S + 8.0) + flh * (S + 4.0);
+                 (2.0 + d) * info->n_surf_points) +
+            vl * (2.0 * S + 8.0) + face_bytes;
     (s == 0 ? info->bytes_fp64 : info->bytes_fp32) = kb[0] + kb[1];
   }
   // Floating-point operations of the kernels as built (FMA = 2, every FP op counted once).
@@ -1217,7 +1263,7 @@ uf_status uf_get_info(const uf_operator *op, uf_info *info) {
       else
         fl += (double)info->n_vol_points * (fb + 2 * 3 * n + 4 + 2 * 3 * n);
       fl += (double)info->n_surf_points * (fb + 2 * 4 * n + 16 + 2 * 3 * n + 6);
-      fl += flines * (fbv + 2 * 2 * n * n + 2 * 2 * n * n);
+      if (!(tables && fmats)) fl += flines * (fbv + 2 * 2 * n * n + 2 * 2 * n * n);
     } else {
       fl += vlines * (fb + 2 * 2 * n * n + 2 * 2 * n * n);
       if (tables)
@@ -1227,7 +1273,10 @@ uf_status uf_get_info(const uf_operator *op, uf_info *info) {
       fl += (double)info->n_surf_points * (fb + 2 * 3 * n + 12 + 2 * 2 * n + 4);
       fl += flines * (2 * 2 * n);
     }
-    fl += 2.0 * (double)info->n_face_points * (fbv + 2 * 2 * n + 8 + 2 * 2 * n);
+    if (tables && fmats)  // two products with the face's mass matrix, 7 flops per row
+      fl += 2.0 * (double)H.n_faces_cut * (2 * 2 * nl2 * nl2 + 7 * nl2);
+    else
+      fl += 2.0 * (double)info->n_face_points * (fbv + 2 * 2 * n + 8 + 2 * 2 * n);
     // traces (jump and flux; Lobatto face values need no arithmetic) and expansion
     fl += 2.0 * (double)H.n_faces_cut * (2 * 2 * nd + 4 * nd / n + 2 * nd + nd / n);
     return fl;

@@ -6,6 +6,10 @@
 namespace uf {
 
 constexpr int kMaxNdev = 9;
+// Largest n (= p + 1) whose FP64 cut faces use per-face mass matrices: at n = 4 a face's matrix
+// (256 values) costs 2 n^4 = 512 FMA against about 760 for its lines and points on a ball; at
+// n = 5 the two are even, and above it the lines are cheaper.
+constexpr int kFaceMatrixMaxN = 4;
 
 // Constant 1D matrices of the structured (tensor-product) terms, all scalings folded in
 // (arXiv 2404.07911, Sec. 3.2, Eq. sum_factorization_cell / Eq. sum_factorization_face: on a
@@ -116,6 +120,15 @@ struct DevArrays {
   // its points and integrating back is these two n x n products (3 n^2 FMA per line instead of
   // 6 n FMA per point).
   const T *vline_km;
+  // FP64, 3D, n <= kFaceMatrixMaxN only (null otherwise), per cut cell ci and cut face f with
+  // index i = fmat_idx[ci * 2d + f] (-1: no lines): the cut face's mass matrix in the in-face
+  // tensor basis over the face's quadrature points,
+  // fmat[i][a][b] = sum_p w_p phi_a(p) phi_b(p), a, b = i_b' + n i_c' (b' < c' the in-face axes),
+  // symmetric bit for bit.  The SIPG integrand of a cut face is linear in the traces' values at
+  // its points, so the point loop of the face's lines is the product of this n^2 x n^2 matrix
+  // with the jump and the flux traces (2 n^4 FMA per face).
+  const T *fmat;
+  const int32_t *fmat_idx;
   int32_t kappa_uniform;
   int32_t n_active, n_cut;
   // the cut-cell kernel gives cut_list[0 .. cut_split[0]) 32 lanes per cell, [cut_split[0] ..

@@ -662,6 +662,9 @@ __device__ __forceinline__ void point_basis(const PointTables<T, N> &pt, const T
 // measured faster without the extra table reads).
 template <typename T>
 constexpr bool kLineIntegrals = sizeof(T) == sizeof(double);
+// FP64 cut faces in 3D through their mass matrices (DevArrays::fmat) up to kFaceMatrixMaxN
+template <typename T, int DIM, int N>
+constexpr bool kFaceMatrices = sizeof(T) == sizeof(double) && DIM == 3 && N <= kFaceMatrixMaxN;
 
 // z += cf w_p (phi'(t_p) phi'(t_p)^T w0, phi phi^T w1, phi phi^T w2) over the line's points.
 template <typename T, int N>
@@ -1233,118 +1236,139 @@ __device__ __forceinline__ void cut_cells(const PointTables<T, N> &pt, const Dev
       s_ft[fi][1][tl] = T(0);
     }
     __syncwarp(gmask);
-    const int fl_beg = (SM::FB >= NF) ? __ldg(koff_cell) : __ldg(koff_cell + cfl[b0] * 3);
-    const int fl_end = (SM::FB >= NF) ? __ldg(koff_cell + (NF - 1) * 3 + 2)
-                                      : __ldg(koff_cell + cfl[b0 + nbf - 1] * 3 + 2);
-#pragma unroll 1
-    for (int l0 = fl_beg; l0 < fl_end; l0 += CH) {
-      const int line = l0 + tid;
-      int tag = -1;
-      if (line < fl_end) {
-        int fi = 0, kk = 0;
-        for (int j = 0; j < nbf; ++j) {
-          const int *ko = koff_cell + cfl[b0 + j] * 3;
-          if (line >= __ldg(ko) && line < __ldg(ko + 2)) {
-            fi = j;
-            kk = (line < __ldg(ko + 1)) ? 0 : 1;
-          }
-        }
-        tag = 2 * fi + kk;
+    if constexpr (kFaceMatrices<T, DIM, N>) {
+      // with the face's mass matrix Mf: ft0 = sigma/h {kappa} Mf [u] - Mf {kappa d_n u} and
+      // ft1 = -kappa/2 Mf [u] (Mf is symmetric: lanes read its columns, consecutive rows)
+      for (int item = tid; item < nbf * NL; item += CH) {
+        const int fi = item / NL, row = item % NL;
         const int f = cfl[b0 + fi];
-        const int nbe = __ldg(d.nbr + (size_t)e * NF + f);
-        const T knb = __ldg(d.kappa + nbe);
-        const T kavg = T(0.5) * (kap + knb);
-        // in-face strides of the line axis and of the outer axis in tl = i_b' + n i_c'
-        const int s_line = (kk == 0) ? 1 : N, s_out = (kk == 0) ? N : 1;
-        T vo[N];
-        if constexpr (DIM == 3) {
-          if constexpr (kPrecomputedBasis<T>) {
+        const T knb = __ldg(d.kappa + __ldg(d.nbr + (size_t)e * NF + f));
+        const T *mf = d.fmat + (size_t)__ldg(d.fmat_idx + (size_t)ci * NF + f) * NL * NL + row;
+        T a = T(0), b = T(0);
 #pragma unroll
-            for (int i = 0; i < N; ++i) vo[i] = __ldg(d.fline_b + (size_t)line * N + i);
-          } else {
-            basis_1d_val<T, N>(pt, __ldg(d.fline_o + line), vo);
-          }
+        for (int col = 0; col < NL; ++col) {
+          const T m = __ldg(mf + col * NL);
+          a = fma(m, s_tr[fi][0][col], a);
+          b = fma(m, s_tr[fi][1][col], b);
         }
-        // jump and flux contracted along the outer in-face axis
-        T r[2][N];
-#pragma unroll
-        for (int m = 0; m < N; ++m) {
-#pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            if constexpr (DIM == 3) {
-              T acc = T(0);
-#pragma unroll
-              for (int io = 0; io < N; ++io) acc = fma(vo[io], s_tr[fi][q][io * s_out + m * s_line], acc);
-              r[q][m] = acc;
-            } else {
-              r[q][m] = s_tr[fi][q][m];
+        s_ft[fi][0][row] = fma(sc.sipg_over_h * (T(0.5) * (kap + knb)), a, -b);
+        s_ft[fi][1][row] = T(-0.5) * kap * a;
+      }
+      __syncwarp(gmask);
+    } else {
+      const int fl_beg = (SM::FB >= NF) ? __ldg(koff_cell) : __ldg(koff_cell + cfl[b0] * 3);
+      const int fl_end = (SM::FB >= NF) ? __ldg(koff_cell + (NF - 1) * 3 + 2)
+                                        : __ldg(koff_cell + cfl[b0 + nbf - 1] * 3 + 2);
+#pragma unroll 1
+      for (int l0 = fl_beg; l0 < fl_end; l0 += CH) {
+        const int line = l0 + tid;
+        int tag = -1;
+        if (line < fl_end) {
+          int fi = 0, kk = 0;
+          for (int j = 0; j < nbf; ++j) {
+            const int *ko = koff_cell + cfl[b0 + j] * 3;
+            if (line >= __ldg(ko) && line < __ldg(ko + 2)) {
+              fi = j;
+              kk = (line < __ldg(ko + 1)) ? 0 : 1;
             }
           }
-        }
-        T zv[N], zd[N];
-#pragma unroll
-        for (int m = 0; m < N; ++m) {
-          zv[m] = T(0);
-          zd[m] = T(0);
-        }
-        const int pb = __ldg(d.fpt_off + line), pe = __ldg(d.fpt_off + line + 1);
-#pragma unroll 1
-        for (int p = pb; p < pe; ++p) {
-          T cv[N];
-          if constexpr (kPrecomputedBasis<T>) {
-#pragma unroll
-            for (int i = 0; i < N; ++i) cv[i] = __ldg(d.fpt_b + (size_t)p * N + i);
-          } else {
-            basis_1d_val<T, N>(pt, __ldg(d.fpt_t + p), cv);
-          }
-          T jump = T(0), avg = T(0);
-#pragma unroll
-          for (int m = 0; m < N; ++m) {
-            jump = fma(cv[m], r[0][m], jump);
-            avg = fma(cv[m], r[1][m], avg);
-          }
-          const T w = __ldg(d.fpt_w + p);
-          // coefficients of the own trace value and own normal derivative of the test function
-          const T cvv = w * (sc.sipg_over_h * kavg * jump - avg);
-          const T cdd = w * (T(-0.5) * kap * jump);
-#pragma unroll
-          for (int m = 0; m < N; ++m) {
-            zv[m] = fma(cvv, cv[m], zv[m]);
-            zd[m] = fma(cdd, cv[m], zd[m]);
-          }
-        }
-#pragma unroll
-        for (int m = 0; m < N; ++m) {
-          s_fz[0][tid][m] = zv[m];
-          s_fz[1][tid][m] = zd[m];
-          s_lvb[tid][m] = (DIM == 3) ? vo[m] : T(1);
-        }
-      }
-      s_tag[tid] = tag;
-      __syncwarp(gmask);
-      const int nlines = min(CH, fl_end - l0);
-      for (int item = tid; item < nbf * NL; item += CH) {
-        const int fi = item / NL, tl = item % NL;
-        T av = T(0), ad = T(0);
-        for (int q = 0; q < nlines; ++q) {
-          const int tg = s_tag[q];
-          if ((tg >> 1) != fi) continue;
-          const int kk = tg & 1;
-          int m, io;
+          tag = 2 * fi + kk;
+          const int f = cfl[b0 + fi];
+          const int nbe = __ldg(d.nbr + (size_t)e * NF + f);
+          const T knb = __ldg(d.kappa + nbe);
+          const T kavg = T(0.5) * (kap + knb);
+          // in-face strides of the line axis and of the outer axis in tl = i_b' + n i_c'
+          const int s_line = (kk == 0) ? 1 : N, s_out = (kk == 0) ? N : 1;
+          T vo[N];
           if constexpr (DIM == 3) {
-            m = (kk == 0) ? (tl % N) : (tl / N);
-            io = (kk == 0) ? (tl / N) : (tl % N);
-          } else {
-            m = tl;
-            io = 0;
+            if constexpr (kPrecomputedBasis<T>) {
+#pragma unroll
+              for (int i = 0; i < N; ++i) vo[i] = __ldg(d.fline_b + (size_t)line * N + i);
+            } else {
+              basis_1d_val<T, N>(pt, __ldg(d.fline_o + line), vo);
+            }
           }
-          av = fma(s_lvb[q][io], s_fz[0][q][m], av);
-          ad = fma(s_lvb[q][io], s_fz[1][q][m], ad);
+          // jump and flux contracted along the outer in-face axis
+          T r[2][N];
+#pragma unroll
+          for (int m = 0; m < N; ++m) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+              if constexpr (DIM == 3) {
+                T acc = T(0);
+#pragma unroll
+                for (int io = 0; io < N; ++io) acc = fma(vo[io], s_tr[fi][q][io * s_out + m * s_line], acc);
+                r[q][m] = acc;
+              } else {
+                r[q][m] = s_tr[fi][q][m];
+              }
+            }
+          }
+          T zv[N], zd[N];
+#pragma unroll
+          for (int m = 0; m < N; ++m) {
+            zv[m] = T(0);
+            zd[m] = T(0);
+          }
+          const int pb = __ldg(d.fpt_off + line), pe = __ldg(d.fpt_off + line + 1);
+#pragma unroll 1
+          for (int p = pb; p < pe; ++p) {
+            T cv[N];
+            if constexpr (kPrecomputedBasis<T>) {
+#pragma unroll
+              for (int i = 0; i < N; ++i) cv[i] = __ldg(d.fpt_b + (size_t)p * N + i);
+            } else {
+              basis_1d_val<T, N>(pt, __ldg(d.fpt_t + p), cv);
+            }
+            T jump = T(0), avg = T(0);
+#pragma unroll
+            for (int m = 0; m < N; ++m) {
+              jump = fma(cv[m], r[0][m], jump);
+              avg = fma(cv[m], r[1][m], avg);
+            }
+            const T w = __ldg(d.fpt_w + p);
+            // coefficients of the own trace value and own normal derivative of the test function
+            const T cvv = w * (sc.sipg_over_h * kavg * jump - avg);
+            const T cdd = w * (T(-0.5) * kap * jump);
+#pragma unroll
+            for (int m = 0; m < N; ++m) {
+              zv[m] = fma(cvv, cv[m], zv[m]);
+              zd[m] = fma(cdd, cv[m], zd[m]);
+            }
+          }
+#pragma unroll
+          for (int m = 0; m < N; ++m) {
+            s_fz[0][tid][m] = zv[m];
+            s_fz[1][tid][m] = zd[m];
+            s_lvb[tid][m] = (DIM == 3) ? vo[m] : T(1);
+          }
         }
-        s_ft[fi][0][tl] += av;
-        s_ft[fi][1][tl] += ad;
+        s_tag[tid] = tag;
+        __syncwarp(gmask);
+        const int nlines = min(CH, fl_end - l0);
+        for (int item = tid; item < nbf * NL; item += CH) {
+          const int fi = item / NL, tl = item % NL;
+          T av = T(0), ad = T(0);
+          for (int q = 0; q < nlines; ++q) {
+            const int tg = s_tag[q];
+            if ((tg >> 1) != fi) continue;
+            const int kk = tg & 1;
+            int m, io;
+            if constexpr (DIM == 3) {
+              m = (kk == 0) ? (tl % N) : (tl / N);
+              io = (kk == 0) ? (tl / N) : (tl % N);
+            } else {
+              m = tl;
+              io = 0;
+            }
+            av = fma(s_lvb[q][io], s_fz[0][q][m], av);
+            ad = fma(s_lvb[q][io], s_fz[1][q][m], ad);
+          }
+          s_ft[fi][0][tl] += av;
+          s_ft[fi][1][tl] += ad;
+        }
+        __syncwarp(gmask);
       }
-      __syncwarp(gmask);
     }
     // expand the face accumulators into the cell: phi_l = phi_{i_a}(side) x in-face product
     for (int l = tid; l < ND; l += CH) {
