@@ -525,62 +525,86 @@ __global__ void __launch_bounds__(32) kgrad_cut_kernel(const __grid_constant__ P
       s_tr[fi][5][tl] = sg * nd;
     }
     __syncwarp();
-    const int *koff_cell = d.fline_koff + (size_t)ci * NF * 3;
-    const int fl_beg = __ldg(koff_cell);
-    const int fl_end = __ldg(koff_cell + (NF - 1) * 3 + 2);
-#pragma unroll 1
-    for (int line = fl_beg + lane; line < fl_end; line += 32) {
-      int fi = 0, kk = 0;
-      for (int j = 0; j < ncf; ++j) {
-        const int *ko = koff_cell + cfl[j] * 3;
-        if (line >= __ldg(ko) && line < __ldg(ko + 2)) {
-          fi = j;
-          kk = (line < __ldg(ko + 1)) ? 0 : 1;
+    if constexpr (kFaceMatrices<double, DIM, N>) {
+      // every face integrand is a product of two traces, so with the face's mass matrix Mf and
+      // a = Mf r, b = Mf dr (J = [x] the jump): the points' sums are a.(sigma/h J / 2 - dx_e / 2)
+      // - b.J / 2 (self) and a.(sigma/h J - dx_nb) / 2 (neighbour)
+      for (int item = lane; item < ncf * NL; item += 32) {
+        const int fi = item / NL, row = item % NL;
+        const int f = cfl[fi];
+        const double *mf = d.fmat + (size_t)__ldg(d.fmat_idx + (size_t)ci * NF + f) * NL * NL + row;
+        double a = 0.0, b = 0.0;
+#pragma unroll
+        for (int col = 0; col < NL; ++col) {
+          const double m = __ldg(mf + col * NL);
+          a = fma(m, s_tr[fi][0][col], a);
+          b = fma(m, s_tr[fi][1][col], b);
         }
+        const double jump = s_tr[fi][2][row] - s_tr[fi][4][row];
+        p_self += -0.5 * b * jump - 0.5 * a * s_tr[fi][3][row] + 0.5 * sc.sipg_over_h * a * jump;
+        const double pnb = -0.5 * a * s_tr[fi][5][row] + 0.5 * sc.sipg_over_h * a * jump;
+#pragma unroll
+        for (int j = 0; j < NF; ++j)
+          if (j == f) p_face[j] += pnb;
       }
-      double vo[N];
-      if constexpr (DIM == 3)
-#pragma unroll
-        for (int i = 0; i < N; ++i) vo[i] = __ldg(d.fline_b + (size_t)line * N + i);
-      double rr[6][N];
-#pragma unroll
-      for (int m = 0; m < N; ++m)
-#pragma unroll
-        for (int q = 0; q < 6; ++q) {
-          if constexpr (DIM == 3) {
-            double acc = 0.0;
-#pragma unroll
-            for (int io = 0; io < N; ++io) {
-              const int tl = (kk == 0) ? (m + N * io) : (io + N * m);
-              acc = fma(vo[io], s_tr[fi][q][tl], acc);
-            }
-            rr[q][m] = acc;
-          } else {
-            rr[q][m] = s_tr[fi][q][m];
+    } else {
+      const int *koff_cell = d.fline_koff + (size_t)ci * NF * 3;
+      const int fl_beg = __ldg(koff_cell);
+      const int fl_end = __ldg(koff_cell + (NF - 1) * 3 + 2);
+#pragma unroll 1
+      for (int line = fl_beg + lane; line < fl_end; line += 32) {
+        int fi = 0, kk = 0;
+        for (int j = 0; j < ncf; ++j) {
+          const int *ko = koff_cell + cfl[j] * 3;
+          if (line >= __ldg(ko) && line < __ldg(ko + 2)) {
+            fi = j;
+            kk = (line < __ldg(ko + 1)) ? 0 : 1;
           }
         }
-      double pf_self = 0.0, pf_nb = 0.0;
-      const int pb = __ldg(d.fpt_off + line), pe = __ldg(d.fpt_off + line + 1);
-#pragma unroll 1
-      for (int p = pb; p < pe; ++p) {
-        double cv[N];
+        double vo[N];
+        if constexpr (DIM == 3)
 #pragma unroll
-        for (int i = 0; i < N; ++i) cv[i] = __ldg(d.fpt_b + (size_t)p * N + i);
-        double ev[6] = {0, 0, 0, 0, 0, 0};
+          for (int i = 0; i < N; ++i) vo[i] = __ldg(d.fline_b + (size_t)line * N + i);
+        double rr[6][N];
 #pragma unroll
         for (int m = 0; m < N; ++m)
 #pragma unroll
-          for (int q = 0; q < 6; ++q) ev[q] = fma(cv[m], rr[q][m], ev[q]);
-        const double w = __ldg(d.fpt_w + p);
-        const double jump = ev[2] - ev[4];
-        // d/dkappa_e:  -1/2 dr J - 1/2 r dx_e + 1/2 sigma/h r J;  d/dkappa_nb: -1/2 r dx_nb + 1/2 sigma/h r J
-        pf_self += w * (-0.5 * ev[1] * jump - 0.5 * ev[0] * ev[3] + 0.5 * sc.sipg_over_h * ev[0] * jump);
-        pf_nb += w * (-0.5 * ev[0] * ev[5] + 0.5 * sc.sipg_over_h * ev[0] * jump);
-      }
-      p_self += pf_self;
+          for (int q = 0; q < 6; ++q) {
+            if constexpr (DIM == 3) {
+              double acc = 0.0;
 #pragma unroll
-      for (int j = 0; j < NF; ++j)
-        if (j == fi) p_face[cfl[j]] += pf_nb;
+              for (int io = 0; io < N; ++io) {
+                const int tl = (kk == 0) ? (m + N * io) : (io + N * m);
+                acc = fma(vo[io], s_tr[fi][q][tl], acc);
+              }
+              rr[q][m] = acc;
+            } else {
+              rr[q][m] = s_tr[fi][q][m];
+            }
+          }
+        double pf_self = 0.0, pf_nb = 0.0;
+        const int pb = __ldg(d.fpt_off + line), pe = __ldg(d.fpt_off + line + 1);
+#pragma unroll 1
+        for (int p = pb; p < pe; ++p) {
+          double cv[N];
+#pragma unroll
+          for (int i = 0; i < N; ++i) cv[i] = __ldg(d.fpt_b + (size_t)p * N + i);
+          double ev[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+          for (int m = 0; m < N; ++m)
+#pragma unroll
+            for (int q = 0; q < 6; ++q) ev[q] = fma(cv[m], rr[q][m], ev[q]);
+          const double w = __ldg(d.fpt_w + p);
+          const double jump = ev[2] - ev[4];
+          // d/dkappa_e:  -1/2 dr J - 1/2 r dx_e + 1/2 sigma/h r J;  d/dkappa_nb: -1/2 r dx_nb + 1/2 sigma/h r J
+          pf_self += w * (-0.5 * ev[1] * jump - 0.5 * ev[0] * ev[3] + 0.5 * sc.sipg_over_h * ev[0] * jump);
+          pf_nb += w * (-0.5 * ev[0] * ev[5] + 0.5 * sc.sipg_over_h * ev[0] * jump);
+        }
+        p_self += pf_self;
+#pragma unroll
+        for (int j = 0; j < NF; ++j)
+          if (j == fi) p_face[cfl[j]] += pf_nb;
+      }
     }
   }
   // warp reductions, lane 0 adds to the structured partials of this cell
