@@ -339,11 +339,8 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
     cost[c] = (H.vol_off[c + 1] - H.vol_off[c]) + (H.surf_off[c + 1] - H.surf_off[c]) +
               (H.cface_off[(c + 1) * nf] - H.cface_off[c * nf]);
     lanes[c] = uf::cut_lanes_of_cell(H, c);
-#ifndef UF_F32_LANES16
-#define UF_F32_LANES16 0
-#endif
     // FP32: the 16-lane groups measured slower than full warps (the 8-lane ones faster)
-    if (!UF_F32_LANES16 && sizeof(T) == sizeof(float) && lanes[c] == 16) lanes[c] = 32;
+    if (sizeof(T) == sizeof(float) && lanes[c] == 16) lanes[c] = 32;
   }
   std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
     return lanes[a] != lanes[b] ? lanes[a] > lanes[b] : cost[a] > cost[b];
