@@ -113,7 +113,9 @@ typedef struct {
    * algorithmic bytes for FP64 / FP32 data and algorithmic floating-point operations (model
    * above) of one launch, and the floating-point operations the kernels execute as built: the
    * FP64 kernels read the 1D basis at lines and points from tables, the FP32 kernels evaluate
-   * it (kernel_flops_built_fp32). */
+   * it (kernel_flops_built_fp32).  In 3D with k <= 4 the FP64 cut-cell kernel applies each cut
+   * face's k^2 x k^2 mass matrix instead of the face's points: its bytes count those matrices
+   * (k^4 values per cut cell and cut face) and its operations two products per face. */
   double kernel_bytes_fp64[2], kernel_bytes_fp32[2], kernel_flops[2], kernel_flops_built[2];
   double kernel_flops_built_fp32[2];
   /* Groups of volume lines (3D): lines of a cut cell along one axis that share one outer
