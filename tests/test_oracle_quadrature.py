@@ -457,3 +457,97 @@ def test_box_covered_by_two_balls_but_by_neither():
     assert mesh.classify(prob, lo, hi) == mesh.CUT
     vol, surf = saye.cell_rules(prob, lo, hi)
     assert surf == [] and abs(sum(w for _, w in vol) - 1e-3) < 1e-17
+
+
+_GL4 = np.polynomial.legendre.leggauss(4)
+
+
+def _composite_gauss(lo, hi, panels):
+    """Points and weights of a composite 4-point Gauss rule with `panels` equal panels."""
+    g, w = 0.5 * (_GL4[0] + 1.0), 0.5 * _GL4[1]
+    t = ((np.arange(panels)[:, None] + g[None, :]) / panels).ravel()
+    return lo + (hi - lo) * t, np.tile(w, panels) * (hi - lo) / panels
+
+
+def _union_of_intervals_length(intervals, lo, hi):
+    """Length of the union of the intervals (a_i, b_i) (arrays over the evaluation points; empty
+    ones given as a = b = hi) clipped to [lo, hi]: sort by start, merge, add up."""
+    A = np.stack([np.clip(a, lo, hi) for a, _ in intervals])
+    B = np.stack([np.clip(b, lo, hi) for _, b in intervals])
+    order = np.argsort(A, axis=0)
+    A = np.take_along_axis(A, order, 0)
+    B = np.take_along_axis(B, order, 0)
+    total = np.zeros(A.shape[1:])
+    ca, cb = A[0].copy(), B[0].copy()
+    for i in range(1, A.shape[0]):
+        apart = A[i] > cb
+        total += np.where(apart, cb - ca, 0.0)
+        ca = np.where(apart, A[i], ca)
+        cb = np.where(apart, B[i], np.maximum(cb, B[i]))
+    return total + (cb - ca)
+
+
+def _chords(balls, pts, axis, lo, hi):
+    """Per ball, the chord of the ball along `axis` through each point of `pts` (the other
+    coordinates), as an interval; empty chords collapse to [hi, hi]."""
+    out = []
+    for *c, R in balls:
+        r2 = sum((pts[a] - c[a]) ** 2 for a in pts)
+        h = np.sqrt(np.maximum(R * R - r2, 0.0))
+        hit = r2 < R * R
+        out.append((np.where(hit, c[axis] - h, hi), np.where(hit, c[axis] + h, hi)))
+    return out
+
+
+def test_union_of_three_balls_cell_volumes_from_chords():
+    """A pin of the union rule that shares nothing with its construction: the volume of the
+    union of three intersecting balls inside a cell is the integral, over the cell's (x, y)
+    square, of the length of the union of the balls' chords along z (merged exactly and clipped
+    to the cell).  A composite Gauss rule of 128 x 128 panels takes that integral to about
+    3e-6 of the cell volume (the chord lengths have square-root edges on the balls'
+    silhouettes: 1e-4 at 32 panels).  Checked on every cut cell met by two or three spheres
+    (where the union's intersection circles and triple points act) and on every fourth other
+    cut cell."""
+    prob = _spheres_prob(16, 8, _THREE)
+    m = mesh.Mesh(prob)
+    checked = multi = 0
+    for e in range(m.n_active):
+        if m.active_type[e] != mesh.CUT:
+            continue
+        lo, hi = mesh.cell_box(prob, m.index_of(e))
+        _, crossing = mesh.crossing_spheres(prob, lo, hi)
+        if len(crossing) < 2 and e % 4:
+            continue
+        multi += len(crossing) >= 2
+        x, wx = _composite_gauss(lo[0], hi[0], 128)
+        y, wy = _composite_gauss(lo[1], hi[1], 128)
+        X, Y = np.meshgrid(x, y, indexing="ij")
+        length = _union_of_intervals_length(_chords(_THREE, {0: X, 1: Y}, 2, lo[2], hi[2]),
+                                            lo[2], hi[2])
+        exact = float(np.sum(np.outer(wx, wy) * length))
+        rule = sum(w for _, w in saye.cell_rules(prob, lo, hi)[0])
+        assert abs(rule - exact) <= 1e-5 * (hi[0] - lo[0]) ** 3, (e, rule, exact)
+        checked += 1
+    assert multi >= 20 and checked >= 100
+
+
+def test_union_of_three_discs_cell_areas_from_chords():
+    """The 2D counterpart: the area of the union of three discs inside a cell is the integral
+    over x of the length of the union of the discs' chords along y, here with 4096 composite
+    Gauss panels (7e-7 of the cell area; 2e-5 at 256 panels).  Every cut cell."""
+    prob = mesh.Problem(2, 2, (16, 16), (0.0, 0.0), (1.0, 1.0), (0.0, 0.0), 1.0, 8, 1, 1, 1, 0.5,
+                        ls_kind="spheres", spheres=_THREE)
+    m = mesh.Mesh(prob)
+    discs = [(cx, cy, R) for cx, cy, _, R in _THREE]
+    checked = 0
+    for e in range(m.n_active):
+        if m.active_type[e] != mesh.CUT:
+            continue
+        lo, hi = mesh.cell_box(prob, m.index_of(e))
+        x, wx = _composite_gauss(lo[0], hi[0], 4096)
+        length = _union_of_intervals_length(_chords(discs, {0: x}, 1, lo[1], hi[1]), lo[1], hi[1])
+        exact = float(np.sum(wx * length))
+        rule = sum(w for _, w in saye.cell_rules(prob, lo, hi)[0])
+        assert abs(rule - exact) <= 2e-6 * (hi[0] - lo[0]) ** 2, (e, rule, exact)
+        checked += 1
+    assert checked >= 40
