@@ -598,6 +598,18 @@ uf_status upload(uf_operator *op, PrecisionData<T> &pd) {
           }
         }
       }
+    // a cut face with an empty rule (none on the workloads scanned) reads a zero matrix: an
+    // empty rule adds nothing to the face integrals
+    int32_t zero = -1;
+    for (int64_t c = 0; c < nc; ++c)
+      for (int f = 0; f < nf; ++f)
+        if (fmat_idx[c * nf + f] < 0 && (H.flags[H.cut_cells[c]] & uf::face_bit_sipg_cut(f))) {
+          if (zero < 0) {
+            zero = cnt++;
+            fmat.resize((size_t)cnt * nl2 * nl2, 0.0);
+          }
+          fmat_idx[c * nf + f] = zero;
+        }
   }
   const size_t o_fm = fmats ? L.take(sizeof(T) * fmat.size()) : 0;
   const size_t o_fmi = fmats ? L.take(sizeof(int32_t) * fmat_idx.size()) : 0;
